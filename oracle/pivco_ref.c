@@ -1,0 +1,721 @@
+/*
+ * PivCo-Huffman CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * restatement of the PivCo-Huffman method that the GPU library is checked
+ * against.  Only the tests, the smoke check and the benchmark's CPU-baseline /
+ * reference leg may load it.  It shares no code, header, table or constant
+ * generator with the CUDA path, and the CUDA path never calls it.
+ *
+ * What it computes, step by step (each function cites its passage):
+ *   1. histogram of a block                        (Sec. 4, "symbol frequency counting")
+ *   2. length-limited code lengths, L = 11         (Sec. 1.2; App. D) -- optimal
+ *      package-merge; the paper names no algorithm, see the readings below
+ *   3. canonical codes                             (Sec. 1 note on canonical coding; App. D)
+ *   4. the pivoted tree: one node per proper code prefix, bit 1 = right
+ *                                                  (Listing 1; Sec. 2, Fig. 2-3)
+ *   5. per-node bitmaps, LSB-first inside bytes    (Sec. 2; Sec. 2.4.2 bit_pos table)
+ *   6. selective ANS: node selection rule and byte-wise static-table ANS
+ *                                                  (Sec. 5.2; App. D marker byte)
+ *   7. the block record (wire format)              (App. D, adapted: see below)
+ *   8. decode by the definition: a per-node cursor walk (Listing 1 applied to
+ *      the pivoted layout, Sec. 2)
+ *
+ * Readings where the paper is silent or loose (each is part of the format):
+ *   R1  code lengths: optimal package-merge; leaves ordered by (count, symbol),
+ *       a leaf sorts before a package of equal weight, packages keep creation
+ *       order; the first 2K-2 items of the shallowest list are selected.
+ *   R2  canonical order: (length, symbol) ascending, consecutive integers,
+ *       most significant bit first.
+ *   R3  node order: breadth-first (depth, then prefix value ascending).
+ *   R4  bitmap bit j lives in byte j>>3 at bit (j&7); pad bits are 0.
+ *   R5  ANS: rANS over bitmap BYTES with 50 static tables t = 50..99 built for
+ *       i.i.d. bits with P(bit = 0) = t/100; frequencies depend only on the
+ *       byte's popcount class (exact integers, M = 2^15, byte 0x00 absorbs the
+ *       rounding slack); 32-bit state in [2^16, 2^32), 16-bit renormalisation
+ *       words; bitmaps split into 16 KiB segments, each with W = min(32,
+ *       max(1, ceil(bytes/512))) interleaved states, byte j -> state j mod W.
+ *   R6  ANS selection: ceil(n/8) >= 32 bytes, skew = max(n0,n1)/n > 0.625,
+ *       (depth + fseH)/(depth + 1) < 0.95 with fseH in Q16; table
+ *       t = round-half-up(100*skew) clamped to 50..99; XOR flag when n1 > n0;
+ *       if the ANS body is not smaller than the raw bitmap, the raw bitmap is
+ *       stored with marker 0xFF.
+ *   R7  record: u32 widths, a node directory of u32 counts, ANS bodies after
+ *       all raw bodies, records padded to 16 bytes.
+ *
+ * Parity status: every function above is pinned by the oracle tests (worked
+ * examples of Sec. 1.1 and 2.2, brute-force optimality, Kraft, closed forms
+ * of Sec. 5.1, round trips).  The exact bytes of an ANS stream are pinned
+ * only by this definition and the round trip: "parity unpinned" beyond that.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define REF_OK 0
+#define REF_ERR_ARG 1
+#define REF_ERR_CAPACITY 2
+#define REF_ERR_CORRUPT 3
+
+#define REF_MAX_LEN_CAP 15
+#define REF_ANS_SCALE 15
+#define REF_ANS_M (1u << REF_ANS_SCALE)
+#define REF_ANS_L (1u << 16)
+#define REF_ANS_SEG 16384u
+#define REF_MARK_RAW_SEL 0xFFu
+
+typedef struct ref_params {
+    int32_t max_len;        /* L (App. D: 11) */
+    int32_t ans_enable;     /* selective ANS on/off (Sec. 5.2) */
+    int32_t ans_min_bytes;  /* PIVCO_FSE_MIN_BITMAP_BYTES, 32 */
+    int32_t ans_skew_num;   /* PIVCO_FSE_MIN_THRESHOLD = num/den = 5/8 */
+    int32_t ans_skew_den;
+    int32_t ans_ratio_pct;  /* PIVCO_FSE_MIN_RATIO, 95 (%) */
+} ref_params;
+
+/* ------------------------------------------------------------------ */
+/* little-endian helpers                                               */
+/* ------------------------------------------------------------------ */
+static void put32(uint8_t *p, uint32_t v) {
+    p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+}
+static uint32_t get32(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+static void put16(uint8_t *p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+static uint32_t get16(const uint8_t *p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+static int popcount8(unsigned b) { int c = 0; while (b) { c += b & 1u; b >>= 1; } return c; }
+
+/* ------------------------------------------------------------------ */
+/* 1. Histogram (Sec. 4: end-to-end encode is dominated by counting)   */
+/* ------------------------------------------------------------------ */
+int ref_histogram(const uint8_t *x, uint64_t n, uint32_t *hist) {
+    for (int s = 0; s < 256; s++) hist[s] = 0;
+    for (uint64_t i = 0; i < n; i++) hist[x[i]]++;
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 2. Length-limited code lengths by package-merge (App. D: L = 11;    */
+/*    reading R1).  Lists are built from the deepest level (L) up to   */
+/*    level 1; each list is the sorted leaves merged with the packages */
+/*    made by pairing neighbours of the list one level deeper.         */
+/* ------------------------------------------------------------------ */
+typedef struct pm_item {
+    uint64_t w;      /* weight */
+    int kind;        /* 0 = leaf, 1 = package */
+    int key;         /* leaf: sorted leaf index; package: creation index */
+    int a, b;        /* package: indices of its two items in the deeper list */
+} pm_item;
+
+static int pm_less(const pm_item *x, const pm_item *y) {
+    if (x->w != y->w) return x->w < y->w;
+    if (x->kind != y->kind) return x->kind < y->kind;   /* leaf first */
+    return x->key < y->key;
+}
+
+/* count how often each leaf occurs inside item `it` of list `lvl` */
+static void pm_expand(pm_item **lists, int lvl, int idx, int *cnt) {
+    const pm_item *it = &lists[lvl][idx];
+    if (it->kind == 0) { cnt[it->key]++; return; }
+    pm_expand(lists, lvl + 1, it->a, cnt);
+    pm_expand(lists, lvl + 1, it->b, cnt);
+}
+
+int ref_code_lengths(const uint32_t *hist, int max_len, uint8_t *lens) {
+    int K = 0, sym[256];
+    uint64_t f[256];
+    for (int s = 0; s < 256; s++) lens[s] = 0;
+    if (max_len < 1 || max_len > REF_MAX_LEN_CAP) return REF_ERR_ARG;
+    for (int s = 0; s < 256; s++) if (hist[s]) { sym[K] = s; f[K] = hist[s]; K++; }
+    if (K <= 1) return REF_OK;                 /* empty / constant block: no code */
+    if (K > (1 << max_len)) return REF_ERR_ARG;
+    /* sort leaves by (count, symbol): insertion sort, K <= 256 */
+    for (int i = 1; i < K; i++) {
+        int s = sym[i]; uint64_t w = f[i]; int j = i - 1;
+        while (j >= 0 && (f[j] > w || (f[j] == w && sym[j] > s))) { f[j + 1] = f[j]; sym[j + 1] = sym[j]; j--; }
+        f[j + 1] = w; sym[j + 1] = s;
+    }
+    pm_item **lists = (pm_item **)calloc((size_t)max_len + 2, sizeof(pm_item *));
+    int *len_of = (int *)calloc((size_t)max_len + 2, sizeof(int));
+    if (!lists || !len_of) { free(lists); free(len_of); return REF_ERR_ARG; }
+    /* level L: the leaves alone */
+    lists[max_len] = (pm_item *)calloc((size_t)K, sizeof(pm_item));
+    for (int i = 0; i < K; i++) { pm_item it = { f[i], 0, i, -1, -1 }; lists[max_len][i] = it; }
+    len_of[max_len] = K;
+    for (int lvl = max_len - 1; lvl >= 1; lvl--) {
+        int np = len_of[lvl + 1] / 2;         /* an odd last item is dropped */
+        int tot = K + np;
+        pm_item *cur = (pm_item *)calloc((size_t)tot, sizeof(pm_item));
+        for (int i = 0; i < K; i++) { pm_item it = { f[i], 0, i, -1, -1 }; cur[i] = it; }
+        for (int j = 0; j < np; j++) {
+            const pm_item *x = &lists[lvl + 1][2 * j], *y = &lists[lvl + 1][2 * j + 1];
+            pm_item it = { x->w + y->w, 1, j, 2 * j, 2 * j + 1 };
+            cur[K + j] = it;
+        }
+        /* plain insertion sort by (weight, leaf-first, key) */
+        for (int i = 1; i < tot; i++) {
+            pm_item v = cur[i]; int j = i - 1;
+            while (j >= 0 && pm_less(&v, &cur[j])) { cur[j + 1] = cur[j]; j--; }
+            cur[j + 1] = v;
+        }
+        lists[lvl] = cur; len_of[lvl] = tot;
+    }
+    int cnt[256];
+    memset(cnt, 0, sizeof(cnt));
+    int take = 2 * K - 2;
+    if (take > len_of[1]) take = len_of[1];
+    for (int i = 0; i < take; i++) pm_expand(lists, 1, i, cnt);
+    for (int i = 0; i < K; i++) lens[sym[i]] = (uint8_t)cnt[i];
+    for (int lvl = 1; lvl <= max_len; lvl++) free(lists[lvl]);
+    free(lists); free(len_of);
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 3. Canonical codes (reading R2).  code[s] holds lens[s] bits, MSB   */
+/*    is the first (root) decision.                                    */
+/* ------------------------------------------------------------------ */
+int ref_canonical_codes(const uint8_t *lens, uint32_t *codes) {
+    int order[256], K = 0;
+    for (int s = 0; s < 256; s++) { codes[s] = 0; if (lens[s]) order[K++] = s; }
+    for (int i = 1; i < K; i++) {   /* sort by (len, sym) */
+        int s = order[i], j = i - 1;
+        while (j >= 0 && (lens[order[j]] > lens[s] || (lens[order[j]] == lens[s] && order[j] > s))) { order[j + 1] = order[j]; j--; }
+        order[j + 1] = s;
+    }
+    uint32_t c = 0;
+    for (int i = 0; i < K; i++) {
+        if (i > 0) c = (c + 1) << (lens[order[i]] - lens[order[i - 1]]);
+        codes[order[i]] = c;
+    }
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 4. The pivoted tree (Listing 1: bit 1 = right; Sec. 2: one bitmap   */
+/*    per internal node = per proper code prefix).  Node order R3.     */
+/* ------------------------------------------------------------------ */
+typedef struct ref_tree {
+    int n_int;
+    int depth[256];
+    uint32_t prefix[256];
+    int child[256][2];   /* >= 0: internal node id; < 0: leaf, symbol = -child-1 */
+} ref_tree;
+
+static int tree_find(const ref_tree *t, int d, uint32_t p) {
+    for (int v = 0; v < t->n_int; v++) if (t->depth[v] == d && t->prefix[v] == p) return v;
+    return -1;
+}
+
+static int build_tree(const uint8_t *lens, const uint32_t *codes, ref_tree *t) {
+    /* collect distinct proper prefixes (d, p), d < len(s) */
+    int nd = 0;
+    int dd[4096]; uint32_t pp[4096];
+    for (int s = 0; s < 256; s++) {
+        for (int d = 0; d < lens[s]; d++) {
+            uint32_t p = codes[s] >> (lens[s] - d);
+            int seen = 0;
+            for (int k = 0; k < nd; k++) if (dd[k] == d && pp[k] == p) { seen = 1; break; }
+            if (!seen) { if (nd >= 4096) return REF_ERR_ARG; dd[nd] = d; pp[nd] = p; nd++; }
+        }
+    }
+    if (nd > 255) return REF_ERR_ARG;
+    /* breadth-first order: sort by (depth, prefix) */
+    for (int i = 1; i < nd; i++) {
+        int d = dd[i]; uint32_t p = pp[i]; int j = i - 1;
+        while (j >= 0 && (dd[j] > d || (dd[j] == d && pp[j] > p))) { dd[j + 1] = dd[j]; pp[j + 1] = pp[j]; j--; }
+        dd[j + 1] = d; pp[j + 1] = p;
+    }
+    t->n_int = nd;
+    for (int v = 0; v < nd; v++) { t->depth[v] = dd[v]; t->prefix[v] = pp[v]; }
+    for (int v = 0; v < nd; v++) {
+        for (int b = 0; b < 2; b++) {
+            int cd = t->depth[v] + 1; uint32_t cp = (t->prefix[v] << 1) | (uint32_t)b;
+            int id = tree_find(t, cd, cp);
+            if (id >= 0) { t->child[v][b] = id; continue; }
+            int leaf = -1;
+            for (int s = 0; s < 256; s++) if (lens[s] == cd && codes[s] == cp) { leaf = s; break; }
+            if (leaf < 0) return REF_ERR_CORRUPT;   /* not a full tree */
+            t->child[v][b] = -leaf - 1;
+        }
+    }
+    return REF_OK;
+}
+
+/* exported view of the tree for tests: depth, prefix, child ids */
+int ref_tree_info(const uint8_t *lens, int32_t *n_int, int32_t *depth, uint32_t *prefix, int32_t *child) {
+    uint32_t codes[256]; ref_tree t;
+    ref_canonical_codes(lens, codes);
+    int rc = build_tree(lens, codes, &t);
+    if (rc) return rc;
+    *n_int = t.n_int;
+    for (int v = 0; v < t.n_int; v++) {
+        depth[v] = t.depth[v]; prefix[v] = t.prefix[v];
+        child[2 * v] = t.child[v][0]; child[2 * v + 1] = t.child[v][1];
+    }
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 6a. ANS tables (Sec. 5.2: 50 static tables for skew 50..99 %, built */
+/*     for bytes of i.i.d. bits; reading R5).                          */
+/* ------------------------------------------------------------------ */
+static const uint32_t BINOM8[9] = { 1, 8, 28, 56, 70, 56, 28, 8, 1 };
+
+/* q[k] = frequency (out of M) of ONE byte with k one-bits under table t */
+int ref_ans_class_freqs(int t, uint32_t *q) {
+    if (t < 50 || t > 99) return REF_ERR_ARG;
+    /* P(byte) * 100^8 = t^(8-k) * (100-t)^k exactly; M / 100^8 = 1 / D */
+    const uint64_t D = 305175781250ull;          /* 10^16 / 2^15 */
+    int64_t total = 0;
+    for (int k = 0; k <= 8; k++) {
+        uint64_t w = 1;
+        for (int i = 0; i < 8 - k; i++) w *= (uint64_t)t;
+        for (int i = 0; i < k; i++) w *= (uint64_t)(100 - t);
+        uint64_t v = w / D;
+        if (v == 0) v = 1;
+        q[k] = (uint32_t)v;
+        total += (int64_t)BINOM8[k] * (int64_t)v;
+    }
+    int64_t q0 = (int64_t)q[0] + ((int64_t)REF_ANS_M - total);
+    if (q0 < 1) return REF_ERR_ARG;
+    q[0] = (uint32_t)q0;
+    return REF_OK;
+}
+
+/* per-byte frequency and cumulative start; bytes ordered by (popcount, value) */
+static void ans_byte_table(int t, uint32_t *freq, uint32_t *cum) {
+    uint32_t q[9];
+    ref_ans_class_freqs(t, q);
+    uint32_t c = 0;
+    for (int k = 0; k <= 8; k++)
+        for (int b = 0; b < 256; b++)
+            if (popcount8((unsigned)b) == k) { freq[b] = q[k]; cum[b] = c; c += q[k]; }
+}
+
+/* expected ANS cost in bits per bitmap bit under table t for i.i.d. bits
+   with P(0) = t/100 (the fse_H of Sec. 5.2), in double precision */
+double ref_fse_h(int t) {
+    uint32_t q[9];
+    if (ref_ans_class_freqs(t, q)) return -1.0;
+    double h = 0.0;
+    for (int k = 0; k <= 8; k++) {
+        double p = pow(t / 100.0, 8 - k) * pow((100 - t) / 100.0, k);
+        h += (double)BINOM8[k] * p * log2((double)REF_ANS_M / (double)q[k]);
+    }
+    return h / 8.0;
+}
+
+int ref_fse_h_q16(int t) {
+    double h = ref_fse_h(t);
+    if (h < 0) return -1;
+    return (int)floor(h * 65536.0 + 0.5);
+}
+
+/* ------------------------------------------------------------------ */
+/* 6b. Interleaved rANS body of one bitmap (reading R5).               */
+/*   body = u32 nwords[S], then per segment: W x u32 final states,     */
+/*          nwords x u16 words (in decoder read order)                 */
+/* ------------------------------------------------------------------ */
+static uint32_t seg_count(uint32_t nbytes) { return (nbytes + REF_ANS_SEG - 1) / REF_ANS_SEG; }
+static uint32_t seg_lanes(uint32_t seg_bytes) {
+    uint32_t w = (seg_bytes + 511) / 512;
+    if (w < 1) w = 1;
+    if (w > 32) w = 32;
+    return w;
+}
+
+int ref_rans_encode(const uint8_t *bytes, uint32_t nbytes, int t, uint8_t *body, uint64_t cap, uint64_t *body_bytes) {
+    uint32_t freq[256], cum[256];
+    if (t < 50 || t > 99 || nbytes == 0) return REF_ERR_ARG;
+    ans_byte_table(t, freq, cum);
+    uint32_t S = seg_count(nbytes);
+    uint64_t pos = 4ull * S;
+    uint16_t *stack = (uint16_t *)malloc(sizeof(uint16_t) * REF_ANS_SEG);
+    if (!stack) return REF_ERR_ARG;
+    for (uint32_t k = 0; k < S; k++) {
+        uint32_t lo = k * REF_ANS_SEG, sb = nbytes - lo;
+        if (sb > REF_ANS_SEG) sb = REF_ANS_SEG;
+        uint32_t W = seg_lanes(sb);
+        uint32_t x[32];
+        for (uint32_t i = 0; i < W; i++) x[i] = REF_ANS_L;
+        uint32_t nw = 0;
+        /* encode in reverse; word emitted while encoding byte j is the word
+           the decoder reads right after decoding byte j */
+        for (int64_t j = (int64_t)sb - 1; j >= 0; j--) {
+            uint32_t lane = (uint32_t)j % W;
+            uint32_t b = bytes[lo + (uint32_t)j];
+            uint64_t xs = x[lane];
+            uint64_t xmax = ((uint64_t)(REF_ANS_L >> REF_ANS_SCALE) << 16) * freq[b];
+            if (xs >= xmax) { stack[nw++] = (uint16_t)(xs & 0xFFFF); xs >>= 16; }
+            xs = ((xs / freq[b]) << REF_ANS_SCALE) + (xs % freq[b]) + cum[b];
+            x[lane] = (uint32_t)xs;
+        }
+        if (pos + 4ull * W + 2ull * nw > cap) { free(stack); return REF_ERR_CAPACITY; }
+        put32(body + 4ull * k, nw);
+        for (uint32_t i = 0; i < W; i++) put32(body + pos + 4ull * i, x[i]);
+        pos += 4ull * W;
+        for (uint32_t i = 0; i < nw; i++) put16(body + pos + 2ull * i, stack[nw - 1 - i]);
+        pos += 2ull * nw;
+    }
+    free(stack);
+    *body_bytes = pos;
+    return REF_OK;
+}
+
+int ref_rans_decode(const uint8_t *body, uint64_t body_bytes, int t, uint8_t *bytes, uint32_t nbytes) {
+    uint32_t freq[256], cum[256], slot2sym_start[257];
+    int order[256];
+    if (t < 50 || t > 99 || nbytes == 0) return REF_ERR_ARG;
+    ans_byte_table(t, freq, cum);
+    /* bytes in cumulative order, to look a slot up by linear search */
+    { int n = 0; for (int k = 0; k <= 8; k++) for (int b = 0; b < 256; b++) if (popcount8((unsigned)b) == k) order[n++] = b; }
+    for (int i = 0; i < 256; i++) slot2sym_start[i] = cum[order[i]];
+    slot2sym_start[256] = REF_ANS_M;
+    uint32_t S = seg_count(nbytes);
+    uint64_t pos = 4ull * S;
+    if (pos > body_bytes) return REF_ERR_CORRUPT;
+    for (uint32_t k = 0; k < S; k++) {
+        uint32_t lo = k * REF_ANS_SEG, sb = nbytes - lo;
+        if (sb > REF_ANS_SEG) sb = REF_ANS_SEG;
+        uint32_t W = seg_lanes(sb), nw = get32(body + 4ull * k);
+        if (pos + 4ull * W + 2ull * nw > body_bytes) return REF_ERR_CORRUPT;
+        uint32_t x[32];
+        for (uint32_t i = 0; i < W; i++) x[i] = get32(body + pos + 4ull * i);
+        pos += 4ull * W;
+        const uint8_t *words = body + pos;
+        uint32_t rd = 0;
+        for (uint32_t i = 0; i < W; i++) if (x[i] < REF_ANS_L) return REF_ERR_CORRUPT;
+        for (uint32_t j = 0; j < sb; j++) {
+            uint32_t lane = j % W;
+            uint32_t slot = x[lane] & (REF_ANS_M - 1);
+            int r = 0;
+            while (slot2sym_start[r + 1] <= slot) r++;
+            uint32_t b = (uint32_t)order[r];
+            x[lane] = freq[b] * (x[lane] >> REF_ANS_SCALE) + slot - cum[b];
+            if (x[lane] < REF_ANS_L) {
+                if (rd >= nw) return REF_ERR_CORRUPT;
+                x[lane] = (x[lane] << 16) | get16(words + 2ull * rd);
+                rd++;
+            }
+            bytes[lo + j] = (uint8_t)b;
+        }
+        if (rd != nw) return REF_ERR_CORRUPT;
+        for (uint32_t i = 0; i < W; i++) if (x[i] != REF_ANS_L) return REF_ERR_CORRUPT;
+        pos += 2ull * nw;
+    }
+    if (pos != body_bytes) return REF_ERR_CORRUPT;
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 6b'. Skew analysis of Sec. 5.1: a node's benefit is the share of all */
+/*      symbols that reach it times the bits entropy coding could save */
+/*      per symbol there, 1 - H_b(skew).                               */
+/* ------------------------------------------------------------------ */
+double ref_binary_entropy(double p) {
+    if (p <= 0.0 || p >= 1.0) return 0.0;
+    return -(p * log2(p) + (1.0 - p) * log2(1.0 - p));
+}
+
+double ref_node_benefit(uint64_t n_v, uint64_t n1, uint64_t n_total) {
+    if (n_v == 0 || n_total == 0) return 0.0;
+    double skew = (double)(n1 > n_v - n1 ? n1 : n_v - n1) / (double)n_v;
+    return ((double)n_v / (double)n_total) * (1.0 - ref_binary_entropy(skew));
+}
+
+/* ------------------------------------------------------------------ */
+/* 6c. Selection rule of Sec. 5.2 (reading R6).  Returns the marker the */
+/*     node gets if ANS is kept: 0 = not selected, else table id        */
+/*     (t - 49) with bit 7 set for the XOR of the bitmap bytes.         */
+/* ------------------------------------------------------------------ */
+int ref_ans_select(uint64_t n_v, uint64_t n1, int depth, const ref_params *p) {
+    if (!p->ans_enable || n_v == 0) return 0;
+    uint64_t bytes = (n_v + 7) / 8;
+    if (bytes < (uint64_t)p->ans_min_bytes) return 0;
+    uint64_t n0 = n_v - n1, mx = n0 > n1 ? n0 : n1;
+    /* skew = mx / n_v must be strictly higher than num/den */
+    if (mx * (uint64_t)p->ans_skew_den <= (uint64_t)p->ans_skew_num * n_v) return 0;
+    uint64_t t = (200 * mx + n_v) / (2 * n_v);      /* round half up of 100*skew */
+    if (t < 50) t = 50;
+    if (t > 99) t = 99;
+    int fq = ref_fse_h_q16((int)t);
+    /* (depth + fseH) / (depth + 1) strictly better (lower) than ratio */
+    uint64_t lhs = ((uint64_t)depth * 65536u + (uint64_t)fq) * 100u;
+    uint64_t rhs = (uint64_t)p->ans_ratio_pct * (uint64_t)(depth + 1) * 65536u;
+    if (!(lhs < rhs)) return 0;
+    int marker = (int)(t - 49);
+    if (n1 > n0) marker |= 0x80;
+    return marker;
+}
+
+/* ------------------------------------------------------------------ */
+/* 7. Block record (App. D, adapted; reading R7)                        */
+/*  0  u32 rec_bytes (multiple of 16)   4 u32 n                         */
+/*  8  u16 n_int  10 u8 kind (0 empty, 1 constant, 2 coded)  11 u8 aux  */
+/*  12 "PVC1"                                                           */
+/*  kind 2: 16 lens[128] (symbol 2k low nibble of byte k)               */
+/*          144 nv[n_int] u32, marker[n_int] u8, pad to 4,              */
+/*          alen[n_sel] u32 (body bytes of each node with marker != 0), */
+/*          raw bodies of marker-0 nodes, then bodies of the others,    */
+/*          zero pad to 16                                              */
+/* ------------------------------------------------------------------ */
+#define HDR_BYTES 16u
+#define LENS_OFF 16u
+#define NV_OFF 144u
+
+static uint64_t pad16(uint64_t x) { return (x + 15) & ~(uint64_t)15; }
+
+static void write_header(uint8_t *rec, uint32_t rec_bytes, uint32_t n, uint32_t n_int, uint32_t kind, uint32_t aux) {
+    put32(rec, rec_bytes);
+    put32(rec + 4, n);
+    put16(rec + 8, n_int);
+    rec[10] = (uint8_t)kind;
+    rec[11] = (uint8_t)aux;
+    rec[12] = 'P'; rec[13] = 'V'; rec[14] = 'C'; rec[15] = '1';
+}
+
+/* largest record the block can produce (every node stored raw) */
+int ref_record_bound(const uint32_t *hist, const ref_params *p, uint64_t *bound) {
+    uint8_t lens[256]; uint32_t codes[256]; ref_tree t;
+    uint64_t n = 0; int K = 0;
+    for (int s = 0; s < 256; s++) { n += hist[s]; if (hist[s]) K++; }
+    if (K <= 1) { *bound = HDR_BYTES; return REF_OK; }
+    int rc = ref_code_lengths(hist, p->max_len, lens);
+    if (rc) return rc;
+    ref_canonical_codes(lens, codes);
+    rc = build_tree(lens, codes, &t);
+    if (rc) return rc;
+    uint64_t nv[256]; memset(nv, 0, sizeof(nv));
+    for (int s = 0; s < 256; s++)
+        for (int d = 0; d < lens[s]; d++)
+            nv[tree_find(&t, d, codes[s] >> (lens[s] - d))] += hist[s];
+    uint64_t sz = NV_OFF + 5ull * (uint64_t)t.n_int;
+    sz = (sz + 3) & ~(uint64_t)3;
+    int nsel_max = 0;
+    for (int v = 0; v < t.n_int; v++) {
+        sz += (nv[v] + 7) / 8;
+        uint64_t n1 = t.child[v][1] >= 0 ? nv[t.child[v][1]] : hist[-t.child[v][1] - 1];
+        if (ref_ans_select(nv[v], n1, t.depth[v], p)) nsel_max++;
+    }
+    sz += 4ull * (uint64_t)nsel_max;
+    (void)n;
+    *bound = pad16(sz);
+    return REF_OK;
+}
+
+int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t *rec, uint64_t cap, uint64_t *rec_bytes) {
+    uint32_t hist[256]; uint8_t lens[256]; uint32_t codes[256]; ref_tree t;
+    if (n > 0xFFFFFFFFull) return REF_ERR_ARG;
+    ref_histogram(x, n, hist);
+    int K = 0, only = 0;
+    for (int s = 0; s < 256; s++) if (hist[s]) { K++; only = s; }
+    if (K <= 1) {
+        if (cap < HDR_BYTES) return REF_ERR_CAPACITY;
+        write_header(rec, HDR_BYTES, (uint32_t)n, 0, K == 0 ? 0u : 1u, K == 0 ? 0u : (uint32_t)only);
+        *rec_bytes = HDR_BYTES;
+        return REF_OK;
+    }
+    int rc = ref_code_lengths(hist, p->max_len, lens);
+    if (rc) return rc;
+    ref_canonical_codes(lens, codes);
+    rc = build_tree(lens, codes, &t);
+    if (rc) return rc;
+    int V = t.n_int;
+
+    /* 5. per-node bitmaps by the definition: append bit d of code(s) to the
+          bitmap of the node named by its first d bits, in block order */
+    uint64_t nv[256]; memset(nv, 0, sizeof(nv));
+    for (int s = 0; s < 256; s++)
+        for (int d = 0; d < lens[s]; d++)
+            nv[tree_find(&t, d, codes[s] >> (lens[s] - d))] += hist[s];
+    uint8_t *bm[256];
+    uint64_t cur[256];
+    int node_of[256][16];
+    for (int s = 0; s < 256; s++)
+        for (int d = 0; d < lens[s]; d++) node_of[s][d] = tree_find(&t, d, codes[s] >> (lens[s] - d));
+    for (int v = 0; v < V; v++) { bm[v] = (uint8_t *)calloc((size_t)((nv[v] + 7) / 8) + 1, 1); cur[v] = 0; }
+    for (uint64_t i = 0; i < n; i++) {
+        int s = x[i];
+        for (int d = 0; d < lens[s]; d++) {
+            int v = node_of[s][d];
+            uint32_t bit = (codes[s] >> (lens[s] - 1 - d)) & 1u;
+            if (bit) bm[v][cur[v] >> 3] |= (uint8_t)(1u << (cur[v] & 7));
+            cur[v]++;
+        }
+    }
+
+    /* 6. selective ANS */
+    int marker[256]; uint8_t *ans_body[256]; uint64_t ans_len[256];
+    for (int v = 0; v < V; v++) {
+        marker[v] = 0; ans_body[v] = NULL; ans_len[v] = 0;
+        uint64_t n1 = t.child[v][1] >= 0 ? nv[t.child[v][1]] : hist[-t.child[v][1] - 1];
+        int m = ref_ans_select(nv[v], n1, t.depth[v], p);
+        if (!m) continue;
+        uint64_t raw = (nv[v] + 7) / 8;
+        uint8_t *src = (uint8_t *)malloc((size_t)raw);
+        for (uint64_t i = 0; i < raw; i++) src[i] = (m & 0x80) ? (uint8_t)(bm[v][i] ^ 0xFF) : bm[v][i];
+        uint64_t bcap = 4 * ((raw + REF_ANS_SEG - 1) / REF_ANS_SEG) * 34 + 2 * raw + 64;
+        uint8_t *body = (uint8_t *)malloc((size_t)bcap);
+        uint64_t blen = 0;
+        rc = ref_rans_encode(src, (uint32_t)raw, (m & 0x7F) + 49, body, bcap, &blen);
+        free(src);
+        if (rc) { free(body); return rc; }
+        if (blen >= raw) { free(body); marker[v] = (int)REF_MARK_RAW_SEL; ans_len[v] = raw; }
+        else { marker[v] = m; ans_body[v] = body; ans_len[v] = blen; }
+    }
+
+    /* 7. serialise */
+    int nsel = 0;
+    for (int v = 0; v < V; v++) if (marker[v]) nsel++;
+    uint64_t off = NV_OFF + 5ull * (uint64_t)V;
+    off = (off + 3) & ~(uint64_t)3;
+    uint64_t alen_off = off;
+    off += 4ull * (uint64_t)nsel;
+    uint64_t total = off;
+    for (int v = 0; v < V; v++) total += marker[v] ? ans_len[v] : (nv[v] + 7) / 8;
+    total = pad16(total);
+    if (total > cap || total > 0xFFFFFFFFull) {
+        for (int v = 0; v < V; v++) { free(bm[v]); free(ans_body[v]); }
+        return REF_ERR_CAPACITY;
+    }
+    memset(rec, 0, (size_t)total);
+    write_header(rec, (uint32_t)total, (uint32_t)n, (uint32_t)V, 2, 0);
+    for (int k = 0; k < 128; k++) rec[LENS_OFF + k] = (uint8_t)(lens[2 * k] | (lens[2 * k + 1] << 4));
+    for (int v = 0; v < V; v++) put32(rec + NV_OFF + 4ull * v, (uint32_t)nv[v]);
+    for (int v = 0; v < V; v++) rec[NV_OFF + 4ull * V + v] = (uint8_t)marker[v];
+    { int k = 0; for (int v = 0; v < V; v++) if (marker[v]) put32(rec + alen_off + 4ull * (k++), (uint32_t)ans_len[v]); }
+    for (int v = 0; v < V; v++) if (!marker[v]) { uint64_t b = (nv[v] + 7) / 8; memcpy(rec + off, bm[v], (size_t)b); off += b; }
+    for (int v = 0; v < V; v++) if (marker[v]) {
+        if (ans_body[v]) memcpy(rec + off, ans_body[v], (size_t)ans_len[v]);
+        else memcpy(rec + off, bm[v], (size_t)ans_len[v]);
+        off += ans_len[v];
+    }
+    for (int v = 0; v < V; v++) { free(bm[v]); free(ans_body[v]); }
+    *rec_bytes = total;
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 8. Decode by the definition: for each output position walk from the */
+/*    root, reading the next unread bit of each visited node (Listing 1 */
+/*    on the pivoted layout of Sec. 2).                                 */
+/* ------------------------------------------------------------------ */
+int ref_decode_block(const uint8_t *rec, uint64_t avail, uint8_t *out, uint64_t cap, uint64_t *n_out) {
+    if (avail < HDR_BYTES) return REF_ERR_CORRUPT;
+    uint32_t rb = get32(rec), n = get32(rec + 4), V = get16(rec + 8), kind = rec[10], aux = rec[11];
+    if (rec[12] != 'P' || rec[13] != 'V' || rec[14] != 'C' || rec[15] != '1') return REF_ERR_CORRUPT;
+    if (rb < HDR_BYTES || (rb & 15u) || rb > avail) return REF_ERR_CORRUPT;
+    if (n > cap) return REF_ERR_CAPACITY;
+    *n_out = n;
+    if (kind == 0) { if (n != 0 || V != 0 || aux != 0 || rb != HDR_BYTES) return REF_ERR_CORRUPT; return REF_OK; }
+    if (kind == 1) {
+        if (n == 0 || V != 0 || rb != HDR_BYTES) return REF_ERR_CORRUPT;
+        for (uint32_t i = 0; i < n; i++) out[i] = (uint8_t)aux;
+        return REF_OK;
+    }
+    if (kind != 2 || aux != 0 || n == 0 || V < 1 || V > 255) return REF_ERR_CORRUPT;
+    if (rb < NV_OFF + 5ull * V) return REF_ERR_CORRUPT;
+    uint8_t lens[256]; uint32_t codes[256]; ref_tree t;
+    int K = 0;
+    for (int k = 0; k < 128; k++) { lens[2 * k] = rec[LENS_OFF + k] & 15; lens[2 * k + 1] = rec[LENS_OFF + k] >> 4; }
+    /* Kraft equality (a full tree) is required */
+    uint64_t kraft = 0;
+    for (int s = 0; s < 256; s++) if (lens[s]) { K++; kraft += 1ull << (15 - lens[s]); }
+    if (K < 2 || kraft != (1ull << 15) || (uint32_t)(K - 1) != V) return REF_ERR_CORRUPT;
+    ref_canonical_codes(lens, codes);
+    if (build_tree(lens, codes, &t) || t.n_int != (int)V) return REF_ERR_CORRUPT;
+    uint64_t nv[256]; int marker[256];
+    for (uint32_t v = 0; v < V; v++) { nv[v] = get32(rec + NV_OFF + 4ull * v); marker[v] = rec[NV_OFF + 4ull * V + v]; }
+    if (nv[0] != n) return REF_ERR_CORRUPT;
+    int nsel = 0;
+    for (uint32_t v = 0; v < V; v++) {
+        int m = marker[v];
+        if (m) { nsel++; if (m != (int)REF_MARK_RAW_SEL && ((m & 0x7F) < 1 || (m & 0x7F) > 50)) return REF_ERR_CORRUPT; }
+        if (nv[v] < 2) return REF_ERR_CORRUPT;
+        for (int b = 0; b < 2; b++) if (t.child[v][b] >= 0 && nv[t.child[v][b]] > nv[v]) return REF_ERR_CORRUPT;
+    }
+    uint64_t off = NV_OFF + 5ull * V;
+    off = (off + 3) & ~(uint64_t)3;
+    uint64_t alen_off = off;
+    off += 4ull * (uint64_t)nsel;
+    if (off > rb) return REF_ERR_CORRUPT;
+    /* bitmaps: raw ones point into the record, ANS ones are decoded */
+    const uint8_t *bm[256]; uint8_t *owned[256];
+    int k = 0;
+    for (uint32_t v = 0; v < V; v++) owned[v] = NULL;
+    uint64_t alen[256];
+    for (uint32_t v = 0; v < V; v++) alen[v] = marker[v] ? get32(rec + alen_off + 4ull * (k++)) : 0;
+    int rc = REF_OK;
+    for (uint32_t v = 0; v < V; v++) if (!marker[v]) {
+        uint64_t b = (nv[v] + 7) / 8;
+        if (off + b > rb) { rc = REF_ERR_CORRUPT; goto done; }
+        bm[v] = rec + off; off += b;
+    }
+    for (uint32_t v = 0; v < V; v++) if (marker[v]) {
+        uint64_t raw = (nv[v] + 7) / 8;
+        if (off + alen[v] > rb) { rc = REF_ERR_CORRUPT; goto done; }
+        if (marker[v] == (int)REF_MARK_RAW_SEL) {
+            if (alen[v] != raw) { rc = REF_ERR_CORRUPT; goto done; }
+            bm[v] = rec + off;
+        } else {
+            owned[v] = (uint8_t *)malloc((size_t)raw);
+            if (ref_rans_decode(rec + off, alen[v], (marker[v] & 0x7F) + 49, owned[v], (uint32_t)raw)) { rc = REF_ERR_CORRUPT; goto done; }
+            if (marker[v] & 0x80) for (uint64_t i = 0; i < raw; i++) owned[v][i] ^= 0xFF;
+            bm[v] = owned[v];
+        }
+        off += alen[v];
+    }
+    if (pad16(off) != rb) { rc = REF_ERR_CORRUPT; goto done; }
+    for (uint64_t i = off; i < rb; i++) if (rec[i]) { rc = REF_ERR_CORRUPT; goto done; }
+    {
+        uint64_t cursor[256];
+        for (uint32_t v = 0; v < V; v++) cursor[v] = 0;
+        for (uint32_t i = 0; i < n; i++) {
+            int v = 0;
+            for (;;) {
+                if (cursor[v] >= nv[v]) { rc = REF_ERR_CORRUPT; goto done; }
+                uint64_t j = cursor[v]++;
+                int bit = (bm[v][j >> 3] >> (j & 7)) & 1;
+                int c = t.child[v][bit];
+                if (c < 0) { out[i] = (uint8_t)(-c - 1); break; }
+                v = c;
+            }
+        }
+        for (uint32_t v = 0; v < V; v++) {
+            if (cursor[v] != nv[v]) { rc = REF_ERR_CORRUPT; goto done; }
+            /* pad bits of the last byte are zero */
+            if (nv[v] & 7) { if (bm[v][nv[v] >> 3] >> (nv[v] & 7)) { rc = REF_ERR_CORRUPT; goto done; } }
+        }
+    }
+done:
+    for (uint32_t v = 0; v < V; v++) free(owned[v]);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Batch helpers (many blocks, caller offsets), used by tests and the  */
+/* CPU baseline.  Records go to rec + rec_off[b]; rec_bytes[b] out.    */
+/* ------------------------------------------------------------------ */
+int ref_encode_batch(const uint8_t *x, const uint64_t *blk_off, int nblk, const ref_params *p,
+                     uint8_t *rec, const uint64_t *rec_off, const uint64_t *rec_cap, uint64_t *rec_bytes) {
+    for (int b = 0; b < nblk; b++) {
+        int rc = ref_encode_block(x + blk_off[b], blk_off[b + 1] - blk_off[b], p, rec + rec_off[b], rec_cap[b], &rec_bytes[b]);
+        if (rc) return rc;
+    }
+    return REF_OK;
+}
+
+int ref_decode_batch(const uint8_t *rec, const uint64_t *rec_off, const uint64_t *rec_avail, int nblk,
+                     uint8_t *out, const uint64_t *out_off, int32_t *status) {
+    int bad = 0;
+    for (int b = 0; b < nblk; b++) {
+        uint64_t n = 0;
+        status[b] = ref_decode_block(rec + rec_off[b], rec_avail[b], out + out_off[b], out_off[b + 1] - out_off[b], &n);
+        if (!status[b] && n != out_off[b + 1] - out_off[b]) status[b] = REF_ERR_CORRUPT;
+        if (status[b]) bad++;
+    }
+    return bad ? REF_ERR_CORRUPT : REF_OK;
+}
