@@ -1,0 +1,179 @@
+/*
+ * pivco.h -- C ABI of the GB300 (sm_103a) PivCo-Huffman library.
+ *
+ * PivCo-Huffman (pivot-coded Huffman) stores each block of 8-bit symbols as a
+ * length-limited canonical Huffman code whose bits are "pivoted": every
+ * internal node of the code tree owns one bitmap holding, in block order, the
+ * next code bit of every symbol whose code passes through that node
+ * (paper Sec. 2, Fig. 2-3).  Decoding rebuilds the block bottom-up by merging
+ * children's symbol sequences through the node bitmaps (Sec. 3); skewed node
+ * bitmaps can be ANS-coded selectively (Sec. 5.2).  The calls below follow the
+ * paper's problem statement: histogram -> length-limited code lengths ->
+ * tree / pivot layout -> encode blocks -> decode blocks (Sec. 4, App. D).
+ *
+ * Conventions for every entry point
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  Pointers named "host" are host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued asynchronously on it; nothing here
+ *     synchronises unless the comment says "synchronous".
+ *   - The library allocates no device memory in any call of this header:
+ *     scratch space is a caller-provided workspace sized by a query call.
+ *   - Blocks are described by `blk_off[nblk + 1]` (device, uint64): block b is
+ *     bytes [blk_off[b], blk_off[b+1]) of a flat buffer.
+ *   - The return value reports host-side argument errors and launch errors.
+ *     Errors found on the device (corrupt input, capacity, a bounded wait that
+ *     expired) are written to a caller-provided `int32_t status[nblk]` array
+ *     (device) and never trap.
+ *
+ * Block record (the wire format, App. D adapted to GPU-sized blocks):
+ *    0 u32 rec_bytes (multiple of 16)   4 u32 n (symbols)
+ *    8 u16 n_int (internal nodes)  10 u8 kind (0 empty, 1 constant, 2 coded)
+ *   11 u8 aux (kind 1: the symbol)  12 "PVC1"
+ *   kind 2: 16 u8 lens[128] (4-bit code lengths, symbol 2k in the low nibble)
+ *          144 u32 n_v[n_int] (symbols through each node, breadth-first order)
+ *              u8 marker[n_int] (0 raw; 1..50 | 0x80 XOR: ANS table id;
+ *                                0xFF: selected for ANS but stored raw)
+ *              zero pad to 4, u32 alen[#nonzero markers] (body bytes)
+ *              bodies: raw ceil(n_v/8)-byte bitmaps of marker-0 nodes,
+ *                      then the bodies of the other nodes; zero pad to 16.
+ *   Bitmap bit j is bit (j & 7) of byte j >> 3 (Sec. 2.4.2 bit order).
+ *   An ANS body is u32 nwords[S] for S = ceil(bytes / 16384) segments, then
+ *   per segment W = min(32, ceil(seg_bytes / 512)) u32 final rANS states and
+ *   nwords u16 renormalisation words.
+ */
+#ifndef PIVCO_H
+#define PIVCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pivco_status;
+#define PIVCO_OK 0
+#define PIVCO_ERR_INVALID_ARG 1   /* bad argument or parameter */
+#define PIVCO_ERR_CAPACITY 2      /* an output or workspace is too small */
+#define PIVCO_ERR_CORRUPT 3       /* a record failed validation */
+#define PIVCO_ERR_TIMEOUT 4       /* a bounded device wait expired */
+#define PIVCO_ERR_CUDA 5          /* a CUDA launch or runtime error */
+
+/* Encoder parameters.  max_len is the code-length limit L (App. D: 11).
+ * The ANS fields are the three knobs of the selection rule of Sec. 5.2:
+ * a node's bitmap is ANS-coded when it has at least ans_min_bytes bytes (32),
+ * its skew max(n0, n1) / n exceeds ans_skew_num / ans_skew_den (5/8 = 0.625),
+ * and (depth + fse_H) / (depth + 1) is below ans_ratio_pct / 100 (0.95). */
+typedef struct pivco_params {
+    int32_t max_len;
+    int32_t ans_enable;
+    int32_t ans_min_bytes;
+    int32_t ans_skew_num;
+    int32_t ans_skew_den;
+    int32_t ans_ratio_pct;
+} pivco_params;
+
+/* Library version string (host, static storage). */
+const char *pivco_version(void);
+
+/* Bytes of the per-block layout record written by pivco_build_layout. */
+int32_t pivco_layout_bytes(void);
+
+/* Histogram (Sec. 4: encode-side statistics).  hist[b * 256 + s] (device,
+ * uint32) receives the count of byte s in block b.  in: device symbols. */
+pivco_status pivco_histogram(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
+                             uint32_t *hist, void *stream);
+
+/* Length-limited code lengths (Sec. 1.2, App. D: limit L = max_len <= 15).
+ * Optimal under the limit (package-merge); ties between equal counts are
+ * broken by symbol value, so equal-count lower byte values get the longer
+ * codes.  lens[b * 256 + s] (device, uint8) is 0 for absent symbols and for
+ * blocks with fewer than two distinct symbols.  status[b] (device) gets
+ * PIVCO_ERR_INVALID_ARG when 2^max_len is smaller than the alphabet. */
+pivco_status pivco_code_lengths(const uint32_t *hist, int32_t nblk, int32_t max_len,
+                                uint8_t *lens, int32_t *status, void *stream);
+
+/* Tree / pivot layout (Sec. 2; Sec. 5.2 selection; App. D record layout).
+ * From lens and hist builds the canonical codes, the breadth-first node
+ * table with per-node counts n_v, the ANS selection of each node, and the
+ * record's byte layout.  layout: device buffer of nblk * pivco_layout_bytes()
+ * bytes (opaque).  rec_bound[b] (device, uint64): the record size with every
+ * node stored raw; the final record is never larger.  params: host. */
+pivco_status pivco_build_layout(const uint32_t *hist, const uint8_t *lens, int32_t nblk,
+                                const pivco_params *params, void *layout, uint64_t *rec_bound,
+                                int32_t *status, void *stream);
+
+/* Device-wide exclusive scan of n uint64 values (single pass, decoupled
+ * look-back): out[0] = 0, out[i+1] = in[0] + ... + in[i] (device arrays,
+ * out has n + 1 entries).  Used to place records from their sizes.  ws:
+ * device workspace of pivco_scan_workspace_size(n) bytes; status_out: device
+ * int32, PIVCO_ERR_TIMEOUT if a look-back wait expired (else untouched). */
+size_t pivco_scan_workspace_size(int32_t n);
+pivco_status pivco_exclusive_scan(const uint64_t *in, int32_t n, uint64_t *out, void *ws,
+                                  size_t ws_bytes, int32_t *status_out, void *stream);
+
+/* Encode blocks (Sec. 4, Table 11: per node, write the bitmap and stably
+ * partition the symbols to the non-leaf children).  Writes block b's record at
+ * out + out_off[b]; its capacity is out_off[b+1] - out_off[b] and must be at
+ * least rec_bound[b].  Nodes selected for ANS are written raw with marker
+ * 0xFF; pivco_ans_encode_blocks then codes them.  rec_bytes[b] (device)
+ * receives the record size.  status[b] (device). */
+pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
+                                 const void *layout, uint8_t *out, const uint64_t *out_off,
+                                 uint64_t *rec_bytes, int32_t *status, void *stream);
+
+/* Selective ANS of encoded records (Sec. 5.2, App. D marker byte): codes the
+ * bitmap bytes of every node with marker 0xFF by static-table rANS and keeps
+ * the result when it is smaller than the raw bitmap; rewrites the record in
+ * place and updates rec_bytes[b].  ws: device workspace of at least
+ * out_off[nblk] + 256 * nblk bytes (the encode output size).  status[b]. */
+pivco_status pivco_ans_encode_blocks(const void *layout, int32_t nblk, uint8_t *out,
+                                     const uint64_t *out_off, uint64_t *rec_bytes, void *ws,
+                                     size_t ws_bytes, int32_t *status, void *stream);
+
+/* Decode workspace.  pivco_decode_plan_bytes(nblk) (host, pure) is the size
+ * of the plan part of the workspace.  pivco_decode_workspace_size
+ * (synchronous) runs the plan for these records in `ws` (device, at least
+ * pivco_decode_plan_bytes(nblk) bytes) and returns in *bytes the total
+ * workspace pivco_decode_blocks needs (plan plus room for the ANS-decoded
+ * bitmaps).  status[b] (device) reports records whose headers are corrupt. */
+size_t pivco_decode_plan_bytes(int32_t nblk);
+pivco_status pivco_decode_workspace_size(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
+                                         void *ws, size_t ws_bytes, int32_t *status, size_t *bytes,
+                                         void *stream);
+
+/* Decode blocks (Sec. 3: bottom-up merge; Sec. 5.2: ANS-coded bitmaps are
+ * decoded first).  Record b starts at comp + comp_off[b] (device; at most
+ * comp_off[b+1] - comp_off[b] bytes are read).  Symbols go to
+ * out + out_off[b]; the capacity out_off[b+1] - out_off[b] must equal the
+ * record's n.  ws: device workspace (pivco_decode_workspace_size).
+ * status[b] (device): PIVCO_OK, PIVCO_ERR_CORRUPT, PIVCO_ERR_CAPACITY,
+ * PIVCO_ERR_TIMEOUT. */
+pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
+                                 uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
+                                 int32_t *status, void *stream);
+
+/* The static ANS tables of this library (host, synchronous): fse_h_q16[50]
+ * = expected coded bits per bitmap bit in Q16 for tables t = 50..99
+ * (Sec. 5.2 fse_H); class_freq[50 * 9] = frequency (out of 2^15) of one byte
+ * with k one-bits under table t.  Either pointer may be NULL. */
+pivco_status pivco_ans_tables(int32_t *fse_h_q16, uint32_t *class_freq);
+
+/* Standalone ANS of bitmaps (Sec. 5.2).  Bitmap i is bytes
+ * [bm_off[i], bm_off[i+1]) of `bitmaps`, coded with table t = table[i] & 0x7F
+ * + 49 after XOR with 0xFF when table[i] & 0x80.  pivco_ans_encode writes
+ * body i at bodies + body_off[i] (capacity body_off[i+1] - body_off[i], at
+ * least 4 * nseg + 132 * nseg + 2 * bytes) and its size to body_bytes[i];
+ * pivco_ans_decode inverts it.  All arrays device.  status[i] (device). */
+pivco_status pivco_ans_encode(const uint8_t *bitmaps, const uint64_t *bm_off, const uint8_t *table,
+                              int32_t nbm, uint8_t *bodies, const uint64_t *body_off,
+                              uint64_t *body_bytes, int32_t *status, void *stream);
+pivco_status pivco_ans_decode(const uint8_t *bodies, const uint64_t *body_off, const uint8_t *table,
+                              int32_t nbm, uint8_t *bitmaps, const uint64_t *bm_off,
+                              int32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIVCO_H */

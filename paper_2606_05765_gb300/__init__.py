@@ -1,0 +1,268 @@
+"""PivCo-Huffman for GB300 (sm_103a): Python binding of the C ABI in include/pivco.h.
+
+Every function here only marshals arguments: torch tensors supply device
+memory and the current CUDA stream; all codec work runs in the CUDA kernels of
+``libpivco.so``.  If the library has not been built the import succeeds but the
+first call raises -- there is no CPU fallback.
+
+Low-level calls mirror the C ABI one to one (``histogram``, ``code_lengths``,
+``build_layout``, ``exclusive_scan``, ``encode_blocks``, ``ans_encode_blocks``,
+``decode_workspace_size``, ``decode_blocks``, ``ans_encode``, ``ans_decode``).
+``encode`` / ``decode`` chain them for a batch of blocks.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpivco.so")
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA = 0, 1, 2, 3, 4, 5
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CORRUPT", 4: "TIMEOUT", 5: "CUDA"}
+
+# name -> argument types; every function returns int32 status unless noted
+_P, _I32, _SZ = C.c_void_p, C.c_int32, C.c_size_t
+_SIGS = {
+    "pivco_histogram": [_P, _P, _I32, _P, _P],
+    "pivco_code_lengths": [_P, _I32, _I32, _P, _P, _P],
+    "pivco_build_layout": [_P, _P, _I32, _P, _P, _P, _P, _P],
+    "pivco_exclusive_scan": [_P, _I32, _P, _P, _SZ, _P, _P],
+    "pivco_encode_blocks": [_P, _P, _I32, _P, _P, _P, _P, _P, _P],
+    "pivco_ans_encode_blocks": [_P, _I32, _P, _P, _P, _P, _SZ, _P, _P],
+    "pivco_decode_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
+    "pivco_decode_blocks": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
+    "pivco_ans_tables": [_P, _P],
+    "pivco_ans_encode": [_P, _P, _P, _I32, _P, _P, _P, _P, _P],
+    "pivco_ans_decode": [_P, _P, _P, _I32, _P, _P, _P, _P],
+}
+_OTHER = {
+    "pivco_version": ([], C.c_char_p),
+    "pivco_layout_bytes": ([], _I32),
+    "pivco_scan_workspace_size": ([_I32], _SZ),
+    "pivco_decode_plan_bytes": ([_I32], _SZ),
+}
+
+
+class Params(C.Structure):
+    """Encoder parameters (struct pivco_params): L = 11 (App. D) and the
+    Sec. 5.2 ANS knobs (32 bytes, skew > 5/8, ratio < 95 %)."""
+    _fields_ = [("max_len", C.c_int32), ("ans_enable", C.c_int32), ("ans_min_bytes", C.c_int32),
+                ("ans_skew_num", C.c_int32), ("ans_skew_den", C.c_int32), ("ans_ratio_pct", C.c_int32)]
+
+
+def params(max_len=11, ans=False):
+    return Params(max_len, 1 if ans else 0, 32, 5, 8, 95)
+
+
+class PivcoError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libpivco.so; fail loudly when it is missing (no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PivcoError("libpivco.so is not built (run paper_2606_05765_gb300/build.py); "
+                             "the PivCo-Huffman path has no CPU fallback")
+        l = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = C.c_int32
+        for name, (args, res) in _OTHER.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = l
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise PivcoError("%s failed: %s" % (what, STATUS_NAMES.get(rc, rc)))
+
+
+def version():
+    return lib().pivco_version().decode()
+
+
+def layout_bytes():
+    return lib().pivco_layout_bytes()
+
+
+# ----------------------------------------------------------------- C ABI ----
+def histogram(data, blk_off, hist, stream=None):
+    nblk = blk_off.numel() - 1
+    _check(lib().pivco_histogram(_ptr(data), _ptr(blk_off), nblk, _ptr(hist), _stream(stream)), "pivco_histogram")
+
+
+def code_lengths(hist, nblk, max_len, lens, status, stream=None):
+    _check(lib().pivco_code_lengths(_ptr(hist), nblk, max_len, _ptr(lens), _ptr(status), _stream(stream)),
+           "pivco_code_lengths")
+
+
+def build_layout(hist, lens, nblk, prm, layout, rec_bound, status, stream=None):
+    _check(lib().pivco_build_layout(_ptr(hist), _ptr(lens), nblk, C.byref(prm), _ptr(layout), _ptr(rec_bound),
+                                    _ptr(status), _stream(stream)), "pivco_build_layout")
+
+
+def scan_workspace_size(n):
+    return lib().pivco_scan_workspace_size(n)
+
+
+def exclusive_scan(values, n, out, ws, status=None, stream=None):
+    _check(lib().pivco_exclusive_scan(_ptr(values), n, _ptr(out), _ptr(ws), ws.numel(), _ptr(status),
+                                      _stream(stream)), "pivco_exclusive_scan")
+
+
+def encode_blocks(data, blk_off, nblk, layout, out, out_off, rec_bytes, status, stream=None):
+    _check(lib().pivco_encode_blocks(_ptr(data), _ptr(blk_off), nblk, _ptr(layout), _ptr(out), _ptr(out_off),
+                                     _ptr(rec_bytes), _ptr(status), _stream(stream)), "pivco_encode_blocks")
+
+
+def ans_encode_blocks(layout, nblk, out, out_off, rec_bytes, ws, status, stream=None):
+    _check(lib().pivco_ans_encode_blocks(_ptr(layout), nblk, _ptr(out), _ptr(out_off), _ptr(rec_bytes), _ptr(ws),
+                                         ws.numel(), _ptr(status), _stream(stream)), "pivco_ans_encode_blocks")
+
+
+def decode_plan_bytes(nblk):
+    return lib().pivco_decode_plan_bytes(nblk)
+
+
+def decode_workspace_size(comp, comp_off, nblk, ws, status, stream=None):
+    need = C.c_size_t(0)
+    _check(lib().pivco_decode_workspace_size(_ptr(comp), _ptr(comp_off), nblk, _ptr(ws), ws.numel(), _ptr(status),
+                                             C.byref(need), _stream(stream)), "pivco_decode_workspace_size")
+    return need.value
+
+
+def decode_blocks(comp, comp_off, nblk, out, out_off, ws, status, stream=None, ws_bytes=None):
+    _check(lib().pivco_decode_blocks(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
+                                     ws.numel() if ws_bytes is None else ws_bytes, _ptr(status), _stream(stream)),
+           "pivco_decode_blocks")
+
+
+def ans_tables():
+    fq = np.zeros(50, np.int32)
+    cf = np.zeros(450, np.uint32)
+    _check(lib().pivco_ans_tables(C.c_void_p(fq.ctypes.data), C.c_void_p(cf.ctypes.data)), "pivco_ans_tables")
+    return fq, cf.reshape(50, 9)
+
+
+def ans_encode(bitmaps, bm_off, table, nbm, bodies, body_off, body_bytes, status, stream=None):
+    _check(lib().pivco_ans_encode(_ptr(bitmaps), _ptr(bm_off), _ptr(table), nbm, _ptr(bodies), _ptr(body_off),
+                                  _ptr(body_bytes), _ptr(status), _stream(stream)), "pivco_ans_encode")
+
+
+def ans_decode(bodies, body_off, table, nbm, bitmaps, bm_off, status, stream=None):
+    _check(lib().pivco_ans_decode(_ptr(bodies), _ptr(body_off), _ptr(table), nbm, _ptr(bitmaps), _ptr(bm_off),
+                                  _ptr(status), _stream(stream)), "pivco_ans_decode")
+
+
+# ------------------------------------------------------ batch pipelines ----
+class Encoded:
+    """Records of a batch: block b's record is comp[off[b] : off[b] + rec_bytes[b]]."""
+
+    def __init__(self, comp, off, rec_bytes, status):
+        self.comp, self.off, self.rec_bytes, self.status = comp, off, rec_bytes, status
+
+
+class Encoder:
+    """Plain (per-step launches) encoder with buffers reused across calls."""
+
+    def __init__(self, nblk, prm=None, device="cuda"):
+        import torch
+        self.nblk, self.prm, self.dev = nblk, prm or params(), device
+        self.hist = torch.empty(nblk * 256, dtype=torch.int32, device=device)
+        self.lens = torch.empty(nblk * 256, dtype=torch.uint8, device=device)
+        self.layout = torch.empty(nblk * layout_bytes(), dtype=torch.uint8, device=device)
+        self.bound = torch.empty(nblk, dtype=torch.int64, device=device)
+        self.off = torch.empty(nblk + 1, dtype=torch.int64, device=device)
+        self.rec_bytes = torch.empty(nblk, dtype=torch.int64, device=device)
+        self.status = torch.empty(nblk, dtype=torch.int32, device=device)
+        self.scan_ws = torch.empty(scan_workspace_size(nblk), dtype=torch.uint8, device=device)
+        self.comp = None
+        self.ans_ws = None
+
+    def plan(self, data, blk_off, stream=None):
+        """Statistics, code and layout; returns the total output bytes (synchronises)."""
+        n = self.nblk
+        histogram(data, blk_off, self.hist, stream)
+        code_lengths(self.hist, n, self.prm.max_len, self.lens, self.status, stream)
+        build_layout(self.hist, self.lens, n, self.prm, self.layout, self.bound, self.status, stream)
+        exclusive_scan(self.bound, n, self.off, self.scan_ws, self.status, stream)
+        return int(self.off[-1].item())
+
+    def ensure(self, total):
+        import torch
+        if self.comp is None or self.comp.numel() < max(total, 1):
+            self.comp = torch.empty(max(total, 1), dtype=torch.uint8, device=self.dev)
+            if self.prm.ans_enable:
+                self.ans_ws = torch.empty(max(total, 1) + 256 * self.nblk, dtype=torch.uint8, device=self.dev)
+
+    def run(self, data, blk_off, stream=None, replan=True):
+        """Full encode without host synchronisation (buffers must be sized)."""
+        n = self.nblk
+        if replan:
+            histogram(data, blk_off, self.hist, stream)
+            code_lengths(self.hist, n, self.prm.max_len, self.lens, self.status, stream)
+            build_layout(self.hist, self.lens, n, self.prm, self.layout, self.bound, self.status, stream)
+            exclusive_scan(self.bound, n, self.off, self.scan_ws, self.status, stream)
+        encode_blocks(data, blk_off, n, self.layout, self.comp, self.off, self.rec_bytes, self.status, stream)
+        if self.prm.ans_enable:
+            ans_encode_blocks(self.layout, n, self.comp, self.off, self.rec_bytes, self.ans_ws, self.status, stream)
+        return Encoded(self.comp, self.off, self.rec_bytes, self.status)
+
+    def __call__(self, data, blk_off, stream=None):
+        self.ensure(self.plan(data, blk_off, stream))
+        return self.run(data, blk_off, stream, replan=False)
+
+
+class Decoder:
+    """Plain decoder: plan + ANS-decode pass + bottom-up merge kernel."""
+
+    def __init__(self, nblk, device="cuda"):
+        import torch
+        self.nblk, self.dev = nblk, device
+        self.status = torch.empty(nblk, dtype=torch.int32, device=device)
+        self.ws = torch.empty(decode_plan_bytes(nblk), dtype=torch.uint8, device=device)
+
+    def prepare(self, comp, comp_off, stream=None):
+        import torch
+        need = decode_workspace_size(comp, comp_off, self.nblk, self.ws, self.status, stream)
+        if need > self.ws.numel():
+            self.ws = torch.empty(need, dtype=torch.uint8, device=self.dev)
+        return need
+
+    def run(self, comp, comp_off, out, out_off, stream=None):
+        decode_blocks(comp, comp_off, self.nblk, out, out_off, self.ws, self.status, stream)
+        return out
+
+    def __call__(self, comp, comp_off, out_off, stream=None):
+        import torch
+        self.prepare(comp, comp_off, stream)
+        out = torch.empty(max(int(out_off[-1].item()), 1), dtype=torch.uint8, device=self.dev)
+        return self.run(comp, comp_off, out, out_off, stream)
+
+
+def encode(data, blk_off, prm=None, stream=None):
+    return Encoder(blk_off.numel() - 1, prm, data.device)(data, blk_off, stream)
+
+
+def decode(comp, comp_off, out_off, stream=None):
+    d = Decoder(out_off.numel() - 1, comp.device)
+    out = d(comp, comp_off, out_off, stream)
+    return out, d.status

@@ -1,0 +1,346 @@
+// Encode-side statistics and code construction kernels:
+//   histogram      -- per-block byte counts (Sec. 4: dominates end-to-end encode)
+//   code_lengths   -- optimal length-limited lengths by package-merge (App. D, L = 11)
+//   build_layout   -- canonical codes, breadth-first node table, n_v, ANS
+//                     selection (Sec. 5.2) and the record layout (App. D)
+#include "pivco_dev.cuh"
+
+namespace pv {
+
+// ---------------------------------------------------------------------------
+// Histogram.  Grid (nblk, slices); each CTA counts one slice of one block.
+// Per-warp shared histograms; the slice's most frequent byte (sampled) is
+// counted in registers with a byte-wise compare so skewed data (P(top) up to
+// 0.95) does not serialise on one shared-memory bin.
+// ---------------------------------------------------------------------------
+constexpr int kHistThreads = 256;
+constexpr int kHistWarps = kHistThreads / 32;
+
+__global__ void zero_u32_kernel(uint32_t *p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = 0;
+}
+
+__device__ inline void hist_add_word(uint32_t w, uint32_t hot4, uint32_t hot, uint32_t *wh, uint32_t &hot_cnt) {
+    const uint32_t eq = __vcmpeq4(w, hot4);
+    hot_cnt += __popc(eq) >> 3;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t b = (w >> (8 * k)) & 0xFF;
+        if (b != hot) atomicAdd(&wh[b], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kHistThreads) histogram_kernel(const uint8_t *__restrict__ in,
+                                                                 const uint64_t *__restrict__ blk_off,
+                                                                 uint32_t *__restrict__ hist, int slices) {
+    __shared__ uint32_t wh[kHistWarps][256];
+    const int b = blockIdx.x, sl = blockIdx.y;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint64_t lo0 = blk_off[b], hi0 = blk_off[b + 1];
+    const uint64_t n = hi0 - lo0;
+    const uint64_t span = ((n + slices - 1) / slices + 15) & ~uint64_t(15);
+    const uint64_t lo = lo0 + min(n, span * sl), hi = lo0 + min(n, span * (sl + 1));
+    for (int i = t; i < kHistWarps * 256; i += kHistThreads) (&wh[0][0])[i] = 0;
+    // hot byte: most frequent of 32 samples of this slice (warp-uniform)
+    uint32_t hot = 0;
+    if (hi > lo) {
+        const uint64_t pos = lo + ((uint64_t)lane * 2654435761u) % (hi - lo);
+        const uint32_t v = in[pos];
+        const uint32_t peers = __match_any_sync(0xffffffffu, v);
+        const int cnt = __popc(peers);
+        int best = cnt, bl = lane;
+        for (int o = 16; o; o >>= 1) {
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
+        }
+        hot = __shfl_sync(0xffffffffu, v, bl);
+    }
+    const uint32_t hot4 = hot * 0x01010101u;
+    uint32_t hot_cnt = 0;
+    __syncthreads();
+    uint32_t *my = wh[warp];
+    // head bytes up to 16-byte alignment, then 16-byte vector loads, then tail
+    uint64_t a = (lo + 15) & ~uint64_t(15);
+    if (a > hi) a = hi;
+    for (uint64_t i = lo + t; i < a; i += kHistThreads) {
+        const uint32_t v = in[i];
+        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
+    }
+    const uint64_t nvec = (hi - a) / 16;
+    const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
+    for (uint64_t i = t; i < nvec; i += kHistThreads) {
+        const uint4 q = __ldg(vp + i);
+        hist_add_word(q.x, hot4, hot, my, hot_cnt);
+        hist_add_word(q.y, hot4, hot, my, hot_cnt);
+        hist_add_word(q.z, hot4, hot, my, hot_cnt);
+        hist_add_word(q.w, hot4, hot, my, hot_cnt);
+    }
+    for (uint64_t i = a + nvec * 16 + t; i < hi; i += kHistThreads) {
+        const uint32_t v = in[i];
+        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
+    }
+    for (int o = 16; o; o >>= 1) hot_cnt += __shfl_xor_sync(0xffffffffu, hot_cnt, o);
+    if (lane == 0 && hot_cnt) atomicAdd(&my[hot], hot_cnt);
+    __syncthreads();
+    for (int s = t; s < 256; s += kHistThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < kHistWarps; w++) sum += wh[w][s];
+        if (slices == 1) hist[(size_t)b * 256 + s] = sum;
+        else if (sum) atomicAdd(&hist[(size_t)b * 256 + s], sum);
+    }
+}
+
+cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist, int slices,
+                             cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    if (slices < 1) slices = 1;
+    if (slices > 1) {
+        zero_u32_kernel<<<min(1024, div_up((long long)nblk * 256, 256)), 256, 0, st>>>(hist, (size_t)nblk * 256);
+    }
+    histogram_kernel<<<dim3(nblk, slices), kHistThreads, 0, st>>>(in, blk_off, hist, slices);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Code lengths by package-merge, one CTA (256 threads) per block.
+// Lists are built from the deepest level L up to level 1.  Level L is the
+// leaves sorted by (count, symbol); level l merges the sorted leaves with the
+// packages formed by pairing neighbours of level l+1 (an odd last item is
+// dropped).  A leaf sorts before a package of equal weight, so a leaf's
+// position is i + #packages lighter than it and a package's position is
+// j + #leaves not heavier than it.  Selecting the first 2K-2 items of level 1
+// and following packages down: at each level the selected items are a
+// prefix of the list; its leaves are the lightest leaves, and each gains one
+// bit of length; its packages select twice as many items one level deeper.
+// ---------------------------------------------------------------------------
+constexpr int kPmThreads = 256;
+
+__device__ inline int count_less_u64(const uint64_t *a, int n, uint64_t x) {   // # a[i] < x (a sorted)
+    int lo = 0, hi = n;
+    while (lo < hi) { const int m = (lo + hi) >> 1; if (a[m] < x) lo = m + 1; else hi = m; }
+    return lo;
+}
+__device__ inline int count_le_u64(const uint64_t *a, int n, uint64_t x) {     // # a[i] <= x
+    int lo = 0, hi = n;
+    while (lo < hi) { const int m = (lo + hi) >> 1; if (a[m] <= x) lo = m + 1; else hi = m; }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t *__restrict__ hist, int max_len,
+                                                                  uint8_t *__restrict__ lens_out,
+                                                                  int32_t *__restrict__ status) {
+    __shared__ uint64_t leafw[256];
+    __shared__ uint8_t leafsym[256];
+    __shared__ uint64_t lw[2][512];
+    __shared__ uint64_t pw[256];
+    __shared__ uint16_t leafpos[kMaxLen + 1][256];
+    __shared__ uint32_t h[256];
+    __shared__ int32_t s_len[kMaxLen + 2];
+    const int b = blockIdx.x, t = threadIdx.x;
+    h[t] = hist[(size_t)b * 256 + t];
+    __syncthreads();
+    const int K = __syncthreads_count(h[t] != 0);
+    uint8_t my_len = 0;
+    if (K >= 2 && K <= (1 << max_len)) {
+        // rank of symbol t among present symbols by (count, symbol)
+        if (h[t]) {
+            int r = 0;
+            const uint32_t f = h[t];
+            for (int s = 0; s < 256; s++) r += (h[s] != 0) && (h[s] < f || (h[s] == f && s < t));
+            leafw[r] = f;
+            leafsym[r] = (uint8_t)t;
+        }
+        __syncthreads();
+        // level L: leaves only
+        for (int i = t; i < K; i += kPmThreads) { lw[max_len & 1][i] = leafw[i]; leafpos[max_len][i] = (uint16_t)i; }
+        int len_prev = K;
+        __syncthreads();
+        for (int lvl = max_len - 1; lvl >= 1; lvl--) {
+            const uint64_t *prev = lw[(lvl + 1) & 1];
+            uint64_t *cur = lw[lvl & 1];
+            const int P = len_prev / 2;
+            for (int j = t; j < P; j += kPmThreads) pw[j] = prev[2 * j] + prev[2 * j + 1];
+            __syncthreads();
+            for (int i = t; i < K; i += kPmThreads) {
+                const int pos = i + count_less_u64(pw, P, leafw[i]);
+                cur[pos] = leafw[i];
+                leafpos[lvl][i] = (uint16_t)pos;
+            }
+            for (int j = t; j < P; j += kPmThreads) cur[j + count_le_u64(leafw, K, pw[j])] = pw[j];
+            len_prev = K + P;
+            __syncthreads();
+        }
+        // selection, top-down
+        if (t == 0) {
+            int m = 2 * K - 2;
+            for (int lvl = 1; lvl <= max_len; lvl++) {
+                int lo = 0, hi = K;       // leaves with position < m (positions increase with i)
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (leafpos[lvl][mid] < m) lo = mid + 1; else hi = mid; }
+                s_len[lvl] = lo;
+                m = 2 * (m - lo);
+            }
+        }
+        __syncthreads();
+        if (t < K) {
+            int l = 0;
+            for (int lvl = 1; lvl <= max_len; lvl++) l += (t < s_len[lvl]);
+            h[leafsym[t]] = 0x80000000u | (uint32_t)l;   // reuse as output staging
+        }
+        __syncthreads();
+        my_len = (h[t] & 0x80000000u) ? (uint8_t)(h[t] & 0xFF) : 0;
+    }
+    lens_out[(size_t)b * 256 + t] = my_len;
+    if (t == 0 && status) status[b] = (K > (1 << max_len)) ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
+}
+
+cudaError_t launch_code_lengths(const uint32_t *hist, int nblk, int max_len, uint8_t *lens, int32_t *status,
+                                cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    code_lengths_kernel<<<nblk, kPmThreads, 0, st>>>(hist, max_len, lens, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Layout: canonical codes, node table, n_v, ANS selection, record layout.
+// One CTA (256 threads) per block.
+// ---------------------------------------------------------------------------
+struct SelectParams {
+    pivco_params p;
+    int32_t fseh_q16[50];
+};
+
+// Sec. 5.2: selected when ceil(n/8) >= min bytes, skew > num/den and
+// (depth + fse_H) / (depth + 1) < ratio.  Table t = round(100 * skew) in
+// 50..99; bit 7 flags a bitmap whose ones are the majority (XOR 0xFF).
+__device__ inline uint8_t ans_select(uint64_t nv, uint64_t n1, int depth, const SelectParams &sp) {
+    if (!sp.p.ans_enable || nv == 0) return 0;
+    const uint64_t bytes = (nv + 7) / 8;
+    if (bytes < (uint64_t)sp.p.ans_min_bytes) return 0;
+    const uint64_t n0 = nv - n1, mx = n0 > n1 ? n0 : n1;
+    if (mx * (uint64_t)sp.p.ans_skew_den <= (uint64_t)sp.p.ans_skew_num * nv) return 0;
+    uint64_t tt = (200 * mx + nv) / (2 * nv);
+    tt = tt < 50 ? 50 : (tt > 99 ? 99 : tt);
+    const uint64_t lhs = ((uint64_t)depth * 65536u + (uint64_t)sp.fseh_q16[tt - 50]) * 100u;
+    const uint64_t rhs = (uint64_t)sp.p.ans_ratio_pct * (uint64_t)(depth + 1) * 65536u;
+    if (!(lhs < rhs)) return 0;
+    uint8_t m = (uint8_t)(tt - 49);
+    if (n1 > n0) m |= 0x80;
+    return m;
+}
+
+constexpr int kLayThreads = 256;
+
+__global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_t *__restrict__ hist,
+                                                                   const uint8_t *__restrict__ lens_in,
+                                                                   const __grid_constant__ SelectParams sp,
+                                                                   BlockLayout *__restrict__ layout,
+                                                                   uint64_t *__restrict__ rec_bound,
+                                                                   int32_t *__restrict__ status) {
+    __shared__ BlockLayout L;
+    __shared__ uint8_t lens[256], sorted[256];
+    __shared__ uint16_t codes[256];
+    __shared__ int32_t scratch[256];
+    __shared__ uint32_t h[256];
+    __shared__ TreeShape ts;
+    const int b = blockIdx.x, t = threadIdx.x;
+    h[t] = hist[(size_t)b * 256 + t];
+    lens[t] = lens_in[(size_t)b * 256 + t];
+    // zero the shared layout
+    for (int i = t; i < (int)(sizeof(BlockLayout) / 4); i += kLayThreads) reinterpret_cast<uint32_t *>(&L)[i] = 0;
+    __syncthreads();
+    const int K = __syncthreads_count(h[t] != 0);
+    uint64_t n = 0;
+    {
+        __shared__ unsigned long long s_n;
+        if (t == 0) s_n = 0;
+        __syncthreads();
+        if (h[t]) atomicAdd(&s_n, (unsigned long long)h[t]);
+        __syncthreads();
+        n = s_n;
+    }
+    int st = PIVCO_OK;
+    if (t == 0) { L.n = (uint32_t)n; L.status = 0; }
+    if (K <= 1) {
+        if (t == 0) {
+            L.kind = K == 0 ? 0 : 1;
+            L.rec_bound = kHdr;
+            L.body0 = kHdr;
+        }
+        if (h[t]) L.csym = (uint8_t)t;
+        __syncthreads();
+    } else {
+        build_tree_shape(lens, ts, codes, sorted, scratch);
+        if (!ts.ok || ts.K != K || n > 0xFFFFFFFFull) {
+            st = PIVCO_ERR_INVALID_ARG;
+        } else {
+            const int V = ts.n_int;
+            if (t == 0) {
+                L.kind = 2;
+                L.n_int = (uint16_t)V;
+                L.max_depth = (uint8_t)ts.max_len;
+                for (int d = 0; d <= 16; d++) L.depth_first[d] = (uint8_t)min(ts.first[min(d, (int)kMaxLen + 1)], 255);
+                for (int d = ts.max_len; d <= 16; d++) L.depth_first[d] = (uint8_t)V;
+                for (int d = 0; d <= 16; d++) L.tree_a[d] = (uint16_t)ts.a[d];
+            }
+            L.code[t] = codes[t];
+            L.len[t] = lens[t];
+            if (t < V) {
+                const int d = node_depth(ts, t);
+                L.depth[t] = (uint8_t)d;
+                L.child[t][0] = (int16_t)node_child(ts, sorted, t, d, 0);
+                L.child[t][1] = (int16_t)node_child(ts, sorted, t, d, 1);
+            }
+            __syncthreads();
+            // n_v: each symbol adds its count to every node on its code path
+            if (lens[t]) {
+                const int l = lens[t];
+                for (int d = 0; d < l; d++) {
+                    const int p = codes[t] >> (l - d);
+                    atomicAdd(&L.nv[ts.first[d] + p - ts.a[d]], h[t]);
+                }
+            }
+            __syncthreads();
+            if (t < V) {
+                const int c = L.child[t][1];
+                const uint64_t n1 = c >= 0 ? L.nv[c] : h[-c - 1];
+                L.sel[t] = ans_select(L.nv[t], n1, L.depth[t], sp);
+            }
+            __syncthreads();
+            if (t == 0) {
+                int nsel = 0;
+                for (int v = 0; v < V; v++) nsel += L.sel[v] != 0;
+                uint32_t off = (kNvOff + 5u * V + 3u) & ~3u;
+                off += 4u * nsel;
+                L.body0 = off;
+                L.n_sel = (uint8_t)nsel;
+                for (int v = 0; v < V; v++) if (!L.sel[v]) { L.body_off[v] = off; off += (L.nv[v] + 7) / 8; }
+                for (int v = 0; v < V; v++) if (L.sel[v]) { L.body_off[v] = off; off += (L.nv[v] + 7) / 8; }
+                L.rec_bound = (off + 15u) & ~15u;
+            }
+        }
+    }
+    if (t == 0) L.status = (uint8_t)st;
+    __syncthreads();
+    if (st != PIVCO_OK && t == 0) { L.kind = 0; L.rec_bound = kHdr; }
+    __syncthreads();
+    uint32_t *dst = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(layout) + (size_t)b * kLayoutBytes);
+    for (int i = t; i < (int)(sizeof(BlockLayout) / 4); i += kLayThreads) dst[i] = reinterpret_cast<uint32_t *>(&L)[i];
+    if (t == 0) {
+        rec_bound[b] = L.rec_bound;
+        if (status) status[b] = st;
+    }
+}
+
+cudaError_t launch_build_layout(const uint32_t *hist, const uint8_t *lens, int nblk, const pivco_params &p,
+                                BlockLayout *layout, uint64_t *rec_bound, int32_t *status, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    SelectParams sp;
+    sp.p = p;
+    const AnsTables &T = host_ans_tables();
+    for (int i = 0; i < 50; i++) sp.fseh_q16[i] = T.fseh_q16[i];
+    build_layout_kernel<<<nblk, kLayThreads, 0, st>>>(hist, lens, sp, layout, rec_bound, status);
+    return cudaGetLastError();
+}
+
+}  // namespace pv

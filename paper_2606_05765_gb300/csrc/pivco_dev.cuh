@@ -1,0 +1,225 @@
+// Internal definitions shared by the library's kernels (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/pivco.h"
+
+namespace pv {
+
+// ---------------------------------------------------------------------------
+// Record format constants (App. D, adapted; documented in include/pivco.h)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kHdr = 16;        // fixed header
+constexpr uint32_t kLensOff = 16;    // 128 bytes of 4-bit lengths
+constexpr uint32_t kNvOff = 144;     // u32 n_v[n_int]
+constexpr uint32_t kMaxLen = 15;     // 4-bit length field
+constexpr uint8_t kMarkRawSel = 0xFF;
+constexpr uint32_t kAnsSeg = 16384;  // bitmap bytes per ANS segment
+constexpr uint32_t kAnsScale = 15;
+constexpr uint32_t kAnsM = 1u << kAnsScale;
+constexpr uint32_t kAnsL = 1u << 16;
+
+__host__ __device__ inline uint32_t ans_seg_count(uint32_t nbytes) { return (nbytes + kAnsSeg - 1) / kAnsSeg; }
+__host__ __device__ inline uint32_t ans_seg_lanes(uint32_t seg_bytes) {
+    uint32_t w = (seg_bytes + 511) / 512;
+    return w < 1 ? 1 : (w > 32 ? 32 : w);
+}
+
+// ---------------------------------------------------------------------------
+// Static ANS tables, passed by value to kernels (Sec. 5.2: 50 tables for skew
+// 50..99 %).  Byte frequencies depend only on the byte's popcount class k.
+// Bytes are ordered by (k, value) in the cumulative table.
+// ---------------------------------------------------------------------------
+struct AnsTables {
+    uint16_t q[50][9];        // frequency of one byte of class k (of 2^15)
+    uint16_t start[50][10];   // cumulative start of class k; start[t][9] = 2^15
+    uint32_t magic[50][9];    // ceil(2^32 / q) for exact division (q >= 2); 0 when q == 1
+    int32_t fseh_q16[50];     // expected bits per bitmap bit, Q16
+    uint8_t rank_in_class[256];   // index of byte b among bytes of its class
+    uint8_t class_member[256];    // bytes sorted by (popcount, value)
+    uint8_t class_base[10];       // first index of class k in class_member
+};
+const AnsTables &host_ans_tables();
+
+// ---------------------------------------------------------------------------
+// Per-block layout written by build_layout and read by the encoders.
+// ---------------------------------------------------------------------------
+struct BlockLayout {
+    uint32_t n;            // symbols
+    uint32_t rec_bound;    // record bytes with every node raw
+    uint32_t body0;        // byte offset of the first body
+    uint16_t n_int;        // internal nodes
+    uint8_t kind;          // 0 empty, 1 constant, 2 coded
+    uint8_t csym;          // kind 1 symbol
+    uint8_t max_depth;     // longest code length
+    uint8_t n_sel;         // nodes selected for ANS
+    uint8_t status;        // PIVCO_* of layout construction
+    uint8_t pad0;
+    uint8_t depth_first[17];   // first node id at depth d (breadth-first); [d+1]-[d] = count
+    uint8_t pad1[15];
+    uint16_t tree_a[17];       // leaf-covered prefix count at depth d (TreeShape::a)
+    uint16_t pad2[15];
+    uint16_t code[256];    // canonical code of symbol s (lens[s] bits, MSB = first decision)
+    uint8_t len[256];      // code length of symbol s
+    uint32_t nv[256];      // symbols through node v
+    uint32_t body_off[256];    // byte offset of node v's body in the record (raw layout)
+    int16_t child[256][2];     // >= 0 internal id; < 0 leaf, symbol = -c - 1
+    uint8_t sel[256];          // ANS candidate marker (table id | 0x80 XOR), 0 if not selected
+    uint8_t depth[256];
+};
+static_assert(sizeof(BlockLayout) <= 8192, "layout too large");
+constexpr int32_t kLayoutBytes = 8192;
+
+// ---------------------------------------------------------------------------
+// Canonical tree from code lengths (Sec. 1 canonical coding, App. D).
+// For a full canonical code the leaves at each depth occupy the smallest
+// prefix values; a[d] counts the d-bit values covered by leaves of length
+// <= d, and the internal nodes at depth d are exactly the prefixes
+// a[d] .. 2^d - 1.  Nodes are numbered breadth-first (depth, prefix).
+// ---------------------------------------------------------------------------
+struct TreeShape {
+    int32_t cnt[kMaxLen + 2];      // symbols of each length
+    int32_t a[kMaxLen + 2];        // leaf-covered prefix count at depth d
+    int32_t first[kMaxLen + 2];    // first node id at depth d
+    int32_t len_base[kMaxLen + 2]; // index of the first symbol of length l in sorted order
+    int32_t n_int;
+    int32_t max_len;
+    int32_t K;
+    int32_t ok;
+};
+
+// Builds the tree shape and the per-symbol canonical codes.  Must be called
+// by all threads of the CTA (blockDim.x >= 256).  lens/codes/sorted are in
+// shared memory; `sorted` receives the symbols ordered by (length, value).
+__device__ inline void build_tree_shape(const uint8_t *lens, TreeShape &ts, uint16_t *codes, uint8_t *sorted,
+                                        int32_t *rank_scratch /* 256 */) {
+    const int t = threadIdx.x;
+    if (t < kMaxLen + 2) ts.cnt[t] = 0;
+    __syncthreads();
+    if (t < 256 && lens[t]) atomicAdd(&ts.cnt[lens[t]], 1);
+    __syncthreads();
+    if (t == 0) {
+        int32_t a = 0, first = 0, base = 0, K = 0, ml = 0;
+        bool ok = true;
+        ts.a[0] = 0;
+        ts.first[0] = 0;
+        for (int l = 1; l <= (int)kMaxLen; l++) {
+            ts.len_base[l] = base;
+            base += ts.cnt[l];
+            K += ts.cnt[l];
+            if (ts.cnt[l]) ml = l;
+        }
+        // open[d] = 2^d - a[d] internal nodes at depth d; a[d] = 2 a[d-1] + cnt[d]
+        for (int d = 0; d <= (int)kMaxLen; d++) {
+            if (d > 0) a = 2 * a + ts.cnt[d];
+            ts.a[d] = a;
+            int64_t open = (int64_t(1) << d) - a;
+            if (open < 0) ok = false;
+            ts.first[d] = first;
+            if (d < ml) {
+                if (open <= 0) ok = false;
+                first += (int32_t)open;
+            } else if (d == ml && open != 0) {
+                ok = false;     // Kraft equality: the tree is full
+            }
+        }
+        ts.first[kMaxLen + 1] = first;
+        ts.n_int = first;
+        ts.max_len = ml;
+        ts.K = K;
+        ts.ok = ok && K >= 2 && first == K - 1;
+    }
+    __syncthreads();
+    // rank of s among symbols of the same length (by value)
+    if (t < 256) {
+        int32_t r = 0;
+        const uint8_t l = lens[t];
+        if (l) {
+            for (int s = 0; s < t; s++) r += (lens[s] == l);
+        }
+        rank_scratch[t] = r;
+    }
+    __syncthreads();
+    if (t < 256) {
+        const uint8_t l = lens[t];
+        if (l && ts.ok) {
+            const int32_t r = rank_scratch[t];
+            sorted[ts.len_base[l] + r] = (uint8_t)t;
+            codes[t] = (uint16_t)(2 * ts.a[l - 1] + r);
+        } else {
+            codes[t] = 0;
+        }
+    }
+    __syncthreads();
+}
+
+// depth of internal node v
+__device__ inline int node_depth(const TreeShape &ts, int v) {
+    int d = 0;
+    while (d < ts.max_len && ts.first[d + 1] <= v) d++;
+    return d;
+}
+
+// child b of internal node v at depth d: >= 0 internal id, < 0 leaf -(sym+1)
+__device__ inline int node_child(const TreeShape &ts, const uint8_t *sorted, int v, int d, int b) {
+    const int32_t p = ts.a[d] + (v - ts.first[d]);
+    const int32_t q = 2 * p + b;
+    if (q < ts.a[d + 1]) return -(int)sorted[ts.len_base[d + 1] + (q - 2 * ts.a[d])] - 1;
+    return ts.first[d + 1] + (q - ts.a[d + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// Small utilities
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t ld_le32(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+__device__ inline void st_le32(uint8_t *p, uint32_t v) {
+    p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+}
+__device__ inline uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // bounded device waits: 1 s
+
+__host__ __device__ inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Launchers implemented in the kernel translation units.
+cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
+                             int slices, cudaStream_t st);
+cudaError_t launch_code_lengths(const uint32_t *hist, int nblk, int max_len, uint8_t *lens, int32_t *status,
+                                cudaStream_t st);
+cudaError_t launch_build_layout(const uint32_t *hist, const uint8_t *lens, int nblk, const pivco_params &p,
+                                BlockLayout *layout, uint64_t *rec_bound, int32_t *status, cudaStream_t st);
+cudaError_t launch_scan(const uint64_t *in, int n, uint64_t *out, void *ws, int32_t *status, cudaStream_t st);
+size_t scan_ws_bytes(int n);
+cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, const BlockLayout *layout,
+                          uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status,
+                          cudaStream_t st);
+cudaError_t launch_ans_encode_blocks(const BlockLayout *layout, int nblk, uint8_t *out, const uint64_t *out_off,
+                                     uint64_t *rec_bytes, uint8_t *ws, size_t ws_bytes, int32_t *status,
+                                     cudaStream_t st);
+cudaError_t launch_ans_encode(const uint8_t *bm, const uint64_t *bm_off, const uint8_t *table, int nbm,
+                              uint8_t *bodies, const uint64_t *body_off, uint64_t *body_bytes, int32_t *status,
+                              cudaStream_t st);
+cudaError_t launch_ans_decode(const uint8_t *bodies, const uint64_t *body_off, const uint8_t *table, int nbm,
+                              uint8_t *bm, const uint64_t *bm_off, int32_t *status, cudaStream_t st);
+// decode workspace: header, look-back states, per-block offsets (see k_ans.cu)
+__host__ __device__ inline size_t decode_ws_fixed_bytes(int nblk) {
+    const size_t f = 64 + 8ull * nblk + 8ull * nblk + 4ull * nblk;
+    return (f + 255) & ~(size_t)255;
+}
+cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
+                               size_t ws_bytes, int32_t *status, cudaStream_t st);
+cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st);
+cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
+                                      size_t ws_bytes, int32_t *status, cudaStream_t st);
+cudaError_t read_decode_ws_need(const uint8_t *ws, int nblk, size_t *need, cudaStream_t st);
+cudaError_t launch_decode(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
+                          const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
+                          cudaStream_t st);
+
+}  // namespace pv

@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every symbol include/pivco.h declares
+(CPU only: no compute call is made here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pivco.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pivco_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_2606_05765_gb300 import build as B
+    path = B.build()
+    return path
+
+
+def test_header_declares_calls():
+    names = declared_functions()
+    for core in ["pivco_histogram", "pivco_code_lengths", "pivco_build_layout", "pivco_encode_blocks",
+                 "pivco_decode_blocks", "pivco_ans_encode_blocks", "pivco_exclusive_scan"]:
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pivco_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_reports(built_lib):
+    import paper_2606_05765_gb300 as P
+    assert "PVC1" in P.version()
+    assert P.layout_bytes() >= 4096
+    assert P.scan_workspace_size(1000) >= 16
+    assert P.decode_plan_bytes(10) % 256 == 0
+
+
+def test_ans_tables_match_oracle(built_lib, oracle):
+    """The library's own static ANS tables equal the oracle's (Sec. 5.2)."""
+    import numpy as np
+    import paper_2606_05765_gb300 as P
+    fq, cf = P.ans_tables()
+    for t in range(50, 100):
+        assert fq[t - 50] == oracle.fse_h_q16(t)
+        assert np.array_equal(cf[t - 50], oracle.ans_class_freqs(t))
+
+
+def test_host_argument_errors(built_lib):
+    """Host-side argument checks return an error without touching the GPU."""
+    import ctypes as C
+    import paper_2606_05765_gb300 as P
+    L = P.lib()
+    assert L.pivco_code_lengths(None, 1, 0, None, None, None) == P.ERR_INVALID_ARG
+    assert L.pivco_code_lengths(None, 1, 16, None, None, None) == P.ERR_INVALID_ARG
+    assert L.pivco_histogram(None, None, -1, None, None) == P.ERR_INVALID_ARG
+    bad = P.params()
+    bad.ans_skew_den = 0
+    assert L.pivco_build_layout(None, None, 0, C.byref(bad), None, None, None, None) == P.ERR_INVALID_ARG
+    assert L.pivco_decode_blocks(None, None, -1, None, None, None, 0, None, None) == P.ERR_INVALID_ARG

@@ -1,0 +1,221 @@
+"""GPU parity: the sm_103a library against the CPU oracle, element by element.
+
+Everything here is integer / byte work, so the bar is bit-exact: histograms,
+code lengths, whole block records (bitmaps, directories, ANS states and words)
+and decoded bytes.  All calls go through the C ABI (ctypes binding).
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_05765_gb300 as P
+    return P
+
+
+def dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def off64(blk_off):
+    return dev(np.asarray(blk_off, np.int64))
+
+
+def edge_workload():
+    """Degenerate and ragged blocks: empty, 1 byte, constant, two symbols,
+    sizes around unit / chunk boundaries, a 256-symbol uniform block."""
+    rng = np.random.default_rng(99)
+    blocks = [np.zeros(0, np.uint8), np.array([7], np.uint8), np.full(1000, 3, np.uint8),
+              np.array([1, 2], np.uint8), rng.integers(0, 2, 33).astype(np.uint8),
+              rng.integers(0, 256, 127).astype(np.uint8), rng.integers(0, 256, 128).astype(np.uint8),
+              rng.integers(0, 256, 129).astype(np.uint8), rng.integers(0, 5, 16383).astype(np.uint8),
+              rng.integers(0, 5, 16384).astype(np.uint8), rng.integers(0, 5, 16385).astype(np.uint8),
+              rng.integers(0, 256, 40000).astype(np.uint8),
+              (rng.random(70000) < 0.97).astype(np.uint8) * 9]
+    sizes = [b.size for b in blocks]
+    off = np.zeros(len(blocks) + 1, np.uint64)
+    off[1:] = np.cumsum(sizes)
+    return workloads.Workload("edge", np.concatenate(blocks), off, True)
+
+
+WORKLOADS = {
+    "zipf1_256k": lambda: workloads.zipf1(n=1 << 18),
+    "skew80_8x64k": lambda: workloads.skew80(nblk=8, bs=65536),
+    "skew95_4x128k": lambda: workloads.skew95(nblk=4, bs=131072),
+    "mixed_24": lambda: workloads.mixed(nblk=24, hi=1 << 18),
+    "edge": edge_workload,
+}
+
+
+def oracle_records(oracle, w, ans):
+    prm = oracle.params(ans=ans)
+    return [oracle.encode_block(w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])], prm) for b in range(w.nblk)]
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_histogram(P, oracle, name):
+    import torch
+    w = WORKLOADS[name]()
+    hist = torch.empty(w.nblk * 256, dtype=torch.int32, device="cuda")
+    P.histogram(dev(w.data), off64(w.blk_off), hist)
+    got = hist.cpu().numpy().view(np.uint32).reshape(w.nblk, 256)
+    for b in range(w.nblk):
+        assert np.array_equal(got[b], oracle.histogram(w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])])), b
+
+
+def test_code_lengths(P, oracle):
+    import torch
+    rng = np.random.default_rng(5)
+    hs = []
+    for i in range(300):
+        h = np.zeros(256, np.uint32)
+        K = int(rng.integers(0, 257)) if i % 7 else int(rng.integers(0, 4))
+        syms = rng.choice(256, K, replace=False)
+        kind = i % 4
+        if kind == 0:
+            h[syms] = rng.integers(1, 1 << 16, K)
+        elif kind == 1:
+            h[syms] = (rng.pareto(0.7, K) * 30).astype(np.uint32) + 1
+        elif kind == 2:
+            h[syms] = 1 + (np.arange(K) % 3)                   # many ties
+        else:
+            h[syms[:min(K, 25)]] = [int(1.618 ** j) + 1 for j in range(min(K, 25))]   # limit binds
+        hs.append(h)
+    H = np.stack(hs)
+    for L in (11, 8, 15):
+        st = torch.empty(len(hs), dtype=torch.int32, device="cuda")
+        lens = torch.empty(len(hs) * 256, dtype=torch.uint8, device="cuda")
+        P.code_lengths(dev(H.reshape(-1).view(np.int32)), len(hs), L, lens, st)
+        got = lens.cpu().numpy().reshape(len(hs), 256)
+        stn = st.cpu().numpy()
+        for i, h in enumerate(hs):
+            if np.count_nonzero(h) > (1 << L):
+                assert stn[i] == P.ERR_INVALID_ARG
+                continue
+            assert stn[i] == 0
+            assert np.array_equal(got[i], oracle.code_lengths(h, L)), (L, i)
+
+
+@pytest.mark.parametrize("ans", [False, True])
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_encode_records(P, oracle, name, ans):
+    w = WORKLOADS[name]()
+    enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=ans))
+    st = enc.status.cpu().numpy()
+    assert not st.any(), st
+    comp, off, rb = enc.comp.cpu().numpy(), enc.off.cpu().numpy(), enc.rec_bytes.cpu().numpy()
+    refs = oracle_records(oracle, w, ans)
+    for b, ref in enumerate(refs):
+        got = comp[int(off[b]):int(off[b]) + int(rb[b])]
+        assert got.size == ref.size, (b, got.size, ref.size)
+        assert np.array_equal(got, ref), b
+
+
+@pytest.mark.parametrize("ans", [False, True])
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_decode_oracle_records(P, oracle, name, ans):
+    """The GPU decodes the oracle's dense records to the original bytes."""
+    w = WORKLOADS[name]()
+    buf, rec_off, sizes = oracle.encode_batch(w.data, w.blk_off, oracle.params(ans=ans))
+    out, st = P.decode(dev(buf if buf.size else np.zeros(16, np.uint8)), off64(rec_off), off64(w.blk_off))
+    assert not st.cpu().numpy().any()
+    assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
+
+
+def test_round_trip_permuted_values(P):
+    w = workloads.skew80(nblk=4, bs=65536, permute=True)
+    enc = P.encode(dev(w.data), off64(w.blk_off))
+    out, st = P.decode(enc.comp, enc.off, off64(w.blk_off))
+    assert not st.cpu().numpy().any()
+    assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
+
+
+def test_decode_rejects_corrupt_records(P, oracle):
+    rng = np.random.default_rng(3)
+    x = rng.choice(40, 30000, p=rng.dirichlet(np.ones(40))).astype(np.uint8)
+    y = (rng.random(200000) < 0.95).astype(np.uint8)
+    recs = [oracle.encode_block(x), oracle.encode_block(y, oracle.params(ans=True))]
+    cases = []
+    for r in recs:
+        V = int(r[8])
+        c = r.copy(); c[12] = ord("Q"); cases.append((c, r))                       # magic
+        c = r.copy(); c[144] ^= 4; cases.append((c, r))                            # n_v of the root
+        c = r.copy(); c[144 + 4 * V] = 99; cases.append((c, r))                    # marker
+        c = r.copy(); c[16] = 0xEE; cases.append((c, r))                           # code lengths
+        c = r.copy(); c[-20] ^= 0x5A; cases.append((c, r))                         # body bytes
+    for c, r in cases:
+        n = int(np.frombuffer(r[4:8].tobytes(), np.uint32)[0])
+        out, st = P.decode(dev(c), off64([0, c.size]), off64([0, n]))
+        s = int(st.cpu().numpy()[0])
+        ok_bytes = s == 0 and np.array_equal(out.cpu().numpy()[:n], oracle.decode_block(r)[1])
+        # a flipped body bit may still be a valid stream; then the oracle must agree on it
+        if s == 0 and not ok_bytes:
+            rc, ref = oracle.decode_block(c)
+            assert rc == 0 and np.array_equal(out.cpu().numpy()[:n], ref)
+        if s != 0:
+            assert oracle.decode_block(c)[0] != 0
+
+
+def test_ans_primitives(P, oracle):
+    import torch
+    rng = np.random.default_rng(17)
+    bms, tables = [], []
+    for nbytes in [1, 32, 511, 512, 513, 4000, 16384, 16385, 50000]:
+        p1 = float(rng.choice([0.02, 0.1, 0.3, 0.9]))
+        bits = (rng.random(8 * nbytes) < p1).astype(np.uint8)
+        bm = np.packbits(bits, bitorder="little")
+        skew = max(p1, 1 - p1)
+        t = max(50, min(99, int(round(100 * skew))))
+        tables.append((t - 49) | (0x80 if p1 > 0.5 else 0))
+        bms.append(bm)
+    sizes = np.array([b.size for b in bms], np.int64)
+    bm_off = np.zeros(len(bms) + 1, np.int64); bm_off[1:] = np.cumsum(sizes)
+    cap = 4 * ((sizes + 16383) // 16384) * 34 + 2 * sizes + 64
+    body_off = np.zeros(len(bms) + 1, np.int64); body_off[1:] = np.cumsum(cap)
+    bodies = torch.zeros(int(body_off[-1]), dtype=torch.uint8, device="cuda")
+    bb = torch.zeros(len(bms), dtype=torch.int64, device="cuda")
+    st = torch.zeros(len(bms), dtype=torch.int32, device="cuda")
+    tab = dev(np.array(tables, np.uint8))
+    P.ans_encode(dev(np.concatenate(bms)), dev(bm_off), tab, len(bms), bodies, dev(body_off), bb, st)
+    assert not st.cpu().numpy().any()
+    got = bodies.cpu().numpy(); bbn = bb.cpu().numpy()
+    for i, bm in enumerate(bms):
+        t = (tables[i] & 0x7F) + 49
+        src = bm ^ 0xFF if tables[i] & 0x80 else bm
+        ref = oracle.rans_encode(src, t)
+        assert np.array_equal(got[int(body_off[i]):int(body_off[i]) + int(bbn[i])], ref), i
+    # decode the oracle's bodies on the GPU
+    refs = [oracle.rans_encode(bm ^ 0xFF if tables[i] & 0x80 else bm, (tables[i] & 0x7F) + 49) for i, bm in enumerate(bms)]
+    roff = np.zeros(len(refs) + 1, np.int64); roff[1:] = np.cumsum([r.size for r in refs])
+    outb = torch.zeros(int(bm_off[-1]), dtype=torch.uint8, device="cuda")
+    P.ans_decode(dev(np.concatenate(refs)), dev(roff), tab, len(refs), outb, dev(bm_off), st)
+    assert not st.cpu().numpy().any()
+    assert np.array_equal(outb.cpu().numpy(), np.concatenate(bms))
+
+
+def test_exclusive_scan(P):
+    import torch
+    rng = np.random.default_rng(2)
+    for n in [0, 1, 5, 1023, 1024, 1025, 100000]:
+        v = rng.integers(0, 1 << 30, n).astype(np.int64)
+        out = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        ws = torch.empty(P.scan_workspace_size(n), dtype=torch.uint8, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        P.exclusive_scan(dev(v) if n else torch.zeros(1, dtype=torch.int64, device="cuda"), n, out, ws, st)
+        ref = np.zeros(n + 1, np.int64); ref[1:] = np.cumsum(v)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert int(st.cpu().numpy()[0]) == 0
