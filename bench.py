@@ -1,0 +1,360 @@
+"""PivCo-Huffman benchmark on GB300: encode + decode throughput of the hot path.
+
+One step = one pass of the whole path over one batch of synthetic blocks:
+histogram -> code lengths -> layout -> record placement (scan) -> encode
+(-> selective ANS) and then decode (plan -> ANS decode -> bottom-up merge).
+Each leg is timed with CUDA events on the launching stream; L2 is flushed
+before each leg.  `value` is raw bytes / (encode time + decode time) summed
+over all ranks' blocks (weak scaling: every rank codes its own batch).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload skew80]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PivCo decode/encode GB/s on 1 GB300 (% HBM peak), batched vs plain; p99 ms"
+WORKLOADS = {
+    # name: (generator kwargs, description)
+    "skew80": ({}, "4096 blocks x 64 KiB (256 MiB), byte 0 with P=0.8, 255 others uniform, no ANS, seed 1"),
+    "skew95": ({}, "2048 blocks x 128 KiB (256 MiB), P(top)=0.95 + Zipf(1.3) tail, selective ANS, seed 2"),
+    "mixed": ({}, "4096 blocks log-uniform 4 KiB-1 MiB, per-block alphabet/Zipf, selective ANS, seed 3"),
+    "zipf1": ({}, "1 block of 2^20 symbols, Zipf(1.0) over 256, no ANS, seed 0"),
+}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pivco", choices=["pivco", "reference"])
+    ap.add_argument("--workload", default="skew80", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args(argv)
+
+
+def shard_blocks(nblk, rank, world):
+    """Contiguous block range of this rank (blocks are independent units)."""
+    per = (nblk + world - 1) // world
+    lo = min(nblk, rank * per)
+    return lo, min(nblk, lo + per)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index, period_ms=20):
+        self.cmd = ["nvidia-smi", "-i", str(gpu_index),
+                    "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                    "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                    "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", str(period_ms)]
+        self.lines, self.proc = [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+            time.sleep(0.1)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s=10.0, ans=False):
+    """The oracle as it stands, single-threaded on the host, on a bounded
+    prefix of the same blocks; returns GB/s of raw bytes per (encode+decode)."""
+    import oracle
+    oracle.build()
+    prm = oracle.params(ans=ans)
+    nb = 1
+    t_all, raw_all, used = 0.0, 0, 0
+    while used < w.nblk and t_all < budget_s:
+        take = min(nb, w.nblk - used)
+        lo, hi = int(w.blk_off[used]), int(w.blk_off[used + take])
+        sub_off = (w.blk_off[used:used + take + 1] - w.blk_off[used]).astype(np.uint64)
+        x = w.data[lo:hi]
+        t0 = time.perf_counter()
+        buf, rec_off, sizes = oracle.encode_batch(x, sub_off, prm)
+        st, out = oracle.decode_batch(buf, rec_off[:-1], sizes, sub_off)
+        t_all += time.perf_counter() - t0
+        assert not st.any() and np.array_equal(out, x)
+        raw_all += hi - lo
+        used += take
+        nb *= 2
+    return {"value": raw_all / t_all / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d blocks (%.1f MB), encode+decode, %.1f s single-threaded"
+                      % (used, w.nblk, raw_all / 1e6, t_all)}
+
+
+def make_workload(name, rank=0):
+    import workloads
+    return workloads.by_name(name)
+
+
+def run_reference(args):
+    """Reference arm: the oracle (the paper's method restated plainly in C)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = make_workload(args.workload)
+    import oracle
+    oracle.build()
+    prm = oracle.params(ans=w.ans)
+    # each step: a bounded sample of the workload (16 blocks, <= a few MB)
+    take = min(w.nblk, 16)
+    lo, hi = 0, int(w.blk_off[take])
+    sub_off = w.blk_off[:take + 1].astype(np.uint64)
+    x = w.data[lo:hi]
+    for _ in range(args.warmup):
+        buf, rec_off, sizes = oracle.encode_batch(x, sub_off, prm)
+        oracle.decode_batch(buf, rec_off[:-1], sizes, sub_off)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        buf, rec_off, sizes = oracle.encode_batch(x, sub_off, prm)
+        st, out = oracle.decode_batch(buf, rec_off[:-1], sizes, sub_off)
+        times.append(time.perf_counter() - t0)
+        assert not st.any()
+    tot = sum(times)
+    value = (hi - lo) * len(times) / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload][1], "sample_blocks": take,
+                       "sample_bytes": hi - lo},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "first %d blocks (%d bytes) per step" % (take, hi - lo)},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_05765_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2606_05765_gb300 import build as B
+    B.build()
+
+    w = make_workload(args.workload)
+    raw = int(w.data.size)
+    nblk = w.nblk
+    data = torch.from_numpy(w.data).to(dev)
+    blk_off = torch.from_numpy(w.blk_off.astype(np.int64)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    enc = P.Encoder(nblk, P.params(ans=w.ans), dev)
+    total = enc.plan(data, blk_off)
+    enc.ensure(total)
+    res = enc.run(data, blk_off, replan=False)
+    dec = P.Decoder(nblk, dev)
+    dec.prepare(res.comp, res.off)
+    out = torch.empty(raw, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    E = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
+
+    def step(record):
+        flush.zero_()
+        E[0].record(stream)
+        enc.run(data, blk_off)
+        E[1].record(stream)
+        flush.zero_()
+        E[2].record(stream)
+        P.decode_plan(res.comp, res.off, nblk, dec.ws, dec.status)
+        P.decode_ans(res.comp, res.off, nblk, dec.ws, dec.status)
+        E[3].record(stream)
+        P.decode_merge(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status)
+        E[4].record(stream)
+        if record is not None:
+            record.append(E)
+
+    # per-kernel timing of the encode kernel inside the step (events around it)
+    Ek = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = P.launch_count()
+    t_enc, t_dec, t_merge = [], [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            step(None)
+            E[4].synchronize()
+            t_enc.append(E[0].elapsed_time(E[1]))
+            t_dec.append(E[2].elapsed_time(E[4]))
+            t_merge.append(E[3].elapsed_time(E[4]))
+    torch.cuda.synchronize()
+    n_launch = P.launch_count() - n_launch0
+    # encode kernel alone (same stream, outside the step loop, statistics already on device)
+    t_enck = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        Ek[0].record(stream)
+        P.encode_blocks(data, blk_off, nblk, enc.layout, enc.comp, enc.off, enc.rec_bytes, enc.status)
+        Ek[1].record(stream)
+        Ek[1].synchronize()
+        t_enck.append(Ek[0].elapsed_time(Ek[1]))
+    if w.ans:
+        # restore the final records (the plain encode left ANS candidates raw)
+        enc.run(data, blk_off)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    # correctness of the timed work
+    st_e = enc.status.cpu().numpy()
+    st_d = dec.status.cpu().numpy()
+    ok = (not st_e.any()) and (not st_d.any()) and bool(torch.equal(out, data))
+    rec_bytes = int(enc.rec_bytes.sum().item())
+    step_ms = [a + b for a, b in zip(t_enc, t_dec)]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * raw * len(step_ms) / (tot_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (largest share of the step)
+    peak, peak_kind = measured_peaks()
+    merge_ms = statistics.mean(t_merge)
+    enck_ms = statistics.mean(t_enck)
+    kernels = {
+        "decode_merge": {"ms": merge_ms, "bytes": rec_bytes + raw},
+        "encode_blocks": {"ms": enck_ms, "bytes": raw + rec_bytes},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    for k in kernels:
+        kernels[k]["gbs"] = kernels[k]["bytes"] / (kernels[k]["ms"] / 1e3) / 1e9
+        kernels[k]["frac"] = kernels[k]["gbs"] / peak
+    ach = kernels[dom]["gbs"]
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = torch.from_numpy(w.data).pin_memory()
+        h_comp = torch.empty(enc.comp.numel(), dtype=torch.uint8).pin_memory()
+        h_out = torch.empty(raw, dtype=torch.uint8).pin_memory()
+        d_in = torch.empty_like(data)
+        d_comp = torch.empty_like(enc.comp)
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_in.copy_(h_in, non_blocking=True)
+            enc.run(d_in, blk_off)
+            h_comp.copy_(enc.comp, non_blocking=True)
+            d_comp.copy_(h_comp, non_blocking=True)
+            P.decode_blocks(d_comp, enc.off, nblk, out, blk_off, dec.ws, dec.status)
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if i == 0:
+                e2e_t = []
+            else:
+                e2e_t.append(dt)
+        assert torch.equal(h_out, h_in)
+        e2e = {"value": raw / statistics.mean(e2e_t) / 1e9 * world, "unit": "GB/s",
+               "h2d_bytes_per_step": raw + enc.comp.numel(), "d2h_bytes_per_step": enc.comp.numel() + raw}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, ans=w.ans)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tot_ms / len(step_ms), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload][1], "blocks": nblk,
+                       "raw_bytes_per_gpu": raw, "compressed_bytes": rec_bytes, "ratio": round(raw / rec_bytes, 4),
+                       "l2": "L2 flushed (256 MiB write) before each leg; inputs 256 MiB > 129 MB L2",
+                       "path": "plain (one launch sequence per batch)", "parallelism": "blocks sharded per GPU"},
+            "encode_gbs": round(raw / (statistics.mean(t_enc) / 1e3) / 1e9, 3),
+            "decode_gbs": round(raw / (statistics.mean(t_dec) / 1e3) / 1e9, 3),
+            "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+            "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+            "batched": None,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": peak,
+                         "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                         "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()}},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks, "verified": ok,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

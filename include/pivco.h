@@ -154,6 +154,26 @@ pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, 
                                  uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
                                  int32_t *status, void *stream);
 
+/* The three steps of pivco_decode_blocks, callable one by one (same
+ * arguments and workspace; call them in this order on one stream):
+ *   pivco_decode_plan   parses every record header, checks its layout and
+ *                       places the ANS work in `ws` (single-pass scan with
+ *                       decoupled look-back over the blocks); sets status[b];
+ *   pivco_decode_ans    rANS-decodes every ANS-coded node bitmap into the
+ *                       workspace (Sec. 5.2), one warp per 16 KiB segment;
+ *   pivco_decode_merge  rebuilds the symbols bottom-up (Sec. 3) through
+ *                       per-chunk rank directories, one CTA per block. */
+pivco_status pivco_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws,
+                               size_t ws_bytes, int32_t *status, void *stream);
+pivco_status pivco_decode_ans(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws,
+                              size_t ws_bytes, int32_t *status, void *stream);
+pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
+                                uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
+                                int32_t *status, void *stream);
+
+/* Number of kernels this library has launched in this process (host). */
+uint64_t pivco_launch_count(void);
+
 /* The static ANS tables of this library (host, synchronous): fse_h_q16[50]
  * = expected coded bits per bitmap bit in Q16 for tables t = 50..99
  * (Sec. 5.2 fse_H); class_freq[50 * 9] = frequency (out of 2^15) of one byte

@@ -33,6 +33,9 @@ _SIGS = {
     "pivco_ans_encode_blocks": [_P, _I32, _P, _P, _P, _P, _SZ, _P, _P],
     "pivco_decode_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
     "pivco_decode_blocks": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
+    "pivco_decode_plan": [_P, _P, _I32, _P, _SZ, _P, _P],
+    "pivco_decode_ans": [_P, _P, _I32, _P, _SZ, _P, _P],
+    "pivco_decode_merge": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
     "pivco_ans_tables": [_P, _P],
     "pivco_ans_encode": [_P, _P, _P, _I32, _P, _P, _P, _P, _P],
     "pivco_ans_decode": [_P, _P, _P, _I32, _P, _P, _P, _P],
@@ -42,6 +45,7 @@ _OTHER = {
     "pivco_layout_bytes": ([], _I32),
     "pivco_scan_workspace_size": ([_I32], _SZ),
     "pivco_decode_plan_bytes": ([_I32], _SZ),
+    "pivco_launch_count": ([], C.c_uint64),
 }
 
 
@@ -153,6 +157,25 @@ def decode_blocks(comp, comp_off, nblk, out, out_off, ws, status, stream=None, w
     _check(lib().pivco_decode_blocks(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
                                      ws.numel() if ws_bytes is None else ws_bytes, _ptr(status), _stream(stream)),
            "pivco_decode_blocks")
+
+
+def decode_plan(comp, comp_off, nblk, ws, status, stream=None):
+    _check(lib().pivco_decode_plan(_ptr(comp), _ptr(comp_off), nblk, _ptr(ws), ws.numel(), _ptr(status),
+                                   _stream(stream)), "pivco_decode_plan")
+
+
+def decode_ans(comp, comp_off, nblk, ws, status, stream=None):
+    _check(lib().pivco_decode_ans(_ptr(comp), _ptr(comp_off), nblk, _ptr(ws), ws.numel(), _ptr(status),
+                                  _stream(stream)), "pivco_decode_ans")
+
+
+def decode_merge(comp, comp_off, nblk, out, out_off, ws, status, stream=None):
+    _check(lib().pivco_decode_merge(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
+                                    ws.numel(), _ptr(status), _stream(stream)), "pivco_decode_merge")
+
+
+def launch_count():
+    return int(lib().pivco_launch_count())
 
 
 def ans_tables():

@@ -2,6 +2,7 @@
 // static ANS tables, and kernel launches.  No call here allocates device memory.
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "pivco_dev.cuh"
@@ -57,6 +58,9 @@ static void build_tables() {
     }
     g_tab.class_base[9] = 0;   // 256 does not fit; unused
 }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 const AnsTables &host_ans_tables() {
     std::call_once(g_tab_once, build_tables);
@@ -150,6 +154,35 @@ pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, 
     return ok_or_cuda(launch_decode(comp, comp_off, nblk, out, out_off, reinterpret_cast<uint8_t *>(ws), ws_bytes,
                                     status, S(stream)));
 }
+
+pivco_status pivco_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws, size_t ws_bytes,
+                               int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    return ok_or_cuda(launch_decode_plan(comp, comp_off, nblk, reinterpret_cast<uint8_t *>(ws), ws_bytes, status,
+                                         S(stream)));
+}
+
+pivco_status pivco_decode_ans(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws, size_t ws_bytes,
+                              int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    return ok_or_cuda(launch_ans_decode_planned(comp, comp_off, nblk, reinterpret_cast<uint8_t *>(ws), ws_bytes,
+                                                status, S(stream)));
+}
+
+pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, uint8_t *out,
+                                const uint64_t *out_off, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !out_off || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    return ok_or_cuda(launch_decode_merge(comp, comp_off, nblk, out, out_off, reinterpret_cast<uint8_t *>(ws),
+                                          ws_bytes, status, S(stream)));
+}
+
+uint64_t pivco_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 pivco_status pivco_ans_tables(int32_t *fse_h_q16, uint32_t *class_freq) {
     const AnsTables &T = host_ans_tables();

@@ -217,6 +217,7 @@ cudaError_t launch_ans_encode(const uint8_t *bm, const uint64_t *bm_off, const u
     cudaError_t e = cudaFuncSetAttribute(ans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     ans_encode_kernel<<<nbm, 32, smem, st>>>(bm, bm_off, table, bodies, body_off, body_bytes, status, host_ans_tables());
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -224,6 +225,7 @@ cudaError_t launch_ans_decode(const uint8_t *bodies, const uint64_t *body_off, c
                               const uint64_t *bm_off, int32_t *status, cudaStream_t st) {
     if (nbm <= 0) return cudaSuccess;
     ans_decode_kernel<<<nbm, 32, 0, st>>>(bodies, body_off, table, bm, bm_off, status, host_ans_tables());
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -486,6 +488,7 @@ cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, in
     cudaError_t e = launch_zero_bytes(ws, 64 + 8ull * nblk, st);
     if (e != cudaSuccess) return e;
     decode_plan_kernel<<<nblk, kPlanThreads, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -97,8 +97,10 @@ cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nbl
     if (slices < 1) slices = 1;
     if (slices > 1) {
         zero_u32_kernel<<<min(1024, div_up((long long)nblk * 256, 256)), 256, 0, st>>>(hist, (size_t)nblk * 256);
+        count_launches(1);
     }
     histogram_kernel<<<dim3(nblk, slices), kHistThreads, 0, st>>>(in, blk_off, hist, slices);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -198,6 +200,7 @@ cudaError_t launch_code_lengths(const uint32_t *hist, int nblk, int max_len, uin
                                 cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     code_lengths_kernel<<<nblk, kPmThreads, 0, st>>>(hist, max_len, lens, status);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -316,6 +319,7 @@ __global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_
                 L.n_sel = (uint8_t)nsel;
                 for (int v = 0; v < V; v++) if (!L.sel[v]) { L.body_off[v] = off; off += (L.nv[v] + 7) / 8; }
                 for (int v = 0; v < V; v++) if (L.sel[v]) { L.body_off[v] = off; off += (L.nv[v] + 7) / 8; }
+                L.body_end = off;
                 L.rec_bound = (off + 15u) & ~15u;
             }
         }
@@ -340,6 +344,7 @@ cudaError_t launch_build_layout(const uint32_t *hist, const uint8_t *lens, int n
     const AnsTables &T = host_ans_tables();
     for (int i = 0; i < 50; i++) sp.fseh_q16[i] = T.fseh_q16[i];
     build_layout_kernel<<<nblk, kLayThreads, 0, st>>>(hist, lens, sp, layout, rec_bound, status);
+    count_launches(1);
     return cudaGetLastError();
 }
 

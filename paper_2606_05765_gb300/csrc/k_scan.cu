@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint64_t *__re
 cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     zero_bytes_kernel<<<min(1024, div_up((long long)n, 256)), 256, 0, st>>>(p, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -82,7 +83,9 @@ cudaError_t launch_scan(const uint64_t *in, int n, uint64_t *out, void *ws, int3
     const int tiles = div_up(n < 1 ? 1 : n, kScanTile);
     const size_t wsb = scan_ws_bytes(n);
     zero_bytes_kernel<<<min(256, div_up((long long)wsb, 256)), 256, 0, st>>>(reinterpret_cast<uint8_t *>(ws), wsb);
+    count_launches(1);
     scan_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, out, reinterpret_cast<uint8_t *>(ws), status);
+    count_launches(1);
     return cudaGetLastError();
 }
 

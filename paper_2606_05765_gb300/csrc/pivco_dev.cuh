@@ -48,6 +48,7 @@ struct BlockLayout {
     uint32_t n;            // symbols
     uint32_t rec_bound;    // record bytes with every node raw
     uint32_t body0;        // byte offset of the first body
+    uint32_t body_end;     // byte offset just past the last body
     uint16_t n_int;        // internal nodes
     uint8_t kind;          // 0 empty, 1 constant, 2 coded
     uint8_t csym;          // kind 1 symbol
@@ -130,20 +131,23 @@ __device__ inline void build_tree_shape(const uint8_t *lens, TreeShape &ts, uint
         ts.ok = ok && K >= 2 && first == K - 1;
     }
     __syncthreads();
-    // rank of s among symbols of the same length (by value)
+    // rank of s among symbols of the same length (by value): lanes of equal
+    // length within the warp, plus the counts of that length in earlier warps
+    if (t < 128) rank_scratch[t] = 0;
+    __syncthreads();
+    int32_t rank_in_warp = 0;
     if (t < 256) {
-        int32_t r = 0;
-        const uint8_t l = lens[t];
-        if (l) {
-            for (int s = 0; s < t; s++) r += (lens[s] == l);
-        }
-        rank_scratch[t] = r;
+        const uint32_t l = lens[t];
+        const uint32_t peers = __match_any_sync(0xffffffffu, l);
+        rank_in_warp = __popc(peers & ((1u << (t & 31)) - 1u));
+        if (rank_in_warp == 0) rank_scratch[(t >> 5) * 16 + (l & 15)] = __popc(peers);
     }
     __syncthreads();
     if (t < 256) {
         const uint8_t l = lens[t];
         if (l && ts.ok) {
-            const int32_t r = rank_scratch[t];
+            int32_t r = rank_in_warp;
+            for (int w = 0; w < (t >> 5); w++) r += rank_scratch[w * 16 + l];
             sorted[ts.len_base[l] + r] = (uint8_t)t;
             codes[t] = (uint16_t)(2 * ts.a[l - 1] + r);
         } else {
@@ -185,6 +189,8 @@ __device__ inline uint64_t globaltimer_ns() {
 constexpr uint64_t kWaitLimitNs = 1000000000ull;   // bounded device waits: 1 s
 
 __host__ __device__ inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+// kernels launched by this library (reported through pivco_launch_count)
+void count_launches(int n);
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Launchers implemented in the kernel translation units.
@@ -217,6 +223,9 @@ cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, in
 cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st);
 cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                       size_t ws_bytes, int32_t *status, cudaStream_t st);
+cudaError_t launch_decode_merge(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
+                                const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
+                                cudaStream_t st);
 cudaError_t read_decode_ws_need(const uint8_t *ws, int nblk, size_t *need, cudaStream_t st);
 cudaError_t launch_decode(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
                           const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,

@@ -52,7 +52,22 @@ def edge_workload():
     return workloads.Workload("edge", np.concatenate(blocks), off, True)
 
 
+def shifting_workload():
+    """Blocks whose statistics change mid-block: a skewed stretch followed by
+    a uniform one, so chunks sized from the whole-block statistics overflow
+    the level buffers and are shortened and redone."""
+    rng = np.random.default_rng(7)
+    blocks = []
+    for n_skew, n_uni in [(60000, 20000), (100000, 60000), (5000, 120000), (200000, 1000)]:
+        skew = np.where(rng.random(n_skew) < 0.97, 0, rng.integers(1, 256, n_skew)).astype(np.uint8)
+        blocks.append(np.concatenate([skew, rng.integers(0, 256, n_uni).astype(np.uint8)]))
+    off = np.zeros(len(blocks) + 1, np.uint64)
+    off[1:] = np.cumsum([b.size for b in blocks])
+    return workloads.Workload("shifting", np.concatenate(blocks), off, True)
+
+
 WORKLOADS = {
+    "shifting": shifting_workload,
     "zipf1_256k": lambda: workloads.zipf1(n=1 << 18),
     "skew80_8x64k": lambda: workloads.skew80(nblk=8, bs=65536),
     "skew95_4x128k": lambda: workloads.skew95(nblk=4, bs=131072),
