@@ -1,115 +1,8 @@
-// Selective ANS of node bitmaps (Sec. 5.2): byte-wise static-table rANS,
-// interleaved over W states per 16 KiB segment, one warp per segment.
-//
-// Coder (per segment of sb bytes, W states, byte j -> state j mod W):
-//   decode round r: lanes i < W take byte j = rW + i; slot = x mod 2^15 picks
-//   the byte b (classes by popcount, bytes ordered by (class, value));
-//   x = f_b (x >> 15) + slot - c_b; a state below 2^16 reads the next 16-bit
-//   word; within a round words are read in lane order.
-//   encode runs the rounds backwards and pushes words so that the decoder's
-//   read order results.
-#include "lookback.cuh"
+// Selective ANS of node bitmaps (Sec. 5.2): the standalone bitmap coder /
+// decoder and the in-record ANS pass of the encoder.
+#include "ans_dev.cuh"
 
 namespace pv {
-
-// tables of one ANS table id in shared memory
-struct AnsSm {
-    uint32_t q[9];
-    uint32_t start[10];
-    uint32_t magic[9];
-    uint8_t member[256];
-    uint8_t base[10];
-    uint8_t rank[256];
-};
-
-__device__ inline void load_ans_table(AnsSm &T, const AnsTables &A, int tid, int lane_id, int nthreads) {
-    for (int i = lane_id; i < 256; i += nthreads) { T.member[i] = A.class_member[i]; T.rank[i] = A.rank_in_class[i]; }
-    if (lane_id < 9) { T.q[lane_id] = A.q[tid][lane_id]; T.magic[lane_id] = A.magic[tid][lane_id]; }
-    if (lane_id < 10) { T.start[lane_id] = A.start[tid][lane_id]; T.base[lane_id] = A.class_base[lane_id]; }
-}
-
-// ---------------------------------------------------------------------------
-// Decode one segment (one warp).  body points at the segment's states; words
-// follow.  Writes sb bytes (XORed with xr) to dst.  Returns false on a
-// malformed segment.
-// ---------------------------------------------------------------------------
-__device__ inline bool ans_decode_segment(const uint8_t *states, const uint8_t *words, uint32_t nw, uint32_t sb,
-                                          const AnsSm &T, uint8_t xr, uint8_t *dst) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t W = ans_seg_lanes(sb);
-    uint32_t x = lane < (int)W ? ld_le32(states + 4 * lane) : kAnsL;
-    bool ok = (x >= kAnsL);
-    uint32_t s1 = T.start[1], s2 = T.start[2], s3 = T.start[3], s4 = T.start[4], s5 = T.start[5], s6 = T.start[6],
-             s7 = T.start[7], s8 = T.start[8];
-    uint32_t rd = 0;
-    const uint32_t rounds = (sb + W - 1) / W;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t r = 0; r < rounds; r++) {
-        const uint32_t j = r * W + lane;
-        const bool active = lane < (int)W && j < sb;
-        uint32_t b = 0;
-        if (active) {
-            const uint32_t slot = x & (kAnsM - 1);
-            const uint32_t k = (slot >= s1) + (slot >= s2) + (slot >= s3) + (slot >= s4) + (slot >= s5) +
-                               (slot >= s6) + (slot >= s7) + (slot >= s8);
-            const uint32_t q = T.q[k], rel = slot - T.start[k];
-            const uint32_t idx = T.magic[k] ? (uint32_t)(((uint64_t)rel * T.magic[k]) >> 32) : rel;
-            b = T.member[T.base[k] + idx];
-            x = q * (x >> kAnsScale) + (rel - idx * q);
-        }
-        const bool need = active && x < kAnsL;
-        const uint32_t m = __ballot_sync(0xffffffffu, need);
-        if (need) {
-            const uint32_t pos = rd + __popc(m & lt);
-            if (pos < nw) x = (x << 16) | ((uint32_t)words[2 * pos] | ((uint32_t)words[2 * pos + 1] << 8));
-            else ok = false;
-        }
-        rd += __popc(m);
-        if (active) dst[j] = (uint8_t)(b ^ xr);
-    }
-    if (lane < (int)W && x != kAnsL) ok = false;
-    if (rd != nw) ok = false;
-    return __all_sync(0xffffffffu, ok);
-}
-
-// ---------------------------------------------------------------------------
-// Encode one segment (one warp).  src: sb raw bytes (XORed with xr before
-// coding).  Words are staged backwards in stage[0 .. cap).  Returns the word
-// count; final states in x (lane < W).
-// ---------------------------------------------------------------------------
-__device__ inline uint32_t ans_encode_segment(const uint8_t *src, uint32_t sb, const AnsSm &T, uint8_t xr,
-                                              uint16_t *stage, uint32_t cap, uint32_t &x_out) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t W = ans_seg_lanes(sb);
-    uint32_t x = kAnsL;
-    uint32_t cnt = 0;
-    const uint32_t rounds = (sb + W - 1) / W;
-    const uint32_t gt = ~((2u << lane) - 1u);
-    for (int r = (int)rounds - 1; r >= 0; r--) {
-        const uint32_t j = (uint32_t)r * W + lane;
-        const bool active = lane < (int)W && j < sb;
-        uint32_t f = 1, c = 0;
-        bool emit = false;
-        if (active) {
-            const uint32_t b = (uint32_t)(src[j] ^ xr);
-            const uint32_t k = __popc(b);
-            f = T.q[k];
-            c = T.start[k] + T.rank[b] * f;
-            emit = (uint64_t)x >= ((uint64_t)f << 17);
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, emit);
-        if (emit) {
-            const uint32_t pos = cnt + __popc(m & gt);
-            if (pos < cap) stage[cap - 1 - pos] = (uint16_t)(x & 0xFFFF);
-            x >>= 16;
-        }
-        cnt += __popc(m);
-        if (active) x = ((x / f) << kAnsScale) + (x % f) + c;
-    }
-    x_out = x;
-    return cnt;
-}
-
 // ---------------------------------------------------------------------------
 // Standalone bitmap ANS (one warp per bitmap; segments sequential).
 // ---------------------------------------------------------------------------
@@ -161,23 +54,6 @@ __global__ void __launch_bounds__(32) ans_encode_kernel(const uint8_t *__restric
 }
 
 // locate segment s of an ANS body: returns byte offset of its states, its word count
-__device__ inline bool ans_segment_at(const uint8_t *body, uint64_t body_len, uint32_t nbytes, uint32_t s,
-                                      uint64_t &st_pos, uint32_t &nw) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t S = ans_seg_count(nbytes);
-    if (4ull * S > body_len) return false;
-    uint64_t acc = 0;
-    for (uint32_t j = lane; j < s; j += 32) {
-        const uint32_t sbj = min(kAnsSeg, nbytes - j * kAnsSeg);
-        acc += 4ull * ans_seg_lanes(sbj) + 2ull * ld_le32(body + 4 * j);
-    }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    st_pos = 4ull * S + acc;
-    nw = ld_le32(body + 4 * s);
-    const uint32_t sb = min(kAnsSeg, nbytes - s * kAnsSeg);
-    return st_pos + 4ull * ans_seg_lanes(sb) + 2ull * nw <= body_len;
-}
-
 __global__ void __launch_bounds__(32) ans_decode_kernel(const uint8_t *__restrict__ bodies, const uint64_t *__restrict__ body_off,
                                                         const uint8_t *__restrict__ table, uint8_t *__restrict__ bm,
                                                         const uint64_t *__restrict__ bm_off, int32_t *__restrict__ status,
@@ -346,234 +222,5 @@ cudaError_t launch_ans_encode_blocks(const BlockLayout *layout, int nblk, uint8_
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Decode plan.  Workspace layout:
-//   [0, 64)            header: u64 total scratch, u32 total segments, u32 ticket
-//   [64, ..)           u64 look-back states[nblk]
-//                      u64 blk_scratch[nblk]   (byte offset in the scratch area)
-//                      u32 blk_seg[nblk]       (first descriptor of the block)
-//   fixed part end F   descriptors (16 B): u32 block, u16 node, u16 seg,
-//                                          u32 body offset, u32 node scratch offset
-//   align256(F + 16 * total_segs): scratch (ANS-decoded bitmaps)
-// Per ANS node the scratch holds ceil(n_v/8) bytes rounded up to 16 plus 16
-// bytes of slack for aligned word reads.
-// ---------------------------------------------------------------------------
-struct DecDesc {
-    uint32_t block;
-    uint16_t node;
-    uint16_t seg;
-    uint32_t body_off;
-    uint32_t scratch_off;
-};
-
-__device__ inline uint32_t scratch_stride(uint32_t raw) { return ((raw + 15u) & ~15u) + 16u; }
-
-// parse the parts of a record the plan needs; returns false if malformed.
-// Fills body offsets for every node (raw region, then the selected region).
-__device__ inline bool parse_bodies(const uint8_t *rec, uint64_t avail, uint32_t &V, uint32_t *nv, uint8_t *marker,
-                                    uint32_t *body_off, uint32_t *body_len) {
-    if (avail < kHdr) return false;
-    const uint32_t rb = ld_le32(rec), kind = rec[10];
-    V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
-    if (rec[12] != 'P' || rec[13] != 'V' || rec[14] != 'C' || rec[15] != '1') return false;
-    if (rb < kHdr || (rb & 15u) || rb > avail) return false;
-    if (kind != 2) { V = 0; return kind <= 1; }
-    if (V < 1 || V > 255 || rb < kNvOff + 5 * V) return false;
-    uint32_t nsel = 0;
-    for (uint32_t v = 0; v < V; v++) {
-        nv[v] = ld_le32(rec + kNvOff + 4 * v);
-        marker[v] = rec[kNvOff + 4 * V + v];
-        if (marker[v]) {
-            nsel++;
-            if (marker[v] != kMarkRawSel && ((marker[v] & 0x7F) < 1 || (marker[v] & 0x7F) > 50)) return false;
-        }
-    }
-    uint64_t off = (kNvOff + 5ull * V + 3) & ~3ull;
-    const uint64_t alen_off = off;
-    off += 4ull * nsel;
-    if (off > rb) return false;
-    for (uint32_t v = 0; v < V; v++)
-        if (!marker[v]) { body_off[v] = (uint32_t)off; body_len[v] = (nv[v] + 7) / 8; off += body_len[v]; }
-    uint32_t k = 0;
-    for (uint32_t v = 0; v < V; v++)
-        if (marker[v]) {
-            body_off[v] = (uint32_t)off;
-            body_len[v] = ld_le32(rec + alen_off + 4 * k++);
-            off += body_len[v];
-            if (off > rb) return false;
-        }
-    if (off > rb || ((off + 15) & ~15ull) != rb) return false;
-    return true;
-}
-
-constexpr int kPlanThreads = 32;
-
-__global__ void __launch_bounds__(kPlanThreads) decode_plan_kernel(const uint8_t *__restrict__ comp,
-                                                                   const uint64_t *__restrict__ comp_off, int nblk,
-                                                                   uint8_t *__restrict__ ws, uint64_t ws_bytes,
-                                                                   int32_t *__restrict__ status) {
-    __shared__ uint32_t nv[256], body_off[256], body_len[256];
-    __shared__ uint8_t marker[256];
-    __shared__ int s_tile;
-    __shared__ uint64_t s_excl;
-    uint64_t *hdr64 = reinterpret_cast<uint64_t *>(ws);
-    uint32_t *hdr32 = reinterpret_cast<uint32_t *>(ws);
-    uint64_t *states = reinterpret_cast<uint64_t *>(ws + 64);
-    uint64_t *blk_scratch = states + nblk;
-    uint32_t *blk_seg = reinterpret_cast<uint32_t *>(blk_scratch + nblk);
-    DecDesc *desc = reinterpret_cast<DecDesc *>(ws + decode_ws_fixed_bytes(nblk));
-    const int lane = threadIdx.x;
-    if (lane == 0) s_tile = (int)atomicAdd(&hdr32[3], 1u);
-    __syncwarp();
-    const int b = s_tile;
-    uint32_t V = 0;
-    bool ok = false;
-    if (lane == 0) ok = parse_bodies(comp + comp_off[b], comp_off[b + 1] - comp_off[b], V, nv, marker, body_off, body_len);
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    V = __shfl_sync(0xffffffffu, V, 0);
-    __syncwarp();
-    uint64_t bytes = 0;
-    uint32_t segs = 0;
-    if (ok) {
-        for (uint32_t v = lane; v < V; v += 32)
-            if (marker[v] && marker[v] != kMarkRawSel) {
-                const uint32_t raw = (nv[v] + 7) / 8;
-                bytes += scratch_stride(raw);
-                segs += ans_seg_count(raw);
-            }
-        for (int o = 16; o; o >>= 1) {
-            bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-            segs += __shfl_xor_sync(0xffffffffu, segs, o);
-        }
-    }
-    // packed (bytes: 40 bits, segments: 22 bits)
-    if (lane == 0) {
-        int to = 0;
-        s_excl = lookback_exclusive(states, b, (bytes << 22) | segs, &to);
-        const uint64_t ex_bytes = s_excl >> 22, ex_segs = s_excl & ((1u << 22) - 1);
-        blk_scratch[b] = ex_bytes;
-        blk_seg[b] = (uint32_t)ex_segs;
-        status[b] = !ok ? PIVCO_ERR_CORRUPT : (to ? PIVCO_ERR_TIMEOUT : PIVCO_OK);
-        if (b == nblk - 1) {
-            hdr64[0] = ex_bytes + bytes;
-            hdr32[2] = (uint32_t)(ex_segs + segs);
-        }
-    }
-    __syncwarp();
-    if (ok && V) {
-        // descriptors in node order (one lane walks the nodes)
-        if (lane == 0) {
-            uint32_t k = (uint32_t)(s_excl & ((1u << 22) - 1)), soff = 0;
-            const uint64_t fixed = decode_ws_fixed_bytes(nblk);
-            for (uint32_t v = 0; v < V; v++)
-                if (marker[v] && marker[v] != kMarkRawSel) {
-                    const uint32_t raw = (nv[v] + 7) / 8, S = ans_seg_count(raw);
-                    for (uint32_t s = 0; s < S; s++, k++) {
-                        if (fixed + 16ull * (k + 1) <= ws_bytes) {
-                            DecDesc d;
-                            d.block = (uint32_t)b; d.node = (uint16_t)v; d.seg = (uint16_t)s;
-                            d.body_off = body_off[v]; d.scratch_off = soff;
-                            desc[k] = d;
-                        }
-                    }
-                    soff += scratch_stride(raw);
-                }
-        }
-    }
-}
-
-cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
-                               int32_t *status, cudaStream_t st) {
-    if (nblk <= 0) return cudaSuccess;
-    cudaError_t e = launch_zero_bytes(ws, 64 + 8ull * nblk, st);
-    if (e != cudaSuccess) return e;
-    decode_plan_kernel<<<nblk, kPlanThreads, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t read_decode_ws_need(const uint8_t *ws, int nblk, size_t *need, cudaStream_t st) {
-    uint64_t h[2];
-    cudaError_t e = cudaMemcpyAsync(h, ws, 16, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    const uint64_t total_scratch = h[0];
-    const uint32_t segs = (uint32_t)(h[1] & 0xFFFFFFFFu);
-    const size_t dstart = (decode_ws_fixed_bytes(nblk) + 16ull * segs + 255) & ~(size_t)255;
-    *need = dstart + total_scratch;
-    return cudaSuccess;
-}
-
-// ---------------------------------------------------------------------------
-// ANS decode of every planned segment: persistent grid, one warp per segment.
-// ---------------------------------------------------------------------------
-constexpr int kAnsDecWarps = 4;
-
-__global__ void __launch_bounds__(32 * kAnsDecWarps) ans_decode_planned_kernel(const uint8_t *__restrict__ comp,
-                                                                               const uint64_t *__restrict__ comp_off,
-                                                                               int nblk, uint8_t *__restrict__ ws,
-                                                                               uint64_t ws_bytes,
-                                                                               int32_t *__restrict__ status,
-                                                                               const __grid_constant__ AnsTables A) {
-    __shared__ AnsSm T[kAnsDecWarps];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t total = reinterpret_cast<const uint32_t *>(ws)[2];
-    const uint64_t *blk_scratch = reinterpret_cast<const uint64_t *>(ws + 64) + nblk;
-    const DecDesc *desc = reinterpret_cast<const DecDesc *>(ws + decode_ws_fixed_bytes(nblk));
-    const uint64_t dstart = (decode_ws_fixed_bytes(nblk) + 16ull * total + 255) & ~255ull;
-    const uint64_t scratch_cap = ws_bytes > dstart ? ws_bytes - dstart : 0;
-    uint8_t *scratch = ws + dstart;
-    const uint64_t fixed_need = decode_ws_fixed_bytes(nblk) + 16ull * total;
-    for (uint32_t g = blockIdx.x * kAnsDecWarps + w; g < total; g += gridDim.x * kAnsDecWarps) {
-        if (fixed_need > ws_bytes) break;
-        const DecDesc d = desc[g];
-        const int b = (int)d.block;
-        if (status[b] != PIVCO_OK) continue;
-        const uint8_t *rec = comp + comp_off[b];
-        const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
-        const uint8_t mk = rec[kNvOff + 4 * V + d.node];
-        const uint32_t nvv = ld_le32(rec + kNvOff + 4 * d.node);
-        const uint32_t raw = (nvv + 7) / 8;
-        // body length from the alen table: index of this node among selected nodes
-        uint32_t k = 0;
-        for (uint32_t v = lane; v < d.node; v += 32) k += rec[kNvOff + 4 * V + v] != 0;
-        for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
-        const uint32_t alen_off = (kNvOff + 5u * V + 3u) & ~3u;
-        const uint32_t blen = ld_le32(rec + alen_off + 4 * k);
-        const uint64_t sdst = blk_scratch[b] + d.scratch_off;
-        bool ok = sdst + scratch_stride(raw) <= scratch_cap;
-        uint64_t sp = 0;
-        uint32_t nw = 0;
-        if (ok) ok = ans_segment_at(rec + d.body_off, blen, raw, d.seg, sp, nw);
-        if (ok) {
-            load_ans_table(T[w], A, (mk & 0x7F) - 1, lane, 32);
-            __syncwarp();
-            const uint32_t sb = min(kAnsSeg, raw - d.seg * kAnsSeg), W = ans_seg_lanes(sb);
-            const uint8_t *body = rec + d.body_off;
-            ok = ans_decode_segment(body + sp, body + sp + 4 * W, nw, sb, T[w], (mk & 0x80) ? 0xFF : 0,
-                                    scratch + sdst + (size_t)d.seg * kAnsSeg);
-            // the last segment also checks that the body is fully consumed
-            if (ok && d.seg + 1 == ans_seg_count(raw) && sp + 4ull * W + 2ull * nw != blen) ok = false;
-            if (d.seg + 1 == ans_seg_count(raw) && lane < 16) {
-                // zero the slack after the bitmap (aligned reads past its end)
-                const uint64_t e = sdst + raw;
-                scratch[e + lane] = 0;
-            }
-        }
-        if (!ok && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
-        __syncwarp();
-    }
-}
-
-cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
-                                      size_t ws_bytes, int32_t *status, cudaStream_t st) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    ans_decode_planned_kernel<<<sms * 8, 32 * kAnsDecWarps, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status,
-                                                                     host_ans_tables());
-    return cudaGetLastError();
-}
 
 }  // namespace pv

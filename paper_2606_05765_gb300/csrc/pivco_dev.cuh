@@ -213,11 +213,53 @@ cudaError_t launch_ans_encode(const uint8_t *bm, const uint64_t *bm_off, const u
                               cudaStream_t st);
 cudaError_t launch_ans_decode(const uint8_t *bodies, const uint64_t *body_off, const uint8_t *table, int nbm,
                               uint8_t *bm, const uint64_t *bm_off, int32_t *status, cudaStream_t st);
-// decode workspace: header, look-back states, per-block offsets (see k_ans.cu)
+// ---------------------------------------------------------------------------
+// Decode workspace (written by the decode plan, read by the later passes):
+//   header (64 B): u64 scratch bytes @0, u32 ANS segments @8, u32 ticket @12,
+//                  u64 directory+cursor bytes @16, u32 tiles @24
+//   per block: u64 look-back states A[nblk], B[nblk]; u64 scratch offset[nblk];
+//              u64 directory offset[nblk]; u32 first segment[nblk];
+//              u32 first tile[nblk]; u32 tile length[nblk]; u32 tiles[nblk]
+//   then: ANS segment descriptors (16 B), tile descriptors (8 B: block, index),
+//         rank directories and tile-boundary cursors, ANS-decoded bitmaps.
+// ---------------------------------------------------------------------------
+struct DecWs {
+    uint64_t *states_a, *states_b, *blk_scratch, *blk_dir;
+    uint32_t *blk_seg, *blk_tile, *blk_T, *blk_ntile;
+};
 __host__ __device__ inline size_t decode_ws_fixed_bytes(int nblk) {
-    const size_t f = 64 + 8ull * nblk + 8ull * nblk + 4ull * nblk;
+    const size_t f = 64 + 32ull * nblk + 16ull * nblk;
     return (f + 255) & ~(size_t)255;
 }
+__host__ __device__ inline DecWs dec_ws(uint8_t *ws, int nblk) {
+    DecWs w;
+    w.states_a = reinterpret_cast<uint64_t *>(ws + 64);
+    w.states_b = w.states_a + nblk;
+    w.blk_scratch = w.states_b + nblk;
+    w.blk_dir = w.blk_scratch + nblk;
+    w.blk_seg = reinterpret_cast<uint32_t *>(w.blk_dir + nblk);
+    w.blk_tile = w.blk_seg + nblk;
+    w.blk_T = w.blk_tile + nblk;
+    w.blk_ntile = w.blk_T + nblk;
+    return w;
+}
+struct DecRegions {
+    size_t seg_desc, tiles, dir, scratch, need;
+};
+__host__ __device__ inline DecRegions dec_regions(int nblk, const uint8_t *ws_header) {
+    const uint64_t scratch = *reinterpret_cast<const uint64_t *>(ws_header);
+    const uint32_t segs = *reinterpret_cast<const uint32_t *>(ws_header + 8);
+    const uint64_t dir = *reinterpret_cast<const uint64_t *>(ws_header + 16);
+    const uint32_t tiles = *reinterpret_cast<const uint32_t *>(ws_header + 24);
+    DecRegions r;
+    r.seg_desc = decode_ws_fixed_bytes(nblk);
+    r.tiles = (r.seg_desc + 16ull * segs + 15) & ~(size_t)15;
+    r.dir = (r.tiles + 8ull * tiles + 255) & ~(size_t)255;
+    r.scratch = (r.dir + dir + 255) & ~(size_t)255;
+    r.need = r.scratch + scratch;
+    return r;
+}
+constexpr int kDirBits = 256;    // rank directory granularity (bits per superblock)
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                size_t ws_bytes, int32_t *status, cudaStream_t st);
 cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st);
