@@ -207,95 +207,135 @@ def main(argv=None):
     nblk = w.nblk
     data = torch.from_numpy(w.data).to(dev)
     blk_off = torch.from_numpy(w.blk_off.astype(np.int64)).to(dev)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)          # everything runs here (graphs need a capturable stream)
+    torch.cuda.synchronize()
 
-    enc = P.Encoder(nblk, P.params(ans=w.ans), dev)
-    total = enc.plan(data, blk_off)
-    enc.ensure(total)
-    res = enc.run(data, blk_off, replan=False)
-    dec = P.Decoder(nblk, dev)
-    dec.prepare(res.comp, res.off)
-    out = torch.empty(raw, dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    with torch.cuda.stream(stream):
+        enc = P.Encoder(nblk, P.params(ans=w.ans), dev)
+        enc.ensure(enc.plan(data, blk_off, stream))
+        res = enc.run(data, blk_off, stream, replan=False)
+        dec = P.Decoder(nblk, dev)
+        P.set_tuning(16384, 256, 0)        # the largest workspace any autotuner candidate needs
+        dec.prepare(res.comp, res.off, stream)
+        P.set_tuning()
+        out = torch.empty(raw, dtype=torch.uint8, device=dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+        # pick the decode launch tuning for this batch (does not change the bytes)
+        tuned, tuned_ms = P.autotune_decode(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status, reps=2,
+                                            stream=stream)
+        dec.prepare(res.comp, res.off, stream)
+        # batched path: the encode launch sequence and the persistent decode, each a CUDA graph
+        n0 = P.launch_count()
+        g_enc = P.Graph(stream)
+        with g_enc:
+            enc.run(data, blk_off, stream)
+        n_enc_graph = P.launch_count() - n0
+        n0 = P.launch_count()
+        g_dec = P.Graph(stream)
+        with g_dec:
+            P.decode_batched(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status, stream)
+        n_dec_graph = P.launch_count() - n0
+    stream.synchronize()
 
-    E = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
+    E = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
 
-    def step(record):
+    def plain_step():
         flush.zero_()
         E[0].record(stream)
-        enc.run(data, blk_off)
+        enc.run(data, blk_off, stream)
         E[1].record(stream)
         flush.zero_()
         E[2].record(stream)
-        P.decode_plan(res.comp, res.off, nblk, dec.ws, dec.status)
-        P.decode_ans(res.comp, res.off, nblk, dec.ws, dec.status)
+        P.decode_plan(res.comp, res.off, nblk, dec.ws, dec.status, stream)
+        P.decode_ans(res.comp, res.off, nblk, dec.ws, dec.status, stream)
         E[3].record(stream)
-        P.decode_merge(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status)
+        P.decode_merge(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status, stream)
         E[4].record(stream)
-        if record is not None:
-            record.append(E)
 
-    # per-kernel timing of the encode kernel inside the step (events around it)
-    Ek = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-
-    for _ in range(args.warmup):
-        step(None)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    n_launch0 = P.launch_count()
-    t_enc, t_dec, t_merge = [], [], []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            step(None)
-            E[4].synchronize()
-            t_enc.append(E[0].elapsed_time(E[1]))
-            t_dec.append(E[2].elapsed_time(E[4]))
-            t_merge.append(E[3].elapsed_time(E[4]))
-    torch.cuda.synchronize()
-    n_launch = P.launch_count() - n_launch0
-    # encode kernel alone (same stream, outside the step loop, statistics already on device)
-    t_enck = []
-    for _ in range(max(3, args.steps // 4)):
+    def batched_step():
         flush.zero_()
-        Ek[0].record(stream)
-        P.encode_blocks(data, blk_off, nblk, enc.layout, enc.comp, enc.off, enc.rec_bytes, enc.status)
-        Ek[1].record(stream)
-        Ek[1].synchronize()
-        t_enck.append(Ek[0].elapsed_time(Ek[1]))
-    if w.ans:
-        # restore the final records (the plain encode left ANS candidates raw)
-        enc.run(data, blk_off)
+        E[0].record(stream)
+        g_enc.launch(stream)
+        E[1].record(stream)
+        flush.zero_()
+        E[2].record(stream)
+        g_dec.launch(stream)
+        E[4].record(stream)
+
+    def timed(step_fn, steps, clk=None):
+        t_enc, t_dec, t_mid = [], [], []
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                step_fn()
+                E[4].synchronize()
+                t_enc.append(E[0].elapsed_time(E[1]))
+                t_dec.append(E[2].elapsed_time(E[4]))
+                t_mid.append(E[3].elapsed_time(E[4]) if step_fn is plain_step else t_dec[-1])
+        return t_enc, t_dec, t_mid
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plain_step()
+            batched_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    # correctness of the timed work
-    st_e = enc.status.cpu().numpy()
-    st_d = dec.status.cpu().numpy()
-    ok = (not st_e.any()) and (not st_d.any()) and bool(torch.equal(out, data))
-    rec_bytes = int(enc.rec_bytes.sum().item())
-    step_ms = [a + b for a, b in zip(t_enc, t_dec)]
-    tot_ms = sum(step_ms)
+    # headline: the batched path, with clocks sampled during the timed region
+    n_launch0 = P.launch_count()
+    with ClockSampler(local) as clk:
+        b_enc, b_dec, _ = timed(batched_step, args.steps)
+    n_launch = P.launch_count() - n_launch0 + args.steps * (n_enc_graph + n_dec_graph)
+    torch.cuda.synchronize()
+    ok_b = (not enc.status.cpu().numpy().any()) and (not dec.status.cpu().numpy().any()) and bool(torch.equal(out, data))
+    # the plain path (one launch per step of the pipeline) on the same batch
+    out.zero_()
+    p_steps = max(3, args.steps // 2)
+    p_enc, p_dec, p_merge = timed(plain_step, p_steps)
+    torch.cuda.synchronize()
+    ok_p = (not enc.status.cpu().numpy().any()) and (not dec.status.cpu().numpy().any()) and bool(torch.equal(out, data))
+    # the encode kernel alone, for its roofline (statistics already on the device)
+    Ek = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    t_enck = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.steps // 4)):
+            flush.zero_()
+            Ek[0].record(stream)
+            P.encode_blocks(data, blk_off, nblk, enc.layout, enc.comp, enc.off, enc.rec_bytes, enc.status, stream)
+            Ek[1].record(stream)
+            Ek[1].synchronize()
+            t_enck.append(Ek[0].elapsed_time(Ek[1]))
+        enc.run(data, blk_off, stream)          # the final records (with ANS) again
+    torch.cuda.synchronize()
     if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * raw * len(step_ms) / (tot_ms / 1e3) / 1e9
+        dist.barrier()
+    torch.cuda.synchronize()
+    ok = ok_b and ok_p and not enc.status.cpu().numpy().any()
+    rec_bytes = int(enc.rec_bytes.sum().item())
 
-    # roofline of the dominant kernel (largest share of the step)
+    def agg(te, td):
+        tot = sum(a + b for a, b in zip(te, td))
+        if world > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return world * raw * len(te) / (tot / 1e3) / 1e9, tot / len(te)
+
+    value, ms_step = agg(b_enc, b_dec)
+    plain_value, plain_ms = agg(p_enc, p_dec)
+    step_ms = [a + b for a, b in zip(b_enc, b_dec)]
+
+    # roofline of the dominant kernel of the headline (batched) step
     peak, peak_kind = measured_peaks()
-    merge_ms = statistics.mean(t_merge)
-    enck_ms = statistics.mean(t_enck)
     kernels = {
-        "decode_merge": {"ms": merge_ms, "bytes": rec_bytes + raw},
-        "encode_blocks": {"ms": enck_ms, "bytes": raw + rec_bytes},
+        "decode_batch_kernel": {"ms": statistics.mean(b_dec), "bytes": rec_bytes + raw},
+        "encode_kernel": {"ms": statistics.mean(t_enck), "bytes": raw + rec_bytes},
+        "decode_merge (plain)": {"ms": statistics.mean(p_merge), "bytes": rec_bytes + raw},
     }
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
     for k in kernels:
         kernels[k]["gbs"] = kernels[k]["bytes"] / (kernels[k]["ms"] / 1e3) / 1e9
         kernels[k]["frac"] = kernels[k]["gbs"] / peak
+    dom = max(["decode_batch_kernel", "encode_kernel"], key=lambda k: kernels[k]["ms"])
     ach = kernels[dom]["gbs"]
 
     # end to end through the public API with pinned host buffers
@@ -306,23 +346,23 @@ def main(argv=None):
         h_out = torch.empty(raw, dtype=torch.uint8).pin_memory()
         d_in = torch.empty_like(data)
         d_comp = torch.empty_like(enc.comp)
-        for i in range(args.e2e_steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            d_in.copy_(h_in, non_blocking=True)
-            enc.run(d_in, blk_off)
-            h_comp.copy_(enc.comp, non_blocking=True)
-            d_comp.copy_(h_comp, non_blocking=True)
-            P.decode_blocks(d_comp, enc.off, nblk, out, blk_off, dec.ws, dec.status)
-            h_out.copy_(out, non_blocking=True)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            if i == 0:
-                e2e_t = []
-            else:
-                e2e_t.append(dt)
-        assert torch.equal(h_out, h_in)
-        e2e = {"value": raw / statistics.mean(e2e_t) / 1e9 * world, "unit": "GB/s",
+        e2e_t = []
+        with torch.cuda.stream(stream):
+            for i in range(args.e2e_steps + 1):
+                stream.synchronize()
+                t0 = time.perf_counter()
+                d_in.copy_(h_in, non_blocking=True)
+                enc.run(d_in, blk_off, stream)
+                h_comp.copy_(enc.comp, non_blocking=True)
+                d_comp.copy_(h_comp, non_blocking=True)
+                P.decode_batched(d_comp, enc.off, nblk, out, blk_off, dec.ws, dec.status, stream)
+                h_out.copy_(out, non_blocking=True)
+                stream.synchronize()
+                if i:
+                    e2e_t.append(time.perf_counter() - t0)
+        ok = ok and (not enc.status.cpu().numpy().any()) and (not dec.status.cpu().numpy().any()) \
+            and bool(torch.equal(h_out, h_in))
+        e2e = {"value": round(raw / statistics.mean(e2e_t) / 1e9 * world, 3), "unit": "GB/s",
                "h2d_bytes_per_step": raw + enc.comp.numel(), "d2h_bytes_per_step": enc.comp.numel() + raw}
 
     cpu = None
@@ -331,24 +371,29 @@ def main(argv=None):
 
     if rank == 0:
         clocks = clk.summary()
+        r4 = lambda x: round(x, 4)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(tot_ms / len(step_ms), 4), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": r4(ms_step), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload][1], "blocks": nblk,
-                       "raw_bytes_per_gpu": raw, "compressed_bytes": rec_bytes, "ratio": round(raw / rec_bytes, 4),
+                       "raw_bytes_per_gpu": raw, "compressed_bytes": rec_bytes, "ratio": r4(raw / rec_bytes),
                        "l2": "L2 flushed (256 MiB write) before each leg; inputs 256 MiB > 129 MB L2",
-                       "path": "plain (one launch sequence per batch)", "parallelism": "blocks sharded per GPU"},
-            "encode_gbs": round(raw / (statistics.mean(t_enc) / 1e3) / 1e9, 3),
-            "decode_gbs": round(raw / (statistics.mean(t_dec) / 1e3) / 1e9, 3),
-            "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
-            "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
-            "batched": None,
+                       "path": "batched: encode launch sequence and persistent work-queue decode, each one CUDA graph",
+                       "tuning": tuned.as_dict(), "parallelism": "blocks sharded per GPU"},
+            "encode_gbs": round(raw / (statistics.mean(b_enc) / 1e3) / 1e9, 3),
+            "decode_gbs": round(raw / (statistics.mean(b_dec) / 1e3) / 1e9, 3),
+            "p50_ms": r4(float(np.percentile(step_ms, 50))), "p99_ms": r4(float(np.percentile(step_ms, 99))),
+            "batched": {"value": round(value, 3), "decode_gbs": round(raw / (statistics.mean(b_dec) / 1e3) / 1e9, 3)},
+            "plain": {"value": round(plain_value, 3), "ms_per_step": r4(plain_ms),
+                      "encode_gbs": round(raw / (statistics.mean(p_enc) / 1e3) / 1e9, 3),
+                      "decode_gbs": round(raw / (statistics.mean(p_dec) / 1e3) / 1e9, 3)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": peak,
-                         "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
-                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                         "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()}},
+                         "unit": "GB/s", "frac": r4(ach / peak), "traffic": None,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                         "kernels": {k: {kk: r4(vv) for kk, vv in v.items()} for k, v in kernels.items()}},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks, "verified": ok,
+            "checks": {"batched": ok_b, "plain": ok_p},
         }
         print(json.dumps(line))
     if world > 1:

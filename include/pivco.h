@@ -174,6 +174,54 @@ pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
 /* Number of kernels this library has launched in this process (host). */
 uint64_t pivco_launch_count(void);
 
+/* ---- Batching (not in the paper: the GPU scheduling of many blocks) ----
+ * pivco_decode_batched decodes the same records as pivco_decode_blocks (same
+ * arguments, same workspace size, identical output) with one persistent
+ * launch whose work queue is keyed by (block, stage): record plans, ANS
+ * segments, rank directories, root tiles.  Each item waits (bounded, 1 s)
+ * only on items earlier in the queue; an expired wait marks the block
+ * PIVCO_ERR_TIMEOUT. */
+pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
+                                  uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
+                                  int32_t *status, void *stream);
+
+/* Launch tuning of the decode (process-wide).  None of it changes any output.
+ * tile_max: longest root tile in symbols (a multiple of 128, 128..65536);
+ * dir_bits: rank-directory granularity in bits (a multiple of 32, 32..1024);
+ * ctas_per_sm: persistent CTAs per SM (0 = as many as fit, at most 32). */
+typedef struct pivco_tuning {
+    int32_t tile_max;
+    int32_t dir_bits;
+    int32_t ctas_per_sm;
+    int32_t reserved;
+} pivco_tuning;
+pivco_status pivco_get_tuning(pivco_tuning *t);
+pivco_status pivco_set_tuning(const pivco_tuning *t);
+
+/* Autotuner (synchronous): times pivco_decode_batched on these records under
+ * a grid of tunings (tile_max x dir_bits x ctas_per_sm), `reps` launches each,
+ * keeps and returns the fastest (*best_ms = its mean time per launch).  The
+ * decoded bytes are the same under every tuning.  A tuning whose workspace
+ * need (pivco_decode_workspace_size under that tuning) exceeds ws_bytes, or
+ * that leaves any status[b] != PIVCO_OK, is never chosen; if none qualifies
+ * the tuning is left unchanged and PIVCO_ERR_CAPACITY is returned.  The
+ * workspace need depends on the tuning: after changing it, size the
+ * workspace again before decoding. */
+pivco_status pivco_autotune_decode(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
+                                   uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
+                                   int32_t *status, int32_t reps, void *stream, pivco_tuning *best,
+                                   float *best_ms);
+
+/* CUDA-graph capture of any sequence of the asynchronous calls above on
+ * `stream` (not the legacy stream): pivco_graph_begin, then the calls, then
+ * pivco_graph_end returns an instantiated graph; pivco_graph_launch replays it
+ * (same pointers, same sizes); pivco_graph_destroy frees it (host). */
+typedef struct pivco_graph pivco_graph;
+pivco_status pivco_graph_begin(void *stream);
+pivco_status pivco_graph_end(void *stream, pivco_graph **graph);
+pivco_status pivco_graph_launch(pivco_graph *graph, void *stream);
+pivco_status pivco_graph_destroy(pivco_graph *graph);
+
 /* The static ANS tables of this library (host, synchronous): fse_h_q16[50]
  * = expected coded bits per bitmap bit in Q16 for tables t = 50..99
  * (Sec. 5.2 fse_H); class_freq[50 * 9] = frequency (out of 2^15) of one byte

@@ -39,6 +39,14 @@ _SIGS = {
     "pivco_ans_tables": [_P, _P],
     "pivco_ans_encode": [_P, _P, _P, _I32, _P, _P, _P, _P, _P],
     "pivco_ans_decode": [_P, _P, _P, _I32, _P, _P, _P, _P],
+    "pivco_decode_batched": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
+    "pivco_get_tuning": [_P],
+    "pivco_set_tuning": [_P],
+    "pivco_autotune_decode": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _I32, _P, _P, _P],
+    "pivco_graph_begin": [_P],
+    "pivco_graph_end": [_P, _P],
+    "pivco_graph_launch": [_P, _P],
+    "pivco_graph_destroy": [_P],
 }
 _OTHER = {
     "pivco_version": ([], C.c_char_p),
@@ -178,6 +186,69 @@ def launch_count():
     return int(lib().pivco_launch_count())
 
 
+# ------------------------------------------------------------- batching ----
+class Tuning(C.Structure):
+    """struct pivco_tuning: longest root tile, rank-directory granularity,
+    persistent CTAs per SM.  Never changes any output."""
+    _fields_ = [("tile_max", C.c_int32), ("dir_bits", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {"tile_max": self.tile_max, "dir_bits": self.dir_bits, "ctas_per_sm": self.ctas_per_sm}
+
+
+def decode_batched(comp, comp_off, nblk, out, out_off, ws, status, stream=None):
+    _check(lib().pivco_decode_batched(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
+                                      ws.numel(), _ptr(status), _stream(stream)), "pivco_decode_batched")
+
+
+def get_tuning():
+    t = Tuning()
+    _check(lib().pivco_get_tuning(C.byref(t)), "pivco_get_tuning")
+    return t
+
+
+def set_tuning(tile_max=65536, dir_bits=256, ctas_per_sm=0):
+    t = Tuning(tile_max, dir_bits, ctas_per_sm, 0)
+    _check(lib().pivco_set_tuning(C.byref(t)), "pivco_set_tuning")
+
+
+def autotune_decode(comp, comp_off, nblk, out, out_off, ws, status, reps=3, stream=None):
+    """Picks the fastest tuning for these records (synchronous); returns (Tuning, ms)."""
+    best = Tuning()
+    ms = C.c_float(0)
+    _check(lib().pivco_autotune_decode(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
+                                       ws.numel(), _ptr(status), reps, _stream(stream), C.byref(best), C.byref(ms)),
+           "pivco_autotune_decode")
+    return best, ms.value
+
+
+class Graph:
+    """A captured sequence of library calls (CUDA graph), replayed with launch()."""
+
+    def __init__(self, stream):
+        self.stream = stream
+        self.handle = C.c_void_p()
+
+    def __enter__(self):
+        _check(lib().pivco_graph_begin(_stream(self.stream)), "pivco_graph_begin")
+        return self
+
+    def __exit__(self, exc_type, exc, tb):
+        rc = lib().pivco_graph_end(_stream(self.stream), C.byref(self.handle))
+        if exc_type is None:
+            _check(rc, "pivco_graph_end")
+        return False
+
+    def launch(self, stream=None):
+        _check(lib().pivco_graph_launch(self.handle, _stream(stream or self.stream)), "pivco_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.pivco_graph_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+
 def ans_tables():
     fq = np.zeros(50, np.int32)
     cf = np.zeros(450, np.uint32)
@@ -255,11 +326,12 @@ class Encoder:
 
 
 class Decoder:
-    """Plain decoder: plan + ANS-decode pass + bottom-up merge kernel."""
+    """Decoder.  batched=False: plan, ANS pass, rank directories and merge as
+    separate launches; batched=True: one persistent work-queue launch."""
 
-    def __init__(self, nblk, device="cuda"):
+    def __init__(self, nblk, device="cuda", batched=False):
         import torch
-        self.nblk, self.dev = nblk, device
+        self.nblk, self.dev, self.batched = nblk, device, batched
         self.status = torch.empty(nblk, dtype=torch.int32, device=device)
         self.ws = torch.empty(decode_plan_bytes(nblk), dtype=torch.uint8, device=device)
 
@@ -271,7 +343,10 @@ class Decoder:
         return need
 
     def run(self, comp, comp_off, out, out_off, stream=None):
-        decode_blocks(comp, comp_off, self.nblk, out, out_off, self.ws, self.status, stream)
+        if self.batched:
+            decode_batched(comp, comp_off, self.nblk, out, out_off, self.ws, self.status, stream)
+        else:
+            decode_blocks(comp, comp_off, self.nblk, out, out_off, self.ws, self.status, stream)
         return out
 
     def __call__(self, comp, comp_off, out_off, stream=None):
@@ -285,7 +360,7 @@ def encode(data, blk_off, prm=None, stream=None):
     return Encoder(blk_off.numel() - 1, prm, data.device)(data, blk_off, stream)
 
 
-def decode(comp, comp_off, out_off, stream=None):
-    d = Decoder(out_off.numel() - 1, comp.device)
+def decode(comp, comp_off, out_off, stream=None, batched=False):
+    d = Decoder(out_off.numel() - 1, comp.device, batched=batched)
     out = d(comp, comp_off, out_off, stream)
     return out, d.status

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "pivco_dev.cuh"
 
@@ -60,6 +61,15 @@ static void build_tables() {
 }
 
 static std::atomic<uint64_t> g_launches{0};
+
+// launch tuning of the decode (process-wide; set by pivco_set_tuning / the autotuner)
+static DecTuning g_tuning = {65536, 256, 0};
+static std::mutex g_tuning_mu;
+const DecTuning &current_tuning() { return g_tuning; }
+void set_tuning(const DecTuning &t) {
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    g_tuning = t;
+}
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 const AnsTables &host_ans_tables() {
@@ -207,6 +217,142 @@ pivco_status pivco_ans_decode(const uint8_t *bodies, const uint64_t *body_off, c
     if (nbm < 0 || (nbm > 0 && (!bitmaps || !bm_off || !table || !bodies || !body_off || !status)))
         return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_ans_decode(bodies, body_off, table, nbm, bitmaps, bm_off, status, S(stream)));
+}
+
+// ---------------------------------------------------------------------------
+// Batching: persistent work-queue decode, tuning, graph capture, autotuner
+// ---------------------------------------------------------------------------
+pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, uint8_t *out,
+                                  const uint64_t *out_off, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !out_off || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    return ok_or_cuda(launch_decode_batch(comp, comp_off, nblk, out, out_off, reinterpret_cast<uint8_t *>(ws), ws_bytes,
+                                          status, S(stream)));
+}
+
+pivco_status pivco_get_tuning(pivco_tuning *t) {
+    if (!t) return PIVCO_ERR_INVALID_ARG;
+    const DecTuning &c = current_tuning();
+    t->tile_max = (int32_t)c.tile_max;
+    t->dir_bits = (int32_t)c.dir_bits;
+    t->ctas_per_sm = (int32_t)c.ctas_per_sm;
+    t->reserved = 0;
+    return PIVCO_OK;
+}
+
+pivco_status pivco_set_tuning(const pivco_tuning *t) {
+    if (!t || t->tile_max < 128 || t->tile_max > 65536 || (t->tile_max & 127) || t->dir_bits < 32 ||
+        t->dir_bits > 1024 || (t->dir_bits & 31) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
+        return PIVCO_ERR_INVALID_ARG;
+    set_tuning(DecTuning{(uint32_t)t->tile_max, (uint32_t)t->dir_bits, (uint32_t)t->ctas_per_sm});
+    return PIVCO_OK;
+}
+
+struct pivco_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+pivco_status pivco_graph_begin(void *stream) {
+    if (!stream) return PIVCO_ERR_INVALID_ARG;   // the legacy stream cannot be captured
+    // kernel attributes and the ANS tables are set up outside the capture
+    host_ans_tables();
+    if (prepare_decode_kernels() != cudaSuccess || prepare_encode_kernels() != cudaSuccess ||
+        prepare_ans_kernels() != cudaSuccess)
+        return PIVCO_ERR_CUDA;
+    return ok_or_cuda(cudaStreamBeginCapture(S(stream), cudaStreamCaptureModeThreadLocal));
+}
+
+pivco_status pivco_graph_end(void *stream, pivco_graph **out) {
+    if (!stream || !out) return PIVCO_ERR_INVALID_ARG;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(S(stream), &g);
+    if (e != cudaSuccess) return PIVCO_ERR_CUDA;
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return PIVCO_ERR_CUDA;
+    }
+    pivco_graph *h = new pivco_graph{g, x};
+    *out = h;
+    return PIVCO_OK;
+}
+
+pivco_status pivco_graph_launch(pivco_graph *g, void *stream) {
+    if (!g) return PIVCO_ERR_INVALID_ARG;
+    return ok_or_cuda(cudaGraphLaunch(g->exec, S(stream)));
+}
+
+pivco_status pivco_graph_destroy(pivco_graph *g) {
+    if (!g) return PIVCO_OK;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return PIVCO_OK;
+}
+
+pivco_status pivco_autotune_decode(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, uint8_t *out,
+                                   const uint64_t *out_off, void *ws, size_t ws_bytes, int32_t *status, int32_t reps,
+                                   void *stream, pivco_tuning *best, float *best_ms) {
+    if (nblk <= 0 || !comp || !comp_off || !out_off || !ws || !status || !best || reps < 1) return PIVCO_ERR_INVALID_ARG;
+    static const uint32_t tiles[] = {16384, 32768, 65536};
+    static const uint32_t dirs[] = {256, 512, 1024};
+    static const uint32_t ctas[] = {0, 2};
+    const DecTuning saved = current_tuning();
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PIVCO_ERR_CUDA;
+    float bms = 1e30f;
+    DecTuning bt = saved;
+    std::vector<int32_t> st_host((size_t)nblk);
+    pivco_status rc = PIVCO_OK;
+    for (uint32_t tm : tiles)
+        for (uint32_t db : dirs)
+            for (uint32_t cs : ctas) {
+                set_tuning(DecTuning{tm, db, cs});
+                // the workspace this tuning needs (tile cursors and directories grow as
+                // tiles shrink): a candidate that does not fit is skipped, not timed
+                cudaError_t e = launch_decode_plan(comp, comp_off, nblk, reinterpret_cast<uint8_t *>(ws), ws_bytes,
+                                                   status, S(stream));
+                size_t need = 0;
+                e = e == cudaSuccess ? read_decode_ws_need(reinterpret_cast<const uint8_t *>(ws), nblk, &need,
+                                                           S(stream)) : e;
+                if (e != cudaSuccess) { rc = PIVCO_ERR_CUDA; break; }
+                if (need > ws_bytes) continue;
+                // one warm launch, then the timed ones
+                e = launch_decode_batch(comp, comp_off, nblk, out, out_off, reinterpret_cast<uint8_t *>(ws), ws_bytes,
+                                        status, S(stream));
+                e = e == cudaSuccess ? cudaEventRecord(e0, S(stream)) : e;
+                for (int r = 0; r < reps && e == cudaSuccess; r++)
+                    e = launch_decode_batch(comp, comp_off, nblk, out, out_off, reinterpret_cast<uint8_t *>(ws), ws_bytes,
+                                            status, S(stream));
+                e = e == cudaSuccess ? cudaEventRecord(e1, S(stream)) : e;
+                e = e == cudaSuccess ? cudaEventSynchronize(e1) : e;
+                float ms = 0;
+                e = e == cudaSuccess ? cudaEventElapsedTime(&ms, e0, e1) : e;
+                e = e == cudaSuccess ? cudaMemcpyAsync(st_host.data(), status, sizeof(int32_t) * (size_t)nblk,
+                                                       cudaMemcpyDeviceToHost, S(stream)) : e;
+                e = e == cudaSuccess ? cudaStreamSynchronize(S(stream)) : e;
+                if (e != cudaSuccess) { rc = PIVCO_ERR_CUDA; break; }
+                bool clean = true;
+                for (int32_t x : st_host) clean = clean && x == PIVCO_OK;
+                if (!clean) continue;     // corrupt input or a failed tuning: never chosen
+                ms /= (float)reps;
+                if (ms < bms) { bms = ms; bt = DecTuning{tm, db, cs}; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == PIVCO_OK && bms >= 1e30f) rc = PIVCO_ERR_CAPACITY;
+    set_tuning(rc == PIVCO_OK ? bt : saved);
+    if (rc == PIVCO_OK) {
+        best->tile_max = (int32_t)bt.tile_max;
+        best->dir_bits = (int32_t)bt.dir_bits;
+        best->ctas_per_sm = (int32_t)bt.ctas_per_sm;
+        best->reserved = 0;
+        if (best_ms) *best_ms = bms;
+    }
+    return rc;
 }
 
 }  // extern "C"

@@ -224,3 +224,12 @@ cudaError_t launch_ans_encode_blocks(const BlockLayout *layout, int nblk, uint8_
 
 
 }  // namespace pv
+
+namespace pv {
+cudaError_t prepare_ans_kernels() {
+    const int smem = (int)(((sizeof(AnsSm) + 15) & ~15) + 2 * kAnsStageWords);
+    cudaError_t e = cudaFuncSetAttribute(ans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ans_encode_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+}  // namespace pv

@@ -171,21 +171,23 @@ __device__ inline bool warp_parse(const uint8_t *rec, uint64_t avail, WarpRec &R
 // Plan: one warp per record (ticket order), two look-back chains over blocks
 //   A: (ANS scratch bytes << 22) | ANS segments
 //   B: (directory + cursor bytes << 22) | tiles
+// Tuning (from the workspace header): the longest tile and the rank
+// directory granularity; neither changes the decoded bytes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) decode_plan_kernel(const uint8_t *__restrict__ comp,
-                                                         const uint64_t *__restrict__ comp_off, int nblk,
-                                                         uint8_t *__restrict__ ws, int32_t *__restrict__ status) {
-    __shared__ WarpRec R;
-    __shared__ uint32_t cntl[16], first[17], lvl[16];
-    __shared__ int s_tile;
-    const int lane = threadIdx.x;
+struct PlanScratch {
+    uint32_t cntl[16], first[17], lvl[16];
+};
+
+__device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                                  int nblk, uint8_t *__restrict__ ws, int32_t *__restrict__ status, WarpRec &R,
+                                  PlanScratch &Q) {
+    const int lane = threadIdx.x & 31;
     uint32_t *hdr32 = reinterpret_cast<uint32_t *>(ws);
     uint64_t *hdr64 = reinterpret_cast<uint64_t *>(ws);
     const DecWs W = dec_ws(ws, nblk);
-    if (lane == 0) s_tile = (int)atomicAdd(&hdr32[3], 1u);
-    if (lane < 16) { cntl[lane] = 0; lvl[lane] = 0; }
+    const uint32_t dir_bits = hdr32[7], tile_max = hdr32[8];
+    if (lane < 16) { Q.cntl[lane] = 0; Q.lvl[lane] = 0; }
     __syncwarp();
-    const int b = s_tile;
     const uint8_t *rec = comp + comp_off[b];
     bool ok = warp_parse(rec, comp_off[b + 1] - comp_off[b], R);
     __syncwarp();
@@ -196,47 +198,42 @@ __global__ void __launch_bounds__(32) decode_plan_kernel(const uint8_t *__restri
         const uint32_t x = ld_le32(rec + kLensOff + 4 * lane);
         for (int j = 0; j < 8; j++) {
             const uint32_t l = (x >> (4 * j)) & 15u;
-            if (l) atomicAdd(&cntl[l], 1u);
+            if (l) atomicAdd(&Q.cntl[l], 1u);
         }
         __syncwarp();
         if (lane == 0) {
             int64_t a = 0, f = 0;
             int ml = 0;
-            for (int l = 1; l < 16; l++) if (cntl[l]) ml = l;
-            first[0] = 0;
+            for (int l = 1; l < 16; l++) if (Q.cntl[l]) ml = l;
+            Q.first[0] = 0;
             for (int d = 0; d < 16; d++) {
-                if (d > 0) a = 2 * a + cntl[d];
-                const int64_t open = (d < 31 ? (int64_t(1) << d) : 0) - a;
+                if (d > 0) a = 2 * a + Q.cntl[d];
+                const int64_t open = (int64_t(1) << d) - a;
                 if (d < ml) f += open > 0 ? open : 0;
-                first[d + 1] = (uint32_t)(f > 255 ? 255 : f);
+                Q.first[d + 1] = (uint32_t)(f > 255 ? 255 : f);
             }
         }
         __syncwarp();
-        if (first[15] != R.V) ok = false;
+        if (Q.first[15] != R.V) ok = false;
         for (int v = lane; v < (int)R.V && ok; v += 32) {
             int d = 0;
-            while (d < 15 && first[d + 1] <= (uint32_t)v) d++;
-            if (d >= 1) atomicAdd(&lvl[d], R.nv[v]);
+            while (d < 15 && Q.first[d + 1] <= (uint32_t)v) d++;
+            if (d >= 1) atomicAdd(&Q.lvl[d], R.nv[v]);
         }
         __syncwarp();
         ok = __all_sync(0xffffffffu, ok);
         if (ok) {
             uint64_t mx = 1;
-            for (int d = 1; d < 16; d++) mx = lvl[d] > mx ? lvl[d] : mx;
+            for (int d = 1; d < 16; d++) mx = Q.lvl[d] > mx ? Q.lvl[d] : mx;
             const uint64_t fit = (uint64_t)(kDLvlCap - 4 * 256) * R.n / mx;
-            if (fit < R.n) {
-                // several tiles, 20 % headroom against uneven symbol statistics
-                uint64_t t2 = fit / 5 * 4;
-                t2 = t2 > (uint64_t)kDMaxRoot ? (uint64_t)kDMaxRoot : t2;
+            uint64_t t2 = 0;
+            if (fit < R.n) t2 = fit / 5 * 4;   // several tiles: 20 % headroom against uneven statistics
+            else if (R.n > tile_max) t2 = tile_max;
+            if (t2) {
+                t2 = t2 > (uint64_t)tile_max ? (uint64_t)tile_max : t2;
                 T = (uint32_t)(t2 < (uint64_t)kDUnit ? kDUnit : (t2 & ~(uint64_t)(kDUnit - 1)));
                 ntile = (R.n + T - 1) / T;
-                const uint32_t ent = warp_scan_loop_d((int)R.V, [&](int v) { return (R.nv[v] + kDirBits - 1) / kDirBits; },
-                                                      [&](int, uint32_t) {});
-                dir_bytes = ((4ull * ent + 4ull * (ntile + 1) * R.V) + 15) & ~15ull;
-            } else if (R.n > (uint32_t)kDMaxRoot) {
-                T = kDMaxRoot;
-                ntile = (R.n + T - 1) / T;
-                const uint32_t ent = warp_scan_loop_d((int)R.V, [&](int v) { return (R.nv[v] + kDirBits - 1) / kDirBits; },
+                const uint32_t ent = warp_scan_loop_d((int)R.V, [&](int v) { return (R.nv[v] + dir_bits - 1) / dir_bits; },
                                                       [&](int, uint32_t) {});
                 dir_bytes = ((4ull * ent + 4ull * (ntile + 1) * R.V) + 15) & ~15ull;
             }
@@ -262,16 +259,43 @@ __global__ void __launch_bounds__(32) decode_plan_kernel(const uint8_t *__restri
             hdr32[6] = (uint32_t)((eb & ((1u << 22) - 1)) + ntile);
         }
     }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) decode_plan_kernel(const uint8_t *__restrict__ comp,
+                                                         const uint64_t *__restrict__ comp_off, int nblk,
+                                                         uint8_t *__restrict__ ws, int32_t *__restrict__ status) {
+    __shared__ WarpRec R;
+    __shared__ PlanScratch Q;
+    __shared__ int s_tile;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&reinterpret_cast<uint32_t *>(ws)[3], 1u);
+    __syncwarp();
+    plan_block(s_tile, comp, comp_off, nblk, ws, status, R, Q);
+}
+
+// zero the header, the look-back states and the batch counters; set the tuning
+__global__ void dec_ws_init_kernel(uint8_t *ws, int nblk, uint32_t dir_bits, uint32_t tile_max) {
+    const DecWs W = dec_ws(ws, nblk);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nblk; i += gridDim.x * blockDim.x) {
+        W.states_a[i] = 0;
+        W.states_b[i] = 0;
+        W.segs_done[i] = 0;
+        W.dir_done[i] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 16) {
+        uint32_t *h = reinterpret_cast<uint32_t *>(ws);
+        h[threadIdx.x] = threadIdx.x == 7 ? dir_bits : (threadIdx.x == 8 ? tile_max : 0u);
+    }
 }
 
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
                                int32_t *status, cudaStream_t st) {
     (void)ws_bytes;
     if (nblk <= 0) return cudaSuccess;
-    cudaError_t e = launch_zero_bytes(ws, 64 + 16ull * nblk, st);   // header + both look-back state arrays
-    if (e != cudaSuccess) return e;
+    const DecTuning &tu = current_tuning();
+    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max);
     decode_plan_kernel<<<nblk, 32, 0, st>>>(comp, comp_off, nblk, ws, status);
-    count_launches(1);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -286,8 +310,70 @@ cudaError_t read_decode_ws_need(const uint8_t *ws, int nblk, size_t *need, cudaS
 }
 
 // ---------------------------------------------------------------------------
-// ANS pass: one warp per planned segment (persistent grid)
+// ANS pass: one warp per planned segment
 // ---------------------------------------------------------------------------
+// Decodes block-local ANS segment g (global numbering) into the scratch.
+// Returns the block index (or -1 when g is out of range).  R caches the
+// parsed record of the last block this warp saw.
+__device__ inline int ans_item(uint32_t g, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                               int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                               const AnsTables &A, WarpRec &R, AnsSm &T, int &last_b, bool &last_ok) {
+    const int lane = threadIdx.x & 31;
+    const DecWs W = dec_ws(ws, nblk);
+    const DecRegions G = dec_regions(nblk, ws);
+    const uint64_t scratch_cap = ws_bytes > G.scratch ? ws_bytes - G.scratch : 0;
+    uint8_t *scratch = ws + G.scratch;
+    const int b = find_block(W.blk_seg, nblk, g);
+    if (status[b] != PIVCO_OK) return b;
+    const uint8_t *rec = comp + comp_off[b];
+    if (b != last_b) {
+        last_ok = warp_parse(rec, comp_off[b + 1] - comp_off[b], R);
+        last_b = b;
+    }
+    bool ok = last_ok;
+    if (ok) {
+        const uint32_t j = g - W.blk_seg[b];
+        int node = -1;
+        for (int v = lane; v < (int)R.V; v += 32) {
+            const uint8_t m = R.marker[v];
+            if (m && m != kMarkRawSel) {
+                const uint32_t s0 = R.segbase[v], ns = ans_seg_count((R.nv[v] + 7) / 8);
+                if (j >= s0 && j < s0 + ns) node = v;
+            }
+        }
+        for (int o = 16; o; o >>= 1) node = max(node, __shfl_xor_sync(0xffffffffu, node, o));
+        if (node < 0) ok = false;
+        if (ok) {
+            const uint32_t s = j - R.segbase[node];
+            const uint32_t raw = (R.nv[node] + 7) / 8;
+            const uint8_t mk = R.marker[node];
+            const uint64_t sdst = W.blk_scratch[b] + R.soff[node];
+            if (sdst + scratch_stride(raw) > scratch_cap) {
+                if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
+                __syncwarp();
+                return b;
+            }
+            uint64_t sp = 0;
+            uint32_t nw = 0;
+            const uint8_t *body = rec + R.body_off[node];
+            const uint32_t blen = R.alen[node];
+            ok = ans_segment_at(body, blen, raw, s, sp, nw);
+            if (ok) {
+                load_ans_table(T, A, (mk & 0x7F) - 1, lane, 32);
+                __syncwarp();
+                const uint32_t sbytes = min(kAnsSeg, raw - s * kAnsSeg), Wl = ans_seg_lanes(sbytes);
+                ok = ans_decode_segment(body + sp, body + sp + 4 * Wl, nw, sbytes, T, (mk & 0x80) ? 0xFF : 0,
+                                        scratch + sdst + (size_t)s * kAnsSeg);
+                if (ok && s + 1 == ans_seg_count(raw) && sp + 4ull * Wl + 2ull * nw != blen) ok = false;
+                if (s + 1 == ans_seg_count(raw) && lane < 16) scratch[sdst + raw + lane] = 0;
+            }
+        }
+    }
+    if (!ok && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+    __syncwarp();
+    return b;
+}
+
 constexpr int kAnsDecWarps = 4;
 
 __global__ void __launch_bounds__(32 * kAnsDecWarps) ans_decode_planned_kernel(const uint8_t *__restrict__ comp,
@@ -298,64 +384,12 @@ __global__ void __launch_bounds__(32 * kAnsDecWarps) ans_decode_planned_kernel(c
                                                                                const __grid_constant__ AnsTables A) {
     __shared__ WarpRec R[kAnsDecWarps];
     __shared__ AnsSm T[kAnsDecWarps];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     const uint32_t total = reinterpret_cast<const uint32_t *>(ws)[2];
-    const DecWs W = dec_ws(ws, nblk);
-    const DecRegions G = dec_regions(nblk, ws);
-    const uint64_t scratch_cap = ws_bytes > G.scratch ? ws_bytes - G.scratch : 0;
-    uint8_t *scratch = ws + G.scratch;
     int last_b = -1;
     bool last_ok = false;
-    for (uint32_t g = blockIdx.x * kAnsDecWarps + w; g < total; g += gridDim.x * kAnsDecWarps) {
-        const int b = find_block(W.blk_seg, nblk, g);
-        if (status[b] != PIVCO_OK) continue;
-        const uint8_t *rec = comp + comp_off[b];
-        if (b != last_b) {
-            last_ok = warp_parse(rec, comp_off[b + 1] - comp_off[b], R[w]);
-            last_b = b;
-        }
-        bool ok = last_ok;
-        if (ok) {
-            // the node holding block-local segment j
-            const uint32_t j = g - W.blk_seg[b];
-            int node = -1;
-            for (int v = lane; v < (int)R[w].V; v += 32) {
-                const uint8_t m = R[w].marker[v];
-                if (m && m != kMarkRawSel) {
-                    const uint32_t s0 = R[w].segbase[v], ns = ans_seg_count((R[w].nv[v] + 7) / 8);
-                    if (j >= s0 && j < s0 + ns) node = v;
-                }
-            }
-            for (int o = 16; o; o >>= 1) node = max(node, __shfl_xor_sync(0xffffffffu, node, o));
-            if (node < 0) ok = false;
-            if (ok) {
-                const uint32_t s = j - R[w].segbase[node];
-                const uint32_t raw = (R[w].nv[node] + 7) / 8;
-                const uint8_t mk = R[w].marker[node];
-                const uint64_t sdst = W.blk_scratch[b] + R[w].soff[node];
-                if (sdst + scratch_stride(raw) > scratch_cap) {
-                    if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
-                    continue;
-                }
-                uint64_t sp = 0;
-                uint32_t nw = 0;
-                const uint8_t *body = rec + R[w].body_off[node];
-                const uint32_t blen = R[w].alen[node];
-                ok = ans_segment_at(body, blen, raw, s, sp, nw);
-                if (ok) {
-                    load_ans_table(T[w], A, (mk & 0x7F) - 1, lane, 32);
-                    __syncwarp();
-                    const uint32_t sbytes = min(kAnsSeg, raw - s * kAnsSeg), Wl = ans_seg_lanes(sbytes);
-                    ok = ans_decode_segment(body + sp, body + sp + 4 * Wl, nw, sbytes, T[w], (mk & 0x80) ? 0xFF : 0,
-                                            scratch + sdst + (size_t)s * kAnsSeg);
-                    if (ok && s + 1 == ans_seg_count(raw) && sp + 4ull * Wl + 2ull * nw != blen) ok = false;
-                    if (s + 1 == ans_seg_count(raw) && lane < 16) scratch[sdst + raw + lane] = 0;
-                }
-            }
-        }
-        if (!ok && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
-        __syncwarp();
-    }
+    for (uint32_t g = blockIdx.x * kAnsDecWarps + w; g < total; g += gridDim.x * kAnsDecWarps)
+        ans_item(g, comp, comp_off, nblk, ws, ws_bytes, status, A, R[w], T[w], last_b, last_ok);
 }
 
 cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
@@ -377,7 +411,7 @@ struct DecSmem {
     uint8_t rec[kDRecSmem];          // record copy (bulk copy destination, 16-aligned)
     uint8_t buf[2][kDLvlBytes];      // level buffers (depth d uses buf[d & 1])
     uint32_t ubase[kDMaxUnits];      // unit popcount, then the unit's rank base within its node
-    uint8_t umap[kDMaxUnits];        // unit -> node (fallback path)
+    uint8_t umap[kDMaxUnits];        // unit -> node
     uint32_t sel[4][16];             // byte-permute selectors by (node kind, 4 bits)
     uint32_t cur[256];               // bits of node v consumed before the current chunk
     uint32_t dem[256];               // bits of node v used by the current chunk
@@ -401,6 +435,7 @@ struct DecSmem {
     int32_t flag;                    // 1 corrupt, 2 capacity
     int32_t overflow;
     uint32_t chunk;
+    uint32_t item;                   // batch queue item of this CTA
 };
 
 __device__ inline uint32_t bits32_g(const uint8_t *base, uint64_t bit, uint64_t limit) {
@@ -447,19 +482,20 @@ __device__ inline uint32_t lds4(const uint8_t *p) {
 }
 
 // popcount of bits [0, c) of node v (c <= n_v) from its rank directory
-__device__ inline uint32_t rank1_dir(const DecSmem &S, const NodeSrc &src, const uint32_t *dir, int v, uint32_t c) {
-    const uint32_t nsb = (S.nv[v] + kDirBits - 1) / kDirBits;
-    uint32_t sb = c / kDirBits;
+__device__ inline uint32_t rank1_dir(const DecSmem &S, const NodeSrc &src, const uint32_t *dir, int v, uint32_t c,
+                                     uint32_t dir_bits) {
+    const uint32_t nsb = (S.nv[v] + dir_bits - 1) / dir_bits;
+    uint32_t sb = c / dir_bits;
     if (sb >= nsb) sb = nsb - 1;
-    const uint32_t base = sb * kDirBits;
+    const uint32_t base = sb * dir_bits;
     uint32_t r = dir[sb];
     for (uint32_t e = base; e < c; e += 32) r += __popc(mask_valid(node_bits(S, src, v, e), (int64_t)c - e));
     return r;
 }
 
-// Per-block setup shared by the directory and merge kernels: tree from the
-// code lengths, node table and bitmap sources.  Returns 0 ok, 1 corrupt,
-// 2 workspace too small.  in_smem: the record is being bulk-copied into S.rec.
+// Per-block setup shared by the directory and merge: tree from the code
+// lengths, node table and bitmap sources.  Returns 0 ok, 1 corrupt, 2
+// workspace too small.  in_smem: the record is being bulk-copied into S.rec.
 __device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb, uint32_t n, uint32_t V, bool in_smem,
                                   uint64_t scratch_lim) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -524,91 +560,96 @@ __device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb,
 }
 
 // ---------------------------------------------------------------------------
-// Rank directories and tile-boundary cursors (blocks with several tiles)
+// Rank directories and tile-boundary cursors of one block (whole CTA)
 // ---------------------------------------------------------------------------
+__device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                                 int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                                 DecSmem &S) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const DecWs W = dec_ws(ws, nblk);
+    const DecRegions G = dec_regions(nblk, ws);
+    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
+    const uint32_t ntile = W.blk_ntile[b];
+    if (ntile <= 1 || status[b] != PIVCO_OK) return;
+    const uint8_t *rec_g = comp + comp_off[b];
+    const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
+    const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8);
+    const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
+    const int bad = block_setup(S, rec_g, rb, n, V, false, slim);
+    if (bad || G.dir + W.blk_dir[b] + 4ull * (ntile + 1) * V > ws_bytes) {
+        if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
+        __syncthreads();
+        return;
+    }
+    NodeSrc src;
+    src.rec_g = rec_g;
+    src.rb = rb;
+    src.scratch = ws + G.scratch + W.blk_scratch[b];
+    src.scratch_lim = slim;
+    uint32_t *dir = reinterpret_cast<uint32_t *>(ws + G.dir + W.blk_dir[b]);
+    // superblocks per node
+    if (warp == 0) {
+        const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + dir_bits - 1) / dir_bits; },
+                                              [&](int v, uint32_t p) { S.ustart[v] = p; });
+        if (lane == 0) S.lvl_units[0] = tot;
+    }
+    __syncthreads();
+    const uint32_t nsb = S.lvl_units[0];
+    uint32_t *cursors = dir + nsb;
+    if (G.dir + W.blk_dir[b] + 4ull * nsb + 4ull * (ntile + 1) * V > ws_bytes) {
+        if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
+        __syncthreads();
+        return;
+    }
+    for (uint32_t g = t; g < nsb; g += kDecThreads) {
+        const int v = find_node_d(S.ustart, 0, (int)V, g);
+        const uint32_t e0 = (g - S.ustart[v]) * dir_bits, nvv = S.nv[v];
+        uint32_t pc = 0;
+        for (uint32_t e = e0; e < e0 + dir_bits && e < nvv; e += 32)
+            pc += __popc(mask_valid(node_bits(S, src, v, e), (int64_t)nvv - e));
+        dir[g] = pc;
+    }
+    __syncthreads();
+    for (int v = warp; v < (int)V; v += kDecWarps) {
+        const uint32_t u0 = S.ustart[v], nu = (S.nv[v] + dir_bits - 1) / dir_bits;
+        warp_scan_loop_d((int)nu, [&](int i) { return dir[u0 + i]; }, [&](int i, uint32_t p) { dir[u0 + i] = p; });
+    }
+    // boundary 0: all cursors 0; boundary ntile: n_v; root cursor at boundary k: k * T
+    for (uint32_t v = t; v < V; v += kDecThreads) { cursors[v] = 0; cursors[(size_t)ntile * V + v] = S.nv[v]; }
+    const uint32_t T = W.blk_T[b];
+    for (uint32_t k = 1 + t; k < ntile; k += kDecThreads) cursors[(size_t)k * V] = k * T;
+    __syncthreads();
+    // top-down by depth: children's cursors from the parent's rank at its cursor
+    const int maxd = S.ts.max_len;
+    int bad2 = 0;
+    for (int d = 0; d < maxd; d++) {
+        const uint32_t f0 = S.first[d], nd = S.first[d + 1] - f0;
+        for (uint32_t i = t; i < (ntile - 1) * nd; i += kDecThreads) {
+            const uint32_t k = 1 + i / nd;
+            const int v = (int)(f0 + i % nd);
+            const uint32_t c = cursors[(size_t)k * V + v];
+            if (c > S.nv[v]) { bad2 = 1; continue; }
+            const uint32_t ones = rank1_dir(S, src, dir + S.ustart[v], v, c, dir_bits);
+            const int c0 = S.child[v][0], c1 = S.child[v][1];
+            if (c0 >= 0) cursors[(size_t)k * V + c0] = c - ones;
+            if (c1 >= 0) cursors[(size_t)k * V + c1] = ones;
+        }
+        __syncthreads();
+    }
+    bad2 = __syncthreads_or(bad2);
+    if (t == 0 && bad2) status[b] = PIVCO_ERR_CORRUPT;
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kDecThreads, 3) decode_dir_kernel(const uint8_t *__restrict__ comp,
                                                                     const uint64_t *__restrict__ comp_off, int nblk,
                                                                     uint8_t *__restrict__ ws, uint64_t ws_bytes,
                                                                     int32_t *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     DecSmem &S = *reinterpret_cast<DecSmem *>(smem_raw);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const DecWs W = dec_ws(ws, nblk);
-    const DecRegions G = dec_regions(nblk, ws);
-    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-        const uint32_t ntile = W.blk_ntile[b];
-        if (ntile <= 1 || status[b] != PIVCO_OK) continue;
-        const uint8_t *rec_g = comp + comp_off[b];
-        const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
-        const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8);
-        const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
-        const int bad = block_setup(S, rec_g, rb, n, V, false, slim);
-        if (bad || G.dir + W.blk_dir[b] + 4ull * (ntile + 1) * V > ws_bytes) {
-            if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
-            __syncthreads();
-            continue;
-        }
-        NodeSrc src;
-        src.rec_g = rec_g;
-        src.rb = rb;
-        src.scratch = ws + G.scratch + W.blk_scratch[b];
-        src.scratch_lim = slim;
-        uint32_t *dir = reinterpret_cast<uint32_t *>(ws + G.dir + W.blk_dir[b]);
-        // superblock counts per node
-        if (warp == 0) {
-            const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + kDirBits - 1) / kDirBits; },
-                                                  [&](int v, uint32_t p) { S.ustart[v] = p; });
-            if (lane == 0) S.lvl_units[0] = tot;
-        }
-        __syncthreads();
-        const uint32_t nsb = S.lvl_units[0];
-        uint32_t *cursors = dir + nsb;
-        if (G.dir + W.blk_dir[b] + 4ull * nsb + 4ull * (ntile + 1) * V > ws_bytes) {
-            if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
-            __syncthreads();
-            continue;
-        }
-        for (uint32_t g = t; g < nsb; g += kDecThreads) {
-            const int v = find_node_d(S.ustart, 0, (int)V, g);
-            const uint32_t e0 = (g - S.ustart[v]) * kDirBits, nvv = S.nv[v];
-            uint32_t pc = 0;
-#pragma unroll
-            for (uint32_t q = 0; q < kDirBits / 32; q++) {
-                const int64_t e = (int64_t)e0 + 32 * q;
-                if (e < nvv) pc += __popc(mask_valid(node_bits(S, src, v, (uint32_t)e), (int64_t)nvv - e));
-            }
-            dir[g] = pc;
-        }
-        __syncthreads();
-        for (int v = warp; v < (int)V; v += kDecWarps) {
-            const uint32_t u0 = S.ustart[v], nu = (S.nv[v] + kDirBits - 1) / kDirBits;
-            warp_scan_loop_d((int)nu, [&](int i) { return dir[u0 + i]; }, [&](int i, uint32_t p) { dir[u0 + i] = p; });
-        }
-        // boundary 0: all cursors 0; boundary ntile: n_v
-        for (uint32_t v = t; v < V; v += kDecThreads) { cursors[v] = 0; cursors[(size_t)ntile * V + v] = S.nv[v]; }
-        const uint32_t T = W.blk_T[b];
-        for (uint32_t k = 1 + t; k < ntile; k += kDecThreads) cursors[(size_t)k * V] = k * T;
-        __syncthreads();
-        // top-down by depth: children's cursors from the parent's rank at its cursor
-        const int maxd = S.ts.max_len;
-        int bad2 = 0;
-        for (int d = 0; d < maxd; d++) {
-            const uint32_t f0 = S.first[d], nd = S.first[d + 1] - f0;
-            for (uint32_t i = t; i < (ntile - 1) * nd; i += kDecThreads) {
-                const uint32_t k = 1 + i / nd;
-                const int v = (int)(f0 + i % nd);
-                const uint32_t c = cursors[(size_t)k * V + v];
-                if (c > S.nv[v]) { bad2 = 1; continue; }
-                const uint32_t ones = rank1_dir(S, src, dir + S.ustart[v], v, c);
-                const int c0 = S.child[v][0], c1 = S.child[v][1];
-                if (c0 >= 0) cursors[(size_t)k * V + c0] = c - ones;
-                if (c1 >= 0) cursors[(size_t)k * V + c1] = ones;
-            }
-            __syncthreads();
-        }
-        bad2 = __syncthreads_or(bad2);
-        if (t == 0 && bad2) status[b] = PIVCO_ERR_CORRUPT;
-    }
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x)
+        if (W.blk_ntile[b] > 1) dir_block(b, comp, comp_off, nblk, ws, ws_bytes, status, S);
 }
 
 cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
@@ -627,16 +668,16 @@ cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int
 }
 
 // ---------------------------------------------------------------------------
-// Merge (one CTA per tile, persistent grid)
+// Merge
 // ---------------------------------------------------------------------------
 // merge every node of depth d for the current chunk: units g in [g0, g1)
 __device__ inline void merge_level(DecSmem &S, const NodeSrc &src, int d, uint32_t g0, uint32_t g1, uint8_t *dst,
-                                   uint32_t P, bool out4, int f0, int f1, bool use_map) {
+                                   uint32_t P, bool out4) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t *bin = S.buf[(d + 1) & 1];
     uint8_t *bout = S.buf[d & 1];
     for (uint32_t g = g0 + warp; g < g1; g += kDecWarps) {
-        const int v = use_map ? (int)S.umap[g] : find_node_d(S.ustart, f0, f1, g);
+        const int v = S.umap[g];
         const uint32_t k0 = (g - S.ustart[v]) * kDUnit, k = k0 + 4 * lane;
         const uint32_t dv = S.dem[v], q = lane >> 3;
         const int64_t e = (int64_t)k0 + 32 * q;
@@ -661,20 +702,14 @@ __device__ inline void merge_level(DecSmem &S, const NodeSrc &src, int d, uint32
     }
 }
 
-__global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const uint8_t *__restrict__ comp,
-                                                                const uint64_t *__restrict__ comp_off,
-                                                                int nblk, uint8_t *__restrict__ out,
-                                                                const uint64_t *__restrict__ out_off,
-                                                                const uint8_t *__restrict__ ws, uint64_t ws_bytes,
-                                                                int32_t *__restrict__ status) {
-    extern __shared__ __align__(128) uint8_t smem_raw[];
-    DecSmem &S = *reinterpret_cast<DecSmem *>(smem_raw);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+// One-time CTA setup of the merge: the mbarrier and the byte-permute selectors.
+// Selector of output byte j for 4 bits `nib`: a one takes the next byte of the
+// right window (bytes 4..7), a zero the next byte of the left window (bytes
+// 0..3); a leaf side always takes its constant.
+__device__ inline void merge_cta_init(DecSmem &S) {
+    const int t = threadIdx.x;
     if (t == 0) mbar_init(&S.mbar, 1);
     if (t < 64) {
-        // selector of output byte j for 4 bits `nib`: a one takes the next
-        // byte of the right window (bytes 4..7), a zero the next byte of the
-        // left window (bytes 0..3); a leaf side always takes its constant
         const int kindsel = t >> 4, nib = t & 15;
         const bool lint = kindsel & 1, rint = kindsel & 2;
         uint32_t s = 0, ones = 0, zeros = 0;
@@ -688,270 +723,420 @@ __global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const uint8_t *_
         S.sel[kindsel][nib] = s;
     }
     __syncthreads();
-    uint32_t phase = 0;
+}
+
+// unit popcounts and per-node scans of the current chunk's units [g0, g1) of
+// the nodes [f0, f1); sets the children's demands when set_children, else
+// checks them.  Returns nonzero on inconsistency.
+__device__ inline int rank_units(DecSmem &S, const NodeSrc &src, int f0, int f1, uint32_t g0, uint32_t g1,
+                                 bool set_children) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (uint32_t g = g0 + t; g < g1; g += kDecThreads) {
+        const int v = find_node_d(S.ustart, f0, f1, g);
+        const uint32_t k0 = (g - S.ustart[v]) * kDUnit, dv = S.dem[v], c = S.cur[v];
+        uint32_t pc = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++) {
+            const int64_t e = (int64_t)k0 + 32 * q;
+            if (e < dv) pc += __popc(mask_valid(node_bits(S, src, v, c + (uint32_t)e), (int64_t)dv - e));
+        }
+        S.ubase[g] = pc;
+        S.umap[g] = (uint8_t)v;
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int v = f0 + warp; v < f1; v += kDecWarps) {
+        const uint32_t dv = S.dem[v];
+        uint32_t ones = 0;
+        if (dv) {
+            const uint32_t u0 = S.ustart[v], nu = (dv + kDUnit - 1) / kDUnit;
+            ones = warp_scan_loop_d((int)nu, [&](int i) { return S.ubase[u0 + i]; },
+                                    [&](int i, uint32_t p) { S.ubase[u0 + i] = p; });
+        }
+        if (lane < 2) {
+            const int ch = S.child[v][lane];
+            if (ch >= 0) {
+                const uint32_t dc = lane ? ones : dv - ones;
+                if (set_children) {
+                    S.dem[ch] = dc;
+                    if ((uint64_t)S.cur[ch] + dc > S.nv[ch]) bad = 1;
+                } else if (S.dem[ch] != dc) {
+                    bad = 1;
+                }
+            }
+        }
+    }
+    return __syncthreads_or(bad);
+}
+
+// Decodes tile gt (whole CTA).  Returns false when a bounded wait expired
+// (the CTA must stop; the affected blocks are marked).
+__device__ inline bool tile_item(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                                 int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
+                                 const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                                 DecSmem &S, uint32_t &phase) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
     const DecRegions G = dec_regions(nblk, ws);
-    const uint32_t total_tiles = reinterpret_cast<const uint32_t *>(ws)[6];
-
-    for (uint32_t gt = blockIdx.x; gt < total_tiles; gt += gridDim.x) {
-        const int b = find_block(W.blk_tile, nblk, gt);
-        if (status[b] != PIVCO_OK) continue;   // the plan / ANS / directory pass already failed this block
-        const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
-        const uint8_t *rec_g = comp + comp_off[b];
-        uint8_t *dst = out + out_off[b];
-        const uint64_t ocap = out_off[b + 1] - out_off[b];
-        const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
-        const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8), kind = rec_g[10], aux = rec_g[11];
-        if ((comp_off[b] & 15) || n != ocap) {   // the plan validated magic / size / layout
-            if (t == 0) status[b] = n != ocap ? PIVCO_ERR_CAPACITY : PIVCO_ERR_CORRUPT;
-            continue;
+    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
+    const int b = find_block(W.blk_tile, nblk, gt);
+    if (status[b] != PIVCO_OK) return true;   // the plan / ANS / directory pass already failed this block
+    const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
+    const uint8_t *rec_g = comp + comp_off[b];
+    uint8_t *dst = out + out_off[b];
+    const uint64_t ocap = out_off[b + 1] - out_off[b];
+    const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
+    const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8), kind = rec_g[10], aux = rec_g[11];
+    if ((comp_off[b] & 15) || n != ocap) {   // the plan validated magic / size / layout
+        if (t == 0) status[b] = n != ocap ? PIVCO_ERR_CAPACITY : PIVCO_ERR_CORRUPT;
+        return true;
+    }
+    if (kind == 0) return true;
+    if (kind == 1) {
+        for (uint32_t i = t; i < n; i += kDecThreads) dst[i] = (uint8_t)aux;
+        return true;
+    }
+    const uint32_t P0 = k * T, P1 = min(n, P0 + T);
+    // ---- record into shared memory (overlaps the tree construction) ----
+    const bool in_smem = rb <= (uint32_t)kDRecSmem;
+    if (in_smem && t == 0) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(&S.mbar, rb);
+        bulk_g2s(S.rec, rec_g, rb, &S.mbar);
+    }
+    const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
+    const int bad = block_setup(S, rec_g, rb, n, V, in_smem, slim);
+    int timed_out = in_smem ? !mbar_wait(&S.mbar, phase) : 0;
+    timed_out = __syncthreads_or(timed_out);
+    if (timed_out) {
+        mbar_wait(&S.mbar, phase);   // one more bounded wait for the copy before the CTA leaves
+        if (t == 0) status[b] = PIVCO_ERR_TIMEOUT;
+        return false;
+    }
+    if (in_smem) phase ^= 1;
+    if (bad) {
+        if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
+        __syncthreads();
+        return true;
+    }
+    NodeSrc src;
+    src.rec_g = rec_g;
+    src.rb = rb;
+    src.scratch = ws + G.scratch + W.blk_scratch[b];
+    src.scratch_lim = slim;
+    const bool out4 = (reinterpret_cast<uintptr_t>(dst) & 3) == 0;
+    const int maxd = S.ts.max_len;
+    // ---- this tile's bit range of every node ----
+    const uint32_t *cursors = nullptr;   // tile-boundary cursors follow the node directories
+    if (warp == 0 && ntile > 1) {
+        const uint32_t ent = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + dir_bits - 1) / dir_bits; },
+                                              [&](int, uint32_t) {});
+        if (lane == 0) S.lvl_units[16] = ent;
+    }
+    __syncthreads();
+    if (ntile > 1) cursors = reinterpret_cast<const uint32_t *>(ws + G.dir + W.blk_dir[b]) + S.lvl_units[16];
+    for (uint32_t v = t; v < V; v += kDecThreads) {
+        const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
+        const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : S.nv[v];
+        S.cur[v] = cs;
+        S.dem[v] = ce >= cs ? ce - cs : 0u;
+        S.alen[v] = (ce < cs || ce > S.nv[v]) ? 1u : 0u;   // reused as a per-node error mark
+    }
+    if (t == 0) { S.flag = 0; S.overflow = 0; }
+    __syncthreads();
+    for (uint32_t v = t; v < V; v += kDecThreads)
+        if (S.alen[v]) S.flag = 1;
+    if (t == 0 && S.dem[0] != P1 - P0) S.flag = 1;
+    // ---- fast path: spans and units of every depth at once ----
+    for (int d = warp; d < maxd; d += kDecWarps) {
+        const int f0 = S.first[d], f1 = S.first[d + 1];
+        uint64_t carry = 0;
+        for (int base = f0; base < f1; base += 32) {
+            const int v = base + lane;
+            const uint32_t dv = v < f1 ? S.dem[v] : 0u;
+            const uint64_t x = ((uint64_t)((dv + kDUnit - 1) / kDUnit) << 32) | ((dv + 3u) & ~3u);
+            uint64_t inc = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint64_t ex = carry + inc - x;
+            if (v < f1) { S.span[v] = (uint32_t)ex; S.ustart[v] = (uint32_t)(ex >> 32); }
+            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
-        if (kind == 0) continue;
-        if (kind == 1) {
-            for (uint32_t i = t; i < n; i += kDecThreads) dst[i] = (uint8_t)aux;
-            continue;
+        if (lane == 0) {
+            S.lvl_units[d] = (uint32_t)(carry >> 32);
+            if (d > 0 && (uint32_t)carry > (uint32_t)kDLvlCap) S.overflow = 1;
         }
-        const uint32_t P0 = k * T, P1 = min(n, P0 + T);
-        // ---- record into shared memory (overlaps the tree construction) ----
-        const bool in_smem = rb <= (uint32_t)kDRecSmem;
-        if (in_smem && t == 0) {
-            fence_proxy_async_smem();
-            mbar_expect_tx(&S.mbar, rb);
-            bulk_g2s(S.rec, rec_g, rb, &S.mbar);
-        }
-        const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
-        int bad = block_setup(S, rec_g, rb, n, V, in_smem, slim);
-        int timed_out = in_smem ? !mbar_wait(&S.mbar, phase) : 0;
-        timed_out = __syncthreads_or(timed_out);
-        if (timed_out) {
-            // bounded wait expired: give the copy one more bounded wait, then stop this CTA
-            mbar_wait(&S.mbar, phase);
-            if (t == 0)
-                for (uint32_t g2 = gt; g2 < total_tiles; g2 += gridDim.x) status[find_block(W.blk_tile, nblk, g2)] = PIVCO_ERR_TIMEOUT;
-            return;
-        }
-        if (in_smem) phase ^= 1;
-        if (bad) {
-            if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
+    }
+    __syncthreads();
+    if (t == 0) {
+        uint32_t acc = 0;
+        for (int d = 0; d < maxd; d++) { const uint32_t u = S.lvl_units[d]; S.lvl_units[d] = acc; acc += u; }
+        S.lvl_units[maxd] = acc;
+        if (acc > (uint32_t)kDMaxUnits) S.overflow = 1;
+    }
+    __syncthreads();
+    if (S.flag) {
+        if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
+        __syncthreads();
+        return true;
+    }
+    if (!S.overflow) {
+        for (uint32_t v = t; v < V; v += kDecThreads) S.ustart[v] += S.lvl_units[S.depth[v]];
+        __syncthreads();
+        if (rank_units(S, src, 0, (int)V, 0, S.lvl_units[maxd], false)) {
+            if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
             __syncthreads();
-            continue;
+            return true;
         }
-        NodeSrc src;
-        src.rec_g = rec_g;
-        src.rb = rb;
-        src.scratch = ws + G.scratch + W.blk_scratch[b];
-        src.scratch_lim = slim;
-        const bool out4 = (reinterpret_cast<uintptr_t>(dst) & 3) == 0;
-        const int maxd = S.ts.max_len;
-        // ---- this tile's bit range of every node ----
-        const uint32_t *cursors = nullptr;   // tile-boundary cursors follow the node directories
-        if (warp == 0 && ntile > 1) {
-            const uint32_t ent = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + kDirBits - 1) / kDirBits; },
-                                                  [&](int, uint32_t) {});
-            if (lane == 0) S.lvl_units[16] = ent;
+        for (int d = maxd - 1; d >= 0; d--) {
+            merge_level(S, src, d, S.lvl_units[d], S.lvl_units[d + 1], dst, P0, out4);
+            __syncthreads();
         }
+    } else {
+        // ---- fallback: chunks whose bit ranges are found top-down ----
+        if (t == 0) S.chunk = max((uint32_t)kDUnit, ((P1 - P0) / 2) & ~(uint32_t)(kDUnit - 1));
         __syncthreads();
-        if (ntile > 1) cursors = reinterpret_cast<const uint32_t *>(ws + G.dir + W.blk_dir[b]) + S.lvl_units[16];
-        for (uint32_t v = t; v < V; v += kDecThreads) {
-            const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
-            const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : S.nv[v];
-            S.cur[v] = cs;
-            S.dem[v] = ce >= cs ? ce - cs : 0u;
-            S.alen[v] = (ce < cs || ce > S.nv[v]) ? 1u : 0u;   // reused as a per-node error mark
-        }
-        if (t == 0) { S.flag = 0; S.overflow = 0; }
-        __syncthreads();
-        for (uint32_t v = t; v < V; v += kDecThreads)
-            if (S.alen[v]) S.flag = 1;
-        if (t == 0 && S.dem[0] != P1 - P0) S.flag = 1;
-        // ---- fast path: spans and units of every depth at once ----
-        for (int d = warp; d < maxd; d += kDecWarps) {
-            const int f0 = S.first[d], f1 = S.first[d + 1];
-            uint64_t carry = 0;
-            for (int base = f0; base < f1; base += 32) {
-                const int v = base + lane;
-                const uint32_t dv = v < f1 ? S.dem[v] : 0u;
-                const uint64_t x = ((uint64_t)((dv + kDUnit - 1) / kDUnit) << 32) | ((dv + 3u) & ~3u);
-                uint64_t inc = x;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
+        for (uint32_t P = P0; P < P1;) {
+            const uint32_t cc = min(S.chunk, P1 - P);
+            if (t == 0) { S.dem[0] = cc; S.lvl_units[0] = 0; S.overflow = 0; }
+            __syncthreads();
+            for (int d = 0; d < maxd; d++) {
+                const int f0 = S.first[d], f1 = S.first[d + 1];
+                if (warp == 0) {
+                    const uint32_t u0 = S.lvl_units[d];
+                    uint64_t carry = 0;
+                    for (int base = f0; base < f1; base += 32) {
+                        const int v = base + lane;
+                        const uint32_t dv = v < f1 ? S.dem[v] : 0u;
+                        const uint64_t x = ((uint64_t)((dv + kDUnit - 1) / kDUnit) << 32) | ((dv + 3u) & ~3u);
+                        uint64_t inc = x;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                            if (lane >= o) inc += y;
+                        }
+                        const uint64_t ex = carry + inc - x;
+                        if (v < f1) { S.span[v] = (uint32_t)ex; S.ustart[v] = u0 + (uint32_t)(ex >> 32); }
+                        carry += __shfl_sync(0xffffffffu, inc, 31);
+                    }
+                    if (lane == 0) {
+                        S.lvl_units[d + 1] = u0 + (uint32_t)(carry >> 32);
+                        if (d > 0 && (uint32_t)carry > (uint32_t)kDLvlCap) S.overflow = 1;
+                        if (S.lvl_units[d + 1] > (uint32_t)kDMaxUnits) S.overflow = 1;
+                    }
                 }
-                const uint64_t ex = carry + inc - x;
-                if (v < f1) { S.span[v] = (uint32_t)ex; S.ustart[v] = (uint32_t)(ex >> 32); }
-                carry += __shfl_sync(0xffffffffu, inc, 31);
+                __syncthreads();
+                if (S.overflow) break;
+                if (rank_units(S, src, f0, f1, S.lvl_units[d], S.lvl_units[d + 1], true)) {
+                    if (t == 0) S.flag = 1;
+                }
+                __syncthreads();
+                if (S.flag) break;
             }
-            if (lane == 0) {
-                S.lvl_units[d] = (uint32_t)(carry >> 32);
-                if (d > 0 && (uint32_t)carry > (uint32_t)kDLvlCap) S.overflow = 1;
+            if (S.flag) break;
+            if (S.overflow) {
+                if (t == 0) S.chunk = max((uint32_t)kDUnit, (S.chunk / 4 * 3) & ~(uint32_t)(kDUnit - 1));
+                __syncthreads();
+                continue;
             }
+            for (int d = maxd - 1; d >= 0; d--) {
+                merge_level(S, src, d, S.lvl_units[d], S.lvl_units[d + 1], dst, P, out4);
+                __syncthreads();
+            }
+            for (uint32_t v = t; v < V; v += kDecThreads) S.cur[v] += S.dem[v];
+            P += cc;
+            __syncthreads();
         }
-        __syncthreads();
-        if (t == 0) {
-            uint32_t acc = 0;
-            for (int d = 0; d < maxd; d++) { const uint32_t u = S.lvl_units[d]; S.lvl_units[d] = acc; acc += u; }
-            S.lvl_units[maxd] = acc;
-            if (acc > (uint32_t)kDMaxUnits) S.overflow = 1;
+        // the chunks must end exactly at the tile's end cursors
+        if (!S.flag) {
+            for (uint32_t v = t; v < V; v += kDecThreads) {
+                const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : S.nv[v];
+                if (S.cur[v] != ce) S.flag = 1;
+            }
         }
         __syncthreads();
         if (S.flag) {
             if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
             __syncthreads();
+            return true;
+        }
+    }
+    // the last tile checks the pad bits of every bitmap
+    if (k + 1 == ntile) {
+        int bad_end = 0;
+        for (uint32_t v = t; v < V && !bad_end; v += kDecThreads) {
+            if (S.nv[v] & 7) {
+                const uint32_t last = node_bits(S, src, (int)v, S.nv[v] & ~7u) & 0xFFu;
+                if (last >> (S.nv[v] & 7)) bad_end = 1;
+            }
+        }
+        bad_end = __syncthreads_or(bad_end);
+        if (t == 0 && bad_end) status[b] = PIVCO_ERR_CORRUPT;
+    }
+    __syncthreads();
+    return true;
+}
+
+__global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const uint8_t *__restrict__ comp,
+                                                                const uint64_t *__restrict__ comp_off,
+                                                                int nblk, uint8_t *__restrict__ out,
+                                                                const uint64_t *__restrict__ out_off,
+                                                                const uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                                int32_t *__restrict__ status) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    DecSmem &S = *reinterpret_cast<DecSmem *>(smem_raw);
+    merge_cta_init(S);
+    uint32_t phase = 0;
+    const uint32_t total_tiles = reinterpret_cast<const uint32_t *>(ws)[6];
+    for (uint32_t gt = blockIdx.x; gt < total_tiles; gt += gridDim.x)
+        if (!tile_item(gt, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S, phase)) return;
+}
+
+// ---------------------------------------------------------------------------
+// Batched decode: one persistent launch over a work queue keyed by
+// (block, stage).  Items, in queue order:
+//   plans      8 blocks per item, one warp each (ticket order = block order,
+//              as the plan's look-back needs)
+//   ANS        8 segments per item, one warp each
+//   directory  one block per item (blocks with one tile skip it)
+//   tiles      one tile per item
+// An item only waits (bounded) on items earlier in the queue: the ANS and
+// later items on all plans; a directory on its block's ANS segments; a tile
+// on its block's ANS segments and directory.  CTAs that took those items are
+// running, so every wait ends.
+// ---------------------------------------------------------------------------
+__device__ inline bool wait_geq(const uint32_t *p, uint32_t want) {
+    if (*reinterpret_cast<const volatile uint32_t *>(p) >= want) { __threadfence(); return true; }
+    const uint64_t t0 = globaltimer_ns();
+    unsigned ns = 64;
+    while (*reinterpret_cast<const volatile uint32_t *>(p) < want) {
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        __nanosleep(ns);
+        if (ns < 2048) ns <<= 1;
+    }
+    __threadfence();
+    return true;
+}
+
+union BatchSmem {
+    DecSmem dec;
+    struct {
+        WarpRec R[kDecWarps];
+        PlanScratch Q[kDecWarps];
+        AnsSm T[kDecWarps];
+    } w;
+};
+
+// plan / ANS items only overwrite the per-tile part of the merge's state
+static_assert(offsetof(DecSmem, sel) >= sizeof(((BatchSmem *)0)->w), "batch scratch overlaps the selectors");
+static_assert(offsetof(DecSmem, mbar) >= sizeof(((BatchSmem *)0)->w), "batch scratch overlaps the mbarrier");
+
+__global__ void __launch_bounds__(kDecThreads, 3) decode_batch_kernel(const uint8_t *__restrict__ comp,
+                                                                      const uint64_t *__restrict__ comp_off, int nblk,
+                                                                      uint8_t *__restrict__ out,
+                                                                      const uint64_t *__restrict__ out_off,
+                                                                      uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                                      int32_t *__restrict__ status,
+                                                                      const __grid_constant__ AnsTables A) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
+    DecSmem &S = B.dec;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
+    const DecWs W = dec_ws(ws, nblk);
+    merge_cta_init(S);
+    uint32_t phase = 0;
+    const uint32_t nplan = (uint32_t)((nblk + kDecWarps - 1) / kDecWarps);
+    int last_b = -1;
+    bool last_ok = false;
+    for (;;) {
+        if (t == 0) S.item = atomicAdd(&hdr[9], 1u);
+        __syncthreads();
+        const uint32_t item = S.item;
+        __syncthreads();
+        if (item < nplan) {
+            // ---- plans ----
+            const int b = (int)(item * kDecWarps + warp);
+            if (b < nblk) plan_block(b, comp, comp_off, nblk, ws, status, B.w.R[warp], B.w.Q[warp]);
+            __syncthreads();
+            if (t == 0) { __threadfence(); atomicAdd(&hdr[10], 1u); }
             continue;
         }
-        if (!S.overflow) {
-            for (uint32_t v = t; v < V; v += kDecThreads) S.ustart[v] += S.lvl_units[S.depth[v]];
-            __syncthreads();
-            const uint32_t nu_all = S.lvl_units[maxd];
-            // unit popcounts of every node (flat)
-            for (uint32_t g = t; g < nu_all; g += kDecThreads) {
-                const int v = find_node_d(S.ustart, 0, (int)V, g);
-                const uint32_t k0 = (g - S.ustart[v]) * kDUnit, dv = S.dem[v], c = S.cur[v];
-                uint32_t pc = 0;
-#pragma unroll
-                for (uint32_t q = 0; q < 4; q++) {
-                    const int64_t e = (int64_t)k0 + 32 * q;
-                    if (e < dv) pc += __popc(mask_valid(node_bits(S, src, v, c + (uint32_t)e), (int64_t)dv - e));
-                }
-                S.ubase[g] = pc;
-                S.umap[g] = (uint8_t)v;
+        // everything after the plans needs all plans
+        int ok = 1;
+        if (t == 0) ok = wait_geq(&hdr[10], nplan);
+        ok = __syncthreads_or(!ok) ? 0 : 1;
+        if (!ok) {
+            if (t == 0) for (int b = 0; b < nblk; b++) if (status[b] == PIVCO_OK) status[b] = PIVCO_ERR_TIMEOUT;
+            return;
+        }
+        const uint32_t total_segs = hdr[2], total_tiles = hdr[6];
+        const uint32_t nseg_items = (total_segs + kDecWarps - 1) / kDecWarps;
+        uint32_t it = item - nplan;
+        if (it < nseg_items) {
+            // ---- ANS segments ----
+            const uint32_t g = it * kDecWarps + warp;
+            if (g < total_segs) {
+                const int b = ans_item(g, comp, comp_off, nblk, ws, ws_bytes, status, A, B.w.R[warp], B.w.T[warp],
+                                       last_b, last_ok);
+                if (lane == 0) { __threadfence(); atomicAdd(&W.segs_done[b], 1u); }
             }
             __syncthreads();
-            // per-node scans (the tile's rank directory); children must match
-            int bad3 = 0;
-            for (int v = warp; v < (int)V; v += kDecWarps) {
-                const uint32_t dv = S.dem[v];
-                uint32_t ones = 0;
-                if (dv) {
-                    const uint32_t u0 = S.ustart[v], nu = (dv + kDUnit - 1) / kDUnit;
-                    ones = warp_scan_loop_d((int)nu, [&](int i) { return S.ubase[u0 + i]; },
-                                            [&](int i, uint32_t p) { S.ubase[u0 + i] = p; });
+            last_b = -1;   // the cached record may be overwritten by a later tile item
+            continue;
+        }
+        it -= nseg_items;
+        if (it < (uint32_t)nblk) {
+            // ---- directory of block it ----
+            const int b = (int)it;
+            if (W.blk_ntile[b] > 1) {
+                const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
+                int okw = 1;
+                if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs);
+                if (__syncthreads_or(!okw)) {
+                    if (t == 0) status[b] = PIVCO_ERR_TIMEOUT;
+                } else {
+                    dir_block(b, comp, comp_off, nblk, ws, ws_bytes, status, S);
                 }
-                if (lane < 2) {
-                    const int ch = S.child[v][lane];
-                    if (ch >= 0 && S.dem[ch] != (lane ? ones : dv - ones)) bad3 = 1;
-                }
+                __syncthreads();
+                if (t == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
             }
-            bad3 = __syncthreads_or(bad3);
-            if (bad3) {
-                if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
+            continue;
+        }
+        it -= (uint32_t)nblk;
+        if (it >= total_tiles) break;
+        // ---- tile it ----
+        {
+            const int b = find_block(W.blk_tile, nblk, it);
+            const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
+            int okw = 1;
+            if (t == 0) {
+                okw = wait_geq(&W.segs_done[b], nsegs);
+                if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u);
+            }
+            if (__syncthreads_or(!okw)) {
+                if (t == 0) status[b] = PIVCO_ERR_TIMEOUT;
                 __syncthreads();
                 continue;
             }
-            for (int d = maxd - 1; d >= 0; d--) {
-                merge_level(S, src, d, S.lvl_units[d], S.lvl_units[d + 1], dst, P0, out4, S.first[d], S.first[d + 1], true);
-                __syncthreads();
-            }
-        } else {
-            // ---- fallback: chunks whose bit ranges are found top-down ----
-            if (t == 0) S.chunk = max((uint32_t)kDUnit, ((P1 - P0) / 2) & ~(uint32_t)(kDUnit - 1));
-            __syncthreads();
-            for (uint32_t P = P0; P < P1;) {
-                const uint32_t cc = min(S.chunk, P1 - P);
-                if (t == 0) { S.dem[0] = cc; S.lvl_units[0] = 0; S.overflow = 0; }
-                __syncthreads();
-                for (int d = 0; d < maxd; d++) {
-                    const int f0 = S.first[d], f1 = S.first[d + 1];
-                    if (warp == 0) {
-                        const uint32_t u0 = S.lvl_units[d];
-                        uint64_t carry = 0;
-                        for (int base = f0; base < f1; base += 32) {
-                            const int v = base + lane;
-                            const uint32_t dv = v < f1 ? S.dem[v] : 0u;
-                            const uint64_t x = ((uint64_t)((dv + kDUnit - 1) / kDUnit) << 32) | ((dv + 3u) & ~3u);
-                            uint64_t inc = x;
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                                if (lane >= o) inc += y;
-                            }
-                            const uint64_t ex = carry + inc - x;
-                            if (v < f1) { S.span[v] = (uint32_t)ex; S.ustart[v] = u0 + (uint32_t)(ex >> 32); }
-                            carry += __shfl_sync(0xffffffffu, inc, 31);
-                        }
-                        if (lane == 0) {
-                            S.lvl_units[d + 1] = u0 + (uint32_t)(carry >> 32);
-                            if (d > 0 && (uint32_t)carry > (uint32_t)kDLvlCap) S.overflow = 1;
-                            if (S.lvl_units[d + 1] > (uint32_t)kDMaxUnits) S.overflow = 1;
-                        }
-                    }
-                    __syncthreads();
-                    if (S.overflow) break;
-                    for (uint32_t g = S.lvl_units[d] + t; g < S.lvl_units[d + 1]; g += kDecThreads) {
-                        const int v = find_node_d(S.ustart, f0, f1, g);
-                        S.umap[g] = (uint8_t)v;
-                        const uint32_t k0 = (g - S.ustart[v]) * kDUnit, dv = S.dem[v], c = S.cur[v];
-                        uint32_t pc = 0;
-#pragma unroll
-                        for (uint32_t q = 0; q < 4; q++) {
-                            const int64_t e = (int64_t)k0 + 32 * q;
-                            if (e < dv) pc += __popc(mask_valid(node_bits(S, src, v, c + (uint32_t)e), (int64_t)dv - e));
-                        }
-                        S.ubase[g] = pc;
-                    }
-                    __syncthreads();
-                    for (int v = f0 + warp; v < f1; v += kDecWarps) {
-                        const uint32_t dv = S.dem[v];
-                        uint32_t ones = 0;
-                        if (dv) {
-                            const uint32_t u0 = S.ustart[v], nu = (dv + kDUnit - 1) / kDUnit;
-                            ones = warp_scan_loop_d((int)nu, [&](int i) { return S.ubase[u0 + i]; },
-                                                    [&](int i, uint32_t p) { S.ubase[u0 + i] = p; });
-                        }
-                        if (lane < 2) {
-                            const int ch = S.child[v][lane];
-                            if (ch >= 0) {
-                                const uint32_t dc = lane ? ones : dv - ones;
-                                S.dem[ch] = dc;
-                                if ((uint64_t)S.cur[ch] + dc > S.nv[ch]) S.flag = 1;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    if (S.flag) break;
-                }
-                if (S.flag) break;
-                if (S.overflow) {
-                    if (t == 0) S.chunk = max((uint32_t)kDUnit, (S.chunk / 4 * 3) & ~(uint32_t)(kDUnit - 1));
-                    __syncthreads();
-                    continue;
-                }
-                for (int d = maxd - 1; d >= 0; d--) {
-                    merge_level(S, src, d, S.lvl_units[d], S.lvl_units[d + 1], dst, P, out4, S.first[d], S.first[d + 1], true);
-                    __syncthreads();
-                }
-                for (uint32_t v = t; v < V; v += kDecThreads) S.cur[v] += S.dem[v];
-                P += cc;
-                __syncthreads();
-            }
-            // the chunks must end exactly at the tile's end cursors
-            if (!S.flag && ntile > 1) {
-                for (uint32_t v = t; v < V; v += kDecThreads)
-                    if (S.cur[v] != cursors[(size_t)(k + 1) * V + v]) S.flag = 1;
-            } else if (!S.flag) {
-                for (uint32_t v = t; v < V; v += kDecThreads)
-                    if (S.cur[v] != S.nv[v]) S.flag = 1;
-            }
-            __syncthreads();
-            if (S.flag) {
-                if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
-                __syncthreads();
-                continue;
-            }
+            if (!tile_item(it, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S, phase)) return;
         }
-        // the last tile checks the pad bits of every bitmap
-        if (k + 1 == ntile) {
-            int bad_end = 0;
-            for (uint32_t v = t; v < V && !bad_end; v += kDecThreads) {
-                if (S.nv[v] & 7) {
-                    const uint32_t last = node_bits(S, src, (int)v, S.nv[v] & ~7u) & 0xFFu;
-                    if (last >> (S.nv[v] & 7)) bad_end = 1;
-                }
-            }
-            bad_end = __syncthreads_or(bad_end);
-            if (t == 0 && bad_end) status[b] = PIVCO_ERR_CORRUPT;
-        }
-        __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static int merge_grid(const void *fn, int smem) {
+    int dev = 0, sms = 148, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kDecThreads, smem);
+    const uint32_t want = current_tuning().ctas_per_sm;
+    if (want && (int)want < occ) occ = (int)want;
+    if (occ < 1) occ = 1;
+    return sms * occ;
 }
 
 cudaError_t launch_decode(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
@@ -973,14 +1158,37 @@ cudaError_t launch_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
     const int smem = (int)sizeof(DecSmem);
     e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148, occ = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel, kDecThreads, smem);
-    if (occ < 1) occ = 1;
-    decode_kernel<<<sms * occ, kDecThreads, smem, st>>>(comp, comp_off, nblk, out, out_off, ws, ws_bytes, status);
+    decode_kernel<<<merge_grid((const void *)decode_kernel, smem), kDecThreads, smem, st>>>(
+        comp, comp_off, nblk, out, out_off, ws, ws_bytes, status);
     count_launches(1);
     return cudaGetLastError();
 }
 
+cudaError_t launch_decode_batch(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
+                                const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
+                                cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    const DecTuning &tu = current_tuning();
+    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max);
+    const int smem = (int)sizeof(BatchSmem);
+    cudaError_t e = cudaFuncSetAttribute(decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    decode_batch_kernel<<<merge_grid((const void *)decode_batch_kernel, smem), kDecThreads, smem, st>>>(
+        comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, host_ans_tables());
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace pv
+
+namespace pv {
+// dynamic shared-memory limits of the decode kernels (set before any capture)
+cudaError_t prepare_decode_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DecSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(decode_dir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DecSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchSmem));
+    return e;
+}
 }  // namespace pv

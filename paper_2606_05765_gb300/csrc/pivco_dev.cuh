@@ -1,5 +1,6 @@
 // Internal definitions shared by the library's kernels (not part of the ABI).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/pivco.h"
@@ -216,21 +217,32 @@ cudaError_t launch_ans_decode(const uint8_t *bodies, const uint64_t *body_off, c
 // ---------------------------------------------------------------------------
 // Decode workspace (written by the decode plan, read by the later passes):
 //   header (64 B): u64 scratch bytes @0, u32 ANS segments @8, u32 ticket @12,
-//                  u64 directory+cursor bytes @16, u32 tiles @24
+//                  u64 directory+cursor bytes @16, u32 tiles @24,
+//                  u32 directory granularity (bits) @28, u32 longest tile @32,
+//                  u32 batch queue ticket @36, u32 batch plans done @40
 //   per block: u64 look-back states A[nblk], B[nblk]; u64 scratch offset[nblk];
 //              u64 directory offset[nblk]; u32 first segment[nblk];
-//              u32 first tile[nblk]; u32 tile length[nblk]; u32 tiles[nblk]
-//   then: ANS segment descriptors (16 B), tile descriptors (8 B: block, index),
-//         rank directories and tile-boundary cursors, ANS-decoded bitmaps.
+//              u32 first tile[nblk]; u32 tile length[nblk]; u32 tiles[nblk];
+//              u32 ANS segments done[nblk]; u32 directory done[nblk]
+//   then: rank directories and tile-boundary cursors, ANS-decoded bitmaps.
 // ---------------------------------------------------------------------------
 struct DecWs {
     uint64_t *states_a, *states_b, *blk_scratch, *blk_dir;
-    uint32_t *blk_seg, *blk_tile, *blk_T, *blk_ntile;
+    uint32_t *blk_seg, *blk_tile, *blk_T, *blk_ntile, *segs_done, *dir_done;
 };
 __host__ __device__ inline size_t decode_ws_fixed_bytes(int nblk) {
-    const size_t f = 64 + 32ull * nblk + 16ull * nblk;
+    const size_t f = 64 + 32ull * nblk + 24ull * nblk;
     return (f + 255) & ~(size_t)255;
 }
+
+// Launch tuning of the decode (never changes the decoded bytes)
+struct DecTuning {
+    uint32_t tile_max;      // longest root tile (symbols), a multiple of 128, <= 65536
+    uint32_t dir_bits;      // rank directory granularity (bits), a multiple of 32, <= 1024
+    uint32_t ctas_per_sm;   // persistent merge CTAs per SM (0: as many as fit)
+};
+const DecTuning &current_tuning();
+void set_tuning(const DecTuning &t);
 __host__ __device__ inline DecWs dec_ws(uint8_t *ws, int nblk) {
     DecWs w;
     w.states_a = reinterpret_cast<uint64_t *>(ws + 64);
@@ -241,31 +253,36 @@ __host__ __device__ inline DecWs dec_ws(uint8_t *ws, int nblk) {
     w.blk_tile = w.blk_seg + nblk;
     w.blk_T = w.blk_tile + nblk;
     w.blk_ntile = w.blk_T + nblk;
+    w.segs_done = w.blk_ntile + nblk;
+    w.dir_done = w.segs_done + nblk;
     return w;
 }
 struct DecRegions {
-    size_t seg_desc, tiles, dir, scratch, need;
+    size_t dir, scratch, need;
 };
 __host__ __device__ inline DecRegions dec_regions(int nblk, const uint8_t *ws_header) {
     const uint64_t scratch = *reinterpret_cast<const uint64_t *>(ws_header);
-    const uint32_t segs = *reinterpret_cast<const uint32_t *>(ws_header + 8);
     const uint64_t dir = *reinterpret_cast<const uint64_t *>(ws_header + 16);
-    const uint32_t tiles = *reinterpret_cast<const uint32_t *>(ws_header + 24);
     DecRegions r;
-    r.seg_desc = decode_ws_fixed_bytes(nblk);
-    r.tiles = (r.seg_desc + 16ull * segs + 15) & ~(size_t)15;
-    r.dir = (r.tiles + 8ull * tiles + 255) & ~(size_t)255;
+    r.dir = decode_ws_fixed_bytes(nblk);
     r.scratch = (r.dir + dir + 255) & ~(size_t)255;
     r.need = r.scratch + scratch;
     return r;
 }
-constexpr int kDirBits = 256;    // rank directory granularity (bits per superblock)
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                size_t ws_bytes, int32_t *status, cudaStream_t st);
 cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st);
 cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                       size_t ws_bytes, int32_t *status, cudaStream_t st);
 cudaError_t launch_decode_merge(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
+                                const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
+                                cudaStream_t st);
+cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
+                              int32_t *status, cudaStream_t st);
+cudaError_t prepare_decode_kernels();
+cudaError_t prepare_encode_kernels();
+cudaError_t prepare_ans_kernels();
+cudaError_t launch_decode_batch(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
                                 const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
                                 cudaStream_t st);
 cudaError_t read_decode_ws_need(const uint8_t *ws, int nblk, size_t *need, cudaStream_t st);
