@@ -154,6 +154,32 @@ pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, 
                                  uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
                                  int32_t *status, void *stream);
 
+/* pivco_decode_blocks without a caller-supplied workspace.  (The paper has
+ * no counterpart: this is an interface convenience of this library.)  It is
+ * for callers that cannot allocate device memory at decode time: a plain C
+ * caller with no device allocator of its own, or a server whose memory is
+ * fully committed to admitted requests, which has nowhere to size a
+ * workspace from.  The workspace is instead one library-owned array in
+ * device memory of PIVCO_DECODE_STATIC_WS_BYTES (16 MiB), created with the
+ * library's module; nothing is allocated per call.
+ *   - The first call on each device looks up that array's address (the
+ *     module loads then) with that device current.  Make that first call
+ *     before any stream capture.
+ *   - nblk whose fixed plan part alone (pivco_decode_plan_bytes) exceeds the
+ *     array returns PIVCO_ERR_CAPACITY without launching anything.  Blocks
+ *     whose ANS scratch or rank directories do not fit in what remains get
+ *     status[b] = PIVCO_ERR_CAPACITY (the others decode normally).
+ *   - The counters and look-back states that must start at zero are cleared
+ *     by the call itself, on `stream`, before its first use of them.
+ *   - There is one array per device: calls whose GPU work overlaps (other
+ *     streams, other host threads) race on it and give undefined results.
+ *     Issue them on one stream, or wait for the previous one.
+ * Other arguments, outputs and statuses as pivco_decode_blocks. */
+#define PIVCO_DECODE_STATIC_WS_BYTES (16u << 20)
+pivco_status pivco_decode_blocks_static(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
+                                        uint8_t *out, const uint64_t *out_off, int32_t *status,
+                                        void *stream);
+
 /* The three steps of pivco_decode_blocks, callable one by one (same
  * arguments and workspace; call them in this order on one stream):
  *   pivco_decode_plan   parses every record header, checks its layout and

@@ -33,6 +33,7 @@ _SIGS = {
     "pivco_ans_encode_blocks": [_P, _I32, _P, _P, _P, _P, _SZ, _P, _P],
     "pivco_decode_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
     "pivco_decode_blocks": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
+    "pivco_decode_blocks_static": [_P, _P, _I32, _P, _P, _P, _P],
     "pivco_decode_plan": [_P, _P, _I32, _P, _SZ, _P, _P],
     "pivco_decode_ans": [_P, _P, _I32, _P, _SZ, _P, _P],
     "pivco_decode_merge": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
@@ -165,6 +166,18 @@ def decode_blocks(comp, comp_off, nblk, out, out_off, ws, status, stream=None, w
     _check(lib().pivco_decode_blocks(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
                                      ws.numel() if ws_bytes is None else ws_bytes, _ptr(status), _stream(stream)),
            "pivco_decode_blocks")
+
+
+DECODE_STATIC_WS_BYTES = 16 << 20
+
+
+def decode_blocks_static(comp, comp_off, nblk, out, out_off, status, stream=None):
+    """pivco_decode_blocks with the library's own 16 MiB device workspace,
+    for callers that cannot allocate one.  Calls whose GPU work overlaps race
+    on that workspace; the first call on a device should precede any stream
+    capture."""
+    _check(lib().pivco_decode_blocks_static(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off),
+                                            _ptr(status), _stream(stream)), "pivco_decode_blocks_static")
 
 
 def decode_plan(comp, comp_off, nblk, ws, status, stream=None):

@@ -81,6 +81,31 @@ const AnsTables &host_ans_tables() {
 
 using namespace pv;
 
+// Library-owned decode workspace for pivco_decode_blocks_static: one array
+// per device, part of this module (no allocation call ever makes it).  Its
+// address is looked up once per device, with that device current.
+static constexpr size_t kStaticWsBytes = 16u << 20;
+static __device__ __align__(256) uint8_t g_static_ws[kStaticWsBytes];
+static constexpr int kMaxDevices = 64;
+static uint8_t *g_static_ws_ptr[kMaxDevices];
+static std::mutex g_static_ws_mu;
+
+static cudaError_t static_ws_address(uint8_t **ptr) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_ws_mu);
+    if (!g_static_ws_ptr[d]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_ws);
+        if (e != cudaSuccess) return e;
+        g_static_ws_ptr[d] = reinterpret_cast<uint8_t *>(p);
+    }
+    *ptr = g_static_ws_ptr[d];
+    return cudaSuccess;
+}
+
 static inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 static inline pivco_status ok_or_cuda(cudaError_t e) { return e == cudaSuccess ? PIVCO_OK : PIVCO_ERR_CUDA; }
 
@@ -163,6 +188,19 @@ pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, 
     if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
     return ok_or_cuda(launch_decode(comp, comp_off, nblk, out, out_off, reinterpret_cast<uint8_t *>(ws), ws_bytes,
                                     status, S(stream)));
+}
+
+pivco_status pivco_decode_blocks_static(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, uint8_t *out,
+                                        const uint64_t *out_off, int32_t *status, void *stream) {
+    static_assert(kStaticWsBytes == PIVCO_DECODE_STATIC_WS_BYTES, "header and library disagree on the size");
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !out_off || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    if (decode_ws_fixed_bytes(nblk) > kStaticWsBytes) return PIVCO_ERR_CAPACITY;
+    uint8_t *ws = nullptr;
+    if (static_ws_address(&ws) != cudaSuccess) return PIVCO_ERR_CUDA;
+    // the plan step's first launch zeroes the header, look-back states and
+    // counters; scratch and directories need no clearing
+    return ok_or_cuda(launch_decode(comp, comp_off, nblk, out, out_off, ws, kStaticWsBytes, status, S(stream)));
 }
 
 pivco_status pivco_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws, size_t ws_bytes,
