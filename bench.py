@@ -45,6 +45,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="skew80", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load time per arrival rate")
     return ap.parse_args(argv)
 
 
@@ -138,6 +140,100 @@ def cpu_baseline(w, budget_s=10.0, ans=False):
     return {"value": raw_all / t_all / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": "first %d of %d blocks (%.1f MB), encode+decode, %.1f s single-threaded"
                       % (used, w.nblk, raw_all / 1e6, t_all)}
+
+
+def serving_leg(P, seconds=2.0, budget=8 << 30, pool_n=48, seed=4):
+    """Poisson decompression requests through the server (device-resident
+    loop, admission by an 8 GiB device budget).  A pool of distinct requests
+    (sizes log-uniform 1 KiB-16 MiB, each drawn from the skew80 / skew95 /
+    mixed distributions) is encoded once; arrivals pick pool entries.  The
+    capacity is measured first (everything submitted at once), then arrivals
+    are offered at 0.5, 0.8 and 0.95 of it.  Latency = result in host memory
+    minus the scheduled arrival."""
+    import ctypes as C
+    import torch
+    import workloads
+    reqs = workloads.serving_requests(pool_n, 1.0, seed=seed)
+    pool = []
+    for r in reqs:
+        data = torch.from_numpy(r.data).cuda()
+        boff = torch.from_numpy(r.blk_off.astype(np.int64)).cuda()
+        enc = P.encode(data, boff, P.params(ans=r.ans))
+        tot = int(enc.off[-1].item())
+        comp = torch.empty(max(tot, 1), dtype=torch.uint8, pin_memory=True)
+        comp[:tot].copy_(enc.comp[:tot])
+        out = torch.zeros(max(r.data.size, 1), dtype=torch.uint8, pin_memory=True)
+        coff = enc.off.cpu().numpy().astype(np.uint64)
+        ooff = r.blk_off.astype(np.uint64)
+        pool.append({"data": r.data, "comp": comp, "out": out, "coff": coff, "ooff": ooff,
+                     "raw": int(r.data.size), "nblk": int(coff.size - 1)})
+    torch.cuda.synchronize()
+    arena = torch.empty(budget + (16 << 20), dtype=torch.uint8, device="cuda")
+    lib = P.lib()
+    rid = C.c_uint64()
+
+    def run(order, arrivals):
+        srv = P.Server(arena, budget_bytes=budget)
+        t_sub, ids = [], []
+        try:
+            t0 = time.perf_counter()
+            i = 0
+            while i < len(order):
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:
+                    if arrivals[i] - now > 2e-4:
+                        time.sleep(1e-4)
+                    continue
+                e = pool[order[i]]
+                rc = lib.pivco_server_submit(srv.handle, C.c_void_p(e["comp"].data_ptr()),
+                                             C.c_void_p(e["coff"].ctypes.data), e["nblk"],
+                                             C.c_void_p(e["ooff"].ctypes.data), C.c_void_p(e["out"].data_ptr()),
+                                             C.byref(rid))
+                if rc != 0:
+                    raise P.PivcoError("pivco_server_submit: %s" % P.STATUS_NAMES.get(rc, rc))
+                t_sub.append(time.perf_counter() - t0)
+                ids.append(rid.value)
+                i += 1
+            srv.drain(600000)
+            t_end = time.perf_counter() - t0
+            lat, bad = [], 0
+            for k, q in enumerate(ids):
+                st, status, l_ms = srv.poll(q)
+                bad += status != 0 or st != P.DONE
+                lat.append(l_ms + 1e3 * (t_sub[k] - arrivals[k]))
+        finally:
+            srv.close()
+        raw = sum(pool[j]["raw"] for j in order)
+        return {"n": len(order), "raw_bytes": raw, "wall_s": t_end, "lat_ms": lat, "bad": bad,
+                "last_done_s": max(arrivals[k] + lat[k] / 1e3 for k in range(len(order)))}
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    burst = [j % pool_n for j in range(4 * pool_n)]
+    run(burst[:pool_n], np.zeros(pool_n))                      # warm-up
+    cap = run(burst, np.zeros(len(burst)))
+    cap_gbs = cap["raw_bytes"] / cap["wall_s"] / 1e9
+    mean_raw = np.mean([e["raw"] for e in pool])
+    rates = []
+    ok = cap["bad"] == 0
+    for frac in (0.5, 0.8, 0.95):
+        lam = frac * cap_gbs * 1e9 / mean_raw                  # requests per second
+        n = int(min(10000, max(200, lam * seconds)))
+        order = rng.integers(0, pool_n, n)
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n))
+        r = run(order, arrivals)
+        ok = ok and r["bad"] == 0
+        span = max(r["last_done_s"], arrivals[-1])
+        rates.append({"load": frac, "requests": n, "offered_gbs": round(r["raw_bytes"] / arrivals[-1] / 1e9, 3),
+                      "gbs": round(r["raw_bytes"] / span / 1e9, 3),
+                      "p50_ms": round(float(np.percentile(r["lat_ms"], 50)), 4),
+                      "p99_ms": round(float(np.percentile(r["lat_ms"], 99)), 4)})
+    for e in pool:
+        n = e["raw"]
+        ok = ok and bool(np.array_equal(e["out"].numpy()[:n], e["data"]))
+    return {"budget_bytes": budget, "pool_requests": pool_n, "capacity_gbs": round(cap_gbs, 3),
+            "capacity_requests": len(burst), "rates": rates, "verified": ok,
+            "latency": "result in pinned host memory minus scheduled arrival",
+            "sizes": "log-uniform 1 KiB-16 MiB; skew80 64 KiB / skew95 128 KiB / mixed 1 MiB blocks"}
 
 
 def make_workload(name, rank=0):
@@ -365,6 +461,11 @@ def main(argv=None):
         e2e = {"value": round(raw / statistics.mean(e2e_t) / 1e9 * world, 3), "unit": "GB/s",
                "h2d_bytes_per_step": raw + enc.comp.numel(), "d2h_bytes_per_step": enc.comp.numel() + raw}
 
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = serving_leg(P, seconds=args.serve_seconds)
+        ok = ok and serving["verified"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, ans=w.ans)
@@ -392,6 +493,7 @@ def main(argv=None):
                          "unit": "GB/s", "frac": r4(ach / peak), "traffic": None,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                          "kernels": {k: {kk: r4(vv) for kk, vv in v.items()} for k, v in kernels.items()}},
+            "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks, "verified": ok,
             "checks": {"batched": ok_b, "plain": ok_p},
         }

@@ -180,6 +180,52 @@ pivco_status pivco_decode_blocks_static(const uint8_t *comp, const uint64_t *com
                                         uint8_t *out, const uint64_t *out_off, int32_t *status,
                                         void *stream);
 
+/* ---- Serving (spec serving pattern; the paper has no serving system) ----
+ * A decompression server: a device-resident request loop (one persistent
+ * kernel that takes the work items of the batched decode, request after
+ * request) fed by a host scheduler thread that admits requests by a device
+ * memory budget.  Continuous batching: a request submitted while others run
+ * is admitted as soon as budget, arena space and a ring entry are free, and
+ * its items run on the device beside those of the requests already there.
+ * No request changes what another decodes: each result is the bytes that
+ * pivco_decode_blocks gives for it alone.
+ *
+ * arena: caller-owned device memory (256-byte aligned) the server lives in:
+ * a control block and a 4096-entry request ring, then per admitted request
+ * its records, offsets, statuses, decode workspace and output.  Nothing is
+ * allocated on the device.  Host side the server allocates pinned mapped
+ * flags, staging and three non-blocking streams, and runs one thread.
+ *
+ * pivco_server_submit: `comp` (host, pinned recommended) holds nblk records,
+ * record b at comp + comp_off[b]; `out` (host, pinned recommended) receives
+ * block b at out + out_off[b]; both must stay valid until the request is
+ * done.  comp_off / out_off (host, nblk + 1 entries) are copied at submit.
+ * *id receives the request id (ids increase by one per submit).  A request
+ * whose device footprint (records + output + offsets + workspace bound)
+ * exceeds the budget returns PIVCO_ERR_CAPACITY.
+ * pivco_server_poll: *state = 0 unknown, 1 pending (not admitted), 2 admitted,
+ * 3 done; for done requests *status = the first non-OK block status (else
+ * PIVCO_OK) and *latency_ms = submit to result-in-host-memory.
+ * pivco_server_drain waits (at most timeout_ms) until every submitted
+ * request is done: PIVCO_ERR_TIMEOUT if not.  pivco_server_forget drops a
+ * done request's record.  Device loop waits are bounded; an expired one ends
+ * as PIVCO_ERR_TIMEOUT in the request's status. */
+typedef struct pivco_server pivco_server;
+typedef struct pivco_server_config {
+    uint64_t budget_bytes;   /* admission budget (0: the whole arena after its control part) */
+    int32_t idle_us;         /* the device loop leaves after this long with nothing to do (default 200) */
+    int32_t epoch_us;        /* lifetime of one loop launch before a fresh one takes over (default 4000) */
+} pivco_server_config;
+pivco_status pivco_server_create(void *arena, size_t arena_bytes, const pivco_server_config *cfg,
+                                 pivco_server **srv);
+pivco_status pivco_server_submit(pivco_server *srv, const uint8_t *comp, const uint64_t *comp_off,
+                                 int32_t nblk, const uint64_t *out_off, uint8_t *out, uint64_t *id);
+pivco_status pivco_server_poll(pivco_server *srv, uint64_t id, int32_t *state, int32_t *status,
+                               double *latency_ms);
+pivco_status pivco_server_drain(pivco_server *srv, int32_t timeout_ms);
+pivco_status pivco_server_forget(pivco_server *srv, uint64_t id);
+pivco_status pivco_server_destroy(pivco_server *srv);
+
 /* The three steps of pivco_decode_blocks, callable one by one (same
  * arguments and workspace; call them in this order on one stream):
  *   pivco_decode_plan   parses every record header, checks its layout and

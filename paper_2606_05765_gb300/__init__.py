@@ -48,6 +48,12 @@ _SIGS = {
     "pivco_graph_end": [_P, _P],
     "pivco_graph_launch": [_P, _P],
     "pivco_graph_destroy": [_P],
+    "pivco_server_create": [_P, _SZ, _P, _P],
+    "pivco_server_submit": [_P, _P, _P, _I32, _P, _P, C.POINTER(C.c_uint64)],
+    "pivco_server_poll": [_P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)],
+    "pivco_server_drain": [_P, _I32],
+    "pivco_server_forget": [_P, C.c_uint64],
+    "pivco_server_destroy": [_P],
 }
 _OTHER = {
     "pivco_version": ([], C.c_char_p),
@@ -259,6 +265,82 @@ class Graph:
     def __del__(self):
         if getattr(self, "handle", None) and self.handle.value and _lib is not None:
             _lib.pivco_graph_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+
+# -------------------------------------------------------------- serving ----
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("idle_us", C.c_int32), ("epoch_us", C.c_int32)]
+
+
+PENDING, ADMITTED, DONE = 1, 2, 3
+
+
+def _host_ptr(a):
+    """Address of a host buffer: a CPU torch tensor (pinned or not) or a numpy array."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise PivcoError("server buffers are host memory")
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+class Server:
+    """Decompression server (pivco_server_*): a device-resident request loop
+    with admission by a device-memory budget.  `arena` is a uint8 CUDA tensor
+    the server lives in; it must outlive the server."""
+
+    def __init__(self, arena, budget_bytes=0, idle_us=200, epoch_us=4000):
+        self.arena = arena
+        self.handle = C.c_void_p()
+        cfg = ServerConfig(budget_bytes, idle_us, epoch_us)
+        _check(lib().pivco_server_create(_ptr(arena), arena.numel(), C.byref(cfg), C.byref(self.handle)),
+               "pivco_server_create")
+        self._keep = {}
+
+    def submit(self, comp, comp_off, out_off, out):
+        """comp / out: host buffers (pinned recommended), kept alive until the
+        request is done; comp_off / out_off: uint64 numpy arrays (nblk + 1)."""
+        co = np.ascontiguousarray(comp_off, np.uint64)
+        oo = np.ascontiguousarray(out_off, np.uint64)
+        rid = C.c_uint64()
+        _check(lib().pivco_server_submit(self.handle, _host_ptr(comp), C.c_void_p(co.ctypes.data), co.size - 1,
+                                         C.c_void_p(oo.ctypes.data), _host_ptr(out), C.byref(rid)),
+               "pivco_server_submit")
+        self._keep[rid.value] = (comp, out)
+        return rid.value
+
+    def poll(self, rid):
+        st, status, lat = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib().pivco_server_poll(self.handle, rid, C.byref(st), C.byref(status), C.byref(lat)),
+               "pivco_server_poll")
+        if st.value == DONE:
+            self._keep.pop(rid, None)
+        return st.value, status.value, lat.value
+
+    def drain(self, timeout_ms=60000):
+        _check(lib().pivco_server_drain(self.handle, timeout_ms), "pivco_server_drain")
+
+    def forget(self, rid):
+        _check(lib().pivco_server_forget(self.handle, rid), "pivco_server_forget")
+
+    def close(self):
+        if self.handle and self.handle.value:
+            rc = lib().pivco_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+            self._keep.clear()
+            _check(rc, "pivco_server_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+        return False
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.pivco_server_destroy(self.handle)
             self.handle = C.c_void_p()
 
 

@@ -38,7 +38,7 @@ constexpr int kDMaxRoot = 65536;             // longest chunk
 constexpr int kDRecSmem = 24576;             // records up to this size are staged in shared memory
 constexpr int kDMaxUnits = kDMaxRoot / kDUnit + 14 * (kDLvlCap / kDUnit) + 256;
 
-__device__ inline uint32_t scratch_stride(uint32_t raw) { return ((raw + 15u) & ~15u) + 16u; }
+__host__ __device__ inline uint32_t scratch_stride(uint32_t raw) { return ((raw + 15u) & ~15u) + 16u; }
 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop_d(int n, F f, G out) {
@@ -1032,6 +1032,107 @@ union BatchSmem {
 static_assert(offsetof(DecSmem, sel) >= sizeof(((BatchSmem *)0)->w), "batch scratch overlaps the selectors");
 static_assert(offsetof(DecSmem, mbar) >= sizeof(((BatchSmem *)0)->w), "batch scratch overlaps the mbarrier");
 
+// One request's (batch's) queue: where its records, output and workspace are.
+struct BatchQueue {
+    const uint8_t *comp;
+    const uint64_t *comp_off;
+    uint8_t *out;
+    const uint64_t *out_off;
+    uint8_t *ws;
+    uint64_t ws_bytes;
+    int32_t *status;
+    int nblk;
+};
+
+// Items of a batch's queue once all plans are done (header written by the last plan).
+__device__ inline uint32_t batch_items_total(const BatchQueue &q) {
+    const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
+    const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
+    return nplan + (hdr[2] + kDecWarps - 1) / kDecWarps + (uint32_t)q.nblk + hdr[6];
+}
+
+enum : int { kItemDone = 0, kItemNone = 1, kItemStop = 2 };
+
+// Runs item `item` of the queue with the whole CTA.  kItemDone: processed;
+// kItemNone: past the end of the queue; kItemStop: a bounded wait expired in a
+// way that leaves this CTA's shared memory unsafe to reuse (a bulk copy may
+// still be in flight), so the CTA must stop.  Statuses of affected blocks are set.
+__device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &B, const AnsTables &A,
+                                 uint32_t &phase, int &last_b, bool &last_ok) {
+    DecSmem &S = B.dec;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nblk = q.nblk;
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
+    const DecWs W = dec_ws(q.ws, nblk);
+    const uint32_t nplan = (uint32_t)((nblk + kDecWarps - 1) / kDecWarps);
+    if (item < nplan) {
+        // ---- plans ----
+        const int b = (int)(item * kDecWarps + warp);
+        if (b < nblk) plan_block(b, q.comp, q.comp_off, nblk, q.ws, q.status, B.w.R[warp], B.w.Q[warp]);
+        __syncthreads();
+        if (t == 0) { __threadfence(); atomicAdd(&hdr[10], 1u); }
+        return kItemDone;
+    }
+    // everything after the plans needs all plans
+    int ok = 1;
+    if (t == 0) ok = wait_geq(&hdr[10], nplan);
+    if (__syncthreads_or(!ok)) {
+        if (t == 0) for (int b = 0; b < nblk; b++) if (q.status[b] == PIVCO_OK) q.status[b] = PIVCO_ERR_TIMEOUT;
+        __syncthreads();
+        return kItemStop;
+    }
+    const uint32_t total_segs = hdr[2], total_tiles = hdr[6];
+    const uint32_t nseg_items = (total_segs + kDecWarps - 1) / kDecWarps;
+    uint32_t it = item - nplan;
+    if (it < nseg_items) {
+        // ---- ANS segments ----
+        const uint32_t g = it * kDecWarps + warp;
+        if (g < total_segs) {
+            const int b = ans_item(g, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, A, B.w.R[warp],
+                                   B.w.T[warp], last_b, last_ok);
+            if (lane == 0) { __threadfence(); atomicAdd(&W.segs_done[b], 1u); }
+        }
+        __syncthreads();
+        last_b = -1;   // the cached record may be overwritten by a later tile item
+        return kItemDone;
+    }
+    it -= nseg_items;
+    if (it < (uint32_t)nblk) {
+        // ---- directory of block it ----
+        const int b = (int)it;
+        if (W.blk_ntile[b] > 1) {
+            const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
+            int okw = 1;
+            if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs);
+            if (__syncthreads_or(!okw)) {
+                if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
+            } else {
+                dir_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, S);
+            }
+            __syncthreads();
+            if (t == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
+        }
+        return kItemDone;
+    }
+    it -= (uint32_t)nblk;
+    if (it >= total_tiles) return kItemNone;
+    // ---- tile it ----
+    const int b = find_block(W.blk_tile, nblk, it);
+    const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
+    int okw = 1;
+    if (t == 0) {
+        okw = wait_geq(&W.segs_done[b], nsegs);
+        if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u);
+    }
+    if (__syncthreads_or(!okw)) {
+        if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
+        __syncthreads();
+        return kItemDone;
+    }
+    return tile_item(it, q.comp, q.comp_off, nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, S, phase)
+               ? kItemDone : kItemStop;
+}
+
 __global__ void __launch_bounds__(kDecThreads, 3) decode_batch_kernel(const uint8_t *__restrict__ comp,
                                                                       const uint64_t *__restrict__ comp_off, int nblk,
                                                                       uint8_t *__restrict__ out,
@@ -1042,87 +1143,156 @@ __global__ void __launch_bounds__(kDecThreads, 3) decode_batch_kernel(const uint
     extern __shared__ __align__(128) uint8_t smem_raw[];
     BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
     DecSmem &S = B.dec;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const BatchQueue q{comp, comp_off, out, out_off, ws, ws_bytes, status, nblk};
     uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
-    const DecWs W = dec_ws(ws, nblk);
     merge_cta_init(S);
     uint32_t phase = 0;
-    const uint32_t nplan = (uint32_t)((nblk + kDecWarps - 1) / kDecWarps);
     int last_b = -1;
     bool last_ok = false;
     for (;;) {
-        if (t == 0) S.item = atomicAdd(&hdr[9], 1u);
+        if (threadIdx.x == 0) S.item = atomicAdd(&hdr[9], 1u);
         __syncthreads();
         const uint32_t item = S.item;
         __syncthreads();
-        if (item < nplan) {
-            // ---- plans ----
-            const int b = (int)(item * kDecWarps + warp);
-            if (b < nblk) plan_block(b, comp, comp_off, nblk, ws, status, B.w.R[warp], B.w.Q[warp]);
-            __syncthreads();
-            if (t == 0) { __threadfence(); atomicAdd(&hdr[10], 1u); }
-            continue;
-        }
-        // everything after the plans needs all plans
-        int ok = 1;
-        if (t == 0) ok = wait_geq(&hdr[10], nplan);
-        ok = __syncthreads_or(!ok) ? 0 : 1;
-        if (!ok) {
-            if (t == 0) for (int b = 0; b < nblk; b++) if (status[b] == PIVCO_OK) status[b] = PIVCO_ERR_TIMEOUT;
-            return;
-        }
-        const uint32_t total_segs = hdr[2], total_tiles = hdr[6];
-        const uint32_t nseg_items = (total_segs + kDecWarps - 1) / kDecWarps;
-        uint32_t it = item - nplan;
-        if (it < nseg_items) {
-            // ---- ANS segments ----
-            const uint32_t g = it * kDecWarps + warp;
-            if (g < total_segs) {
-                const int b = ans_item(g, comp, comp_off, nblk, ws, ws_bytes, status, A, B.w.R[warp], B.w.T[warp],
-                                       last_b, last_ok);
-                if (lane == 0) { __threadfence(); atomicAdd(&W.segs_done[b], 1u); }
-            }
-            __syncthreads();
-            last_b = -1;   // the cached record may be overwritten by a later tile item
-            continue;
-        }
-        it -= nseg_items;
-        if (it < (uint32_t)nblk) {
-            // ---- directory of block it ----
-            const int b = (int)it;
-            if (W.blk_ntile[b] > 1) {
-                const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
-                int okw = 1;
-                if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs);
-                if (__syncthreads_or(!okw)) {
-                    if (t == 0) status[b] = PIVCO_ERR_TIMEOUT;
-                } else {
-                    dir_block(b, comp, comp_off, nblk, ws, ws_bytes, status, S);
-                }
-                __syncthreads();
-                if (t == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
-            }
-            continue;
-        }
-        it -= (uint32_t)nblk;
-        if (it >= total_tiles) break;
-        // ---- tile it ----
-        {
-            const int b = find_block(W.blk_tile, nblk, it);
-            const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
-            int okw = 1;
-            if (t == 0) {
-                okw = wait_geq(&W.segs_done[b], nsegs);
-                if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u);
-            }
-            if (__syncthreads_or(!okw)) {
-                if (t == 0) status[b] = PIVCO_ERR_TIMEOUT;
-                __syncthreads();
-                continue;
-            }
-            if (!tile_item(it, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S, phase)) return;
-        }
+        if (batch_item(q, item, B, A, phase, last_b, last_ok) != kItemDone) return;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a device-resident request loop over the batch queue items.
+// Requests are published by the host in sequence order into a ring (entry r
+// at ring[r % kServeRing], the count in flags->tail, host memory mapped into
+// the device).  Every CTA repeatedly takes the next item of request ctl->cur;
+// when that request has no items left it moves ctl->cur on, so the items of
+// consecutive requests overlap on the device and a request published while
+// others run is picked up by the first CTA that frees up.  The CTA that
+// finishes a request's last item writes its worst block status and then its
+// done flag into mapped host memory.  A CTA leaves when it has found nothing
+// to do for idle_ns, when its launch has lived life_ns (checked between
+// items), or on flags->stop; the host then launches the loop again if work
+// remains.  A request's ring entry and memory are reused only after a launch
+// that started later has ended with ctl->cur past it, so no CTA can still
+// touch them.
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t ld_acquire_sys_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ inline void st_release_sys_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kDecThreads, 3) serve_loop_kernel(ServeCtl *__restrict__ ctl,
+                                                                    const ServeDesc *__restrict__ ring,
+                                                                    ServeFlags *flags, uint64_t idle_ns,
+                                                                    uint64_t life_ns,
+                                                                    const __grid_constant__ AnsTables A) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
+    __shared__ ServeDesc D;
+    __shared__ uint32_t s_cmd, s_item, s_r;
+    const int t = threadIdx.x;
+    merge_cta_init(B.dec);
+    uint32_t phase = 0;
+    int last_b = -1;
+    bool last_ok = false;
+    uint32_t have = 0xFFFFFFFFu;   // request whose ring entry is in D (thread 0's view)
+    uint32_t used = 0xFFFFFFFFu;   // request of the last item (all threads)
+    const uint64_t t0 = globaltimer_ns();
+    uint64_t idle_since = 0;
+    for (;;) {
+        if (t == 0) {
+            uint32_t cmd = 0;   // 0 work, 1 nothing yet, 2 leave
+            const uint64_t now = globaltimer_ns();
+            const uint32_t r = *reinterpret_cast<volatile uint32_t *>(&ctl->cur);
+            const uint32_t tail = ld_acquire_sys_u32(&flags->tail);
+            if (ld_acquire_sys_u32(&flags->stop) || now - t0 > life_ns) {
+                cmd = 2;
+            } else if (r >= tail) {
+                if (!idle_since) idle_since = now;
+                cmd = now - idle_since > idle_ns ? 2u : 1u;
+            } else {
+                idle_since = 0;
+                if (r != have) {
+                    D = ring[r % kServeRing];
+                    if (D.seq != r) cmd = 1;   // not written yet (cannot happen once published)
+                    else have = r;
+                }
+                if (cmd == 0) {
+                    s_item = atomicAdd(&reinterpret_cast<uint32_t *>(D.ws)[9], 1u);
+                    s_r = r;
+                }
+            }
+            s_cmd = cmd;
+        }
+        __syncthreads();
+        const uint32_t cmd = s_cmd, item = s_item, r = s_r;
+        __syncthreads();
+        if (cmd == 2) return;
+        if (cmd == 1) {
+            if (t == 0) __nanosleep(1000);
+            continue;
+        }
+        if (r != used) { last_b = -1; used = r; }
+        const BatchQueue q{D.comp, D.comp_off, D.out, D.out_off, D.ws, D.ws_bytes, D.status, D.nblk};
+        const int res = batch_item(q, item, B, A, phase, last_b, last_ok);
+        if (res == kItemNone) {
+            if (t == 0) atomicCAS(&ctl->cur, r, r + 1);
+            __syncthreads();
+            continue;
+        }
+        if (t == 0) {
+            uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
+            __threadfence();
+            const uint32_t n = atomicAdd(&hdr[11], 1u) + 1;
+            const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
+            if (*reinterpret_cast<volatile uint32_t *>(&hdr[10]) >= nplan) {
+                __threadfence();
+                if (n == batch_items_total(q)) {
+                    int32_t worst = PIVCO_OK;
+                    for (int b = 0; b < q.nblk && worst == PIVCO_OK; b++)
+                        worst = *reinterpret_cast<volatile int32_t *>(&q.status[b]);
+                    flags->worst[r % kServeRing] = worst;
+                    __threadfence_system();
+                    st_release_sys_u32(&flags->done[r % kServeRing], r + 1);
+                }
+            }
+        }
+        if (res == kItemStop) return;   // its shared memory may still receive a bulk copy
+        __syncthreads();
+    }
+}
+
+// Host: an upper bound, from host copies of the records, of the workspace the
+// decode of these blocks needs under tuning `tu` (never below what the plan
+// computes for valid records): the scratch of every ANS-coded node exactly,
+// and rank directories plus tile cursors for the most tiles the plan can
+// choose (a level of a valid record holds at most n symbols).
+size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, const DecTuning &tu) {
+    uint64_t dir = 0, scratch = 0;
+    const uint64_t t_fit = ((uint64_t)(kDLvlCap - 4 * 256) / 5 * 4) & ~(uint64_t)(kDUnit - 1);
+    uint64_t t_min = tu.tile_max < t_fit ? tu.tile_max : t_fit;
+    if (t_min < (uint64_t)kDUnit) t_min = kDUnit;
+    for (int b = 0; b < nblk; b++) {
+        const uint8_t *rec = comp + comp_off[b];
+        const uint64_t avail = comp_off[b + 1] > comp_off[b] ? comp_off[b + 1] - comp_off[b] : 0;
+        if (avail < kNvOff || rec[10] != 2) continue;
+        const uint32_t n = (uint32_t)rec[4] | ((uint32_t)rec[5] << 8) | ((uint32_t)rec[6] << 16) | ((uint32_t)rec[7] << 24);
+        const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
+        if (V < 1 || V > 255 || kNvOff + 5 * V > avail) continue;
+        uint64_t ent = 0;
+        for (uint32_t v = 0; v < V; v++) {
+            const uint8_t *p = rec + kNvOff + 4 * v;
+            const uint32_t nv = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+            const uint8_t m = rec[kNvOff + 4 * V + v];
+            ent += (nv + (uint64_t)tu.dir_bits - 1) / tu.dir_bits;
+            if (m && m != kMarkRawSel) scratch += scratch_stride((nv + 7) / 8);
+        }
+        const uint64_t ntile = ((uint64_t)n + t_min - 1) / t_min;
+        dir += (4 * ent + 4 * (ntile + 1) * V + 15) & ~(uint64_t)15;
+    }
+    return ((decode_ws_fixed_bytes(nblk) + dir + 255) & ~(size_t)255) + scratch + 256;
 }
 
 // ---------------------------------------------------------------------------
@@ -1164,6 +1334,17 @@ cudaError_t launch_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_serve_loop(ServeCtl *ctl, const ServeDesc *ring, ServeFlags *flags, uint64_t idle_ns,
+                              uint64_t life_ns, cudaStream_t st) {
+    const int smem = (int)sizeof(BatchSmem);
+    cudaError_t e = cudaFuncSetAttribute(serve_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    serve_loop_kernel<<<merge_grid((const void *)serve_loop_kernel, smem), kDecThreads, smem, st>>>(
+        ctl, ring, flags, idle_ns, life_ns, host_ans_tables());
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decode_batch(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
                                 const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
                                 cudaStream_t st) {
@@ -1189,6 +1370,8 @@ cudaError_t prepare_decode_kernels() {
         e = cudaFuncSetAttribute(decode_dir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DecSmem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(serve_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchSmem));
     return e;
 }
 }  // namespace pv

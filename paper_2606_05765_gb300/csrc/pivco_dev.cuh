@@ -269,6 +269,35 @@ __host__ __device__ inline DecRegions dec_regions(int nblk, const uint8_t *ws_he
     r.need = r.scratch + scratch;
     return r;
 }
+// ---- serving (device-resident request loop) ----
+constexpr uint32_t kServeRing = 4096;       // ring entries (requests admitted and not yet retired)
+struct ServeDesc {                          // one published request (device memory)
+    const uint8_t *comp;
+    const uint64_t *comp_off;
+    uint8_t *out;
+    const uint64_t *out_off;
+    uint8_t *ws;
+    uint64_t ws_bytes;
+    int32_t *status;
+    int32_t nblk;
+    uint32_t seq;
+};
+static_assert(sizeof(ServeDesc) == 64, "ring entry layout");
+struct ServeCtl {                           // device memory
+    uint32_t cur;                           // requests before cur hand out no more items
+    uint32_t pad[63];
+};
+struct ServeFlags {                         // pinned host memory mapped into the device
+    uint32_t tail;                          // requests published (host writes)
+    uint32_t stop;                          // nonzero: every CTA leaves (host writes)
+    uint32_t pad[30];
+    uint32_t done[kServeRing];              // seq + 1 once request seq is decoded (device writes)
+    int32_t worst[kServeRing];              // its first non-OK block status, else 0 (device writes)
+};
+cudaError_t launch_serve_loop(ServeCtl *ctl, const ServeDesc *ring, ServeFlags *flags, uint64_t idle_ns,
+                              uint64_t life_ns, cudaStream_t st);
+size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, const DecTuning &tu);
+
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                size_t ws_bytes, int32_t *status, cudaStream_t st);
 cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st);
