@@ -46,6 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default decode tuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load time per arrival rate")
     return ap.parse_args(argv)
 
@@ -55,6 +56,23 @@ def shard_blocks(nblk, rank, world):
     per = (nblk + world - 1) // world
     lo = min(nblk, rank * per)
     return lo, min(nblk, lo + per)
+
+
+def reduce_max(value, device=None):
+    """Max over ranks of a per-rank figure (the timed region's duration); the
+    only collective of the multi-GPU bench (blocks shard with no exchange)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(raw_per_rank, steps, tot_ms_max, world):
+    """Whole-job throughput: the bytes all ranks processed / the slowest rank's time."""
+    return world * raw_per_rank * steps / (tot_ms_max / 1e3) / 1e9
 
 
 def measured_peaks():
@@ -317,8 +335,11 @@ def main(argv=None):
         out = torch.empty(raw, dtype=torch.uint8, device=dev)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
         # pick the decode launch tuning for this batch (does not change the bytes)
-        tuned, tuned_ms = P.autotune_decode(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status, reps=2,
-                                            stream=stream)
+        if args.no_autotune:
+            tuned = P.get_tuning()
+        else:
+            tuned, _ = P.autotune_decode(res.comp, res.off, nblk, out, blk_off, dec.ws, dec.status, reps=2,
+                                         stream=stream)
         dec.prepare(res.comp, res.off, stream)
         # batched path: the encode launch sequence and the persistent decode, each a CUDA graph
         n0 = P.launch_count()
@@ -410,12 +431,8 @@ def main(argv=None):
     rec_bytes = int(enc.rec_bytes.sum().item())
 
     def agg(te, td):
-        tot = sum(a + b for a, b in zip(te, td))
-        if world > 1:
-            t = torch.tensor([tot], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return world * raw * len(te) / (tot / 1e3) / 1e9, tot / len(te)
+        tot = reduce_max(sum(a + b for a, b in zip(te, td)), dev)
+        return whole_job_gbs(raw, len(te), tot, world), tot / len(te)
 
     value, ms_step = agg(b_enc, b_dec)
     plain_value, plain_ms = agg(p_enc, p_dec)
