@@ -2,27 +2,30 @@
 // (Sec. 3; Sec. 5.2 for ANS-coded bitmaps).
 //
 //   plan       one warp per record: validates the header and body layout,
-//              sizes the ANS scratch, and splits the block into root tiles
-//              whose levels fit the merge's buffers; per-block offsets come
-//              from two single-pass scans with decoupled look-back.
+//              sizes the ANS scratch, builds the block's node table (bitmap
+//              source and children of every internal node, from the
+//              canonical tree of the code lengths) and splits the block into
+//              root tiles whose levels fit one warp's buffers; per-block
+//              offsets come from two single-pass scans with decoupled look-back.
 //   ans        one warp per 16 KiB ANS segment: decodes the bitmap bytes into
 //              the workspace scratch.
 //   directory  for blocks with several tiles: per-node rank directories
-//              (exclusive popcount per 256-bit superblock) and, from them,
-//              every node's bitmap cursor at every tile boundary (the root
-//              cursor is the position; a child's cursor is the parent's
-//              rank0 / rank1 there).
-//   merge      one CTA per tile (persistent).  With both boundary cursors
-//              known, each node's bit range for the tile is known; its
-//              128-bit units are popcounted in one flat pass and scanned per
-//              node (the tile's rank directory).  Bottom-up, every node
-//              rebuilds its symbol sequence
+//              (exclusive popcount per superblock) and, from them, every
+//              node's bitmap cursor at every tile boundary (the root cursor is
+//              the position; a child's cursor is the parent's rank0 / rank1).
+//   tiles      one warp per tile, independent of the other warps.  With both
+//              boundary cursors known, every node's bit range in the tile is
+//              known.  Bottom-up, level by level, every node rebuilds its
+//              symbol sequence
 //                  out_v[k] = bit ? R[rank1(k)] : L[k - rank1(k)]
-//              from its children's sequences or leaf constants (MVV / MCV /
-//              MVC / MCC of Table 8), 4 symbols per lane with one byte
-//              permute.  The root writes the output.  A tile whose levels do
-//              not fit is decoded in shorter chunks whose bit ranges are
-//              found top-down from popcounts.
+//              from its children's sequences or leaf constants (the MVV /
+//              MCV / MVC / MCC cases of Sec. 3.2).  A lane takes one 32-bit
+//              bitmap word (32 symbols) of one node; ranks come from a
+//              segmented warp scan of the words' popcounts; 4 output symbols
+//              are one byte permute of a left and a right 4-byte window.  The
+//              root writes the output.  A tile whose levels do not fit is
+//              decoded in shorter chunks whose bit ranges are found top-down
+//              from popcounts.
 #include "ans_dev.cuh"
 #include "lookback.cuh"
 #include "tma.cuh"
@@ -31,12 +34,12 @@ namespace pv {
 
 constexpr int kDecThreads = 256;
 constexpr int kDecWarps = kDecThreads / 32;
-constexpr int kDUnit = 128;
-constexpr int kDLvlCap = 14336;              // level buffer capacity (depths >= 1)
-constexpr int kDLvlBytes = kDLvlCap + 16;    // slack for 4-byte windows
-constexpr int kDMaxRoot = 65536;             // longest chunk
-constexpr int kDRecSmem = 24576;             // records up to this size are staged in shared memory
-constexpr int kDMaxUnits = kDMaxRoot / kDUnit + 14 * (kDLvlCap / kDUnit) + 256;
+constexpr int kWBuf = 4864;                  // one level buffer of a warp tile (bytes)
+constexpr int kWSlack = 64;                  // over-read room of the byte windows
+constexpr uint32_t kNtabHdr = 32;            // node table header (see plan_block)
+
+// bytes of a block's node table: header, u32 source and u32 children per node
+__host__ __device__ inline uint32_t ntab_bytes(uint32_t V) { return (kNtabHdr + 8u * V + 15u) & ~15u; }
 
 __host__ __device__ inline uint32_t scratch_stride(uint32_t raw) { return ((raw + 15u) & ~15u) + 16u; }
 
@@ -170,31 +173,47 @@ __device__ inline bool warp_parse(const uint8_t *rec, uint64_t avail, WarpRec &R
 // ---------------------------------------------------------------------------
 // Plan: one warp per record (ticket order), two look-back chains over blocks
 //   A: (ANS scratch bytes << 22) | ANS segments
-//   B: (directory + cursor bytes << 22) | tiles
+//   B: (node table + directory + cursor bytes << 22) | tiles
 // Tuning (from the workspace header): the longest tile and the rank
 // directory granularity; neither changes the decoded bytes.
+//
+// Node table of a coded block (start of its directory region):
+//    0 u8 first[17]   first node of each depth (breadth-first node order)
+//   17 u8 maxd        depth of the deepest leaf
+//   20 u32 ent        rank-directory entries (blocks with several tiles)
+//   24 u32 T          root symbols per tile
+//   32 u32 src[V]     bit address of node v's bitmap: 8 x record byte offset,
+//                     or 8 x block scratch offset | 2^31 for ANS-coded nodes
+//      u32 ch[V]      children: child c in bits [16c, 16c + 16), 0x8000 |
+//                     symbol for a leaf, else the child's node index
 // ---------------------------------------------------------------------------
 struct PlanScratch {
-    uint32_t cntl[16], first[17], lvl[16];
+    uint32_t cntl[16], lvl[16], run[16];
+    int32_t a[17], first[18], start[17];
+    int32_t good, maxd;
+    uint32_t ch[256];
+    uint8_t sorted[256];
 };
 
 __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
-                                  int nblk, uint8_t *__restrict__ ws, int32_t *__restrict__ status, WarpRec &R,
-                                  PlanScratch &Q) {
+                                  int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                                  WarpRec &R, PlanScratch &Q) {
     const int lane = threadIdx.x & 31;
     uint32_t *hdr32 = reinterpret_cast<uint32_t *>(ws);
     uint64_t *hdr64 = reinterpret_cast<uint64_t *>(ws);
     const DecWs W = dec_ws(ws, nblk);
     const uint32_t dir_bits = hdr32[7], tile_max = hdr32[8];
-    if (lane < 16) { Q.cntl[lane] = 0; Q.lvl[lane] = 0; }
+    if (lane < 16) { Q.cntl[lane] = 0; Q.lvl[lane] = 0; Q.run[lane] = 0; }
     __syncwarp();
     const uint8_t *rec = comp + comp_off[b];
     bool ok = warp_parse(rec, comp_off[b + 1] - comp_off[b], R);
     __syncwarp();
-    uint32_t ntile = 1, T = ok ? R.n : 0;
+    uint32_t ntile = 1, T = ok ? R.n : 0, ent = 0;
     uint64_t dir_bytes = 0;
-    if (ok && R.kind == 2) {
-        // node depths from the code lengths (canonical tree shape)
+    const bool coded = ok && R.kind == 2;
+    if (coded) {
+        // canonical tree of the code lengths: a[d] prefixes of depth d are
+        // leaves or under leaves, the others are internal nodes (Sec. 1.1)
         const uint32_t x = ld_le32(rec + kLensOff + 4 * lane);
         for (int j = 0; j < 8; j++) {
             const uint32_t l = (x >> (4 * j)) & 15u;
@@ -202,49 +221,103 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         }
         __syncwarp();
         if (lane == 0) {
-            int64_t a = 0, f = 0;
-            int ml = 0;
-            for (int l = 1; l < 16; l++) if (Q.cntl[l]) ml = l;
-            Q.first[0] = 0;
-            for (int d = 0; d < 16; d++) {
-                if (d > 0) a = 2 * a + Q.cntl[d];
+            int64_t a = 0;
+            int32_t f = 0, base = 0, K = 0, m = 0;
+            bool good = true;
+            Q.start[0] = 0;
+            for (int l = 1; l < 16; l++) { Q.start[l] = base; base += (int32_t)Q.cntl[l]; if (Q.cntl[l]) m = l; }
+            K = base;
+            for (int d = 0; d <= 16; d++) {
+                if (d > 0) a = 2 * a + (d < 16 ? Q.cntl[d] : 0);
+                Q.a[d] = (int32_t)a;
                 const int64_t open = (int64_t(1) << d) - a;
-                if (d < ml) f += open > 0 ? open : 0;
-                Q.first[d + 1] = (uint32_t)(f > 255 ? 255 : f);
+                if (open < 0) good = false;
+                Q.first[d] = f;
+                if (d < m) {
+                    if (open <= 0) good = false;
+                    else f += (int32_t)open;
+                } else if (d == m && open != 0) {
+                    good = false;   // Kraft equality: the tree is full
+                }
             }
+            Q.first[17] = f;
+            Q.good = good && K >= 2 && f == K - 1 && f == (int32_t)R.V;
+            Q.maxd = m;
         }
         __syncwarp();
-        if (Q.first[15] != R.V) ok = false;
-        for (int v = lane; v < (int)R.V && ok; v += 32) {
+        const bool good = Q.good != 0;
+        // symbols in canonical order (length, then value): rounds of 32 symbols
+        for (int j = 0; j < 8; j++) {
+            const int sym = 32 * j + lane;
+            const uint32_t l = (rec[kLensOff + (sym >> 1)] >> (4 * (sym & 1))) & 15u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, l);
+            const uint32_t r = __popc(peers & ((1u << lane) - 1u));
+            if (l && good) Q.sorted[Q.start[l] + Q.run[l] + r] = (uint8_t)sym;
+            __syncwarp();
+            if (l && r == 0) Q.run[l] += __popc(peers);
+            __syncwarp();
+        }
+        // children of every internal node and the symbols of each depth
+        bool okn = good;
+        for (int v = lane; v < (int)R.V && good; v += 32) {
             int d = 0;
-            while (d < 15 && Q.first[d + 1] <= (uint32_t)v) d++;
+            while (d < 15 && Q.first[d + 1] <= v) d++;
             if (d >= 1) atomicAdd(&Q.lvl[d], R.nv[v]);
+            const int32_t p = Q.a[d] + (v - Q.first[d]);
+            uint32_t code2 = 0;
+            for (int c = 0; c < 2; c++) {
+                const int32_t cp = 2 * p + c;
+                uint32_t code = 0;
+                if (cp < Q.a[d + 1]) {             // a leaf of length d + 1
+                    const int32_t i = cp - 2 * Q.a[d];
+                    if (d + 1 > 15 || i < 0 || i >= (int32_t)Q.cntl[d + 1]) okn = false;
+                    else code = 0x8000u | Q.sorted[Q.start[d + 1] + i];
+                } else {
+                    const int32_t node = Q.first[d + 1] + (cp - Q.a[d + 1]);
+                    if (node <= v || node >= (int32_t)R.V) okn = false;
+                    else code = (uint32_t)node;
+                }
+                code2 |= code << (16 * c);
+            }
+            Q.ch[v] = code2;
         }
         __syncwarp();
-        ok = __all_sync(0xffffffffu, ok);
+        ok = __all_sync(0xffffffffu, okn);
         if (ok) {
-            uint64_t mx = 1;
-            for (int d = 1; d < 16; d++) mx = Q.lvl[d] > mx ? Q.lvl[d] : mx;
-            const uint64_t fit = (uint64_t)(kDLvlCap - 4 * 256) * R.n / mx;
-            uint64_t t2 = 0;
-            if (fit < R.n) t2 = fit / 5 * 4;   // several tiles: 20 % headroom against uneven statistics
-            else if (R.n > tile_max) t2 = tile_max;
-            if (t2) {
-                t2 = t2 > (uint64_t)tile_max ? (uint64_t)tile_max : t2;
-                T = (uint32_t)(t2 < (uint64_t)kDUnit ? kDUnit : (t2 & ~(uint64_t)(kDUnit - 1)));
-                ntile = (R.n + T - 1) / T;
-                const uint32_t ent = warp_scan_loop_d((int)R.V, [&](int v) { return (R.nv[v] + dir_bits - 1) / dir_bits; },
-                                                      [&](int, uint32_t) {});
-                dir_bytes = ((4ull * ent + 4ull * (ntile + 1) * R.V) + 15) & ~15ull;
+            // root symbols per tile: every level of a tile must fit one warp's
+            // buffer (with 16-byte rounding per node), with 20 % headroom
+            uint64_t tfit = ~0ull;
+            for (int d = 1; d < 16; d++) {
+                if (!Q.lvl[d]) continue;
+                const uint32_t nodes = (uint32_t)(Q.first[d + 1] - Q.first[d]);
+                const uint64_t room = (uint64_t)kWBuf > 16ull * nodes + 32 ? kWBuf - 16ull * nodes - 32 : 0;
+                const uint64_t t = room * R.n / Q.lvl[d] / 5 * 4;
+                tfit = t < tfit ? t : tfit;
             }
+            if (R.n <= tile_max && tfit >= R.n) {
+                T = R.n;
+                ntile = 1;
+            } else {
+                uint64_t t2 = (tfit < (uint64_t)tile_max ? tfit : (uint64_t)tile_max) & ~127ull;
+                if (t2 < 128) t2 = 128;
+                const uint64_t tmin = ((uint64_t)R.n + (1u << 21) - 1) >> 21;   // at most 2^21 tiles
+                if (t2 < tmin) t2 = (tmin + 127) & ~127ull;
+                T = (uint32_t)t2;
+                ntile = (R.n + T - 1) / T;
+            }
+            if (ntile > 1)
+                ent = warp_scan_loop_d((int)R.V, [&](int v) { return (R.nv[v] + dir_bits - 1) / dir_bits; },
+                                       [&](int, uint32_t) {});
+            dir_bytes = ntab_bytes(R.V) + (ntile > 1 ? ((4ull * ent + 4ull * (ntile + 1) * R.V + 15) & ~15ull) : 0ull);
         }
     }
     const uint64_t sb = ok ? R.scratch_bytes : 0, sg = ok ? R.nsegs : 0;
     if (!ok) { ntile = 1; T = 0; dir_bytes = 0; }
+    uint64_t eb = 0;
     if (lane == 0) {
         int to = 0;
         const uint64_t ea = lookback_exclusive(W.states_a, b, (sb << 22) | sg, &to);
-        const uint64_t eb = lookback_exclusive(W.states_b, b, (dir_bytes << 22) | ntile, &to);
+        eb = lookback_exclusive(W.states_b, b, (dir_bytes << 22) | ntile, &to);
         W.blk_scratch[b] = ea >> 22;
         W.blk_seg[b] = (uint32_t)(ea & ((1u << 22) - 1));
         W.blk_dir[b] = eb >> 22;
@@ -259,18 +332,37 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
             hdr32[6] = (uint32_t)((eb & ((1u << 22) - 1)) + ntile);
         }
     }
+    eb = __shfl_sync(0xffffffffu, eb, 0);
+    // the node table (only where the workspace holds it: a sizing run may not)
+    const uint64_t nbase = decode_ws_fixed_bytes(nblk) + (eb >> 22);
+    if (ok && coded && nbase + ntab_bytes(R.V) <= ws_bytes) {
+        uint8_t *nt = ws + nbase;
+        if (lane < 17) nt[lane] = (uint8_t)Q.first[lane];
+        if (lane == 17) nt[17] = (uint8_t)Q.maxd;
+        if (lane == 0) {
+            *reinterpret_cast<uint32_t *>(nt + 20) = ent;
+            *reinterpret_cast<uint32_t *>(nt + 24) = T;
+        }
+        uint32_t *src = reinterpret_cast<uint32_t *>(nt + kNtabHdr);
+        for (int v = lane; v < (int)R.V; v += 32) {
+            const uint8_t m = R.marker[v];
+            src[v] = (m && m != kMarkRawSel) ? (8u * R.soff[v]) | 0x80000000u : 8u * R.body_off[v];
+            src[R.V + v] = Q.ch[v];
+        }
+    }
     __syncwarp();
 }
 
 __global__ void __launch_bounds__(32) decode_plan_kernel(const uint8_t *__restrict__ comp,
                                                          const uint64_t *__restrict__ comp_off, int nblk,
-                                                         uint8_t *__restrict__ ws, int32_t *__restrict__ status) {
+                                                         uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                         int32_t *__restrict__ status) {
     __shared__ WarpRec R;
     __shared__ PlanScratch Q;
     __shared__ int s_tile;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&reinterpret_cast<uint32_t *>(ws)[3], 1u);
     __syncwarp();
-    plan_block(s_tile, comp, comp_off, nblk, ws, status, R, Q);
+    plan_block(s_tile, comp, comp_off, nblk, ws, ws_bytes, status, R, Q);
 }
 
 // zero the header, the look-back states and the batch counters; set the tuning
@@ -290,11 +382,10 @@ __global__ void dec_ws_init_kernel(uint8_t *ws, int nblk, uint32_t dir_bits, uin
 
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
                                int32_t *status, cudaStream_t st) {
-    (void)ws_bytes;
     if (nblk <= 0) return cudaSuccess;
     const DecTuning &tu = current_tuning();
     dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max);
-    decode_plan_kernel<<<nblk, 32, 0, st>>>(comp, comp_off, nblk, ws, status);
+    decode_plan_kernel<<<nblk, 32, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -405,18 +496,10 @@ cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory state of one CTA working on one block (directory and merge)
+// Shared-memory state of one CTA building one block's rank directory
 // ---------------------------------------------------------------------------
 struct DecSmem {
-    uint8_t rec[kDRecSmem];          // record copy (bulk copy destination, 16-aligned)
-    uint8_t buf[2][kDLvlBytes];      // level buffers (depth d uses buf[d & 1])
-    uint32_t ubase[kDMaxUnits];      // unit popcount, then the unit's rank base within its node
-    uint8_t umap[kDMaxUnits];        // unit -> node
-    uint32_t sel[4][16];             // byte-permute selectors by (node kind, 4 bits)
-    uint32_t cur[256];               // bits of node v consumed before the current chunk
-    uint32_t dem[256];               // bits of node v used by the current chunk
-    uint32_t span[256];              // span of node v in its level buffer
-    uint32_t ustart[256];            // first unit of node v
+    uint32_t ustart[256];            // first directory entry of node v
     uint32_t nv[256];
     uint32_t src_off[256];           // bitmap start: record byte offset or scratch offset
     uint32_t alen[256];
@@ -424,34 +507,24 @@ struct DecSmem {
     int32_t first[17];
     int16_t child[256][2];
     uint8_t depth[256];
-    uint8_t src_kind[256];           // 0: record (shared copy), 1: record (global), 2: scratch
+    uint8_t src_kind[256];           // 1: record, 2: scratch
     uint8_t lens[256];
     uint8_t sorted[256];
     uint8_t marker[256];
     uint16_t codes[256];
     int32_t rank_scratch[256];
     TreeShape ts;
-    uint64_t mbar;
-    int32_t flag;                    // 1 corrupt, 2 capacity
-    int32_t overflow;
-    uint32_t chunk;
-    uint32_t item;                   // batch queue item of this CTA
 };
 
+// 32 bits from bit `bit` of a bitmap at `base` (bytes [0, limit) readable).
+// L2-cached loads: ANS-decoded bitmaps are written earlier in the same launch.
 __device__ inline uint32_t bits32_g(const uint8_t *base, uint64_t bit, uint64_t limit) {
     const uint64_t wi = bit >> 5;
     const uint32_t sh = (uint32_t)(bit & 31);
     const uint32_t *w = reinterpret_cast<const uint32_t *>(base);
-    const uint32_t lo = (4 * wi + 4 <= limit) ? __ldg(w + wi) : 0u;
-    const uint32_t hi = (sh && 4 * wi + 8 <= limit) ? __ldg(w + wi + 1) : 0u;
+    const uint32_t lo = (4 * wi + 4 <= limit) ? __ldcg(w + wi) : 0u;
+    const uint32_t hi = (sh && 4 * wi + 8 <= limit) ? __ldcg(w + wi + 1) : 0u;
     return sh ? __funnelshift_r(lo, hi, sh) : lo;
-}
-__device__ inline uint32_t bits32_s(const uint8_t *base, uint32_t bit, uint32_t limit) {
-    const uint32_t wi = bit >> 5, sh = bit & 31;
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(base);
-    const uint32_t lo = (4 * wi + 4 <= limit) ? w[wi] : 0u;
-    const uint32_t hi = (4 * wi + 8 <= limit) ? w[wi + 1] : 0u;
-    return __funnelshift_r(lo, hi, sh);
 }
 
 struct NodeSrc {
@@ -463,22 +536,13 @@ struct NodeSrc {
 
 // bits [c, c + 32) of node v's bitmap
 __device__ inline uint32_t node_bits(const DecSmem &S, const NodeSrc &src, int v, uint32_t c) {
-    const uint8_t k = S.src_kind[v];
-    if (k == 0) return bits32_s(S.rec, 8u * S.src_off[v] + c, src.rb);
-    if (k == 1) return bits32_g(src.rec_g, 8ull * S.src_off[v] + c, src.rb);
+    if (S.src_kind[v] != 2) return bits32_g(src.rec_g, 8ull * S.src_off[v] + c, src.rb);
     const uint64_t off = S.src_off[v];
     return bits32_g(src.scratch + off, c, src.scratch_lim > off ? src.scratch_lim - off : 0);
 }
 
 __device__ inline uint32_t mask_valid(uint32_t w, int64_t valid) {
     return valid >= 32 ? w : (valid <= 0 ? 0u : (w & ((1u << valid) - 1u)));
-}
-
-// 4 bytes at any byte offset of a level buffer (reads up to 7 bytes past p)
-__device__ inline uint32_t lds4(const uint8_t *p) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~uintptr_t(3));
-    return __funnelshift_r(w[0], w[1], (uint32_t)(a & 3) * 8);
 }
 
 // popcount of bits [0, c) of node v (c <= n_v) from its rank directory
@@ -493,10 +557,9 @@ __device__ inline uint32_t rank1_dir(const DecSmem &S, const NodeSrc &src, const
     return r;
 }
 
-// Per-block setup shared by the directory and merge: tree from the code
-// lengths, node table and bitmap sources.  Returns 0 ok, 1 corrupt, 2
-// workspace too small.  in_smem: the record is being bulk-copied into S.rec.
-__device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb, uint32_t n, uint32_t V, bool in_smem,
+// Per-block setup of the directory pass: tree from the code lengths, node
+// table and bitmap sources.  Returns 0 ok, 1 corrupt, 2 workspace too small.
+__device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb, uint32_t n, uint32_t V, 
                                   uint64_t scratch_lim) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t < 128) {
@@ -538,7 +601,7 @@ __device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb,
             const uint32_t al = S.marker[v] ? ld_le32(rec_g + alen_off + 4 * S.src_off[v]) : raw;
             S.alen[v] = al;
             if (S.marker[v] == kMarkRawSel && al != raw) bad = 1;
-            S.src_kind[v] = (S.marker[v] && S.marker[v] != kMarkRawSel) ? 2 : (in_smem ? 0 : 1);
+            S.src_kind[v] = (S.marker[v] && S.marker[v] != kMarkRawSel) ? 2 : 1;
         }
         __syncwarp();
         const uint32_t base1 = alen_off + 4 * nsel;
@@ -559,8 +622,10 @@ __device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb,
     return (bad & 1) ? 1 : (bad ? 2 : 0);
 }
 
+
 // ---------------------------------------------------------------------------
-// Rank directories and tile-boundary cursors of one block (whole CTA)
+// Rank directories and tile-boundary cursors of one block (whole CTA).  They
+// follow the block's node table in its directory region.
 // ---------------------------------------------------------------------------
 __device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
                                  int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
@@ -575,8 +640,9 @@ __device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const 
     const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
     const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8);
     const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
-    const int bad = block_setup(S, rec_g, rb, n, V, false, slim);
-    if (bad || G.dir + W.blk_dir[b] + 4ull * (ntile + 1) * V > ws_bytes) {
+    const int bad = block_setup(S, rec_g, rb, n, V, slim);
+    const uint64_t dbase = G.dir + W.blk_dir[b] + ntab_bytes(V);
+    if (bad || dbase + 4ull * (ntile + 1) * V > ws_bytes) {
         if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
         __syncthreads();
         return;
@@ -586,7 +652,7 @@ __device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const 
     src.rb = rb;
     src.scratch = ws + G.scratch + W.blk_scratch[b];
     src.scratch_lim = slim;
-    uint32_t *dir = reinterpret_cast<uint32_t *>(ws + G.dir + W.blk_dir[b]);
+    uint32_t *dir = reinterpret_cast<uint32_t *>(ws + dbase);
     // superblocks per node
     if (warp == 0) {
         const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + dir_bits - 1) / dir_bits; },
@@ -596,7 +662,7 @@ __device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const 
     __syncthreads();
     const uint32_t nsb = S.lvl_units[0];
     uint32_t *cursors = dir + nsb;
-    if (G.dir + W.blk_dir[b] + 4ull * nsb + 4ull * (ntile + 1) * V > ws_bytes) {
+    if (dbase + 4ull * nsb + 4ull * (ntile + 1) * V > ws_bytes) {
         if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
         __syncthreads();
         return;
@@ -641,7 +707,7 @@ __device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kDecThreads, 3) decode_dir_kernel(const uint8_t *__restrict__ comp,
+__global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_t *__restrict__ comp,
                                                                     const uint64_t *__restrict__ comp_off, int nblk,
                                                                     uint8_t *__restrict__ ws, uint64_t ws_bytes,
                                                                     int32_t *__restrict__ status) {
@@ -661,57 +727,38 @@ cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = nblk < sms * 3 ? nblk : sms * 3;
+    const int grid = nblk < sms * 4 ? nblk : sms * 4;
     decode_dir_kernel<<<grid, kDecThreads, smem, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
     count_launches(1);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Merge
+// Warp tiles (the bottom-up merge, Sec. 3)
 // ---------------------------------------------------------------------------
-// merge every node of depth d for the current chunk: units g in [g0, g1)
-__device__ inline void merge_level(DecSmem &S, const NodeSrc &src, int d, uint32_t g0, uint32_t g1, uint8_t *dst,
-                                   uint32_t P, bool out4) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint8_t *bin = S.buf[(d + 1) & 1];
-    uint8_t *bout = S.buf[d & 1];
-    for (uint32_t g = g0 + warp; g < g1; g += kDecWarps) {
-        const int v = S.umap[g];
-        const uint32_t k0 = (g - S.ustart[v]) * kDUnit, k = k0 + 4 * lane;
-        const uint32_t dv = S.dem[v], q = lane >> 3;
-        const int64_t e = (int64_t)k0 + 32 * q;
-        const uint32_t wq = e < dv ? mask_valid(node_bits(S, src, v, S.cur[v] + (uint32_t)e), (int64_t)dv - e) : 0u;
-        const uint32_t w0 = __shfl_sync(0xffffffffu, wq, 0), w1 = __shfl_sync(0xffffffffu, wq, 8),
-                       w2 = __shfl_sync(0xffffffffu, wq, 16);
-        if (k >= dv) continue;
-        const uint32_t r1 = S.ubase[g] + (q > 0 ? __popc(w0) : 0) + (q > 1 ? __popc(w1) : 0) + (q > 2 ? __popc(w2) : 0) +
-                            __popc(wq & ((1u << (4 * (lane & 7))) - 1u));
-        const uint32_t nib = (wq >> (4 * (lane & 7))) & 15u;
-        const int c0 = S.child[v][0], c1 = S.child[v][1];
-        const uint32_t xl = c0 >= 0 ? lds4(bin + S.span[c0] + (k - r1)) : (uint32_t)(-c0 - 1) * 0x01010101u;
-        const uint32_t xr = c1 >= 0 ? lds4(bin + S.span[c1] + r1) : (uint32_t)(-c1 - 1) * 0x01010101u;
-        const uint32_t o = __byte_perm(xl, xr, S.sel[(c0 >= 0) | ((c1 >= 0) << 1)][nib]);
-        if (d > 0) {
-            *reinterpret_cast<uint32_t *>(bout + S.span[v] + k) = o;
-        } else {
-            uint8_t *op = dst + P + k;
-            if (out4 && k + 4 <= dv) *reinterpret_cast<uint32_t *>(op) = o;
-            else for (uint32_t j = 0; j < 4 && k + j < dv; j++) op[j] = (uint8_t)(o >> (8 * j));
-        }
-    }
-}
+struct WarpTile {
+    uint8_t buf[2][kWBuf + kWSlack];   // level buffers: depth d writes buf[d & 1]
+    uint32_t pos[256];                 // bit address of node v's next bit (bit 31: in the ANS scratch)
+    uint32_t dem[256];                 // bits of node v in the current chunk
+    uint32_t ch[256];                  // children (node table format)
+    uint16_t sp[256];                  // byte offset of node v's sequence in its level buffer
+    uint16_t gs[256];                  // first 32-symbol group of node v within its level
+    uint16_t lg[16];                   // groups of each level
+    uint8_t first[17];
+    uint8_t maxd;
+    uint8_t pad[14];
+};
+static_assert(sizeof(WarpTile) % 16 == 0, "warp tiles must stay 16-byte aligned");
 
-// One-time CTA setup of the merge: the mbarrier and the byte-permute selectors.
-// Selector of output byte j for 4 bits `nib`: a one takes the next byte of the
-// right window (bytes 4..7), a zero the next byte of the left window (bytes
-// 0..3); a leaf side always takes its constant.
-__device__ inline void merge_cta_init(DecSmem &S) {
+// Byte-permute selectors by (children kind, 4 bitmap bits): a one takes the
+// next byte of the right window (bytes 4..7), a zero the next byte of the
+// left window (bytes 0..3); a leaf side always takes its constant.  Kind bit
+// 0: the left child is a node, bit 1: the right child is.
+__device__ inline void sel_init(uint32_t (*sel)[16]) {
     const int t = threadIdx.x;
-    if (t == 0) mbar_init(&S.mbar, 1);
     if (t < 64) {
-        const int kindsel = t >> 4, nib = t & 15;
-        const bool lint = kindsel & 1, rint = kindsel & 2;
+        const int kd = t >> 4, nib = t & 15;
+        const bool lint = kd & 1, rint = kd & 2;
         uint32_t s = 0, ones = 0, zeros = 0;
         for (int j = 0; j < 4; j++) {
             const uint32_t bit = (nib >> j) & 1u;
@@ -720,291 +767,414 @@ __device__ inline void merge_cta_init(DecSmem &S) {
             ones += bit;
             zeros += 1 - bit;
         }
-        S.sel[kindsel][nib] = s;
+        sel[kd][nib] = s;
     }
-    __syncthreads();
 }
 
-// unit popcounts and per-node scans of the current chunk's units [g0, g1) of
-// the nodes [f0, f1); sets the children's demands when set_children, else
-// checks them.  Returns nonzero on inconsistency.
-__device__ inline int rank_units(DecSmem &S, const NodeSrc &src, int f0, int f1, uint32_t g0, uint32_t g1,
-                                 bool set_children) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (uint32_t g = g0 + t; g < g1; g += kDecThreads) {
-        const int v = find_node_d(S.ustart, f0, f1, g);
-        const uint32_t k0 = (g - S.ustart[v]) * kDUnit, dv = S.dem[v], c = S.cur[v];
-        uint32_t pc = 0;
+struct TileSrc {
+    const uint8_t *rec;
+    const uint8_t *scr;
+    uint64_t scr_bytes;
+    uint32_t rec_bytes;
+};
+
+// 32 bits of a node bitmap from bit address pos + k (bit 31 of pos: scratch)
+__device__ inline uint32_t tile_bits(const TileSrc &s, uint32_t pos, uint32_t k) {
+    const bool sc = (pos >> 31) != 0;
+    const uint64_t e = (uint64_t)(pos & 0x7FFFFFFFu) + k;
+    const uint64_t wi = e >> 5;
+    const uint32_t sh = (uint32_t)e & 31u;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(sc ? s.scr : s.rec);
+    const uint64_t lim = sc ? s.scr_bytes : (uint64_t)s.rec_bytes;
+    const uint32_t lo = 4 * wi + 4 <= lim ? __ldcg(w + wi) : 0u;
+    const uint32_t hi = (sh && 4 * wi + 8 <= lim) ? __ldcg(w + wi + 1) : 0u;
+    return __funnelshift_r(lo, hi, sh);
+}
+
+// 8 bytes of a level buffer from byte a (reads up to 11 bytes past a)
+__device__ inline void win8(const uint8_t *buf, uint32_t a, uint32_t &x0, uint32_t &x1) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(buf + (a & ~3u));
+    const uint32_t sh = (a & 3u) * 8u;
+    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+    x0 = __funnelshift_r(w0, w1, sh);
+    x1 = __funnelshift_r(w1, w2, sh);
+}
+
+// 32 output symbols of a node from bitmap word w: r0 / r1 zeros / ones of the
+// node before this word, i.e. the start of its left / right window.
+__device__ inline void merge32(const WarpTile &S, const uint8_t *bin, uint32_t chv, uint32_t r0, uint32_t r1,
+                               uint32_t w, const uint32_t (*sel)[16], uint32_t (&o)[8]) {
+    const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
+    const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
+    const uint32_t *sk = sel[(i0 ? 1 : 0) | (i1 ? 2 : 0)];
+    uint32_t la = i0 ? min((uint32_t)S.sp[c0 & 0xFFu] + r0, (uint32_t)kWBuf) : 0u;
+    uint32_t ra = i1 ? min((uint32_t)S.sp[c1 & 0xFFu] + r1, (uint32_t)kWBuf) : 0u;
+    const uint32_t kl = (c0 & 0xFFu) * 0x01010101u, kr = (c1 & 0xFFu) * 0x01010101u;
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++) {
-            const int64_t e = (int64_t)k0 + 32 * q;
-            if (e < dv) pc += __popc(mask_valid(node_bits(S, src, v, c + (uint32_t)e), (int64_t)dv - e));
-        }
-        S.ubase[g] = pc;
-        S.umap[g] = (uint8_t)v;
+    for (int q = 0; q < 4; q++) {
+        const uint32_t b8 = (w >> (8 * q)) & 0xFFu;
+        const uint32_t n0 = b8 & 15u, n1 = b8 >> 4;
+        const uint32_t p0 = __popc(n0), p8 = __popc(b8);
+        uint32_t L0 = kl, L1 = kl, R0 = kr, R1 = kr;
+        if (i0) win8(bin, la, L0, L1);
+        if (i1) win8(bin, ra, R0, R1);
+        const uint32_t Lh = __funnelshift_rc(L0, L1, 8u * (4u - p0));
+        const uint32_t Rh = __funnelshift_rc(R0, R1, 8u * p0);
+        o[2 * q] = __byte_perm(L0, R0, sk[n0]);
+        o[2 * q + 1] = __byte_perm(Lh, Rh, sk[n1]);
+        la += 8u - p8;
+        ra += p8;
     }
-    __syncthreads();
-    int bad = 0;
-    for (int v = f0 + warp; v < f1; v += kDecWarps) {
-        const uint32_t dv = S.dem[v];
-        uint32_t ones = 0;
-        if (dv) {
-            const uint32_t u0 = S.ustart[v], nu = (dv + kDUnit - 1) / kDUnit;
-            ones = warp_scan_loop_d((int)nu, [&](int i) { return S.ubase[u0 + i]; },
-                                    [&](int i, uint32_t p) { S.ubase[u0 + i] = p; });
-        }
-        if (lane < 2) {
-            const int ch = S.child[v][lane];
-            if (ch >= 0) {
-                const uint32_t dc = lane ? ones : dv - ones;
-                if (set_children) {
-                    S.dem[ch] = dc;
-                    if ((uint64_t)S.cur[ch] + dc > S.nv[ch]) bad = 1;
-                } else if (S.dem[ch] != dc) {
-                    bad = 1;
-                }
+}
+
+// the children's demands must be the node's zeros and ones
+__device__ inline bool children_ok(const WarpTile &S, uint32_t chv, uint32_t dv, uint32_t ones) {
+    const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
+    bool ok = true;
+    if (!(c0 & 0x8000u)) ok = ok && S.dem[c0] == dv - ones;
+    if (!(c1 & 0x8000u)) ok = ok && S.dem[c1] == ones;
+    return ok;
+}
+
+// up to 32 output bytes at p (any alignment)
+__device__ inline void st_out32(uint8_t *p, const uint32_t (&o)[8], uint32_t valid) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if (valid >= 32 && !(a & 15)) {
+        reinterpret_cast<uint4 *>(p)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<uint4 *>(p)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else if (!(a & 3)) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (4u * j + 4 <= valid) {
+                reinterpret_cast<uint32_t *>(p)[j] = o[j];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+                    if (4u * j + i < valid) p[4 * j + i] = (uint8_t)(o[j] >> (8 * i));
             }
         }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (4u * j + i < valid) p[4 * j + i] = (uint8_t)(o[j] >> (8 * i));
     }
-    return __syncthreads_or(bad);
 }
 
-// Decodes tile gt (whole CTA).  Returns false when a bounded wait expired
-// (the CTA must stop; the affected blocks are marked).
-__device__ inline bool tile_item(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
-                                 int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
-                                 const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
-                                 DecSmem &S, uint32_t &phase) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
-    const DecRegions G = dec_regions(nblk, ws);
-    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
-    const int b = find_block(W.blk_tile, nblk, gt);
-    if (status[b] != PIVCO_OK) return true;   // the plan / ANS / directory pass already failed this block
-    const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
-    const uint8_t *rec_g = comp + comp_off[b];
-    uint8_t *dst = out + out_off[b];
-    const uint64_t ocap = out_off[b + 1] - out_off[b];
-    const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
-    const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8), kind = rec_g[10], aux = rec_g[11];
-    if ((comp_off[b] & 15) || n != ocap) {   // the plan validated magic / size / layout
-        if (t == 0) status[b] = n != ocap ? PIVCO_ERR_CAPACITY : PIVCO_ERR_CORRUPT;
-        return true;
-    }
-    if (kind == 0) return true;
-    if (kind == 1) {
-        for (uint32_t i = t; i < n; i += kDecThreads) dst[i] = (uint8_t)aux;
-        return true;
-    }
-    const uint32_t P0 = k * T, P1 = min(n, P0 + T);
-    // ---- record into shared memory (overlaps the tree construction) ----
-    const bool in_smem = rb <= (uint32_t)kDRecSmem;
-    if (in_smem && t == 0) {
-        fence_proxy_async_smem();
-        mbar_expect_tx(&S.mbar, rb);
-        bulk_g2s(S.rec, rec_g, rb, &S.mbar);
-    }
-    const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
-    const int bad = block_setup(S, rec_g, rb, n, V, in_smem, slim);
-    int timed_out = in_smem ? !mbar_wait(&S.mbar, phase) : 0;
-    timed_out = __syncthreads_or(timed_out);
-    if (timed_out) {
-        mbar_wait(&S.mbar, phase);   // one more bounded wait for the copy before the CTA leaves
-        if (t == 0) status[b] = PIVCO_ERR_TIMEOUT;
-        return false;
-    }
-    if (in_smem) phase ^= 1;
-    if (bad) {
-        if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
-        __syncthreads();
-        return true;
-    }
-    NodeSrc src;
-    src.rec_g = rec_g;
-    src.rb = rb;
-    src.scratch = ws + G.scratch + W.blk_scratch[b];
-    src.scratch_lim = slim;
-    const bool out4 = (reinterpret_cast<uintptr_t>(dst) & 3) == 0;
-    const int maxd = S.ts.max_len;
-    // ---- this tile's bit range of every node ----
-    const uint32_t *cursors = nullptr;   // tile-boundary cursors follow the node directories
-    if (warp == 0 && ntile > 1) {
-        const uint32_t ent = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + dir_bits - 1) / dir_bits; },
-                                              [&](int, uint32_t) {});
-        if (lane == 0) S.lvl_units[16] = ent;
-    }
-    __syncthreads();
-    if (ntile > 1) cursors = reinterpret_cast<const uint32_t *>(ws + G.dir + W.blk_dir[b]) + S.lvl_units[16];
-    for (uint32_t v = t; v < V; v += kDecThreads) {
-        const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
-        const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : S.nv[v];
-        S.cur[v] = cs;
-        S.dem[v] = ce >= cs ? ce - cs : 0u;
-        S.alen[v] = (ce < cs || ce > S.nv[v]) ? 1u : 0u;   // reused as a per-node error mark
-    }
-    if (t == 0) { S.flag = 0; S.overflow = 0; }
-    __syncthreads();
-    for (uint32_t v = t; v < V; v += kDecThreads)
-        if (S.alen[v]) S.flag = 1;
-    if (t == 0 && S.dem[0] != P1 - P0) S.flag = 1;
-    // ---- fast path: spans and units of every depth at once ----
-    for (int d = warp; d < maxd; d += kDecWarps) {
+// Spans and groups of every level for the current demands.  False when a
+// level (depth >= 1) does not fit a buffer.
+__device__ inline bool wt_layout(WarpTile &S) {
+    const int lane = threadIdx.x & 31;
+    bool fits = true;
+    for (int d = 0; d < (int)S.maxd; d++) {
         const int f0 = S.first[d], f1 = S.first[d + 1];
         uint64_t carry = 0;
         for (int base = f0; base < f1; base += 32) {
             const int v = base + lane;
-            const uint32_t dv = v < f1 ? S.dem[v] : 0u;
-            const uint64_t x = ((uint64_t)((dv + kDUnit - 1) / kDUnit) << 32) | ((dv + 3u) & ~3u);
+            uint64_t x = 0;
+            if (v < f1) {
+                const uint32_t dv = S.dem[v];
+                if (d && dv > (uint32_t)kWBuf) fits = false;
+                const uint32_t by = d ? ((min(dv, (uint32_t)kWBuf) + 15u) & ~15u) : 0u;
+                x = ((uint64_t)by << 32) | max(1u, (dv + 31u) >> 5);
+            }
             uint64_t inc = x;
+#pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += y;
             }
             const uint64_t ex = carry + inc - x;
-            if (v < f1) { S.span[v] = (uint32_t)ex; S.ustart[v] = (uint32_t)(ex >> 32); }
+            if (v < f1) {
+                S.sp[v] = (uint16_t)min((uint64_t)kWBuf, ex >> 32);
+                S.gs[v] = (uint16_t)ex;
+            }
             carry += __shfl_sync(0xffffffffu, inc, 31);
         }
+        if (d && (carry >> 32) > (uint64_t)kWBuf) fits = false;
+        if ((uint32_t)carry > 0xFFFFu) fits = false;
+        if (lane == 0) S.lg[d] = (uint16_t)carry;
+    }
+    __syncwarp();
+    return __all_sync(0xffffffffu, fits);
+}
+
+// Demands of a chunk of C root symbols from the current cursors, top-down:
+// a node's popcount over its range splits its demand between its children.
+__device__ inline void wt_demand(WarpTile &S, const TileSrc &src, uint32_t V, uint32_t C) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t v = lane; v < V; v += 32) S.dem[v] = 0;
+    __syncwarp();
+    if (lane == 0) S.dem[0] = C;
+    __syncwarp();
+    for (uint32_t v = 0; v < V; v++) {   // breadth-first: parents before children
+        const uint32_t dv = S.dem[v];
+        uint32_t ones = 0;
+        for (uint32_t e = 32 * lane; e < dv; e += 1024) {
+            uint32_t w = tile_bits(src, S.pos[v], e);
+            if (dv - e < 32) w &= (1u << (dv - e)) - 1u;
+            ones += __popc(w);
+        }
+        ones = __reduce_add_sync(0xffffffffu, ones);
         if (lane == 0) {
-            S.lvl_units[d] = (uint32_t)(carry >> 32);
-            if (d > 0 && (uint32_t)carry > (uint32_t)kDLvlCap) S.overflow = 1;
+            const uint32_t chv = S.ch[v];
+            const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
+            if (!(c0 & 0x8000u)) S.dem[c0] = dv - ones;
+            if (!(c1 & 0x8000u)) S.dem[c1] = ones;
+        }
+        __syncwarp();
+    }
+}
+
+// One level (depth d >= 1) of the current chunk into its buffer.
+__device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const uint32_t (*sel)[16]) {
+    const int lane = threadIdx.x & 31;
+    const uint8_t *bin = S.buf[(d + 1) & 1];
+    uint8_t *bout = S.buf[d & 1];
+    const uint32_t f0 = S.first[d], f1 = S.first[d + 1], G = S.lg[d];
+    const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
+    uint32_t vcur = f0, carry = 0;
+    bool bad = false;
+    for (uint32_t base = 0; base < G; base += 32) {
+        // node of this lane's group: count the nodes that start in the window at or before it
+        const uint32_t cand = vcur + 1 + lane;
+        uint32_t bit = 0;
+        if (cand < f1) {
+            const uint32_t s = (uint32_t)S.gs[cand] - base;
+            if (s < 32) bit = 1u << s;
+        }
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
+        const uint32_t v = vcur + __popc(starts & le);
+        const uint32_t g = base + lane;
+        const uint32_t kk = (g - S.gs[v]) * 32u;
+        const uint32_t dv = S.dem[v];
+        const bool act = g < G && kk < dv;
+        uint32_t w = 0;
+        if (act) {
+            w = tile_bits(src, S.pos[v], kk);
+            if (dv - kk < 32) w &= (1u << (dv - kk)) - 1u;
+        }
+        const uint32_t pc = __popc(w);
+        // ones of the node before this word: segmented scan over the window
+        uint32_t inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t sl = starts & le;
+        const int s0 = sl ? 31 - __clz(sl) : -1;
+        const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
+        const uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u) + (s0 < 0 ? carry : 0u);
+        carry = __shfl_sync(0xffffffffu, r1 + pc, 31);
+        vcur = __shfl_sync(0xffffffffu, v, 31);
+        if (act) {
+            const uint32_t chv = S.ch[v];
+            if (kk + 32 >= dv && !children_ok(S, chv, dv, r1 + pc)) bad = true;
+            uint32_t o[8];
+            merge32(S, bin, chv, kk - r1, r1, w, sel, o);
+            uint8_t *p = bout + S.sp[v] + kk;
+            *reinterpret_cast<uint4 *>(p) = make_uint4(o[0], o[1], o[2], o[3]);
+            if (dv - kk > 16) *reinterpret_cast<uint4 *>(p + 16) = make_uint4(o[4], o[5], o[6], o[7]);
         }
     }
-    __syncthreads();
-    if (t == 0) {
-        uint32_t acc = 0;
-        for (int d = 0; d < maxd; d++) { const uint32_t u = S.lvl_units[d]; S.lvl_units[d] = acc; acc += u; }
-        S.lvl_units[maxd] = acc;
-        if (acc > (uint32_t)kDMaxUnits) S.overflow = 1;
+    return !__any_sync(0xffffffffu, bad);
+}
+
+// The root level of the current chunk into the output.
+__device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, const uint32_t (*sel)[16]) {
+    const int lane = threadIdx.x & 31;
+    const uint8_t *bin = S.buf[1];
+    const uint32_t dv = S.dem[0], chv = S.ch[0], p0 = S.pos[0];
+    uint32_t carry = 0;
+    for (uint32_t kb = 0; kb < dv; kb += 1024) {
+        const uint32_t kk = kb + 32u * lane;
+        const bool act = kk < dv;
+        uint32_t w = 0;
+        if (act) {
+            w = tile_bits(src, p0, kk);
+            if (dv - kk < 32) w &= (1u << (dv - kk)) - 1u;
+        }
+        const uint32_t pc = __popc(w);
+        uint32_t inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t r1 = carry + inc - pc;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+        if (act) {
+            uint32_t o[8];
+            merge32(S, bin, chv, kk - r1, r1, w, sel, o);
+            st_out32(out + kk, o, min(32u, dv - kk));
+        }
     }
-    __syncthreads();
-    if (S.flag) {
-        if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
-        __syncthreads();
-        return true;
+    return children_ok(S, chv, dv, carry);
+}
+
+// fills n bytes at p with x (whole warp)
+__device__ inline void warp_fill(uint8_t *p, uint32_t n, uint8_t x) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t head = min(n, (uint32_t)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15));
+    if (lane < (int)head) p[lane] = x;
+    const uint32_t body = (n - head) / 16;
+    const uint32_t x4 = x * 0x01010101u;
+    uint4 *q = reinterpret_cast<uint4 *>(p + head);
+    for (uint32_t i = lane; i < body; i += 32) q[i] = make_uint4(x4, x4, x4, x4);
+    for (uint32_t i = head + 16 * body + lane; i < n; i += 32) p[i] = x;
+}
+
+// Decodes tile gt of the queue with one warp.
+__device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                                 int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
+                                 const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                                 WarpTile &S, const uint32_t (*sel)[16]) {
+    const int lane = threadIdx.x & 31;
+    const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
+    const DecRegions G = dec_regions(nblk, ws);
+    const int b = find_block(W.blk_tile, nblk, gt);
+    if (*reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
+    const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
+    const uint8_t *rec = comp + comp_off[b];
+    uint8_t *dst = out + out_off[b];
+    const uint64_t ocap = out_off[b + 1] - out_off[b];
+    const uint32_t rb = ld_le32(rec), n = ld_le32(rec + 4);
+    const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8), kind = rec[10], aux = rec[11];
+    if (n != ocap) {                     // the plan validated magic / size / layout
+        if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
+        return;
     }
-    if (!S.overflow) {
-        for (uint32_t v = t; v < V; v += kDecThreads) S.ustart[v] += S.lvl_units[S.depth[v]];
-        __syncthreads();
-        if (rank_units(S, src, 0, (int)V, 0, S.lvl_units[maxd], false)) {
-            if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
-            __syncthreads();
-            return true;
+    if (kind == 0) return;
+    const uint32_t P0 = k * T, P1 = min(n, P0 + T);
+    if (kind == 1) {
+        warp_fill(dst + P0, P1 - P0, (uint8_t)aux);
+        return;
+    }
+    const uint64_t nbase = G.dir + W.blk_dir[b], ntb = ntab_bytes(V);
+    const uint8_t *nt = ws + nbase;
+    const uint32_t ent = nbase + ntb <= ws_bytes ? *reinterpret_cast<const uint32_t *>(nt + 20) : 0u;
+    const uint32_t *cursors = reinterpret_cast<const uint32_t *>(nt + ntb) + ent;
+    if (nbase + ntb > ws_bytes ||
+        (ntile > 1 && nbase + ntb + 4ull * ent + 4ull * (ntile + 1) * V > ws_bytes)) {
+        if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
+        return;
+    }
+    const uint32_t *nsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr);
+    const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
+    if (lane < 17) S.first[lane] = nt[lane];
+    if (lane == 17) S.maxd = nt[17];
+    const uint64_t sbase = G.scratch + W.blk_scratch[b];
+    TileSrc src;
+    src.rec = rec;
+    src.rec_bytes = rb;
+    src.scr = ws + sbase;
+    src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
+    int bad = 0;
+    for (uint32_t v = lane; v < V; v += 32) {
+        const uint32_t nvv = __ldg(nv + v);
+        const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
+        const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : nvv;
+        const uint32_t s0 = nsrc[v];
+        if (ce < cs || ce > nvv || (uint64_t)(s0 & 0x7FFFFFFFu) + nvv >= 0x80000000ull) bad = 1;
+        S.pos[v] = s0 + cs;
+        S.dem[v] = ce - cs;
+        S.ch[v] = nsrc[V + v];
+    }
+    __syncwarp();
+    if (lane == 0 && S.dem[0] != P1 - P0) bad = 1;
+    for (uint32_t v = lane; v < V; v += 32) {   // a child never has more symbols than its parent
+        const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
+        const uint32_t dc = ((c0 & 0x8000u) ? 0u : S.dem[c0]) + ((c1 & 0x8000u) ? 0u : S.dem[c1]);
+        if (dc > S.dem[v]) bad = 1;
+    }
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+        return;
+    }
+    // the whole tile at once when its levels fit, else chunks found top-down
+    uint32_t P = P0, C = P1 - P0;
+    bool chunked = false;
+    while (P < P1) {
+        if (chunked) wt_demand(S, src, V, C);
+        if (!wt_layout(S)) {
+            chunked = true;
+            C = max(32u, (C / 2) & ~31u);
+            continue;
         }
-        for (int d = maxd - 1; d >= 0; d--) {
-            merge_level(S, src, d, S.lvl_units[d], S.lvl_units[d + 1], dst, P0, out4);
-            __syncthreads();
+        bool ok = true;
+        for (int d = (int)S.maxd - 1; d >= 1; d--) {
+            ok = wt_level(S, src, d, sel) && ok;
+            __syncwarp();
         }
-    } else {
-        // ---- fallback: chunks whose bit ranges are found top-down ----
-        if (t == 0) S.chunk = max((uint32_t)kDUnit, ((P1 - P0) / 2) & ~(uint32_t)(kDUnit - 1));
-        __syncthreads();
-        for (uint32_t P = P0; P < P1;) {
-            const uint32_t cc = min(S.chunk, P1 - P);
-            if (t == 0) { S.dem[0] = cc; S.lvl_units[0] = 0; S.overflow = 0; }
-            __syncthreads();
-            for (int d = 0; d < maxd; d++) {
-                const int f0 = S.first[d], f1 = S.first[d + 1];
-                if (warp == 0) {
-                    const uint32_t u0 = S.lvl_units[d];
-                    uint64_t carry = 0;
-                    for (int base = f0; base < f1; base += 32) {
-                        const int v = base + lane;
-                        const uint32_t dv = v < f1 ? S.dem[v] : 0u;
-                        const uint64_t x = ((uint64_t)((dv + kDUnit - 1) / kDUnit) << 32) | ((dv + 3u) & ~3u);
-                        uint64_t inc = x;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                            if (lane >= o) inc += y;
-                        }
-                        const uint64_t ex = carry + inc - x;
-                        if (v < f1) { S.span[v] = (uint32_t)ex; S.ustart[v] = u0 + (uint32_t)(ex >> 32); }
-                        carry += __shfl_sync(0xffffffffu, inc, 31);
-                    }
-                    if (lane == 0) {
-                        S.lvl_units[d + 1] = u0 + (uint32_t)(carry >> 32);
-                        if (d > 0 && (uint32_t)carry > (uint32_t)kDLvlCap) S.overflow = 1;
-                        if (S.lvl_units[d + 1] > (uint32_t)kDMaxUnits) S.overflow = 1;
-                    }
-                }
-                __syncthreads();
-                if (S.overflow) break;
-                if (rank_units(S, src, f0, f1, S.lvl_units[d], S.lvl_units[d + 1], true)) {
-                    if (t == 0) S.flag = 1;
-                }
-                __syncthreads();
-                if (S.flag) break;
-            }
-            if (S.flag) break;
-            if (S.overflow) {
-                if (t == 0) S.chunk = max((uint32_t)kDUnit, (S.chunk / 4 * 3) & ~(uint32_t)(kDUnit - 1));
-                __syncthreads();
-                continue;
-            }
-            for (int d = maxd - 1; d >= 0; d--) {
-                merge_level(S, src, d, S.lvl_units[d], S.lvl_units[d + 1], dst, P, out4);
-                __syncthreads();
-            }
-            for (uint32_t v = t; v < V; v += kDecThreads) S.cur[v] += S.dem[v];
-            P += cc;
-            __syncthreads();
+        ok = wt_root(S, src, dst + P, sel) && ok;
+        if (!ok) {
+            if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+            return;
         }
-        // the chunks must end exactly at the tile's end cursors
-        if (!S.flag) {
-            for (uint32_t v = t; v < V; v += kDecThreads) {
-                const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : S.nv[v];
-                if (S.cur[v] != ce) S.flag = 1;
-            }
-        }
-        __syncthreads();
-        if (S.flag) {
-            if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
-            __syncthreads();
-            return true;
+        for (uint32_t v = lane; v < V; v += 32) S.pos[v] += S.dem[v];
+        __syncwarp();
+        P += C;
+        C = min(C, P1 - P);
+    }
+    if (chunked) {   // the chunks must end exactly at the tile's end cursors
+        for (uint32_t v = lane; v < V; v += 32) {
+            const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : __ldg(nv + v);
+            if (S.pos[v] != nsrc[v] + ce) bad = 1;
         }
     }
     // the last tile checks the pad bits of every bitmap
     if (k + 1 == ntile) {
-        int bad_end = 0;
-        for (uint32_t v = t; v < V && !bad_end; v += kDecThreads) {
-            if (S.nv[v] & 7) {
-                const uint32_t last = node_bits(S, src, (int)v, S.nv[v] & ~7u) & 0xFFu;
-                if (last >> (S.nv[v] & 7)) bad_end = 1;
-            }
+        for (uint32_t v = lane; v < V; v += 32) {
+            const uint32_t nvv = __ldg(nv + v);
+            if ((nvv & 7) && (tile_bits(src, nsrc[v], nvv & ~7u) & 0xFFu) >> (nvv & 7)) bad = 1;
         }
-        bad_end = __syncthreads_or(bad_end);
-        if (t == 0 && bad_end) status[b] = PIVCO_ERR_CORRUPT;
     }
-    __syncthreads();
-    return true;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+    __syncwarp();
 }
 
-__global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const uint8_t *__restrict__ comp,
+struct TileSmem {
+    uint32_t sel[4][16];
+    WarpTile w[kDecWarps];
+};
+
+// Plain tile pass: every warp takes tiles by ticket (workspace header word 12).
+__global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *__restrict__ comp,
                                                                 const uint64_t *__restrict__ comp_off,
                                                                 int nblk, uint8_t *__restrict__ out,
                                                                 const uint64_t *__restrict__ out_off,
-                                                                const uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                                uint8_t *__restrict__ ws, uint64_t ws_bytes,
                                                                 int32_t *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    DecSmem &S = *reinterpret_cast<DecSmem *>(smem_raw);
-    merge_cta_init(S);
-    uint32_t phase = 0;
-    const uint32_t total_tiles = reinterpret_cast<const uint32_t *>(ws)[6];
-    for (uint32_t gt = blockIdx.x; gt < total_tiles; gt += gridDim.x)
-        if (!tile_item(gt, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S, phase)) return;
+    TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
+    sel_init(S.sel);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
+    const uint32_t total_tiles = hdr[6];
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&hdr[12], 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total_tiles) break;
+        warp_tile(it, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S.w[warp], S.sel);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Batched decode: one persistent launch over a work queue keyed by
-// (block, stage).  Items, in queue order:
+// (block, stage).  CTA items, in queue order:
 //   plans      8 blocks per item, one warp each (ticket order = block order,
 //              as the plan's look-back needs)
 //   ANS        8 segments per item, one warp each
 //   directory  one block per item (blocks with one tile skip it)
-//   tiles      one tile per item
-// An item only waits (bounded) on items earlier in the queue: the ANS and
-// later items on all plans; a directory on its block's ANS segments; a tile
-// on its block's ANS segments and directory.  CTAs that took those items are
-// running, so every wait ends.
+// then warp items: tiles, one per warp.  A CTA turns to tiles once the CTA
+// items are all taken.  An item only waits (bounded) on items earlier in the
+// queue: the ANS and later items on all plans; a directory on its block's ANS
+// segments; a tile on its block's ANS segments and directory.  The CTAs that
+// took those items are running, so every wait ends.
 // ---------------------------------------------------------------------------
 __device__ inline bool wait_geq(const uint32_t *p, uint32_t want) {
     if (*reinterpret_cast<const volatile uint32_t *>(p) >= want) { __threadfence(); return true; }
@@ -1019,18 +1189,20 @@ __device__ inline bool wait_geq(const uint32_t *p, uint32_t want) {
     return true;
 }
 
-union BatchSmem {
-    DecSmem dec;
-    struct {
-        WarpRec R[kDecWarps];
-        PlanScratch Q[kDecWarps];
-        AnsSm T[kDecWarps];
-    } w;
+struct PlanAnsSmem {
+    WarpRec R[kDecWarps];
+    PlanScratch Q[kDecWarps];
+    AnsSm T[kDecWarps];
 };
-
-// plan / ANS items only overwrite the per-tile part of the merge's state
-static_assert(offsetof(DecSmem, sel) >= sizeof(((BatchSmem *)0)->w), "batch scratch overlaps the selectors");
-static_assert(offsetof(DecSmem, mbar) >= sizeof(((BatchSmem *)0)->w), "batch scratch overlaps the mbarrier");
+union BatchUnion {
+    DecSmem dir;
+    PlanAnsSmem pa;
+    WarpTile tw[kDecWarps];
+};
+struct BatchSmem {
+    uint32_t sel[4][16];
+    BatchUnion u;
+};
 
 // One request's (batch's) queue: where its records, output and workspace are.
 struct BatchQueue {
@@ -1053,13 +1225,11 @@ __device__ inline uint32_t batch_items_total(const BatchQueue &q) {
 
 enum : int { kItemDone = 0, kItemNone = 1, kItemStop = 2 };
 
-// Runs item `item` of the queue with the whole CTA.  kItemDone: processed;
-// kItemNone: past the end of the queue; kItemStop: a bounded wait expired in a
-// way that leaves this CTA's shared memory unsafe to reuse (a bulk copy may
-// still be in flight), so the CTA must stop.  Statuses of affected blocks are set.
-__device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &B, const AnsTables &A,
-                                 uint32_t &phase, int &last_b, bool &last_ok) {
-    DecSmem &S = B.dec;
+// Runs CTA item `item` of the queue with the whole CTA.  kItemDone: processed;
+// kItemNone: no CTA items left (tiles follow); kItemStop: the wait for the
+// plans expired (every block is marked), the CTA must stop.
+__device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &B, const AnsTables &A, int &last_b,
+                                 bool &last_ok) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int nblk = q.nblk;
     uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
@@ -1068,7 +1238,7 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
     if (item < nplan) {
         // ---- plans ----
         const int b = (int)(item * kDecWarps + warp);
-        if (b < nblk) plan_block(b, q.comp, q.comp_off, nblk, q.ws, q.status, B.w.R[warp], B.w.Q[warp]);
+        if (b < nblk) plan_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.pa.R[warp], B.u.pa.Q[warp]);
         __syncthreads();
         if (t == 0) { __threadfence(); atomicAdd(&hdr[10], 1u); }
         return kItemDone;
@@ -1081,19 +1251,19 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
         __syncthreads();
         return kItemStop;
     }
-    const uint32_t total_segs = hdr[2], total_tiles = hdr[6];
+    const uint32_t total_segs = hdr[2];
     const uint32_t nseg_items = (total_segs + kDecWarps - 1) / kDecWarps;
     uint32_t it = item - nplan;
     if (it < nseg_items) {
         // ---- ANS segments ----
         const uint32_t g = it * kDecWarps + warp;
         if (g < total_segs) {
-            const int b = ans_item(g, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, A, B.w.R[warp],
-                                   B.w.T[warp], last_b, last_ok);
+            const int b = ans_item(g, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, A, B.u.pa.R[warp],
+                                   B.u.pa.T[warp], last_b, last_ok);
             if (lane == 0) { __threadfence(); atomicAdd(&W.segs_done[b], 1u); }
         }
         __syncthreads();
-        last_b = -1;   // the cached record may be overwritten by a later tile item
+        last_b = -1;   // the cached record may be overwritten by a later item
         return kItemDone;
     }
     it -= nseg_items;
@@ -1107,33 +1277,35 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
             if (__syncthreads_or(!okw)) {
                 if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
             } else {
-                dir_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, S);
+                dir_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.dir);
             }
             __syncthreads();
             if (t == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
         }
         return kItemDone;
     }
-    it -= (uint32_t)nblk;
-    if (it >= total_tiles) return kItemNone;
-    // ---- tile it ----
-    const int b = find_block(W.blk_tile, nblk, it);
-    const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
-    int okw = 1;
-    if (t == 0) {
-        okw = wait_geq(&W.segs_done[b], nsegs);
-        if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u);
-    }
-    if (__syncthreads_or(!okw)) {
-        if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
-        __syncthreads();
-        return kItemDone;
-    }
-    return tile_item(it, q.comp, q.comp_off, nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, S, phase)
-               ? kItemDone : kItemStop;
+    return kItemNone;
 }
 
-__global__ void __launch_bounds__(kDecThreads, 3) decode_batch_kernel(const uint8_t *__restrict__ comp,
+// Tile `it` of the queue with one warp, after its block's ANS segments and
+// directory (bounded waits; an expired one marks the block).
+__device__ inline void batch_tile(const BatchQueue &q, uint32_t it, WarpTile &S, const uint32_t (*sel)[16]) {
+    const int lane = threadIdx.x & 31;
+    const DecWs W = dec_ws(q.ws, q.nblk);
+    const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
+    const int b = find_block(W.blk_tile, q.nblk, it);
+    const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
+    int okw = 1;
+    if (lane == 0) {
+        okw = wait_geq(&W.segs_done[b], nsegs);
+        if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u);
+        if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
+    }
+    if (!__shfl_sync(0xffffffffu, okw, 0)) return;
+    warp_tile(it, q.comp, q.comp_off, q.nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, S, sel);
+}
+
+__global__ void __launch_bounds__(kDecThreads, 2) decode_batch_kernel(const uint8_t *__restrict__ comp,
                                                                       const uint64_t *__restrict__ comp_off, int nblk,
                                                                       uint8_t *__restrict__ out,
                                                                       const uint64_t *__restrict__ out_off,
@@ -1142,19 +1314,30 @@ __global__ void __launch_bounds__(kDecThreads, 3) decode_batch_kernel(const uint
                                                                       const __grid_constant__ AnsTables A) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
-    DecSmem &S = B.dec;
+    __shared__ uint32_t s_item;
     const BatchQueue q{comp, comp_off, out, out_off, ws, ws_bytes, status, nblk};
     uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
-    merge_cta_init(S);
-    uint32_t phase = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    sel_init(B.sel);
     int last_b = -1;
     bool last_ok = false;
     for (;;) {
-        if (threadIdx.x == 0) S.item = atomicAdd(&hdr[9], 1u);
+        if (threadIdx.x == 0) s_item = atomicAdd(&hdr[9], 1u);
         __syncthreads();
-        const uint32_t item = S.item;
+        const uint32_t item = s_item;
         __syncthreads();
-        if (batch_item(q, item, B, A, phase, last_b, last_ok) != kItemDone) return;
+        const int r = batch_item(q, item, B, A, last_b, last_ok);
+        if (r == kItemStop) return;
+        if (r == kItemNone) break;
+    }
+    // tiles: every warp on its own
+    const uint32_t total_tiles = hdr[6];
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&hdr[12], 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total_tiles) break;
+        batch_tile(q, it, B.u.tw[warp], B.sel);
     }
 }
 
@@ -1183,7 +1366,24 @@ __device__ inline void st_release_sys_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kDecThreads, 3) serve_loop_kernel(ServeCtl *__restrict__ ctl,
+// Counts one finished item of request r; the item that completes the
+// request's queue writes its worst block status, then its done flag.
+__device__ inline void serve_item_done(const BatchQueue &q, uint32_t r, ServeFlags *flags) {
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
+    __threadfence();
+    const uint32_t n = atomicAdd(&hdr[11], 1u) + 1;
+    const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
+    if (*reinterpret_cast<volatile uint32_t *>(&hdr[10]) < nplan) return;   // totals not known yet: not the last
+    __threadfence();
+    if (n != batch_items_total(q)) return;
+    int32_t worst = PIVCO_OK;
+    for (int b = 0; b < q.nblk && worst == PIVCO_OK; b++) worst = *reinterpret_cast<volatile int32_t *>(&q.status[b]);
+    flags->worst[r % kServeRing] = worst;
+    __threadfence_system();
+    st_release_sys_u32(&flags->done[r % kServeRing], r + 1);
+}
+
+__global__ void __launch_bounds__(kDecThreads, 2) serve_loop_kernel(ServeCtl *__restrict__ ctl,
                                                                     const ServeDesc *__restrict__ ring,
                                                                     ServeFlags *flags, uint64_t idle_ns,
                                                                     uint64_t life_ns,
@@ -1192,9 +1392,8 @@ __global__ void __launch_bounds__(kDecThreads, 3) serve_loop_kernel(ServeCtl *__
     BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
     __shared__ ServeDesc D;
     __shared__ uint32_t s_cmd, s_item, s_r;
-    const int t = threadIdx.x;
-    merge_cta_init(B.dec);
-    uint32_t phase = 0;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    sel_init(B.sel);
     int last_b = -1;
     bool last_ok = false;
     uint32_t have = 0xFFFFFFFFu;   // request whose ring entry is in D (thread 0's view)
@@ -1236,30 +1435,27 @@ __global__ void __launch_bounds__(kDecThreads, 3) serve_loop_kernel(ServeCtl *__
         }
         if (r != used) { last_b = -1; used = r; }
         const BatchQueue q{D.comp, D.comp_off, D.out, D.out_off, D.ws, D.ws_bytes, D.status, D.nblk};
-        const int res = batch_item(q, item, B, A, phase, last_b, last_ok);
-        if (res == kItemNone) {
-            if (t == 0) atomicCAS(&ctl->cur, r, r + 1);
+        const int res = batch_item(q, item, B, A, last_b, last_ok);
+        if (res != kItemNone) {
+            if (t == 0) serve_item_done(q, r, flags);
+            if (res == kItemStop) return;
             __syncthreads();
             continue;
         }
-        if (t == 0) {
-            uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
-            __threadfence();
-            const uint32_t n = atomicAdd(&hdr[11], 1u) + 1;
-            const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
-            if (*reinterpret_cast<volatile uint32_t *>(&hdr[10]) >= nplan) {
-                __threadfence();
-                if (n == batch_items_total(q)) {
-                    int32_t worst = PIVCO_OK;
-                    for (int b = 0; b < q.nblk && worst == PIVCO_OK; b++)
-                        worst = *reinterpret_cast<volatile int32_t *>(&q.status[b]);
-                    flags->worst[r % kServeRing] = worst;
-                    __threadfence_system();
-                    st_release_sys_u32(&flags->done[r % kServeRing], r + 1);
-                }
-            }
+        // the request's CTA items are all taken: its tiles, every warp on its own
+        uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
+        const uint32_t total_tiles = hdr[6];
+        for (;;) {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(&hdr[12], 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= total_tiles) break;
+            batch_tile(q, it, B.u.tw[warp], B.sel);
+            if (lane == 0) serve_item_done(q, r, flags);
+            __syncwarp();
         }
-        if (res == kItemStop) return;   // its shared memory may still receive a bulk copy
+        __syncthreads();
+        if (t == 0) atomicCAS(&ctl->cur, r, r + 1);
         __syncthreads();
     }
 }
@@ -1271,9 +1467,11 @@ __global__ void __launch_bounds__(kDecThreads, 3) serve_loop_kernel(ServeCtl *__
 // choose (a level of a valid record holds at most n symbols).
 size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, const DecTuning &tu) {
     uint64_t dir = 0, scratch = 0;
-    const uint64_t t_fit = ((uint64_t)(kDLvlCap - 4 * 256) / 5 * 4) & ~(uint64_t)(kDUnit - 1);
+    // the shortest tile the plan can choose: a level of at most 128 nodes and
+    // at most n symbols in a buffer, 20 % headroom, a multiple of 128
+    const uint64_t t_fit = ((uint64_t)(kWBuf - 16 * 128 - 32) / 5 * 4) & ~127ull;
     uint64_t t_min = tu.tile_max < t_fit ? tu.tile_max : t_fit;
-    if (t_min < (uint64_t)kDUnit) t_min = kDUnit;
+    if (t_min < 128) t_min = 128;
     for (int b = 0; b < nblk; b++) {
         const uint8_t *rec = comp + comp_off[b];
         const uint64_t avail = comp_off[b + 1] > comp_off[b] ? comp_off[b + 1] - comp_off[b] : 0;
@@ -1289,8 +1487,9 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
             ent += (nv + (uint64_t)tu.dir_bits - 1) / tu.dir_bits;
             if (m && m != kMarkRawSel) scratch += scratch_stride((nv + 7) / 8);
         }
-        const uint64_t ntile = ((uint64_t)n + t_min - 1) / t_min;
-        dir += (4 * ent + 4 * (ntile + 1) * V + 15) & ~(uint64_t)15;
+        uint64_t ntile = ((uint64_t)n + t_min - 1) / t_min;
+        if (ntile > (1u << 21)) ntile = 1u << 21;
+        dir += ntab_bytes(V) + ((4 * ent + 4 * (ntile + 1) * V + 15) & ~(uint64_t)15);
     }
     return ((decode_ws_fixed_bytes(nblk) + dir + 255) & ~(size_t)255) + scratch + 256;
 }
@@ -1325,7 +1524,7 @@ cudaError_t launch_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
     if (nblk <= 0) return cudaSuccess;
     cudaError_t e = launch_decode_dir(comp, comp_off, nblk, ws, ws_bytes, status, st);
     if (e != cudaSuccess) return e;
-    const int smem = (int)sizeof(DecSmem);
+    const int smem = (int)sizeof(TileSmem);
     e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     decode_kernel<<<merge_grid((const void *)decode_kernel, smem), kDecThreads, smem, st>>>(
@@ -1365,7 +1564,7 @@ cudaError_t launch_decode_batch(const uint8_t *comp, const uint64_t *comp_off, i
 namespace pv {
 // dynamic shared-memory limits of the decode kernels (set before any capture)
 cudaError_t prepare_decode_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DecSmem));
+    cudaError_t e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(decode_dir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DecSmem));
     if (e == cudaSuccess)
