@@ -329,7 +329,7 @@ def main(argv=None):
         enc.ensure(enc.plan(data, blk_off, stream))
         res = enc.run(data, blk_off, stream, replan=False)
         dec = P.Decoder(nblk, dev)
-        P.set_tuning(16384, 256, 0)        # the largest workspace any autotuner candidate needs
+        P.set_tuning(16384, 64, 0)         # the largest workspace any autotuner candidate needs
         dec.prepare(res.comp, res.off, stream)
         P.set_tuning()
         out = torch.empty(raw, dtype=torch.uint8, device=dev)

@@ -63,7 +63,7 @@ static void build_tables() {
 static std::atomic<uint64_t> g_launches{0};
 
 // launch tuning of the decode (process-wide; set by pivco_set_tuning / the autotuner)
-static DecTuning g_tuning = {65536, 256, 0};
+static DecTuning g_tuning = {65536, 128, 0};
 static std::mutex g_tuning_mu;
 const DecTuning &current_tuning() { return g_tuning; }
 void set_tuning(const DecTuning &t) {
@@ -336,7 +336,7 @@ pivco_status pivco_autotune_decode(const uint8_t *comp, const uint64_t *comp_off
                                    void *stream, pivco_tuning *best, float *best_ms) {
     if (nblk <= 0 || !comp || !comp_off || !out_off || !ws || !status || !best || reps < 1) return PIVCO_ERR_INVALID_ARG;
     static const uint32_t tiles[] = {16384, 32768, 65536};
-    static const uint32_t dirs[] = {256, 512, 1024};
+    static const uint32_t dirs[] = {64, 128, 256};
     static const uint32_t ctas[] = {0, 2};
     const DecTuning saved = current_tuning();
     cudaEvent_t e0, e1;

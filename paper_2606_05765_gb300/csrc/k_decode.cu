@@ -496,244 +496,6 @@ cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory state of one CTA building one block's rank directory
-// ---------------------------------------------------------------------------
-struct DecSmem {
-    uint32_t ustart[256];            // first directory entry of node v
-    uint32_t nv[256];
-    uint32_t src_off[256];           // bitmap start: record byte offset or scratch offset
-    uint32_t alen[256];
-    uint32_t lvl_units[17];
-    int32_t first[17];
-    int16_t child[256][2];
-    uint8_t depth[256];
-    uint8_t src_kind[256];           // 1: record, 2: scratch
-    uint8_t lens[256];
-    uint8_t sorted[256];
-    uint8_t marker[256];
-    uint16_t codes[256];
-    int32_t rank_scratch[256];
-    TreeShape ts;
-};
-
-// 32 bits from bit `bit` of a bitmap at `base` (bytes [0, limit) readable).
-// L2-cached loads: ANS-decoded bitmaps are written earlier in the same launch.
-__device__ inline uint32_t bits32_g(const uint8_t *base, uint64_t bit, uint64_t limit) {
-    const uint64_t wi = bit >> 5;
-    const uint32_t sh = (uint32_t)(bit & 31);
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(base);
-    const uint32_t lo = (4 * wi + 4 <= limit) ? __ldcg(w + wi) : 0u;
-    const uint32_t hi = (sh && 4 * wi + 8 <= limit) ? __ldcg(w + wi + 1) : 0u;
-    return sh ? __funnelshift_r(lo, hi, sh) : lo;
-}
-
-struct NodeSrc {
-    const uint8_t *rec_g;
-    const uint8_t *scratch;
-    uint64_t scratch_lim;
-    uint32_t rb;
-};
-
-// bits [c, c + 32) of node v's bitmap
-__device__ inline uint32_t node_bits(const DecSmem &S, const NodeSrc &src, int v, uint32_t c) {
-    if (S.src_kind[v] != 2) return bits32_g(src.rec_g, 8ull * S.src_off[v] + c, src.rb);
-    const uint64_t off = S.src_off[v];
-    return bits32_g(src.scratch + off, c, src.scratch_lim > off ? src.scratch_lim - off : 0);
-}
-
-__device__ inline uint32_t mask_valid(uint32_t w, int64_t valid) {
-    return valid >= 32 ? w : (valid <= 0 ? 0u : (w & ((1u << valid) - 1u)));
-}
-
-// popcount of bits [0, c) of node v (c <= n_v) from its rank directory
-__device__ inline uint32_t rank1_dir(const DecSmem &S, const NodeSrc &src, const uint32_t *dir, int v, uint32_t c,
-                                     uint32_t dir_bits) {
-    const uint32_t nsb = (S.nv[v] + dir_bits - 1) / dir_bits;
-    uint32_t sb = c / dir_bits;
-    if (sb >= nsb) sb = nsb - 1;
-    const uint32_t base = sb * dir_bits;
-    uint32_t r = dir[sb];
-    for (uint32_t e = base; e < c; e += 32) r += __popc(mask_valid(node_bits(S, src, v, e), (int64_t)c - e));
-    return r;
-}
-
-// Per-block setup of the directory pass: tree from the code lengths, node
-// table and bitmap sources.  Returns 0 ok, 1 corrupt, 2 workspace too small.
-__device__ inline int block_setup(DecSmem &S, const uint8_t *rec_g, uint32_t rb, uint32_t n, uint32_t V, 
-                                  uint64_t scratch_lim) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t < 128) {
-        const uint8_t x = rec_g[kLensOff + t];
-        S.lens[2 * t] = x & 15;
-        S.lens[2 * t + 1] = x >> 4;
-    }
-    __syncthreads();
-    build_tree_shape(S.lens, S.ts, S.codes, S.sorted, S.rank_scratch);
-    if (!S.ts.ok || (uint32_t)S.ts.n_int != V) return 1;
-    if (t < 17) S.first[t] = S.ts.first[t];
-    if (t < (int)V) {
-        const int d = node_depth(S.ts, t);
-        S.depth[t] = (uint8_t)d;
-        S.child[t][0] = (int16_t)node_child(S.ts, S.sorted, t, d, 0);
-        S.child[t][1] = (int16_t)node_child(S.ts, S.sorted, t, d, 1);
-        S.nv[t] = ld_le32(rec_g + kNvOff + 4 * t);
-        S.marker[t] = rec_g[kNvOff + 4 * V + t];
-    }
-    __syncthreads();
-    int bad = 0;
-    if (t < (int)V) {
-        const uint32_t nvv = S.nv[t];
-        if (nvv < 2) bad = 1;
-        for (int c = 0; c < 2; c++) {
-            const int ch = S.child[t][c];
-            if (ch >= 0 && S.nv[ch] > nvv) bad = 1;
-        }
-    }
-    if (t == 0 && S.nv[0] != n) bad = 1;
-    if (warp == 0) {
-        const int Vi = (int)V;
-        const uint32_t alen_off = (kNvOff + 5 * V + 3) & ~3u;
-        const uint32_t nsel = warp_scan_loop_d(Vi, [&](int v) { return (uint32_t)(S.marker[v] != 0); },
-                                               [&](int v, uint32_t p) { S.src_off[v] = p; });
-        __syncwarp();
-        for (int v = lane; v < Vi; v += 32) {
-            const uint32_t raw = (S.nv[v] + 7) / 8;
-            const uint32_t al = S.marker[v] ? ld_le32(rec_g + alen_off + 4 * S.src_off[v]) : raw;
-            S.alen[v] = al;
-            if (S.marker[v] == kMarkRawSel && al != raw) bad = 1;
-            S.src_kind[v] = (S.marker[v] && S.marker[v] != kMarkRawSel) ? 2 : 1;
-        }
-        __syncwarp();
-        const uint32_t base1 = alen_off + 4 * nsel;
-        const uint32_t raw_tot = warp_scan_loop_d(Vi, [&](int v) { return S.marker[v] ? 0u : S.alen[v]; },
-                                                  [&](int v, uint32_t p) { if (!S.marker[v]) S.src_off[v] = base1 + p; });
-        const uint32_t base2 = base1 + raw_tot;
-        const uint32_t sel_tot = warp_scan_loop_d(Vi, [&](int v) { return S.marker[v] ? S.alen[v] : 0u; },
-                                                  [&](int v, uint32_t p) { if (S.marker[v] == kMarkRawSel) S.src_off[v] = base2 + p; });
-        const uint32_t scr_tot = warp_scan_loop_d(Vi, [&](int v) {
-            return S.src_kind[v] == 2 ? scratch_stride((S.nv[v] + 7) / 8) : 0u;
-        }, [&](int v, uint32_t p) { if (S.src_kind[v] == 2) S.src_off[v] = p; });
-        if (lane == 0) {
-            if (((base2 + sel_tot + 15u) & ~15u) != rb) bad = 1;
-            if (scr_tot > scratch_lim) bad |= 2;
-        }
-    }
-    bad = __syncthreads_or(bad);
-    return (bad & 1) ? 1 : (bad ? 2 : 0);
-}
-
-
-// ---------------------------------------------------------------------------
-// Rank directories and tile-boundary cursors of one block (whole CTA).  They
-// follow the block's node table in its directory region.
-// ---------------------------------------------------------------------------
-__device__ inline void dir_block(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
-                                 int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
-                                 DecSmem &S) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const DecWs W = dec_ws(ws, nblk);
-    const DecRegions G = dec_regions(nblk, ws);
-    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
-    const uint32_t ntile = W.blk_ntile[b];
-    if (ntile <= 1 || status[b] != PIVCO_OK) return;
-    const uint8_t *rec_g = comp + comp_off[b];
-    const uint32_t rb = ld_le32(rec_g), n = ld_le32(rec_g + 4);
-    const uint32_t V = (uint32_t)rec_g[8] | ((uint32_t)rec_g[9] << 8);
-    const uint64_t slim = ws_bytes > G.scratch + W.blk_scratch[b] ? ws_bytes - G.scratch - W.blk_scratch[b] : 0;
-    const int bad = block_setup(S, rec_g, rb, n, V, slim);
-    const uint64_t dbase = G.dir + W.blk_dir[b] + ntab_bytes(V);
-    if (bad || dbase + 4ull * (ntile + 1) * V > ws_bytes) {
-        if (t == 0) status[b] = bad == 1 ? PIVCO_ERR_CORRUPT : PIVCO_ERR_CAPACITY;
-        __syncthreads();
-        return;
-    }
-    NodeSrc src;
-    src.rec_g = rec_g;
-    src.rb = rb;
-    src.scratch = ws + G.scratch + W.blk_scratch[b];
-    src.scratch_lim = slim;
-    uint32_t *dir = reinterpret_cast<uint32_t *>(ws + dbase);
-    // superblocks per node
-    if (warp == 0) {
-        const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (S.nv[v] + dir_bits - 1) / dir_bits; },
-                                              [&](int v, uint32_t p) { S.ustart[v] = p; });
-        if (lane == 0) S.lvl_units[0] = tot;
-    }
-    __syncthreads();
-    const uint32_t nsb = S.lvl_units[0];
-    uint32_t *cursors = dir + nsb;
-    if (dbase + 4ull * nsb + 4ull * (ntile + 1) * V > ws_bytes) {
-        if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
-        __syncthreads();
-        return;
-    }
-    for (uint32_t g = t; g < nsb; g += kDecThreads) {
-        const int v = find_node_d(S.ustart, 0, (int)V, g);
-        const uint32_t e0 = (g - S.ustart[v]) * dir_bits, nvv = S.nv[v];
-        uint32_t pc = 0;
-        for (uint32_t e = e0; e < e0 + dir_bits && e < nvv; e += 32)
-            pc += __popc(mask_valid(node_bits(S, src, v, e), (int64_t)nvv - e));
-        dir[g] = pc;
-    }
-    __syncthreads();
-    for (int v = warp; v < (int)V; v += kDecWarps) {
-        const uint32_t u0 = S.ustart[v], nu = (S.nv[v] + dir_bits - 1) / dir_bits;
-        warp_scan_loop_d((int)nu, [&](int i) { return dir[u0 + i]; }, [&](int i, uint32_t p) { dir[u0 + i] = p; });
-    }
-    // boundary 0: all cursors 0; boundary ntile: n_v; root cursor at boundary k: k * T
-    for (uint32_t v = t; v < V; v += kDecThreads) { cursors[v] = 0; cursors[(size_t)ntile * V + v] = S.nv[v]; }
-    const uint32_t T = W.blk_T[b];
-    for (uint32_t k = 1 + t; k < ntile; k += kDecThreads) cursors[(size_t)k * V] = k * T;
-    __syncthreads();
-    // top-down by depth: children's cursors from the parent's rank at its cursor
-    const int maxd = S.ts.max_len;
-    int bad2 = 0;
-    for (int d = 0; d < maxd; d++) {
-        const uint32_t f0 = S.first[d], nd = S.first[d + 1] - f0;
-        for (uint32_t i = t; i < (ntile - 1) * nd; i += kDecThreads) {
-            const uint32_t k = 1 + i / nd;
-            const int v = (int)(f0 + i % nd);
-            const uint32_t c = cursors[(size_t)k * V + v];
-            if (c > S.nv[v]) { bad2 = 1; continue; }
-            const uint32_t ones = rank1_dir(S, src, dir + S.ustart[v], v, c, dir_bits);
-            const int c0 = S.child[v][0], c1 = S.child[v][1];
-            if (c0 >= 0) cursors[(size_t)k * V + c0] = c - ones;
-            if (c1 >= 0) cursors[(size_t)k * V + c1] = ones;
-        }
-        __syncthreads();
-    }
-    bad2 = __syncthreads_or(bad2);
-    if (t == 0 && bad2) status[b] = PIVCO_ERR_CORRUPT;
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_t *__restrict__ comp,
-                                                                    const uint64_t *__restrict__ comp_off, int nblk,
-                                                                    uint8_t *__restrict__ ws, uint64_t ws_bytes,
-                                                                    int32_t *__restrict__ status) {
-    extern __shared__ __align__(128) uint8_t smem_raw[];
-    DecSmem &S = *reinterpret_cast<DecSmem *>(smem_raw);
-    const DecWs W = dec_ws(ws, nblk);
-    for (int b = blockIdx.x; b < nblk; b += gridDim.x)
-        if (W.blk_ntile[b] > 1) dir_block(b, comp, comp_off, nblk, ws, ws_bytes, status, S);
-}
-
-cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
-                              int32_t *status, cudaStream_t st) {
-    if (nblk <= 0) return cudaSuccess;
-    const int smem = (int)sizeof(DecSmem);
-    cudaError_t e = cudaFuncSetAttribute(decode_dir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = nblk < sms * 4 ? nblk : sms * 4;
-    decode_dir_kernel<<<grid, kDecThreads, smem, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Warp tiles (the bottom-up merge, Sec. 3)
 // ---------------------------------------------------------------------------
 struct WarpTile {
@@ -1135,12 +897,193 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Rank directory and tile-boundary cursors of one block (whole CTA).  They
+// follow the block's node table in its directory region:
+//   dir[u_v + i]   ones of node v before its superblock i (dir_bits bits each)
+//   cur[k V + v]   node v's bitmap cursor at tile boundary k (k = 0..ntile)
+// The root's cursor at boundary k is k T; top-down, a child's cursor is the
+// parent's rank0 / rank1 there (Sec. 3.2's running counts, made random-access).
+// The superblocks of all nodes, node after node, are cut into one contiguous
+// part per warp; each warp scans its part, and the parts' carries are added
+// to the first node of the following parts.
+// ---------------------------------------------------------------------------
+struct DirSmem {
+    uint32_t u[256];        // first superblock of node v
+    uint32_t nv[256];
+    uint32_t src[256];
+    uint32_t ch[256];
+    uint32_t first_node[kDecWarps], last_node[kDecWarps], tail[kDecWarps], add[kDecWarps];
+    uint8_t first[17];
+    uint8_t maxd;
+    int32_t bad;
+};
+
+__device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                               int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                               DirSmem &D) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const DecWs W = dec_ws(ws, nblk);
+    const DecRegions G = dec_regions(nblk, ws);
+    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
+    const uint32_t ntile = W.blk_ntile[b], T = W.blk_T[b];
+    if (ntile <= 1) return;
+    // one decision for the whole CTA (every thread reaches the same barriers)
+    if (__syncthreads_or(*reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK)) return;
+    const uint8_t *rec = comp + comp_off[b];
+    const uint32_t rb = ld_le32(rec);
+    const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
+    const uint64_t nbase = G.dir + W.blk_dir[b], ntb = ntab_bytes(V);
+    const uint8_t *nt = ws + nbase;
+    const uint32_t ent = nbase + ntb <= ws_bytes ? *reinterpret_cast<const uint32_t *>(nt + 20) : 0u;
+    if (nbase + ntb + 4ull * ent + 4ull * (ntile + 1) * V > ws_bytes) {
+        __syncthreads();
+        if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
+        return;
+    }
+    uint32_t *dirp = reinterpret_cast<uint32_t *>(ws + nbase + ntb);
+    uint32_t *cur = dirp + ent;
+    const uint32_t *nsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr);
+    const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
+    const uint64_t sbase = G.scratch + W.blk_scratch[b];
+    TileSrc src;
+    src.rec = rec;
+    src.rec_bytes = rb;
+    src.scr = ws + sbase;
+    src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
+    if (t < 17) D.first[t] = nt[t];
+    if (t == 17) D.maxd = nt[17];
+    if (t == 0) D.bad = 0;
+    for (uint32_t v = t; v < V; v += kDecThreads) {
+        D.nv[v] = __ldg(nv + v);
+        D.src[v] = nsrc[v];
+        D.ch[v] = nsrc[V + v];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (D.nv[v] + dir_bits - 1) / dir_bits; },
+                                              [&](int v, uint32_t p) { D.u[v] = p; });
+        if (lane == 0 && tot != ent) D.bad = 1;
+    }
+    __syncthreads();
+    if (D.bad) {
+        if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
+        __syncthreads();
+        return;
+    }
+    // phase 1: superblock popcounts scanned within each node, per part
+    const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
+    const uint32_t g0 = (uint32_t)((uint64_t)ent * warp / kDecWarps), g1 = (uint32_t)((uint64_t)ent * (warp + 1) / kDecWarps);
+    {
+        uint32_t vcur = (uint32_t)find_node_d(D.u, 0, (int)V, g0), carry = 0;
+        if (lane == 0) D.first_node[warp] = vcur;
+        for (uint32_t base = g0; base < g1; base += 32) {
+            const uint32_t cand = vcur + 1 + lane;
+            uint32_t bit = 0;
+            if (cand < V) {
+                const uint32_t s = D.u[cand] - base;
+                if (s < 32) bit = 1u << s;
+            }
+            const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
+            const uint32_t v = vcur + __popc(starts & le);
+            const uint32_t g = base + lane;
+            uint32_t pc = 0;
+            if (g < g1) {
+                const uint32_t e0 = (g - D.u[v]) * dir_bits, nvv = D.nv[v], s0 = D.src[v];
+                for (uint32_t e = e0; e < e0 + dir_bits && e < nvv; e += 32) {
+                    uint32_t w = tile_bits(src, s0, e);
+                    if (nvv - e < 32) w &= (1u << (nvv - e)) - 1u;
+                    pc += __popc(w);
+                }
+            }
+            uint32_t inc = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t sl = starts & le;
+            const int sa = sl ? 31 - __clz(sl) : -1;
+            const uint32_t before = __shfl_sync(0xffffffffu, inc, sa > 0 ? sa - 1 : 0);
+            const uint32_t ex = inc - pc - (sa > 0 ? before : 0u) + (sa < 0 ? carry : 0u);
+            if (g < g1) dirp[g] = ex;
+            // the last lane inside the part carries its node's count onwards
+            const int last = (int)min(31u, g1 - 1 - base);
+            carry = __shfl_sync(0xffffffffu, ex + pc, last);
+            vcur = __shfl_sync(0xffffffffu, v, last);
+        }
+        if (lane == 0) { D.last_node[warp] = vcur; D.tail[warp] = carry; }
+    }
+    __syncthreads();
+    // phase 2: ones of each part's first node in the parts before it
+    if (t == 0) {
+        D.add[0] = 0;
+        for (int w = 1; w < kDecWarps; w++) {
+            const uint32_t v0 = D.first_node[w];
+            uint32_t a = 0;
+            if ((uint64_t)ent * w / kDecWarps > (uint64_t)ent * (w - 1) / kDecWarps && D.last_node[w - 1] == v0)
+                a = D.tail[w - 1] + (D.first_node[w - 1] == v0 ? D.add[w - 1] : 0u);
+            else if ((uint64_t)ent * w / kDecWarps == (uint64_t)ent * (w - 1) / kDecWarps)
+                a = D.add[w - 1];   // an empty part passes its predecessor's sum through
+            D.add[w] = a;
+        }
+    }
+    __syncthreads();
+    if (D.add[warp]) {
+        const uint32_t v0 = D.first_node[warp], a = D.add[warp];
+        const uint32_t gend = min(g1, D.u[v0] + (D.nv[v0] + dir_bits - 1) / dir_bits);
+        for (uint32_t g = g0 + lane; g < gend; g += 32) dirp[g] += a;
+    }
+    // boundary 0: all cursors 0; boundary ntile: n_v; the root at boundary k: k T
+    for (uint32_t v = t; v < V; v += kDecThreads) { cur[v] = 0; cur[(size_t)ntile * V + v] = D.nv[v]; }
+    for (uint32_t k = 1 + t; k < ntile; k += kDecThreads) cur[(size_t)k * V] = k * T;
+    __syncthreads();
+    // phase 3: cursors top-down, depth by depth
+    int bad = 0;
+    for (int d = 0; d < (int)D.maxd; d++) {
+        const uint32_t f0 = D.first[d], nd = D.first[d + 1] - f0;
+        for (uint32_t i = t; i < (ntile - 1) * nd; i += kDecThreads) {
+            const uint32_t k = 1 + i / nd, v = f0 + i % nd;
+            const uint32_t c = cur[(size_t)k * V + v], nvv = D.nv[v];
+            if (c > nvv) { bad = 1; continue; }
+            const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
+            uint32_t sb = c / dir_bits;
+            if (sb >= nsb) sb = nsb - 1;
+            uint32_t ones = dirp[D.u[v] + sb];
+            const uint32_t s0 = D.src[v];
+            for (uint32_t e = sb * dir_bits; e < c; e += 32) {
+                uint32_t w = tile_bits(src, s0, e);
+                if (c - e < 32) w &= (1u << (c - e)) - 1u;
+                ones += __popc(w);
+            }
+            const uint32_t chv = D.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
+            if (!(c0 & 0x8000u)) cur[(size_t)k * V + c0] = c - ones;
+            if (!(c1 & 0x8000u)) cur[(size_t)k * V + c1] = ones;
+        }
+        __syncthreads();
+    }
+    bad = __syncthreads_or(bad);
+    if (t == 0 && bad) status[b] = PIVCO_ERR_CORRUPT;
+    __syncthreads();
+}
+
 struct TileSmem {
     uint32_t sel[4][16];
     WarpTile w[kDecWarps];
 };
 
 // Plain tile pass: every warp takes tiles by ticket (workspace header word 12).
+// Plain directory pass: every CTA takes blocks with several tiles.
+__global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_t *__restrict__ comp,
+                                                                    const uint64_t *__restrict__ comp_off, int nblk,
+                                                                    uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                                    int32_t *__restrict__ status) {
+    __shared__ DirSmem D;
+    const DecWs W = dec_ws(ws, nblk);
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x)
+        if (W.blk_ntile[b] > 1) dir_cta(b, comp, comp_off, nblk, ws, ws_bytes, status, D);
+}
+
 __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *__restrict__ comp,
                                                                 const uint64_t *__restrict__ comp_off,
                                                                 int nblk, uint8_t *__restrict__ out,
@@ -1169,7 +1112,7 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *_
 //   plans      8 blocks per item, one warp each (ticket order = block order,
 //              as the plan's look-back needs)
 //   ANS        8 segments per item, one warp each
-//   directory  one block per item (blocks with one tile skip it)
+//   directory  one block per item, whole CTA (blocks with one tile skip it)
 // then warp items: tiles, one per warp.  A CTA turns to tiles once the CTA
 // items are all taken.  An item only waits (bounded) on items earlier in the
 // queue: the ANS and later items on all plans; a directory on its block's ANS
@@ -1195,8 +1138,8 @@ struct PlanAnsSmem {
     AnsSm T[kDecWarps];
 };
 union BatchUnion {
-    DecSmem dir;
     PlanAnsSmem pa;
+    DirSmem dir;
     WarpTile tw[kDecWarps];
 };
 struct BatchSmem {
@@ -1277,7 +1220,7 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
             if (__syncthreads_or(!okw)) {
                 if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
             } else {
-                dir_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.dir);
+                dir_cta(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.dir);
             }
             __syncthreads();
             if (t == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
@@ -1508,6 +1451,18 @@ static int merge_grid(const void *fn, int smem) {
     return sms * occ;
 }
 
+cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
+                              int32_t *status, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nblk < sms * 4 ? nblk : sms * 4;
+    decode_dir_kernel<<<grid, kDecThreads, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decode(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
                           const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
@@ -1565,8 +1520,6 @@ namespace pv {
 // dynamic shared-memory limits of the decode kernels (set before any capture)
 cudaError_t prepare_decode_kernels() {
     cudaError_t e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(decode_dir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DecSmem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchSmem));
     if (e == cudaSuccess)

@@ -397,7 +397,9 @@ pivco_status pivco_server_submit(pivco_server *s, const uint8_t *comp, const uin
     r->comp_h = comp + comp_off[0];
     r->out_h = out + out_off[0];
     const pv::DecTuning tu = pv::current_tuning();
-    r->ws_bytes = pv::align_up(nblk ? pv::decode_ws_bound(r->comp_h, r->comp_off.data(), nblk, tu) : 0);
+    // the workspace header and counters exist even for an empty request (the loop steps over it)
+    r->ws_bytes = pv::align_up(std::max(nblk ? pv::decode_ws_bound(r->comp_h, r->comp_off.data(), nblk, tu) : (size_t)0,
+                                        pv::decode_ws_fixed_bytes(nblk)));
     const size_t n1 = (size_t)nblk + 1;
     r->need = pv::align_up(r->comp_bytes) + 2 * pv::align_up(8 * n1) + pv::align_up(4 * (size_t)nblk) + r->ws_bytes +
               pv::align_up(r->raw_bytes);
