@@ -1,69 +1,57 @@
-// Encode kernel: per-node bitmap emission by stable partition (Sec. 4, Table 11).
+// Encode kernel: per-node bitmap emission by stable partition (Sec. 4, Sec. 2.4.1).
 //
-// One CTA encodes one block in root chunks.  The root reads the chunk straight
-// from global memory; only depths >= 1 need level buffers, so a chunk can be
-// as long as the busiest level below the root allows (for skewed data a
-// whole block).  Within a chunk the symbols of depth d sit in a level buffer
-// ordered by (d-bit code prefix, block position), each node owning one
-// aligned span.  For every depth:
-//   A) the code bit d of every symbol is computed (the node's bitmap bits in
-//      block order) and ORed into a shared-memory window of the node's bitmap;
-//      each 128-symbol unit's popcount is recorded,
-//   B) per node, the unit popcounts are scanned (rank directory); the node's
-//      ones are its right child's symbol count in this chunk, its zeros the
-//      left child's,
-//   C) each node's span is stably partitioned into its internal children's
-//      spans (bit 0 -> left, 1 -> right): EPF / EPL / EPR / EPN of Table 11;
-//      meanwhile the depth's windows are written to the record and the
-//      partial last word of each window is kept for the next chunk.
-// A chunk whose levels would overflow the buffers is shortened and redone
-// (a redo rewrites the same leading bits, so the record stays exact).
+// One CTA encodes one block; its warps split the block into contiguous
+// chunks and work independently.  A node's bitmap holds, in block order, the
+// code bit of every symbol passing through it, so a warp's first bit of node
+// v is the number of the block's earlier symbols under v: the chunk
+// histograms, prefix-summed over the warps and summed over each node's
+// subtree, give every warp its start cursors.  A warp encodes its chunk in
+// sub-chunks whose levels fit its buffers:
+//   - the sub-chunk's histogram gives every node's symbol count (demand),
+//     hence the spans of each level buffer;
+//   - top-down, a lane takes 32 consecutive symbols of one node: their code
+//     bits at the node's depth form one 32-bit bitmap word (written to the
+//     record at the node's cursor, assembled across lanes; words shared with
+//     a neighbour are ORed in), and the symbols are stably partitioned into
+//     the internal children's spans (EPF / EPL / EPR / EPN of Sec. 2.4.1).
+// Below the root a symbol travels as its remaining code bits, most
+// significant first in 16 bits, so a node's bit is bit 15 and the child
+// receives the value shifted left by one.
 #include "tma.cuh"
 
 namespace pv {
 
 constexpr int kEncThreads = 256;
 constexpr int kEncWarps = kEncThreads / 32;
-constexpr int kUnit = 128;
-constexpr int kECap = 14336;                 // level buffer capacity (depths >= 1)
-constexpr int kELvlBytes = kECap + 16;
-constexpr int kEMaxRoot = 65536;             // longest chunk
-constexpr int kERegion = kEMaxRoot / 32 + 32;  // staging words of one depth's windows
-constexpr int kEUnits = kEMaxRoot / kUnit + 256;
+constexpr int kEncCtasPerSm = 2;
+constexpr int kEBufE = kEncCtasPerSm == 1 ? 5376 : 2304;   // symbols per level buffer of a warp
+constexpr int kESlack = 48;                                  // over-read room (symbols)
+constexpr uint32_t kEMinChunk = 4096;                        // shortest warp chunk (symbols)
+
+struct __align__(16) EncWarp {
+    uint16_t buf[2][kEBufE + kESlack];   // depth d >= 1 reads buf[d & 1], writes its children to the other
+    uint32_t pos[256];                   // bit address of node v's next bitmap bit in the record
+    uint32_t dem[256];                   // symbols of node v in the current sub-chunk
+    uint32_t start[256];                 // symbols before this warp's chunk, per symbol
+    uint16_t sp[256];                    // first symbol of node v's span in its level buffer
+    uint16_t gs[256];                    // first 32-symbol group of node v within its level
+    uint16_t lg[16];                     // groups of each level
+};
+static_assert(sizeof(EncWarp) % 16 == 0 && ((kEBufE + kESlack) * 2) % 16 == 0, "16-byte aligned level buffers");
 
 struct EncSmem {
-    uint8_t buf[2][kELvlBytes];  // level buffers (depth d >= 1 uses buf[d & 1])
-    uint32_t stage[2][kERegion]; // bitmap windows of depth d in stage[d & 1]
-    uint32_t unit_pc[kEUnits];
-    uint32_t unit_base[kEUnits];
-    uint32_t cnt[256];           // symbols of node v in this chunk
-    uint32_t cur[256];           // bits of node v already emitted
-    uint32_t pend[256];          // partial bitmap word holding bits below cur % 32
-    uint32_t npend[256];         // pend after this chunk
-    uint32_t span[256];
-    uint32_t ustart[256];        // first unit of node v within its depth
-    uint32_t st_off[256];        // first word of node v's window in its depth's region
-    uint32_t nwin[256];
-    uint32_t body_off[256];
-    uint32_t nv[256];
-    uint32_t lvl_tot[17];
-    uint32_t nunits[17];
-    uint32_t nwords[17];
-    uint16_t rc[256];            // bit d = code bit at depth d
-    int16_t child[256][2];
-    uint8_t depth[256];
-    uint8_t depth_first[17];
-    int32_t overflow;
-    uint32_t chunk;
+    uint16_t code16[256];    // code of symbol s, most significant bit at bit 15 (0: absent)
+    uint32_t ch[256];        // children: 0x8000 | symbol for a leaf, else the node index
+    uint32_t bitsrc[256];    // bit address of node v's bitmap in the record
+    uint32_t tot[256];       // symbols of node v in the block (checked against the layout)
+    uint32_t htot[256];      // the block's histogram
+    int32_t a[17];           // d-bit prefixes under leaves of length <= d
+    uint8_t first[17];       // first node of each depth
+    uint8_t maxd;
+    uint8_t pad[6];
+    EncWarp w[kEncWarps];
 };
-
-__device__ inline int find_node(const uint32_t *key, int lo, int hi, uint32_t g) {
-    while (hi - lo > 1) {
-        const int m = (lo + hi) >> 1;
-        if (key[m] <= g) lo = m; else hi = m;
-    }
-    return lo;
-}
+static_assert(offsetof(EncSmem, w) % 16 == 0, "16-byte aligned warp areas");
 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop(int n, F f, G out) {
@@ -83,70 +71,151 @@ __device__ inline uint32_t warp_scan_loop(int n, F f, G out) {
     return carry;
 }
 
-// 4 input bytes at p (any alignment, p < end) from global memory
-__device__ inline uint32_t ldg4_any(const uint8_t *p, const uint8_t *end) {
+// 32 input bytes at p (any alignment; bytes at or past `end` read as 0)
+__device__ inline void ldg32(const uint8_t *p, const uint8_t *end, uint32_t (&x)[8]) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if (!(a & 15) && p + 32 <= end) {
+        const uint4 u0 = __ldg(reinterpret_cast<const uint4 *>(p)), u1 = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+        x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
+        x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
+        return;
+    }
     const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~uintptr_t(3));
     const uint32_t sh = (uint32_t)(a & 3) * 8;
-    const uint32_t lo = __ldg(w);
-    if (!sh) return lo;
-    const uint32_t hi = (reinterpret_cast<const uint8_t *>(w + 1) < end) ? __ldg(w + 1) : 0u;
-    return __funnelshift_r(lo, hi, sh);
+    const uint8_t *wend = reinterpret_cast<const uint8_t *>(w);
+    uint32_t prev = wend < end ? __ldg(w) : 0u;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint32_t nx = (wend + 4 * (j + 1) < end) ? __ldg(w + j + 1) : 0u;
+        x[j] = sh ? __funnelshift_r(prev, nx, sh) : prev;
+        prev = nx;
+    }
 }
 
-// one warp: spans / units / windows of the depth-d nodes for this chunk
-__device__ inline void level_setup(EncSmem &S, int d) {
+// adds the 32 bytes x (first vl valid) to a shared histogram; lanes holding
+// the same byte add once (skewed data would otherwise collide on one counter)
+__device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32_t vl) {
     const int lane = threadIdx.x & 31;
-    const int f0 = S.depth_first[d], f1 = S.depth_first[d + 1];
-    uint64_t carry = 0;
-    uint32_t wcarry = 0;
-    for (int base = f0; base < f1; base += 32) {
-        const int v = base + lane;
-        const uint32_t c = v < f1 ? S.cnt[v] : 0u;
-        const uint32_t win = c ? ((S.cur[v] & 31u) + c + 31u) >> 5 : 0u;
-        const uint64_t x = ((uint64_t)((c + kUnit - 1) / kUnit) << 32) | ((c + 3u) & ~3u);
-        uint64_t inc = x;
-        uint32_t winc = win;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            const uint32_t wy = __shfl_up_sync(0xffffffffu, winc, o);
-            if (lane >= o) { inc += y; winc += wy; }
-        }
-        if (v < f1) {
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        const uint32_t sym = (uint32_t)j < vl ? (x[j >> 2] >> (8 * (j & 3))) & 0xFFu : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, sym);
+        if (sym < 256 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&hist[sym], (uint32_t)__popc(peers));
+    }
+}
+
+// node index of the depth-d prefix of code c (length l > d)
+__device__ inline uint32_t enc_node(const EncSmem &S, uint32_t c, uint32_t l, int d) {
+    return (uint32_t)S.first[d] + ((c >> (l - d)) - (uint32_t)S.a[d]);
+}
+
+// node symbol counts of a histogram (each symbol counts in every node on its path)
+__device__ inline void enc_node_counts(const EncSmem &S, const BlockLayout &L, const uint32_t *hist, uint32_t *cnt,
+                                       int V) {
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < V; v += 32) cnt[v] = 0;
+    __syncwarp();
+    for (int s = lane; s < 256; s += 32) {
+        const uint32_t h = hist[s], l = L.len[s], c = L.code[s];
+        if (!h || !l) continue;
+        for (int d = 0; d < (int)l; d++) atomicAdd(&cnt[enc_node(S, c, l, d)], h);
+    }
+    __syncwarp();
+}
+
+// Spans and groups of every level for the current demands; false when a
+// level (depth >= 1) does not fit a buffer.
+__device__ inline bool enc_layout(const EncSmem &S, EncWarp &E) {
+    const int lane = threadIdx.x & 31;
+    bool fits = true;
+    for (int d = 0; d < (int)S.maxd; d++) {
+        const int f0 = S.first[d], f1 = S.first[d + 1];
+        uint64_t carry = 0;
+        for (int base = f0; base < f1; base += 32) {
+            const int v = base + lane;
+            uint64_t x = 0;
+            if (v < f1) {
+                const uint32_t dv = E.dem[v];
+                if (d && dv > (uint32_t)kEBufE) fits = false;
+                const uint32_t el = d ? ((min(dv, (uint32_t)kEBufE) + 1u) & ~1u) : 0u;
+                x = ((uint64_t)el << 32) | max(1u, (dv + 31u) >> 5);
+            }
+            uint64_t inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
             const uint64_t ex = carry + inc - x;
-            S.span[v] = (uint32_t)ex;
-            S.ustart[v] = (uint32_t)(ex >> 32);
-            S.st_off[v] = wcarry + winc - win;
-            S.nwin[v] = win;
+            if (v < f1) {
+                E.sp[v] = (uint16_t)min((uint64_t)kEBufE, ex >> 32);
+                E.gs[v] = (uint16_t)ex;
+            }
+            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-        wcarry += __shfl_sync(0xffffffffu, winc, 31);
+        if (d && (carry >> 32) > (uint64_t)kEBufE) fits = false;
+        if ((uint32_t)carry > 0xFFFFu) fits = false;
+        if (lane == 0) E.lg[d] = (uint16_t)carry;
     }
-    if (lane == 0) {
-        S.nunits[d] = (uint32_t)(carry >> 32);
-        S.nwords[d] = wcarry;
-        if ((d > 0 && (uint32_t)carry > (uint32_t)kECap) || (carry >> 32) > (uint64_t)kEUnits || wcarry > (uint32_t)kERegion)
-            S.overflow = 1;
+    __syncwarp();
+    return __all_sync(0xffffffffu, fits);
+}
+
+// Writes bits bw (vl of them valid) of one node at bit address a of the
+// record.  Lanes of the same node hold consecutive 32-bit runs; a lane
+// stores the aligned word its run starts in, completed with the previous
+// lane's spill; words shared with another run (or another node) are ORed.
+__device__ inline void enc_put_bits(uint32_t *rec32, bool act, uint32_t v, uint32_t a, uint32_t bw, uint32_t vl) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t sh = a & 31u, wi = a >> 5;
+    const uint32_t lo = bw << sh;
+    const uint32_t hi = sh ? bw >> (32 - sh) : 0u;
+    const uint32_t key = act ? v : 0xFFFFFFFFu;
+    const uint32_t pkey = __shfl_up_sync(0xffffffffu, key, 1), nkey = __shfl_down_sync(0xffffffffu, key, 1);
+    const uint32_t phi = __shfl_up_sync(0xffffffffu, hi, 1);
+    const bool prev_same = lane > 0 && act && pkey == v;
+    const bool next_same = lane < 31 && act && nkey == v;
+    if (!act) return;
+    const uint32_t word = lo | (prev_same ? phi : 0u);
+    const bool full = (sh == 0 || prev_same) && vl >= 32 - sh;
+    if (full) rec32[wi] = word;
+    else if (word) atomicOr(&rec32[wi], word);
+    if (hi && !next_same) atomicOr(&rec32[wi + 1], hi);
+}
+
+// The top bit of each of the 8 16-bit values in x0..x3 (value j at bits j)
+__device__ inline uint32_t top_bits8(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    const uint32_t h0 = __byte_perm(x0, x1, 0x7531), h1 = __byte_perm(x2, x3, 0x7531);
+    const uint32_t b0 = ((h0 & 0x80808080u) * 0x00204081u) >> 28;
+    const uint32_t b1 = ((h1 & 0x80808080u) * 0x00204081u) >> 28;
+    return b0 | (b1 << 4);
+}
+
+// Stable partition of up to 32 symbols (values y[j], bits in bw, vl valid)
+// into the left (bit 0) and right (bit 1) spans of the next level.
+__device__ inline void enc_split(uint16_t *lp, uint16_t *rp, bool i0, bool i1, const uint32_t (&y)[16], uint32_t bw,
+                                 uint32_t vl) {
+    uint32_t zl = 0, ol = 0;
+    // which side keeps its symbols (a leaf child keeps none), among the valid ones
+    const uint32_t keep = ((i1 ? bw : 0u) | (i0 ? ~bw : 0u)) & (vl >= 32 ? 0xFFFFFFFFu : ((1u << vl) - 1u));
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        const uint32_t bit = (bw >> j) & 1u;
+        const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
+        uint16_t *dst = bit ? rp + ol : lp + zl;
+        if ((keep >> j) & 1u) *dst = val;
+        ol += bit;
+        zl += 1u - bit;
     }
 }
 
-// zero the depth-d windows; each node's pending partial word goes first
-__device__ inline void level_windows_init(EncSmem &S, int d) {
-    const int f0 = S.depth_first[d], f1 = S.depth_first[d + 1];
-    uint32_t *reg = S.stage[d & 1];
-    for (uint32_t i = threadIdx.x; i < S.nwords[d]; i += kEncThreads) {
-        const int v = find_node(S.st_off, f0, f1, i);
-        reg[i] = (i == S.st_off[v]) ? S.pend[v] : 0u;
-    }
-}
-
-__global__ void __launch_bounds__(kEncThreads, 3) encode_kernel(const uint8_t *__restrict__ in,
-                                                                const uint64_t *__restrict__ blk_off,
-                                                                const BlockLayout *__restrict__ layout,
-                                                                uint8_t *__restrict__ out,
-                                                                const uint64_t *__restrict__ out_off,
-                                                                uint64_t *__restrict__ rec_bytes,
-                                                                int32_t *__restrict__ status) {
+__global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(const uint8_t *__restrict__ in,
+                                                                            const uint64_t *__restrict__ blk_off,
+                                                                            const BlockLayout *__restrict__ layout,
+                                                                            uint8_t *__restrict__ out,
+                                                                            const uint64_t *__restrict__ out_off,
+                                                                            uint64_t *__restrict__ rec_bytes,
+                                                                            int32_t *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -199,178 +268,221 @@ __global__ void __launch_bounds__(kEncThreads, 3) encode_kernel(const uint8_t *_
         }
         for (uint32_t i = L.body_end + t; i < L.rec_bound; i += kEncThreads) rec[i] = 0;
     }
+    // ---- the bitmaps are ORed into a zeroed body ----
+    {
+        const uint32_t b0 = L.body0, b1 = L.body_end;
+        const uint32_t h0 = min(b1, (b0 + 15u) & ~15u), h1 = max(h0, b1 & ~15u);
+        for (uint32_t i = b0 + t; i < h0; i += kEncThreads) rec[i] = 0;
+        for (uint32_t i = h0 + 16 * t; i < h1; i += 16 * kEncThreads)
+            *reinterpret_cast<uint4 *>(rec + i) = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t i = h1 + t; i < b1; i += kEncThreads) rec[i] = 0;
+    }
     // ---- per-block tables ----
     {
-        const int s = t;
-        const int l = L.len[s];
-        uint32_t r = 0;
-        for (int d = 0; d < l; d++) r |= ((uint32_t)(L.code[s] >> (l - 1 - d)) & 1u) << d;
-        S.rc[s] = (uint16_t)r;
-        S.cur[s] = 0;
-        S.pend[s] = 0;
-        S.body_off[s] = L.body_off[s];
-        S.nv[s] = L.nv[s];
-        S.child[s][0] = L.child[s][0];
-        S.child[s][1] = L.child[s][1];
-        S.depth[s] = L.depth[s];
-    }
-    if (t < 17) { S.depth_first[t] = L.depth_first[t]; S.lvl_tot[t] = 0; }
-    __syncthreads();
-    if (t < V) {
-        // per-depth symbol totals below the root (chunk sizing)
-        for (int c = 0; c < 2; c++) {
-            const int ch = S.child[t][c];
-            if (ch >= 0) atomicAdd(&S.lvl_tot[S.depth[ch]], S.nv[ch]);
+        const uint32_t l = L.len[t];
+        S.code16[t] = l ? (uint16_t)((uint32_t)L.code[t] << (16 - l)) : 0;
+        if (t < V) {
+            uint32_t code2 = 0;
+            for (int c = 0; c < 2; c++) {
+                const int ch = L.child[t][c];
+                code2 |= (ch >= 0 ? (uint32_t)ch : (0x8000u | (uint32_t)(-ch - 1))) << (16 * c);
+            }
+            S.ch[t] = code2;
+            S.bitsrc[t] = 8u * L.body_off[t];
         }
+        S.tot[t] = 0;
+        if (t < 17) { S.a[t] = L.tree_a[t]; S.first[t] = L.depth_first[t]; }
+        if (t == 0) S.maxd = L.max_depth;
     }
-    __syncthreads();
-    if (t == 0) {
-        uint64_t mx = 1;
-        for (int d = 1; d < 16; d++) mx = S.lvl_tot[d] > mx ? S.lvl_tot[d] : mx;
-        uint64_t X = (uint64_t)(kECap - 4 * 256) * n / mx;
-        X = X > (uint64_t)kEMaxRoot ? (uint64_t)kEMaxRoot : X;
-        X = X < n ? (X & ~(uint64_t)(kUnit - 1)) : n;
-        S.chunk = X < (uint64_t)kUnit ? (uint32_t)kUnit : (uint32_t)X;
-    }
-    __syncthreads();
-    const int maxd = L.max_depth;
+    // ---- warp chunks and their histograms ----
+    const uint32_t nw = (uint32_t)min((uint64_t)kEncWarps, max((uint64_t)1, n / kEMinChunk));
+    const uint32_t Q0 = (uint32_t)(((uint64_t)n * warp / nw) & ~31ull);
+    const uint32_t Q1 = warp + 1 >= (int)nw ? (uint32_t)n : (uint32_t)(((uint64_t)n * (warp + 1) / nw) & ~31ull);
     const uint8_t *src = in + blk_off[b];
     const uint8_t *src_end = in + blk_off[b + 1];
-
-    for (uint64_t P = 0; P < n;) {
-        const uint32_t cc = (uint32_t)umin64(S.chunk, n - P);
-        const uint8_t *in0 = src + P;
-        if (t == 0) { S.cnt[0] = cc; S.overflow = 0; }
-        __syncthreads();
-        if (warp == 0) level_setup(S, 0);
-        __syncthreads();
-        level_windows_init(S, 0);
-        __syncthreads();
-
-        for (int d = 0; d < maxd; d++) {
-            const uint8_t *bin = S.buf[d & 1];
-            uint8_t *bout = S.buf[(d + 1) & 1];
-            uint32_t *reg = S.stage[d & 1];
-            const int f0 = S.depth_first[d], f1 = S.depth_first[d + 1];
-            const uint32_t nu = S.nunits[d];
-            // A: bits of every unit into the node windows, unit popcounts
-            for (uint32_t g = warp; g < nu; g += kEncWarps) {
-                const int v = find_node(S.ustart, f0, f1, g);
-                const uint32_t k0 = (g - S.ustart[v]) * kUnit, k = k0 + 4 * lane;
-                const uint32_t cntv = S.cnt[v];
-                uint32_t nib = 0;
-                if (k < cntv) {
-                    const uint32_t w = d == 0 ? ldg4_any(in0 + k, src_end) : *reinterpret_cast<const uint32_t *>(bin + S.span[v] + k);
-                    const uint32_t nval = min(4u, cntv - k);
-                    for (uint32_t j = 0; j < nval; j++) nib |= ((uint32_t)(S.rc[(w >> (8 * j)) & 0xFF] >> d) & 1u) << j;
-                }
-                uint32_t word = nib << (4 * (lane & 7));
-                word |= __shfl_xor_sync(0xffffffffu, word, 1);
-                word |= __shfl_xor_sync(0xffffffffu, word, 2);
-                word |= __shfl_xor_sync(0xffffffffu, word, 4);
-                const uint32_t pc = __popc(word);
-                const uint32_t tot = __shfl_sync(0xffffffffu, pc, 0) + __shfl_sync(0xffffffffu, pc, 8) +
-                                     __shfl_sync(0xffffffffu, pc, 16) + __shfl_sync(0xffffffffu, pc, 24);
-                if (lane == 0) S.unit_pc[g] = tot;
-                if ((lane & 7) == 0 && word) {
-                    const uint32_t pos = (S.cur[v] & 31u) + k0 + 4 * lane;   // 4 * lane = 32 * word index
-                    const uint32_t wi = pos >> 5, sh = pos & 31u;
-                    uint32_t *win = reg + S.st_off[v];
-                    atomicOr(&win[wi], word << sh);
-                    if (sh && (word >> (32 - sh))) atomicOr(&win[wi + 1], word >> (32 - sh));
-                }
-            }
-            __syncthreads();
-            // B: rank directory of each node; children's counts for this chunk
-            for (int v = f0 + warp; v < f1; v += kEncWarps) {
-                const uint32_t cntv = S.cnt[v];
-                uint32_t ones = 0;
-                if (cntv) {
-                    const uint32_t u0 = S.ustart[v], nuv = (cntv + kUnit - 1) / kUnit;
-                    ones = warp_scan_loop((int)nuv, [&](int i) { return S.unit_pc[u0 + i]; },
-                                          [&](int i, uint32_t p) { S.unit_base[u0 + i] = p; });
-                }
-                if (lane < 2 && S.child[v][lane] >= 0) S.cnt[S.child[v][lane]] = lane ? ones : cntv - ones;
-            }
-            __syncthreads();
-            if (d + 1 < maxd && warp == 0) level_setup(S, d + 1);
-            __syncthreads();
-            if (S.overflow) break;
-            // C: stable partition into the internal children's spans
-            if (d + 1 < maxd) {
-                for (uint32_t g = warp; g < nu; g += kEncWarps) {
-                    const int v = find_node(S.ustart, f0, f1, g);
-                    const int c0 = S.child[v][0], c1 = S.child[v][1];
-                    if (c0 < 0 && c1 < 0) continue;   // both children are leaves: nothing moves
-                    const uint32_t k0 = (g - S.ustart[v]) * kUnit, k = k0 + 4 * lane;
-                    const uint32_t cntv = S.cnt[v];
-                    uint32_t nib = 0, w = 0, nval = 0;
-                    if (k < cntv) {
-                        w = d == 0 ? ldg4_any(in0 + k, src_end) : *reinterpret_cast<const uint32_t *>(bin + S.span[v] + k);
-                        nval = min(4u, cntv - k);
-                        for (uint32_t j = 0; j < nval; j++) nib |= ((uint32_t)(S.rc[(w >> (8 * j)) & 0xFF] >> d) & 1u) << j;
-                    }
-                    uint32_t word = nib << (4 * (lane & 7));
-                    word |= __shfl_xor_sync(0xffffffffu, word, 1);
-                    word |= __shfl_xor_sync(0xffffffffu, word, 2);
-                    word |= __shfl_xor_sync(0xffffffffu, word, 4);
-                    const uint32_t w0 = __shfl_sync(0xffffffffu, word, 0), w1 = __shfl_sync(0xffffffffu, word, 8),
-                                   w2 = __shfl_sync(0xffffffffu, word, 16);
-                    const uint32_t q = lane >> 3;
-                    uint32_t r = S.unit_base[g] + (q > 0 ? __popc(w0) : 0) + (q > 1 ? __popc(w1) : 0) +
-                                 (q > 2 ? __popc(w2) : 0) + __popc(word & ((1u << (4 * (lane & 7))) - 1u));
-                    const uint32_t sp0 = c0 >= 0 ? S.span[c0] : 0, sp1 = c1 >= 0 ? S.span[c1] : 0;
-                    for (uint32_t j = 0; j < nval; j++) {
-                        const uint32_t bit = (nib >> j) & 1u;
-                        if (bit) { if (c1 >= 0) bout[sp1 + r] = (uint8_t)(w >> (8 * j)); }
-                        else if (c0 >= 0) bout[sp0 + (k + j - r)] = (uint8_t)(w >> (8 * j));
-                        r += bit;
-                    }
-                }
-                level_windows_init(S, d + 1);
-            }
-            // write the depth-d windows to the record; keep the partial last words
-            for (uint32_t i = t; i < S.nwords[d]; i += kEncThreads) {
-                const int v = find_node(S.st_off, f0, f1, i);
-                const uint32_t j = i - S.st_off[v];
-                if (j >= S.nwin[v]) continue;
-                const uint32_t word = reg[i];
-                const uint32_t c = S.cur[v], nc = c + S.cnt[v];
-                if (j == ((nc >> 5) - (c >> 5))) S.npend[v] = (nc & 31u) ? word : 0u;
-                const uint32_t byte0 = 4 * ((c >> 5) + j), raw = (S.nv[v] + 7) / 8;
-                uint8_t *dstp = rec + S.body_off[v] + byte0;
-                if (byte0 + 4 <= raw && ((reinterpret_cast<uintptr_t>(dstp) & 3) == 0)) {
-                    *reinterpret_cast<uint32_t *>(dstp) = word;
-                } else {
-#pragma unroll
-                    for (int qb = 0; qb < 4; qb++)
-                        if (byte0 + qb < raw) dstp[qb] = (uint8_t)(word >> (8 * qb));
-                }
-            }
-            __syncthreads();
+    EncWarp &E = S.w[warp];
+    // histograms live in the first level buffer until the levels need it
+    uint32_t *hist = reinterpret_cast<uint32_t *>(E.buf[0]);
+    for (int s = lane; s < 256; s += 32) hist[s] = 0;
+    __syncwarp();
+    if ((uint32_t)warp < nw) {
+        for (uint32_t kb = Q0; kb < Q1; kb += 1024) {
+            const uint32_t k = kb + 32 * lane;
+            uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (k < Q1) ldg32(src + k, src_end, x);
+            hist_add32(hist, x, k < Q1 ? min(32u, Q1 - k) : 0u);
         }
-        if (S.overflow) {
-            // a level did not fit: shorten the chunk and redo it
-            if (t == 0) S.chunk = max((uint32_t)kUnit, (S.chunk / 4 * 3) & ~(uint32_t)(kUnit - 1));
-            __syncthreads();
-            continue;
-        }
-        for (int v = t; v < V; v += kEncThreads) {
-            if (S.cnt[v]) {
-                const uint32_t nc = S.cur[v] + S.cnt[v];
-                S.pend[v] = (nc & 31u) ? S.npend[v] : 0u;
-                S.cur[v] = nc;
-            }
-        }
-        P += cc;
-        __syncthreads();
     }
-    // every node must have emitted exactly n_v bits
-    int bad = 0;
-    for (int v = t; v < V; v += kEncThreads) bad |= S.cur[v] != S.nv[v];
-    bad = __syncthreads_or(bad);
+    __syncthreads();
+    // exclusive prefix over the warps (each warp's start counts), block totals
+    {
+        uint32_t run = 0;
+        for (uint32_t w = 0; w < nw; w++) {
+            const uint32_t h = reinterpret_cast<const uint32_t *>(S.w[w].buf[0])[t];
+            S.w[w].start[t] = run;
+            run += h;
+        }
+        S.htot[t] = run;
+        const uint32_t l = L.len[t], c = L.code[t];
+        if (run && l)
+            for (int d = 0; d < (int)l; d++) atomicAdd(&S.tot[enc_node(S, c, l, d)], run);
+        if (run && !l) S.tot[255] = 0xFFFFFFFFu;   // a symbol the code does not have: mismatch below
+    }
+    __syncthreads();
+    {
+        int bad = t < V && S.tot[t] != L.nv[t];
+        if (t == 255 && V < 256 && S.tot[255] == 0xFFFFFFFFu) bad = 1;
+        if (__syncthreads_or(bad)) {
+            if (t == 0) { status[b] = PIVCO_ERR_INVALID_ARG; rec_bytes[b] = 0; }
+            return;
+        }
+    }
+    uint32_t *rec32 = reinterpret_cast<uint32_t *>(rec);
+    if ((uint32_t)warp < nw) {
+        // start cursors of this warp's chunk
+        enc_node_counts(S, L, E.start, E.pos, V);
+        for (int v = lane; v < V; v += 32) E.pos[v] += S.bitsrc[v];
+        __syncwarp();
+        // sub-chunk length from the block's busiest level below the root
+        uint32_t C0 = Q1 - Q0;
+        {
+            uint32_t mx = 1;
+            for (int d = 1; d < (int)S.maxd; d++) {
+                uint32_t s = 0;
+                for (int v = S.first[d]; v < S.first[d + 1]; v++) s += L.nv[v];
+                mx = s > mx ? s : mx;
+            }
+            const uint64_t c = (uint64_t)(kEBufE - 2 * 128) * n / mx / 5 * 4;
+            if (c < C0) C0 = max(32u, (uint32_t)c & ~31u);
+        }
+        uint32_t C = C0;
+        for (uint32_t P = Q0; P < Q1;) {
+            C = min(C, Q1 - P);
+            // ---- sub-chunk histogram -> node demands -> level spans ----
+            if (C == Q1 - Q0) {
+                // the whole chunk: its histogram is the next warp's start counts minus ours
+                for (int s = lane; s < 256; s += 32)
+                    hist[s] = ((uint32_t)warp + 1 < nw ? S.w[warp + 1].start[s] : S.htot[s]) - E.start[s];
+            } else {
+                for (int s = lane; s < 256; s += 32) hist[s] = 0;
+                __syncwarp();
+                for (uint32_t kb = P; kb < P + C; kb += 1024) {
+                    const uint32_t k = kb + 32 * lane;
+                    uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (k < P + C) ldg32(src + k, src_end, x);
+                    hist_add32(hist, x, k < P + C ? min(32u, P + C - k) : 0u);
+                }
+            }
+            __syncwarp();
+            enc_node_counts(S, L, hist, E.dem, V);
+            if (!enc_layout(S, E)) {
+                C = max(32u, (C / 2) & ~31u);
+                continue;
+            }
+            // ---- the root: input bytes -> codes; bits; children ----
+            {
+                const uint32_t chv = S.ch[0], c0 = chv & 0xFFFFu, c1 = chv >> 16;
+                const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
+                uint16_t *nb = E.buf[1];
+                uint16_t *lp0 = nb + (i0 ? E.sp[c0 & 0xFFu] : 0), *rp0 = nb + (i1 ? E.sp[c1 & 0xFFu] : 0);
+                uint32_t carry = 0;
+                for (uint32_t kb = 0; kb < C; kb += 1024) {
+                    const uint32_t kk = kb + 32u * lane;
+                    const bool act = kk < C;
+                    const uint32_t vl = act ? min(32u, C - kk) : 0u;
+                    uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (act) ldg32(src + P + kk, src_end, x);
+                    uint32_t y[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const uint32_t s0 = (x[j >> 1] >> (16 * (j & 1))) & 0xFFu, s1 = (x[j >> 1] >> (16 * (j & 1) + 8)) & 0xFFu;
+                        y[j] = (uint32_t)S.code16[s0] | ((uint32_t)S.code16[s1] << 16);
+                    }
+                    uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
+                                  (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
+                                  (top_bits8(y[12], y[13], y[14], y[15]) << 24);
+                    if (vl < 32) bw &= (1u << vl) - 1u;
+                    const uint32_t pc = __popc(bw);
+                    uint32_t inc = pc;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t yy = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += yy;
+                    }
+                    const uint32_t r1 = carry + inc - pc;
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                    enc_put_bits(rec32, act, 0u, E.pos[0] + kk, bw, vl);
+                    if (act) enc_split(lp0 + (kk - r1), rp0 + r1, i0, i1, y, bw, vl);
+                }
+            }
+            __syncwarp();
+            // ---- depths 1.. : node spans of buf[d & 1] into the children's spans ----
+            for (int d = 1; d < (int)S.maxd; d++) {
+                const uint16_t *bin = E.buf[d & 1];
+                uint16_t *bout = E.buf[(d + 1) & 1];
+                const uint32_t f0 = S.first[d], f1 = S.first[d + 1], G = E.lg[d];
+                const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
+                uint32_t vcur = f0, carry = 0;
+                for (uint32_t base = 0; base < G; base += 32) {
+                    const uint32_t cand = vcur + 1 + lane;
+                    uint32_t bit = 0;
+                    if (cand < f1) {
+                        const uint32_t s = (uint32_t)E.gs[cand] - base;
+                        if (s < 32) bit = 1u << s;
+                    }
+                    const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
+                    const uint32_t v = vcur + __popc(starts & le);
+                    const uint32_t g = base + lane;
+                    const uint32_t kk = (g - E.gs[v]) * 32u;
+                    const uint32_t dv = E.dem[v];
+                    const bool act = g < G && kk < dv;
+                    const uint32_t vl = act ? min(32u, dv - kk) : 0u;
+                    uint32_t y[16];
+                    if (act) {
+                        const uint32_t *p = reinterpret_cast<const uint32_t *>(bin + E.sp[v] + kk);
+#pragma unroll
+                        for (int q = 0; q < 16; q++) y[q] = p[q];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) y[j] = 0;
+                    }
+                    uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
+                                  (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
+                                  (top_bits8(y[12], y[13], y[14], y[15]) << 24);
+                    if (vl < 32) bw &= (1u << vl) - 1u;
+                    const uint32_t pc = __popc(bw);
+                    uint32_t inc = pc;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t yy = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += yy;
+                    }
+                    const uint32_t sl = starts & le;
+                    const int s0 = sl ? 31 - __clz(sl) : -1;
+                    const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
+                    const uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u) + (s0 < 0 ? carry : 0u);
+                    carry = __shfl_sync(0xffffffffu, r1 + pc, 31);
+                    vcur = __shfl_sync(0xffffffffu, v, 31);
+                    enc_put_bits(rec32, act, v, E.pos[v] + kk, bw, vl);
+                    if (act) {
+                        const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
+                        const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
+                        uint16_t *lp = bout + (i0 ? E.sp[c0 & 0xFFu] : 0) + (kk - r1);
+                        uint16_t *rp = bout + (i1 ? E.sp[c1 & 0xFFu] : 0) + r1;
+                        enc_split(lp, rp, i0, i1, y, bw, vl);
+                    }
+                }
+                __syncwarp();
+            }
+            for (int v = lane; v < V; v += 32) E.pos[v] += E.dem[v];
+            __syncwarp();
+            P += C;
+            C = C0;
+        }
+    }
+    __syncthreads();
     if (t == 0) {
-        status[b] = bad ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
+        status[b] = PIVCO_OK;
         rec_bytes[b] = L.rec_bound;
     }
 }
