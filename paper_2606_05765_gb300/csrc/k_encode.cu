@@ -36,6 +36,7 @@ struct __align__(16) EncWarp {
     uint16_t sp[256];                    // first symbol of node v's span in its level buffer
     uint16_t gs[256];                    // first 32-symbol group of node v within its level
     uint16_t lg[16];                     // groups of each level
+    uint16_t sink[64];                   // where a leaf side's symbols go
 };
 static_assert(sizeof(EncWarp) % 16 == 0 && ((kEBufE + kESlack) * 2) % 16 == 0, "16-byte aligned level buffers");
 
@@ -48,7 +49,8 @@ struct EncSmem {
     int32_t a[17];           // d-bit prefixes under leaves of length <= d
     uint8_t first[17];       // first node of each depth
     uint8_t maxd;
-    uint8_t pad[6];
+    uint8_t pad[2];
+    uint32_t hot;            // the symbol with the shortest code (the most frequent one)
     EncWarp w[kEncWarps];
 };
 static_assert(offsetof(EncSmem, w) % 16 == 0, "16-byte aligned warp areas");
@@ -92,16 +94,26 @@ __device__ inline void ldg32(const uint8_t *p, const uint8_t *end, uint32_t (&x)
     }
 }
 
-// adds the 32 bytes x (first vl valid) to a shared histogram; lanes holding
-// the same byte add once (skewed data would otherwise collide on one counter)
-__device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32_t vl) {
+// adds the 32 bytes x (first vl valid) to a shared histogram.  The block's
+// most frequent symbol h is counted with a 4-byte compare and added once per
+// warp; only the other bytes use atomics (skewed data would otherwise
+// serialize on one counter).
+__device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32_t vl, uint32_t h) {
     const int lane = threadIdx.x & 31;
+    const uint32_t h4 = h * 0x01010101u;
+    uint32_t hot = 0;
 #pragma unroll
-    for (int j = 0; j < 32; j++) {
-        const uint32_t sym = (uint32_t)j < vl ? (x[j >> 2] >> (8 * (j & 3))) & 0xFFu : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, sym);
-        if (sym < 256 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&hist[sym], (uint32_t)__popc(peers));
+    for (int q = 0; q < 8; q++) {
+        const uint32_t nb = vl > 4u * q ? min(4u, vl - 4u * q) : 0u;   // valid bytes of word q
+        const uint32_t bm = nb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
+        const uint32_t m = __vcmpeq4(x[q], h4) & bm;
+        hot += __popc(m) >> 3;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if ((uint32_t)i < nb && !((m >> (8 * i)) & 1u)) atomicAdd(&hist[(x[q] >> (8 * i)) & 0xFFu], 1u);
     }
+    hot = __reduce_add_sync(0xffffffffu, hot);
+    if (lane == 0 && hot) atomicAdd(&hist[h], hot);
 }
 
 // node index of the depth-d prefix of code c (length l > d)
@@ -125,9 +137,10 @@ __device__ inline void enc_node_counts(const EncSmem &S, const BlockLayout &L, c
 
 // Spans and groups of every level for the current demands; false when a
 // level (depth >= 1) does not fit a buffer.
-__device__ inline bool enc_layout(const EncSmem &S, EncWarp &E) {
+__device__ inline bool enc_layout(const EncSmem &S, EncWarp &E, uint64_t &maxlvl) {
     const int lane = threadIdx.x & 31;
     bool fits = true;
+    maxlvl = 0;
     for (int d = 0; d < (int)S.maxd; d++) {
         const int f0 = S.first[d], f1 = S.first[d + 1];
         uint64_t carry = 0;
@@ -155,6 +168,7 @@ __device__ inline bool enc_layout(const EncSmem &S, EncWarp &E) {
         }
         if (d && (carry >> 32) > (uint64_t)kEBufE) fits = false;
         if ((uint32_t)carry > 0xFFFFu) fits = false;
+        if (d && (carry >> 32) > maxlvl) maxlvl = carry >> 32;
         if (lane == 0) E.lg[d] = (uint16_t)carry;
     }
     __syncwarp();
@@ -192,20 +206,27 @@ __device__ inline uint32_t top_bits8(uint32_t x0, uint32_t x1, uint32_t x2, uint
 }
 
 // Stable partition of up to 32 symbols (values y[j], bits in bw, vl valid)
-// into the left (bit 0) and right (bit 1) spans of the next level.
-__device__ inline void enc_split(uint16_t *lp, uint16_t *rp, bool i0, bool i1, const uint32_t (&y)[16], uint32_t bw,
-                                 uint32_t vl) {
-    uint32_t zl = 0, ol = 0;
-    // which side keeps its symbols (a leaf child keeps none), among the valid ones
-    const uint32_t keep = ((i1 ? bw : 0u) | (i0 ? ~bw : 0u)) & (vl >= 32 ? 0xFFFFFFFFu : ((1u << vl) - 1u));
+// into the left (bit 0) and right (bit 1) spans of the next level.  A leaf
+// side keeps nothing: its pointer is the warp's sink.  A full group stores
+// every symbol (one address select each); a partial one stores the valid ones.
+__device__ inline void enc_split(uint16_t *lp, uint16_t *rp, const uint32_t (&y)[16], uint32_t bw, uint32_t vl) {
+    uint32_t ol = 0;
+    if (vl >= 32) {
 #pragma unroll
-    for (int j = 0; j < 32; j++) {
-        const uint32_t bit = (bw >> j) & 1u;
-        const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
-        uint16_t *dst = bit ? rp + ol : lp + zl;
-        if ((keep >> j) & 1u) *dst = val;
-        ol += bit;
-        zl += 1u - bit;
+        for (int j = 0; j < 32; j++) {
+            const uint32_t bit = (bw >> j) & 1u;
+            const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
+            *(bit ? rp + ol : lp + (j - ol)) = val;
+            ol += bit;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const uint32_t bit = (bw >> j) & 1u;
+            const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
+            if ((uint32_t)j < vl) *(bit ? rp + ol : lp + (j - ol)) = val;
+            ol += bit;
+        }
     }
 }
 
@@ -292,8 +313,16 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         }
         S.tot[t] = 0;
         if (t < 17) { S.a[t] = L.tree_a[t]; S.first[t] = L.depth_first[t]; }
-        if (t == 0) S.maxd = L.max_depth;
+        if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; }
     }
+    __syncthreads();
+    {
+        const uint32_t l = L.len[t];
+        const uint32_t key = __reduce_min_sync(0xffffffffu, l ? (l << 8) | (uint32_t)t : 0xFFFFu);
+        if (lane == 0) atomicMin(&S.hot, key);
+    }
+    __syncthreads();
+    const uint32_t hot = S.hot & 0xFFu;
     // ---- warp chunks and their histograms ----
     const uint32_t nw = (uint32_t)min((uint64_t)kEncWarps, max((uint64_t)1, n / kEMinChunk));
     const uint32_t Q0 = (uint32_t)(((uint64_t)n * warp / nw) & ~31ull);
@@ -310,7 +339,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             const uint32_t k = kb + 32 * lane;
             uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (k < Q1) ldg32(src + k, src_end, x);
-            hist_add32(hist, x, k < Q1 ? min(32u, Q1 - k) : 0u);
+            hist_add32(hist, x, k < Q1 ? min(32u, Q1 - k) : 0u, hot);
         }
     }
     __syncthreads();
@@ -343,24 +372,14 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         enc_node_counts(S, L, E.start, E.pos, V);
         for (int v = lane; v < V; v += 32) E.pos[v] += S.bitsrc[v];
         __syncwarp();
-        // sub-chunk length from the block's busiest level below the root
-        uint32_t C0 = Q1 - Q0;
-        {
-            uint32_t mx = 1;
-            for (int d = 1; d < (int)S.maxd; d++) {
-                uint32_t s = 0;
-                for (int v = S.first[d]; v < S.first[d + 1]; v++) s += L.nv[v];
-                mx = s > mx ? s : mx;
-            }
-            const uint64_t c = (uint64_t)(kEBufE - 2 * 128) * n / mx / 5 * 4;
-            if (c < C0) C0 = max(32u, (uint32_t)c & ~31u);
-        }
-        uint32_t C = C0;
+        // the whole chunk at once when its levels fit; else equal sub-chunks
+        // sized from the chunk's busiest level (each with its own histogram)
+        const uint32_t Q = Q1 - Q0;
+        uint32_t C = Q;
+        bool whole = true;
         for (uint32_t P = Q0; P < Q1;) {
             C = min(C, Q1 - P);
-            // ---- sub-chunk histogram -> node demands -> level spans ----
-            if (C == Q1 - Q0) {
-                // the whole chunk: its histogram is the next warp's start counts minus ours
+            if (whole) {
                 for (int s = lane; s < 256; s += 32)
                     hist[s] = ((uint32_t)warp + 1 < nw ? S.w[warp + 1].start[s] : S.htot[s]) - E.start[s];
             } else {
@@ -370,13 +389,21 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     const uint32_t k = kb + 32 * lane;
                     uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     if (k < P + C) ldg32(src + k, src_end, x);
-                    hist_add32(hist, x, k < P + C ? min(32u, P + C - k) : 0u);
+                    hist_add32(hist, x, k < P + C ? min(32u, P + C - k) : 0u, hot);
                 }
             }
             __syncwarp();
             enc_node_counts(S, L, hist, E.dem, V);
-            if (!enc_layout(S, E)) {
-                C = max(32u, (C / 2) & ~31u);
+            uint64_t maxlvl = 0;
+            if (!enc_layout(S, E, maxlvl)) {
+                uint32_t nc = C / 2;
+                if (whole) {
+                    const uint64_t room = kEBufE - 2 * 128;
+                    const uint32_t ns = (uint32_t)min((uint64_t)Q, (maxlvl * 9 / 8 + room - 1) / room);
+                    nc = (Q + ns - 1) / max(ns, 1u);
+                }
+                whole = false;
+                C = max(32u, (min(nc, C / 2 + 32)) & ~31u);
                 continue;
             }
             // ---- the root: input bytes -> codes; bits; children ----
@@ -384,7 +411,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 const uint32_t chv = S.ch[0], c0 = chv & 0xFFFFu, c1 = chv >> 16;
                 const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
                 uint16_t *nb = E.buf[1];
-                uint16_t *lp0 = nb + (i0 ? E.sp[c0 & 0xFFu] : 0), *rp0 = nb + (i1 ? E.sp[c1 & 0xFFu] : 0);
+                uint16_t *lp0 = i0 ? nb + E.sp[c0 & 0xFFu] : E.sink, *rp0 = i1 ? nb + E.sp[c1 & 0xFFu] : E.sink;
                 uint32_t carry = 0;
                 for (uint32_t kb = 0; kb < C; kb += 1024) {
                     const uint32_t kk = kb + 32u * lane;
@@ -412,7 +439,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     const uint32_t r1 = carry + inc - pc;
                     carry += __shfl_sync(0xffffffffu, inc, 31);
                     enc_put_bits(rec32, act, 0u, E.pos[0] + kk, bw, vl);
-                    if (act) enc_split(lp0 + (kk - r1), rp0 + r1, i0, i1, y, bw, vl);
+                    if (act) enc_split(i0 ? lp0 + (kk - r1) : lp0, i1 ? rp0 + r1 : rp0, y, bw, vl);
                 }
             }
             __syncwarp();
@@ -467,9 +494,9 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     if (act) {
                         const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
                         const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-                        uint16_t *lp = bout + (i0 ? E.sp[c0 & 0xFFu] : 0) + (kk - r1);
-                        uint16_t *rp = bout + (i1 ? E.sp[c1 & 0xFFu] : 0) + r1;
-                        enc_split(lp, rp, i0, i1, y, bw, vl);
+                        uint16_t *lp = i0 ? bout + E.sp[c0 & 0xFFu] + (kk - r1) : E.sink;
+                        uint16_t *rp = i1 ? bout + E.sp[c1 & 0xFFu] + r1 : E.sink;
+                        enc_split(lp, rp, y, bw, vl);
                     }
                 }
                 __syncwarp();
@@ -477,7 +504,6 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             for (int v = lane; v < V; v += 32) E.pos[v] += E.dem[v];
             __syncwarp();
             P += C;
-            C = C0;
         }
     }
     __syncthreads();
