@@ -145,13 +145,30 @@ __global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t
     const int K = __syncthreads_count(h[t] != 0);
     uint8_t my_len = 0;
     if (K >= 2 && K <= (1 << max_len)) {
-        // rank of symbol t among present symbols by (count, symbol)
-        if (h[t]) {
-            int r = 0;
-            const uint32_t f = h[t];
-            for (int s = 0; s < 256; s++) r += (h[s] != 0) && (h[s] < f || (h[s] == f && s < t));
-            leafw[r] = f;
-            leafsym[r] = (uint8_t)t;
+        // present symbols sorted by (count, symbol): bitonic sort of one key per
+        // thread (absent symbols sort last); in-warp steps exchange by shuffle
+        {
+            uint64_t key = h[t] ? (((uint64_t)h[t] << 8) | (uint64_t)t) : ~0ull;
+            for (int k = 2; k <= 256; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    uint64_t other;
+                    if (j >= 32) {
+                        pw[t] = key;
+                        __syncthreads();
+                        other = pw[t ^ j];
+                        __syncthreads();
+                    } else {
+                        other = __shfl_xor_sync(0xffffffffu, key, j);
+                    }
+                    const bool lower = (t & j) == 0, up = (t & k) == 0;
+                    // the lower partner keeps the smaller key in an ascending run
+                    key = (lower == up) ? (key < other ? key : other) : (key < other ? other : key);
+                }
+            }
+            if (t < K) {
+                leafw[t] = key >> 8;
+                leafsym[t] = (uint8_t)(key & 0xFF);
+            }
         }
         __syncthreads();
         // level L: leaves only
@@ -295,32 +312,57 @@ __global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_
                 L.child[t][1] = (int16_t)node_child(ts, sorted, t, d, 1);
             }
             __syncthreads();
-            // n_v: each symbol adds its count to every node on its code path
-            if (lens[t]) {
-                const int l = lens[t];
-                for (int d = 0; d < l; d++) {
-                    const int p = codes[t] >> (l - d);
-                    atomicAdd(&L.nv[ts.first[d] + p - ts.a[d]], h[t]);
+            // n_v bottom-up, one depth at a time: a node's count is its children's
+            for (int d = ts.max_len - 1; d >= 0; d--) {
+                const int v = ts.first[d] + t;
+                if (v < ts.first[d + 1]) {
+                    uint32_t c = 0;
+                    for (int k = 0; k < 2; k++) {
+                        const int ch = L.child[v][k];
+                        c += ch >= 0 ? L.nv[ch] : h[-ch - 1];
+                    }
+                    L.nv[v] = c;
                 }
+                __syncthreads();
             }
-            __syncthreads();
             if (t < V) {
                 const int c = L.child[t][1];
                 const uint64_t n1 = c >= 0 ? L.nv[c] : h[-c - 1];
                 L.sel[t] = ans_select(L.nv[t], n1, L.depth[t], sp);
             }
             __syncthreads();
-            if (t == 0) {
-                int nsel = 0;
-                for (int v = 0; v < V; v++) nsel += L.sel[v] != 0;
-                uint32_t off = (kNvOff + 5u * V + 3u) & ~3u;
-                off += 4u * nsel;
-                L.body0 = off;
-                L.n_sel = (uint8_t)nsel;
-                for (int v = 0; v < V; v++) if (!L.sel[v]) { L.body_off[v] = off; off += (L.nv[v] + 7) / 8; }
-                for (int v = 0; v < V; v++) if (L.sel[v]) { L.body_off[v] = off; off += (L.nv[v] + 7) / 8; }
-                L.body_end = off;
-                L.rec_bound = (off + 15u) & ~15u;
+            if (t < 32) {
+                // bodies: the raw (unselected) nodes first, then the selected ones, node order
+                const int lane = t;
+                uint32_t nsel = 0, raw_tot = 0;
+                for (int base = 0; base < V; base += 32) {
+                    const int v = base + lane;
+                    const bool in = v < V;
+                    nsel += __popc(__ballot_sync(0xffffffffu, in && L.sel[v]));
+                    raw_tot += __reduce_add_sync(0xffffffffu, (in && !L.sel[v]) ? (L.nv[v] + 7) / 8 : 0u);
+                }
+                const uint32_t off0 = ((kNvOff + 5u * V + 3u) & ~3u) + 4u * nsel;
+                uint32_t c_raw = off0, c_sel = off0 + raw_tot;
+                for (int base = 0; base < V; base += 32) {
+                    const int v = base + lane;
+                    const bool in = v < V, sel = in && L.sel[v];
+                    const uint32_t by = in ? (L.nv[v] + 7) / 8 : 0u;
+                    uint32_t xr = (in && !sel) ? by : 0u, xs = sel ? by : 0u;
+                    uint32_t ir = xr, is = xs;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t yr = __shfl_up_sync(0xffffffffu, ir, o), ys = __shfl_up_sync(0xffffffffu, is, o);
+                        if (lane >= o) { ir += yr; is += ys; }
+                    }
+                    if (in) L.body_off[v] = sel ? c_sel + is - xs : c_raw + ir - xr;
+                    c_raw += __shfl_sync(0xffffffffu, ir, 31);
+                    c_sel += __shfl_sync(0xffffffffu, is, 31);
+                }
+                if (lane == 0) {
+                    L.body0 = off0;
+                    L.n_sel = (uint8_t)nsel;
+                    L.body_end = c_sel;
+                    L.rec_bound = (c_sel + 15u) & ~15u;
+                }
             }
         }
     }
