@@ -1067,21 +1067,159 @@ __device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const ui
     __syncthreads();
 }
 
+// Warp version of the directory pass, for blocks with at most kDirWarpMax
+// superblocks: one warp sweeps every node's superblocks in one flat pass
+// (segmented scan per node), then finds the cursors top-down.  u / nv /
+// first / maxd are the warp's scratch.
+constexpr uint32_t kDirWarpMax = 8192;
+
+// superblock count of block b's rank directory (0: the block has one tile)
+__device__ inline uint32_t dir_entries(int b, const uint8_t *comp, const uint64_t *comp_off, int nblk,
+                                       const uint8_t *ws, uint64_t ws_bytes) {
+    const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
+    if (W.blk_ntile[b] <= 1) return 0;
+    const DecRegions G = dec_regions(nblk, ws);
+    const uint8_t *rec = comp + comp_off[b];
+    const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
+    const uint64_t nbase = G.dir + W.blk_dir[b];
+    return nbase + ntab_bytes(V) <= ws_bytes ? *reinterpret_cast<const uint32_t *>(ws + nbase + 20) : 0xFFFFFFFFu;
+}
+
+__device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                                int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                                uint32_t *u, uint32_t *nvs, uint8_t *first, uint8_t &maxd) {
+    const int lane = threadIdx.x & 31;
+    const DecWs W = dec_ws(ws, nblk);
+    const DecRegions G = dec_regions(nblk, ws);
+    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
+    const uint32_t ntile = W.blk_ntile[b], T = W.blk_T[b];
+    if (ntile <= 1 || *reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
+    const uint8_t *rec = comp + comp_off[b];
+    const uint32_t rb = ld_le32(rec);
+    const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
+    const uint64_t nbase = G.dir + W.blk_dir[b], ntb = ntab_bytes(V);
+    const uint8_t *nt = ws + nbase;
+    const uint32_t ent = nbase + ntb <= ws_bytes ? *reinterpret_cast<const uint32_t *>(nt + 20) : 0u;
+    if (nbase + ntb + 4ull * ent + 4ull * (ntile + 1) * V > ws_bytes) {
+        if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
+        return;
+    }
+    uint32_t *dirp = reinterpret_cast<uint32_t *>(ws + nbase + ntb);
+    uint32_t *cur = dirp + ent;
+    const uint32_t *nsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr), *nch = nsrc + V;
+    const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
+    const uint64_t sbase = G.scratch + W.blk_scratch[b];
+    TileSrc src;
+    src.rec = rec;
+    src.rec_bytes = rb;
+    src.scr = ws + sbase;
+    src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
+    if (lane < 17) first[lane] = nt[lane];
+    if (lane == 17) maxd = nt[17];
+    const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (__ldg(nv + v) + dir_bits - 1) / dir_bits; },
+                                          [&](int v, uint32_t p) { u[v] = p; nvs[v] = __ldg(nv + v); });
+    __syncwarp();
+    if (tot != ent) {
+        if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+        return;
+    }
+    const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
+    uint32_t vcur = 0, carry = 0;
+    for (uint32_t base = 0; base < ent; base += 32) {
+        const uint32_t cand = vcur + 1 + lane;
+        uint32_t bit = 0;
+        if (cand < V) {
+            const uint32_t sd = u[cand] - base;
+            if (sd < 32) bit = 1u << sd;
+        }
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
+        const uint32_t v = vcur + __popc(starts & le);
+        const uint32_t g = base + lane;
+        uint32_t pc = 0;
+        if (g < ent) {
+            const uint32_t e0 = (g - u[v]) * dir_bits, nvv = nvs[v], s0 = nsrc[v];
+            for (uint32_t e = e0; e < e0 + dir_bits && e < nvv; e += 32) {
+                uint32_t w = tile_bits(src, s0, e);
+                if (nvv - e < 32) w &= (1u << (nvv - e)) - 1u;
+                pc += __popc(w);
+            }
+        }
+        uint32_t inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t sl = starts & le;
+        const int sa = sl ? 31 - __clz(sl) : -1;
+        const uint32_t before = __shfl_sync(0xffffffffu, inc, sa > 0 ? sa - 1 : 0);
+        const uint32_t ex = inc - pc - (sa > 0 ? before : 0u) + (sa < 0 ? carry : 0u);
+        if (g < ent) dirp[g] = ex;
+        carry = __shfl_sync(0xffffffffu, ex + pc, 31);
+        vcur = __shfl_sync(0xffffffffu, v, 31);
+    }
+    for (uint32_t v = lane; v < V; v += 32) { cur[v] = 0; cur[(size_t)ntile * V + v] = nvs[v]; }
+    for (uint32_t k = 1 + lane; k < ntile; k += 32) cur[(size_t)k * V] = k * T;
+    __syncwarp();
+    int bad = 0;
+    for (int d = 0; d < (int)maxd; d++) {
+        const uint32_t f0 = first[d], nd = first[d + 1] - f0;
+        for (uint32_t i = lane; i < (ntile - 1) * nd; i += 32) {
+            const uint32_t k = 1 + i / nd, v = f0 + i % nd;
+            const uint32_t c = cur[(size_t)k * V + v], nvv = nvs[v];
+            if (c > nvv) { bad = 1; continue; }
+            const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
+            uint32_t sb = c / dir_bits;
+            if (sb >= nsb) sb = nsb - 1;
+            uint32_t ones = dirp[u[v] + sb];
+            const uint32_t s0 = nsrc[v];
+            for (uint32_t e = sb * dir_bits; e < c; e += 32) {
+                uint32_t w = tile_bits(src, s0, e);
+                if (c - e < 32) w &= (1u << (c - e)) - 1u;
+                ones += __popc(w);
+            }
+            const uint32_t chv = nch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
+            if (!(c0 & 0x8000u)) cur[(size_t)k * V + c0] = c - ones;
+            if (!(c1 & 0x8000u)) cur[(size_t)k * V + c1] = ones;
+        }
+        __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+    __syncwarp();
+}
+
+struct DirWarpSmem {
+    uint32_t u[256], nv[256];
+    uint8_t first[17];
+    uint8_t maxd;
+    uint8_t pad[14];
+};
+
 struct TileSmem {
     uint32_t sel[4][16];
     WarpTile w[kDecWarps];
 };
 
 // Plain tile pass: every warp takes tiles by ticket (workspace header word 12).
-// Plain directory pass: every CTA takes blocks with several tiles.
+// Plain directory pass: CTAs take the blocks with many superblocks, then
+// every warp takes the blocks with few.
 __global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_t *__restrict__ comp,
                                                                     const uint64_t *__restrict__ comp_off, int nblk,
                                                                     uint8_t *__restrict__ ws, uint64_t ws_bytes,
                                                                     int32_t *__restrict__ status) {
     __shared__ DirSmem D;
-    const DecWs W = dec_ws(ws, nblk);
-    for (int b = blockIdx.x; b < nblk; b += gridDim.x)
-        if (W.blk_ntile[b] > 1) dir_cta(b, comp, comp_off, nblk, ws, ws_bytes, status, D);
+    __shared__ DirWarpSmem DW[kDecWarps];
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const uint32_t e = dir_entries(b, comp, comp_off, nblk, ws, ws_bytes);
+        if (e > kDirWarpMax) dir_cta(b, comp, comp_off, nblk, ws, ws_bytes, status, D);
+    }
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kDecWarps + warp, nw = gridDim.x * kDecWarps;
+    DirWarpSmem &M = DW[warp];
+    for (int b = gw; b < nblk; b += nw) {
+        const uint32_t e = dir_entries(b, comp, comp_off, nblk, ws, ws_bytes);
+        if (e && e <= kDirWarpMax) dir_warp(b, comp, comp_off, nblk, ws, ws_bytes, status, M.u, M.nv, M.first, M.maxd);
+    }
 }
 
 __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *__restrict__ comp,
@@ -1112,8 +1250,10 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *_
 //   plans      8 blocks per item, one warp each (ticket order = block order,
 //              as the plan's look-back needs)
 //   ANS        8 segments per item, one warp each
-//   directory  one block per item, whole CTA (blocks with one tile skip it)
-// then warp items: tiles, one per warp.  A CTA turns to tiles once the CTA
+//   directory  one block per item, whole CTA, for blocks with many
+//              superblocks (other blocks skip it)
+// then warp items: the directories of the other multi-tile blocks, then the
+// tiles, one per warp.  A CTA turns to tiles once the CTA
 // items are all taken.  An item only waits (bounded) on items earlier in the
 // queue: the ANS and later items on all plans; a directory on its block's ANS
 // segments; a tile on its block's ANS segments and directory.  The CTAs that
@@ -1163,7 +1303,7 @@ struct BatchQueue {
 __device__ inline uint32_t batch_items_total(const BatchQueue &q) {
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
     const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
-    return nplan + (hdr[2] + kDecWarps - 1) / kDecWarps + (uint32_t)q.nblk + hdr[6];
+    return nplan + (hdr[2] + kDecWarps - 1) / kDecWarps + 2u * (uint32_t)q.nblk + hdr[6];
 }
 
 enum : int { kItemDone = 0, kItemNone = 1, kItemStop = 2 };
@@ -1213,7 +1353,7 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
     if (it < (uint32_t)nblk) {
         // ---- directory of block it ----
         const int b = (int)it;
-        if (W.blk_ntile[b] > 1) {
+        if (dir_entries(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes) > kDirWarpMax) {
             const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
             int okw = 1;
             if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs);
@@ -1230,12 +1370,31 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
     return kItemNone;
 }
 
-// Tile `it` of the queue with one warp, after its block's ANS segments and
-// directory (bounded waits; an expired one marks the block).
-__device__ inline void batch_tile(const BatchQueue &q, uint32_t it, WarpTile &S, const uint32_t (*sel)[16]) {
+// Warp item `it` of the queue: items 0..nblk-1 are the directories of the
+// blocks with few superblocks (after the block's ANS segments), then the
+// tiles (after the block's ANS segments and directory).  Waits are bounded;
+// an expired one marks the block.
+__device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTile &S, const uint32_t (*sel)[16]) {
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(q.ws, q.nblk);
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
+    if (it < (uint32_t)q.nblk) {
+        const int b = (int)it;
+        const uint32_t e = dir_entries(b, q.comp, q.comp_off, q.nblk, q.ws, q.ws_bytes);
+        if (!e || e > kDirWarpMax) return;
+        const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
+        int okw = 1;
+        if (lane == 0) {
+            okw = wait_geq(&W.segs_done[b], nsegs);
+            if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
+        }
+        if (__shfl_sync(0xffffffffu, okw, 0))
+            dir_warp(b, q.comp, q.comp_off, q.nblk, q.ws, q.ws_bytes, q.status, S.pos, S.dem, S.first, S.maxd);
+        __syncwarp();
+        if (lane == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
+        return;
+    }
+    it -= (uint32_t)q.nblk;
     const int b = find_block(W.blk_tile, q.nblk, it);
     const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
     int okw = 1;
@@ -1273,14 +1432,14 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_batch_kernel(const uint
         if (r == kItemStop) return;
         if (r == kItemNone) break;
     }
-    // tiles: every warp on its own
-    const uint32_t total_tiles = hdr[6];
+    // warp items (small directories, tiles): every warp on its own
+    const uint32_t total = (uint32_t)nblk + hdr[6];
     for (;;) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(&hdr[12], 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= total_tiles) break;
-        batch_tile(q, it, B.u.tw[warp], B.sel);
+        if (it >= total) break;
+        batch_warp_item(q, it, B.u.tw[warp], B.sel);
     }
 }
 
@@ -1387,13 +1546,13 @@ __global__ void __launch_bounds__(kDecThreads, 2) serve_loop_kernel(ServeCtl *__
         }
         // the request's CTA items are all taken: its tiles, every warp on its own
         uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
-        const uint32_t total_tiles = hdr[6];
+        const uint32_t total = (uint32_t)q.nblk + hdr[6];
         for (;;) {
             uint32_t it = 0;
             if (lane == 0) it = atomicAdd(&hdr[12], 1u);
             it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= total_tiles) break;
-            batch_tile(q, it, B.u.tw[warp], B.sel);
+            if (it >= total) break;
+            batch_warp_item(q, it, B.u.tw[warp], B.sel);
             if (lane == 0) serve_item_done(q, r, flags);
             __syncwarp();
         }
