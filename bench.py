@@ -75,6 +75,23 @@ def whole_job_gbs(raw_per_rank, steps, tot_ms_max, world):
     return world * raw_per_rank * steps / (tot_ms_max / 1e3) / 1e9
 
 
+KERNEL_SOURCES = {"encode_kernel": "paper_2606_05765_gb300/csrc/k_encode.cu",
+                  "decode_batch_kernel": "paper_2606_05765_gb300/csrc/k_decode.cu"}
+
+
+def kernel_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/traffic.json), only while the kernel's source file is
+    byte-identical to the one profiled (else None)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload][kernel]
+        src = open(os.path.join(ROOT, KERNEL_SOURCES[kernel]), "rb").read()
+    except (OSError, KeyError, ValueError):
+        return None
+    return rec["bytes"] if hashlib.sha256(src).hexdigest() == rec["source_sha256"] else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -507,7 +524,7 @@ def main(argv=None):
                       "encode_gbs": round(raw / (statistics.mean(p_enc) / 1e3) / 1e9, 3),
                       "decode_gbs": round(raw / (statistics.mean(p_dec) / 1e3) / 1e9, 3)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": peak,
-                         "unit": "GB/s", "frac": r4(ach / peak), "traffic": None,
+                         "unit": "GB/s", "frac": r4(ach / peak), "traffic": kernel_traffic(dom, args.workload),
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                          "kernels": {k: {kk: r4(vv) for kk, vv in v.items()} for k, v in kernels.items()}},
             "serving": serving,

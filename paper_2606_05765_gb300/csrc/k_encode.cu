@@ -36,7 +36,6 @@ struct __align__(16) EncWarp {
     uint16_t sp[256];                    // first symbol of node v's span in its level buffer
     uint16_t gs[256];                    // first 32-symbol group of node v within its level
     uint16_t lg[16];                     // groups of each level
-    uint16_t sink[64];                   // where a leaf side's symbols go
 };
 static_assert(sizeof(EncWarp) % 16 == 0 && ((kEBufE + kESlack) * 2) % 16 == 0, "16-byte aligned level buffers");
 
@@ -206,26 +205,41 @@ __device__ inline uint32_t top_bits8(uint32_t x0, uint32_t x1, uint32_t x2, uint
 }
 
 // Stable partition of up to 32 symbols (values y[j], bits in bw, vl valid)
-// into the left (bit 0) and right (bit 1) spans of the next level.  A leaf
-// side keeps nothing: its pointer is the warp's sink.  A full group stores
-// every symbol (one address select each); a partial one stores the valid ones.
-__device__ inline void enc_split(uint16_t *lp, uint16_t *rp, const uint32_t (&y)[16], uint32_t bw, uint32_t vl) {
-    uint32_t ol = 0;
-    if (vl >= 32) {
+// into the left (bit 0) and right (bit 1) spans of the next level.  Only
+// internal children keep symbols: with both internal every symbol is stored
+// (one address select each); with one, only that side's symbols are.
+__device__ inline void enc_split(uint16_t *lp, uint16_t *rp, bool i0, bool i1, const uint32_t (&y)[16], uint32_t bw,
+                                 uint32_t vl) {
+    const uint32_t vm = vl >= 32 ? 0xFFFFFFFFu : ((1u << vl) - 1u);
+    if (i0 && i1) {
+        uint32_t ol = 0;
+        if (vl >= 32) {
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
-            const uint32_t bit = (bw >> j) & 1u;
-            const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
-            *(bit ? rp + ol : lp + (j - ol)) = val;
-            ol += bit;
+            for (int j = 0; j < 32; j++) {
+                const uint32_t bit = (bw >> j) & 1u;
+                const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
+                *(bit ? rp + ol : lp + (j - ol)) = val;
+                ol += bit;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const uint32_t bit = (bw >> j) & 1u;
+                const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
+                if ((uint32_t)j < vl) *(bit ? rp + ol : lp + (j - ol)) = val;
+                ol += bit;
+            }
         }
-    } else {
+    } else if (i0 || i1) {
+        // one side: its symbols are the set bits of m, stored in order
+        const uint32_t m = (i1 ? bw : ~bw) & vm;
+        uint16_t *p = i1 ? rp : lp;
+        uint32_t c = 0;
 #pragma unroll
         for (int j = 0; j < 32; j++) {
-            const uint32_t bit = (bw >> j) & 1u;
             const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
-            if ((uint32_t)j < vl) *(bit ? rp + ol : lp + (j - ol)) = val;
-            ol += bit;
+            if ((m >> j) & 1u) p[c] = val;
+            c += (m >> j) & 1u;
         }
     }
 }
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 const uint32_t chv = S.ch[0], c0 = chv & 0xFFFFu, c1 = chv >> 16;
                 const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
                 uint16_t *nb = E.buf[1];
-                uint16_t *lp0 = i0 ? nb + E.sp[c0 & 0xFFu] : E.sink, *rp0 = i1 ? nb + E.sp[c1 & 0xFFu] : E.sink;
+                uint16_t *lp0 = nb + (i0 ? E.sp[c0 & 0xFFu] : 0), *rp0 = nb + (i1 ? E.sp[c1 & 0xFFu] : 0);
                 uint32_t carry = 0;
                 for (uint32_t kb = 0; kb < C; kb += 1024) {
                     const uint32_t kk = kb + 32u * lane;
@@ -439,7 +453,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     const uint32_t r1 = carry + inc - pc;
                     carry += __shfl_sync(0xffffffffu, inc, 31);
                     enc_put_bits(rec32, act, 0u, E.pos[0] + kk, bw, vl);
-                    if (act) enc_split(i0 ? lp0 + (kk - r1) : lp0, i1 ? rp0 + r1 : rp0, y, bw, vl);
+                    if (act) enc_split(lp0 + (kk - r1), rp0 + r1, i0, i1, y, bw, vl);
                 }
             }
             __syncwarp();
@@ -494,9 +508,9 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     if (act) {
                         const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
                         const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-                        uint16_t *lp = i0 ? bout + E.sp[c0 & 0xFFu] + (kk - r1) : E.sink;
-                        uint16_t *rp = i1 ? bout + E.sp[c1 & 0xFFu] + r1 : E.sink;
-                        enc_split(lp, rp, y, bw, vl);
+                        uint16_t *lp = bout + (i0 ? E.sp[c0 & 0xFFu] : 0) + (kk - r1);
+                        uint16_t *rp = bout + (i1 ? E.sp[c1 & 0xFFu] : 0) + r1;
+                        enc_split(lp, rp, i0, i1, y, bw, vl);
                     }
                 }
                 __syncwarp();
