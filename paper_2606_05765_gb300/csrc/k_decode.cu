@@ -28,7 +28,6 @@
 //              from popcounts.
 #include "ans_dev.cuh"
 #include "lookback.cuh"
-#include "tma.cuh"
 
 namespace pv {
 

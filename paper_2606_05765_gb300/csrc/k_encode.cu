@@ -17,7 +17,6 @@
 // Below the root a symbol travels as its remaining code bits, most
 // significant first in 16 bits, so a node's bit is bit 15 and the child
 // receives the value shifted left by one.
-#include "tma.cuh"
 
 namespace pv {
 
