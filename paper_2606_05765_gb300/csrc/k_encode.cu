@@ -18,6 +18,8 @@
 // significant first in 16 bits, so a node's bit is bit 15 and the child
 // receives the value shifted left by one.
 
+#include "pivco_dev.cuh"
+
 namespace pv {
 
 constexpr int kEncThreads = 256;
@@ -539,6 +541,8 @@ cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, 
 }
 
 }  // namespace pv
+
+#include "pivco_dev.cuh"
 
 namespace pv {
 cudaError_t prepare_encode_kernels() {
