@@ -542,8 +542,6 @@ cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, 
 
 }  // namespace pv
 
-#include "pivco_dev.cuh"
-
 namespace pv {
 cudaError_t prepare_encode_kernels() {
     return cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmem));
