@@ -116,23 +116,23 @@ __device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32
     if (lane == 0 && hot) atomicAdd(&hist[h], hot);
 }
 
-// node index of the depth-d prefix of code c (length l > d)
-__device__ inline uint32_t enc_node(const EncSmem &S, uint32_t c, uint32_t l, int d) {
-    return (uint32_t)S.first[d] + ((c >> (l - d)) - (uint32_t)S.a[d]);
-}
-
-// node symbol counts of a histogram (each symbol counts in every node on its path)
-__device__ inline void enc_node_counts(const EncSmem &S, const BlockLayout &L, const uint32_t *hist, uint32_t *cnt,
-                                       int V) {
+// node symbol counts of a histogram, bottom-up one depth at a time: a node
+// counts its children (a leaf child: its symbol's count).  One warp.
+__device__ inline void enc_node_counts(const EncSmem &S, const uint32_t *hist, uint32_t *cnt) {
     const int lane = threadIdx.x & 31;
-    for (int v = lane; v < V; v += 32) cnt[v] = 0;
-    __syncwarp();
-    for (int s = lane; s < 256; s += 32) {
-        const uint32_t h = hist[s], l = L.len[s], c = L.code[s];
-        if (!h || !l) continue;
-        for (int d = 0; d < (int)l; d++) atomicAdd(&cnt[enc_node(S, c, l, d)], h);
+    for (int d = (int)S.maxd - 1; d >= 0; d--) {
+        for (int v = S.first[d] + lane; v < (int)S.first[d + 1]; v += 32) {
+            const uint32_t chv = S.ch[v];
+            uint32_t c = 0;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const uint32_t code = (chv >> (16 * k)) & 0xFFFFu;
+                c += (code & 0x8000u) ? hist[code & 0xFFu] : cnt[code];
+            }
+            cnt[v] = c;
+        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // Spans and groups of every level for the current demands; false when a
@@ -367,11 +367,10 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             run += h;
         }
         S.htot[t] = run;
-        const uint32_t l = L.len[t], c = L.code[t];
-        if (run && l)
-            for (int d = 0; d < (int)l; d++) atomicAdd(&S.tot[enc_node(S, c, l, d)], run);
-        if (run && !l) S.tot[255] = 0xFFFFFFFFu;   // a symbol the code does not have: mismatch below
+        if (run && !L.len[t]) S.tot[255] = 0xFFFFFFFFu;   // a symbol the code does not have: mismatch below
     }
+    __syncthreads();
+    if (warp == 0) enc_node_counts(S, S.htot, S.tot);
     __syncthreads();
     {
         int bad = t < V && S.tot[t] != L.nv[t];
@@ -384,7 +383,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     uint32_t *rec32 = reinterpret_cast<uint32_t *>(rec);
     if ((uint32_t)warp < nw) {
         // start cursors of this warp's chunk
-        enc_node_counts(S, L, E.start, E.pos, V);
+        enc_node_counts(S, E.start, E.pos);
         for (int v = lane; v < V; v += 32) E.pos[v] += S.bitsrc[v];
         __syncwarp();
         // the whole chunk at once when its levels fit; else equal sub-chunks
@@ -408,7 +407,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 }
             }
             __syncwarp();
-            enc_node_counts(S, L, hist, E.dem, V);
+            enc_node_counts(S, hist, E.dem);
             uint64_t maxlvl = 0;
             if (!enc_layout(S, E, maxlvl)) {
                 uint32_t nc = C / 2;
