@@ -259,7 +259,7 @@ pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off,
 
 /* Launch tuning of the decode (process-wide).  None of it changes any output.
  * tile_max: longest root tile in symbols (a multiple of 128, 128..65536);
- * dir_bits: rank-directory granularity in bits (a multiple of 32, 32..1024);
+ * dir_bits: rank-directory granularity in bits (a multiple of 32, 32..256);
  * ctas_per_sm: persistent CTAs per SM (0 = as many as fit, at most 32). */
 typedef struct pivco_tuning {
     int32_t tile_max;

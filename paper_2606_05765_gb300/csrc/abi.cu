@@ -281,7 +281,7 @@ pivco_status pivco_get_tuning(pivco_tuning *t) {
 
 pivco_status pivco_set_tuning(const pivco_tuning *t) {
     if (!t || t->tile_max < 128 || t->tile_max > 65536 || (t->tile_max & 127) || t->dir_bits < 32 ||
-        t->dir_bits > 1024 || (t->dir_bits & 31) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
+        t->dir_bits > 256 || (t->dir_bits & 31) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
         return PIVCO_ERR_INVALID_ARG;
     set_tuning(DecTuning{(uint32_t)t->tile_max, (uint32_t)t->dir_bits, (uint32_t)t->ctas_per_sm});
     return PIVCO_OK;

@@ -552,6 +552,34 @@ __device__ inline uint32_t tile_bits(const TileSrc &s, uint32_t pos, uint32_t k)
     return __funnelshift_r(lo, hi, sh);
 }
 
+// popcount of bits [e, e + len) (len <= 256) of the bitmap at bit address
+// pos: the covering words are loaded together, then counted
+__device__ inline uint32_t tile_popc(const TileSrc &s, uint32_t pos, uint32_t e, uint32_t len) {
+    const bool sc = (pos >> 31) != 0;
+    const uint64_t a = (uint64_t)(pos & 0x7FFFFFFFu) + e;
+    const uint64_t w0 = a >> 5;
+    const uint32_t sh = (uint32_t)a & 31u;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(sc ? s.scr : s.rec);
+    const uint64_t lim = sc ? s.scr_bytes : (uint64_t)s.rec_bytes;
+    const uint32_t nw = (sh + len + 31) >> 5;   // words holding the range (<= 9)
+    uint32_t x[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) x[i] = ((uint32_t)i < nw && 4 * (w0 + i) + 4 <= lim) ? __ldcg(w + w0 + i) : 0u;
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        // bits of word i inside [sh, sh + len)
+        const int lo = 32 * i, hi = lo + 32;
+        const int b0 = max(lo, (int)sh), b1 = min(hi, (int)(sh + len));
+        if (b1 > b0) {
+            const uint32_t n = (uint32_t)(b1 - b0), st = (uint32_t)(b0 - lo);
+            const uint32_t m = n >= 32 ? 0xFFFFFFFFu : (((1u << n) - 1u) << st);
+            c += __popc(x[i] & m);
+        }
+    }
+    return c;
+}
+
 // 8 bytes of a level buffer from byte a (reads up to 11 bytes past a)
 __device__ inline void win8(const uint8_t *buf, uint32_t a, uint32_t &x0, uint32_t &x1) {
     const uint32_t *w = reinterpret_cast<const uint32_t *>(buf + (a & ~3u));
@@ -988,12 +1016,8 @@ __device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const ui
             const uint32_t g = base + lane;
             uint32_t pc = 0;
             if (g < g1) {
-                const uint32_t e0 = (g - D.u[v]) * dir_bits, nvv = D.nv[v], s0 = D.src[v];
-                for (uint32_t e = e0; e < e0 + dir_bits && e < nvv; e += 32) {
-                    uint32_t w = tile_bits(src, s0, e);
-                    if (nvv - e < 32) w &= (1u << (nvv - e)) - 1u;
-                    pc += __popc(w);
-                }
+                const uint32_t e0 = (g - D.u[v]) * dir_bits, nvv = D.nv[v];
+                pc = tile_popc(src, D.src[v], e0, min(dir_bits, nvv - e0));
             }
             uint32_t inc = pc;
 #pragma unroll
@@ -1048,13 +1072,7 @@ __device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const ui
             const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
             uint32_t sb = c / dir_bits;
             if (sb >= nsb) sb = nsb - 1;
-            uint32_t ones = dirp[D.u[v] + sb];
-            const uint32_t s0 = D.src[v];
-            for (uint32_t e = sb * dir_bits; e < c; e += 32) {
-                uint32_t w = tile_bits(src, s0, e);
-                if (c - e < 32) w &= (1u << (c - e)) - 1u;
-                ones += __popc(w);
-            }
+            const uint32_t ones = dirp[D.u[v] + sb] + tile_popc(src, D.src[v], sb * dir_bits, c - sb * dir_bits);
             const uint32_t chv = D.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
             if (!(c0 & 0x8000u)) cur[(size_t)k * V + c0] = c - ones;
             if (!(c1 & 0x8000u)) cur[(size_t)k * V + c1] = ones;
@@ -1136,12 +1154,8 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
         const uint32_t g = base + lane;
         uint32_t pc = 0;
         if (g < ent) {
-            const uint32_t e0 = (g - u[v]) * dir_bits, nvv = nvs[v], s0 = nsrc[v];
-            for (uint32_t e = e0; e < e0 + dir_bits && e < nvv; e += 32) {
-                uint32_t w = tile_bits(src, s0, e);
-                if (nvv - e < 32) w &= (1u << (nvv - e)) - 1u;
-                pc += __popc(w);
-            }
+            const uint32_t e0 = (g - u[v]) * dir_bits, nvv = nvs[v];
+            pc = tile_popc(src, nsrc[v], e0, min(dir_bits, nvv - e0));
         }
         uint32_t inc = pc;
 #pragma unroll
@@ -1170,13 +1184,7 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
             const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
             uint32_t sb = c / dir_bits;
             if (sb >= nsb) sb = nsb - 1;
-            uint32_t ones = dirp[u[v] + sb];
-            const uint32_t s0 = nsrc[v];
-            for (uint32_t e = sb * dir_bits; e < c; e += 32) {
-                uint32_t w = tile_bits(src, s0, e);
-                if (c - e < 32) w &= (1u << (c - e)) - 1u;
-                ones += __popc(w);
-            }
+            const uint32_t ones = dirp[u[v] + sb] + tile_popc(src, nsrc[v], sb * dir_bits, c - sb * dir_bits);
             const uint32_t chv = nch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
             if (!(c0 & 0x8000u)) cur[(size_t)k * V + c0] = c - ones;
             if (!(c1 & 0x8000u)) cur[(size_t)k * V + c1] = ones;

@@ -66,3 +66,19 @@ def test_host_argument_errors(built_lib):
     bad.ans_skew_den = 0
     assert L.pivco_build_layout(None, None, 0, C.byref(bad), None, None, None, None) == P.ERR_INVALID_ARG
     assert L.pivco_decode_blocks(None, None, -1, None, None, None, 0, None, None) == P.ERR_INVALID_ARG
+
+
+def test_tuning_validation(built_lib):
+    """Host-side checks of the decode tuning (no device work)."""
+    import paper_2606_05765_gb300 as P
+    try:
+        for bad in [(65536, 512, 0), (65536, 100, 0), (100, 128, 0), (65536, 128, 33), (131072, 128, 0)]:
+            with pytest.raises(P.PivcoError):
+                P.set_tuning(*bad)
+        P.set_tuning(16384, 256, 2)
+        t = P.get_tuning()
+        assert (t.tile_max, t.dir_bits, t.ctas_per_sm) == (16384, 256, 2)
+    finally:
+        P.set_tuning()
+    t = P.get_tuning()
+    assert (t.tile_max, t.dir_bits, t.ctas_per_sm) == (65536, 128, 0)
