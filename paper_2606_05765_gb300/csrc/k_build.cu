@@ -68,7 +68,21 @@ __global__ void __launch_bounds__(kHistThreads) histogram_kernel(const uint8_t *
     }
     const uint64_t nvec = (hi - a) / 16;
     const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
-    for (uint64_t i = t; i < nvec; i += kHistThreads) {
+    // four loads in flight per thread, then their bytes
+    uint64_t i = t;
+    for (; i + 3 * kHistThreads < nvec; i += 4 * kHistThreads) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = __ldg(vp + i + u * kHistThreads);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            hist_add_word(q[u].x, hot4, hot, my, hot_cnt);
+            hist_add_word(q[u].y, hot4, hot, my, hot_cnt);
+            hist_add_word(q[u].z, hot4, hot, my, hot_cnt);
+            hist_add_word(q[u].w, hot4, hot, my, hot_cnt);
+        }
+    }
+    for (; i < nvec; i += kHistThreads) {
         const uint4 q = __ldg(vp + i);
         hist_add_word(q.x, hot4, hot, my, hot_cnt);
         hist_add_word(q.y, hot4, hot, my, hot_cnt);

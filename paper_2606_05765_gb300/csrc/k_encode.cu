@@ -205,42 +205,48 @@ __device__ inline uint32_t top_bits8(uint32_t x0, uint32_t x1, uint32_t x2, uint
     return b0 | (b1 << 4);
 }
 
+__device__ inline uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ inline void sts16(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+}
+
 // Stable partition of up to 32 symbols (values y[j], bits in bw, vl valid)
-// into the left (bit 0) and right (bit 1) spans of the next level.  Only
-// internal children keep symbols: with both internal every symbol is stored
-// (one address select each); with one, only that side's symbols are.
-__device__ inline void enc_split(uint16_t *lp, uint16_t *rp, bool i0, bool i1, const uint32_t (&y)[16], uint32_t bw,
+// into the left (bit 0) and right (bit 1) spans of the next level, given as
+// shared-memory byte addresses.  Only internal children keep symbols: with
+// both internal every symbol is stored (one address select each); with one,
+// only that side's symbols are.
+__device__ inline void enc_split(uint32_t la, uint32_t ra, bool i0, bool i1, const uint32_t (&y)[16], uint32_t bw,
                                  uint32_t vl) {
     const uint32_t vm = vl >= 32 ? 0xFFFFFFFFu : ((1u << vl) - 1u);
     if (i0 && i1) {
-        uint32_t ol = 0;
+        // the j-th symbol goes to ra + 2 ones_before(j) or la + 2 (j - ones_before(j))
+        uint32_t ob = 0;
         if (vl >= 32) {
 #pragma unroll
             for (int j = 0; j < 32; j++) {
                 const uint32_t bit = (bw >> j) & 1u;
-                const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
-                *(bit ? rp + ol : lp + (j - ol)) = val;
-                ol += bit;
+                const uint32_t val = (y[j >> 1] >> (16 * (j & 1))) << 1;
+                sts16(bit ? ra + ob : la + (2u * j - ob), val);
+                ob += 2u * bit;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 32; j++) {
                 const uint32_t bit = (bw >> j) & 1u;
-                const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
-                if ((uint32_t)j < vl) *(bit ? rp + ol : lp + (j - ol)) = val;
-                ol += bit;
+                const uint32_t val = (y[j >> 1] >> (16 * (j & 1))) << 1;
+                if ((uint32_t)j < vl) sts16(bit ? ra + ob : la + (2u * j - ob), val);
+                ob += 2u * bit;
             }
         }
     } else if (i0 || i1) {
         // one side: its symbols are the set bits of m, stored in order
         const uint32_t m = (i1 ? bw : ~bw) & vm;
-        uint16_t *p = i1 ? rp : lp;
-        uint32_t c = 0;
+        uint32_t a = i1 ? ra : la;
 #pragma unroll
         for (int j = 0; j < 32; j++) {
-            const uint16_t val = (uint16_t)((y[j >> 1] >> (16 * (j & 1))) << 1);
-            if ((m >> j) & 1u) p[c] = val;
-            c += (m >> j) & 1u;
+            const uint32_t val = (y[j >> 1] >> (16 * (j & 1))) << 1;
+            if ((m >> j) & 1u) sts16(a, val);
+            a += 2u * ((m >> j) & 1u);
         }
     }
 }
@@ -424,8 +430,8 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             {
                 const uint32_t chv = S.ch[0], c0 = chv & 0xFFFFu, c1 = chv >> 16;
                 const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-                uint16_t *nb = E.buf[1];
-                uint16_t *lp0 = nb + (i0 ? E.sp[c0 & 0xFFu] : 0), *rp0 = nb + (i1 ? E.sp[c1 & 0xFFu] : 0);
+                const uint32_t nb = smem_addr(E.buf[1]);
+                const uint32_t lp0 = nb + 2u * (i0 ? E.sp[c0 & 0xFFu] : 0u), rp0 = nb + 2u * (i1 ? E.sp[c1 & 0xFFu] : 0u);
                 uint32_t carry = 0;
                 for (uint32_t kb = 0; kb < C; kb += 1024) {
                     const uint32_t kk = kb + 32u * lane;
@@ -453,7 +459,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     const uint32_t r1 = carry + inc - pc;
                     carry += __shfl_sync(0xffffffffu, inc, 31);
                     enc_put_bits(rec32, act, 0u, E.pos[0] + kk, bw, vl);
-                    if (act) enc_split(lp0 + (kk - r1), rp0 + r1, i0, i1, y, bw, vl);
+                    if (act) enc_split(lp0 + 2u * (kk - r1), rp0 + 2u * r1, i0, i1, y, bw, vl);
                 }
             }
             __syncwarp();
@@ -508,8 +514,9 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     if (act) {
                         const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
                         const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-                        uint16_t *lp = bout + (i0 ? E.sp[c0 & 0xFFu] : 0) + (kk - r1);
-                        uint16_t *rp = bout + (i1 ? E.sp[c1 & 0xFFu] : 0) + r1;
+                        const uint32_t ob = smem_addr(bout);
+                        const uint32_t lp = ob + 2u * ((i0 ? E.sp[c0 & 0xFFu] : 0u) + (kk - r1));
+                        const uint32_t rp = ob + 2u * ((i1 ? E.sp[c1 & 0xFFu] : 0u) + r1);
                         enc_split(lp, rp, i0, i1, y, bw, vl);
                     }
                 }
