@@ -54,6 +54,7 @@ struct EncSmem {
     EncWarp w[kEncWarps];
 };
 static_assert(offsetof(EncSmem, w) % 16 == 0, "16-byte aligned warp areas");
+static_assert(((sizeof(BlockLayout) + 15) / 16) * 16 <= sizeof(EncWarp::buf[1]), "the staged layout fits a level buffer");
 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop(int n, F f, G out) {
@@ -261,8 +262,17 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     extern __shared__ __align__(128) uint8_t smem_raw[];
     EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const BlockLayout &L = *reinterpret_cast<const BlockLayout *>(reinterpret_cast<const uint8_t *>(layout) +
-                                                                   (size_t)b * kLayoutBytes);
+    // the block's layout, staged into shared memory once (coalesced): every
+    // later read of it is a shared-memory read.  It borrows the last warp's
+    // second level buffer, unused until that warp's levels start.
+    {
+        const uint4 *g = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(layout) +
+                                                          (size_t)b * kLayoutBytes);
+        uint4 *d = reinterpret_cast<uint4 *>(S.w[kEncWarps - 1].buf[1]);
+        for (int i = t; i < (int)((sizeof(BlockLayout) + 15) / 16); i += kEncThreads) d[i] = __ldg(g + i);
+    }
+    __syncthreads();
+    const BlockLayout &L = *reinterpret_cast<const BlockLayout *>(S.w[kEncWarps - 1].buf[1]);
     const uint64_t n = blk_off[b + 1] - blk_off[b];
     uint8_t *rec = out + out_off[b];
     const uint64_t cap = out_off[b + 1] - out_off[b];
@@ -276,6 +286,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         return;
     }
     const int V = L.n_int;
+    const uint32_t rec_bound = L.rec_bound;   // the staged layout is overwritten once the levels start
     // ---- record header (App. D, adapted) ----
     if (t < 16) {
         uint8_t v = 0;
@@ -356,11 +367,14 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     for (int s = lane; s < 256; s += 32) hist[s] = 0;
     __syncwarp();
     if ((uint32_t)warp < nw) {
-        for (uint32_t kb = Q0; kb < Q1; kb += 1024) {
-            const uint32_t k = kb + 32 * lane;
-            uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (k < Q1) ldg32(src + k, src_end, x);
-            hist_add32(hist, x, k < Q1 ? min(32u, Q1 - k) : 0u, hot);
+        // two input loads in flight per lane
+        for (uint32_t kb = Q0; kb < Q1; kb += 2048) {
+            const uint32_t k0 = kb + 32 * lane, k1 = k0 + 1024;
+            uint32_t x0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, x1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (k0 < Q1) ldg32(src + k0, src_end, x0);
+            if (k1 < Q1) ldg32(src + k1, src_end, x1);
+            hist_add32(hist, x0, k0 < Q1 ? min(32u, Q1 - k0) : 0u, hot);
+            hist_add32(hist, x1, k1 < Q1 ? min(32u, Q1 - k1) : 0u, hot);
         }
     }
     __syncthreads();
@@ -530,7 +544,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     __syncthreads();
     if (t == 0) {
         status[b] = PIVCO_OK;
-        rec_bytes[b] = L.rec_bound;
+        rec_bytes[b] = rec_bound;
     }
 }
 
