@@ -262,6 +262,14 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     extern __shared__ __align__(128) uint8_t smem_raw[];
     EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // the block's input is read by the chunk histograms and again by the
+    // root pass: ask L2 for it now, so those reads overlap the setup below
+    {
+        const uint8_t *p0 = in + blk_off[b];
+        const uint64_t nb = blk_off[b + 1] - blk_off[b];
+        for (uint64_t i = 128ull * t; i < nb; i += 128ull * kEncThreads)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + i));
+    }
     // the block's layout, staged into shared memory once (coalesced): every
     // later read of it is a shared-memory read.  It borrows the last warp's
     // second level buffer, unused until that warp's levels start.
