@@ -132,15 +132,28 @@ cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nbl
 // ---------------------------------------------------------------------------
 constexpr int kPmThreads = 256;
 
-__device__ inline int count_less_u64(const uint64_t *a, int n, uint64_t x) {   // # a[i] < x (a sorted)
-    int lo = 0, hi = n;
-    while (lo < hi) { const int m = (lo + hi) >> 1; if (a[m] < x) lo = m + 1; else hi = m; }
-    return lo;
+// # of a[0..n) below x (a sorted, n <= 256): a fixed 9-step search with no
+// data-dependent branch
+__device__ inline int count_less_u64(const uint64_t *a, int n, uint64_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 256; step >= 1; step >>= 1) {
+        const int q = pos + step;
+        const bool ok = q <= n && a[max(0, min(q, n) - 1)] < x;   // the index stays in [0, 256)
+        pos = ok ? q : pos;
+    }
+    return pos;
 }
-__device__ inline int count_le_u64(const uint64_t *a, int n, uint64_t x) {     // # a[i] <= x
-    int lo = 0, hi = n;
-    while (lo < hi) { const int m = (lo + hi) >> 1; if (a[m] <= x) lo = m + 1; else hi = m; }
-    return lo;
+// # of a[0..n) not above x
+__device__ inline int count_le_u64(const uint64_t *a, int n, uint64_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 256; step >= 1; step >>= 1) {
+        const int q = pos + step;
+        const bool ok = q <= n && a[max(0, min(q, n) - 1)] <= x;
+        pos = ok ? q : pos;
+    }
+    return pos;
 }
 
 __global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t *__restrict__ hist, int max_len,
@@ -204,14 +217,20 @@ __global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t
             len_prev = K + P;
             __syncthreads();
         }
-        // selection, top-down
-        if (t == 0) {
+        // selection, top-down (one warp): at each level the selected items are
+        // the first m; count the leaves among them (their positions increase
+        // with i) by testing blocks of 8 leaves, then within the boundary block
+        if (t < 32) {
             int m = 2 * K - 2;
             for (int lvl = 1; lvl <= max_len; lvl++) {
-                int lo = 0, hi = K;       // leaves with position < m (positions increase with i)
-                while (lo < hi) { const int mid = (lo + hi) >> 1; if (leafpos[lvl][mid] < m) lo = mid + 1; else hi = mid; }
-                s_len[lvl] = lo;
-                m = 2 * (m - lo);
+                const int last = min(8 * t + 7, K - 1);
+                const bool full = 8 * t < K && leafpos[lvl][last] < m;
+                const int nb = __popc(__ballot_sync(0xffffffffu, full));
+                const int i2 = 8 * nb + t;
+                const bool below = t < 8 && i2 < K && leafpos[lvl][min(i2, 255)] < m;
+                const int cnt = min(8 * nb, K) + __popc(__ballot_sync(0xffffffffu, below));
+                if (t == 0) s_len[lvl] = cnt;
+                m = 2 * (m - cnt);
             }
         }
         __syncthreads();
@@ -286,12 +305,15 @@ __global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_
     const int K = __syncthreads_count(h[t] != 0);
     uint64_t n = 0;
     {
-        __shared__ unsigned long long s_n;
-        if (t == 0) s_n = 0;
+        // block total: warp sums, then the 8 partial sums (no same-address atomics)
+        __shared__ unsigned long long s_part[kLayThreads / 32];
+        uint64_t x = h[t];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((t & 31) == 0) s_part[t >> 5] = x;
         __syncthreads();
-        if (h[t]) atomicAdd(&s_n, (unsigned long long)h[t]);
-        __syncthreads();
-        n = s_n;
+#pragma unroll
+        for (int w = 0; w < kLayThreads / 32; w++) n += s_part[w];
     }
     int st = PIVCO_OK;
     if (t == 0) { L.n = (uint32_t)n; L.status = 0; }

@@ -98,7 +98,14 @@ __device__ inline void build_tree_shape(const uint8_t *lens, TreeShape &ts, uint
     const int t = threadIdx.x;
     if (t < kMaxLen + 2) ts.cnt[t] = 0;
     __syncthreads();
-    if (t < 256 && lens[t]) atomicAdd(&ts.cnt[lens[t]], 1);
+    if (t < 256) {
+        // symbols of each length: one ballot per length per warp
+        const uint32_t l = lens[t];
+        for (uint32_t k = 1; k <= kMaxLen; k++) {
+            const uint32_t c = __popc(__ballot_sync(0xffffffffu, l == k));
+            if ((t & 31) == 0 && c) atomicAdd(&ts.cnt[k], (int32_t)c);
+        }
+    }
     __syncthreads();
     if (t == 0) {
         int32_t a = 0, first = 0, base = 0, K = 0, ml = 0;
