@@ -284,12 +284,12 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         ok = __all_sync(0xffffffffu, okn);
         if (ok) {
             // root symbols per tile: every level of a tile must fit one warp's
-            // buffer (with 16-byte rounding per node), with 20 % headroom
+            // buffer (with 4-byte rounding per node), with 20 % headroom
             uint64_t tfit = ~0ull;
             for (int d = 1; d < 16; d++) {
                 if (!Q.lvl[d]) continue;
                 const uint32_t nodes = (uint32_t)(Q.first[d + 1] - Q.first[d]);
-                const uint64_t room = (uint64_t)kWBuf > 16ull * nodes + 32 ? kWBuf - 16ull * nodes - 32 : 0;
+                const uint64_t room = (uint64_t)kWBuf > 4ull * nodes + 32 ? kWBuf - 4ull * nodes - 32 : 0;
                 const uint64_t t = room * R.n / Q.lvl[d] / 5 * 4;
                 tfit = t < tfit ? t : tfit;
             }
@@ -665,7 +665,7 @@ __device__ inline bool wt_layout(WarpTile &S) {
             if (v < f1) {
                 const uint32_t dv = S.dem[v];
                 if (d && dv > (uint32_t)kWBuf) fits = false;
-                const uint32_t by = d ? ((min(dv, (uint32_t)kWBuf) + 15u) & ~15u) : 0u;
+                const uint32_t by = d ? ((min(dv, (uint32_t)kWBuf) + 3u) & ~3u) : 0u;
                 x = ((uint64_t)by << 32) | max(1u, (dv + 31u) >> 5);
             }
             uint64_t inc = x;
@@ -764,8 +764,11 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
             uint32_t o[8];
             merge32(S, bin, chv, kk - r1, r1, w, sel, o);
             uint8_t *p = bout + S.sp[v] + kk;
-            *reinterpret_cast<uint4 *>(p) = make_uint4(o[0], o[1], o[2], o[3]);
-            if (dv - kk > 16) *reinterpret_cast<uint4 *>(p + 16) = make_uint4(o[4], o[5], o[6], o[7]);
+            // spans are 4-byte aligned: 32-bit stores, the ones inside the node's span
+            uint32_t *p4 = reinterpret_cast<uint32_t *>(p);
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (4u * j < dv - kk) p4[j] = o[j];
         }
     }
     return !__any_sync(0xffffffffu, bad);
@@ -1578,7 +1581,7 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
     uint64_t dir = 0, scratch = 0;
     // the shortest tile the plan can choose: a level of at most 128 nodes and
     // at most n symbols in a buffer, 20 % headroom, a multiple of 128
-    const uint64_t t_fit = ((uint64_t)(kWBuf - 16 * 128 - 32) / 5 * 4) & ~127ull;
+    const uint64_t t_fit = ((uint64_t)(kWBuf - 4 * 128 - 32) / 5 * 4) & ~127ull;
     uint64_t t_min = tu.tile_max < t_fit ? tu.tile_max : t_fit;
     if (t_min < 128) t_min = 128;
     for (int b = 0; b < nblk; b++) {
