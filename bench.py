@@ -435,7 +435,8 @@ def main(argv=None):
         for _ in range(max(3, args.steps // 4)):
             flush.zero_()
             Ek[0].record(stream)
-            P.encode_blocks(data, blk_off, nblk, enc.layout, enc.comp, enc.off, enc.rec_bytes, enc.status, stream)
+            P.encode_blocks_chunked(data, blk_off, nblk, enc.layout, enc.chunk_hist, enc.comp, enc.off, enc.rec_bytes,
+                                    enc.status, stream)
             Ek[1].record(stream)
             Ek[1].synchronize()
             t_enck.append(Ek[0].elapsed_time(Ek[1]))

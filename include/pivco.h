@@ -123,6 +123,25 @@ pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int
                                  const void *layout, uint8_t *out, const uint64_t *out_off,
                                  uint64_t *rec_bytes, int32_t *status, void *stream);
 
+/* The encoder's warp chunks counted in the histogram pass.  Block b of n
+ * symbols is cut into nw = min(8, max(1, n / 4096)) contiguous chunks, chunk
+ * w starting at floor(n w / nw) rounded down to a multiple of 32 (the split
+ * pivco_encode_blocks uses for its warps).  pivco_histogram_chunks writes the
+ * block histograms to hist[nblk][256] exactly as pivco_histogram does, and
+ * each chunk's histogram to chunk_hist[nblk][8][256] (device; the chunks a
+ * block does not have are zeros).  pivco_encode_blocks_chunked is
+ * pivco_encode_blocks reading those chunk histograms instead of counting the
+ * chunks again; the records are byte-identical.  Chunk histograms that do not
+ * describe `in` (another input, or stale) make status[b] =
+ * PIVCO_ERR_INVALID_ARG for the blocks they do not fit; nothing is written
+ * outside each block's record. */
+pivco_status pivco_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
+                                    uint32_t *hist, uint32_t *chunk_hist, void *stream);
+pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
+                                         const void *layout, const uint32_t *chunk_hist, uint8_t *out,
+                                         const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status,
+                                         void *stream);
+
 /* Selective ANS of encoded records (Sec. 5.2, App. D marker byte): codes the
  * bitmap bytes of every node with marker 0xFF by static-table rANS and keeps
  * the result when it is smaller than the raw bitmap; rewrites the record in

@@ -30,6 +30,8 @@ _SIGS = {
     "pivco_build_layout": [_P, _P, _I32, _P, _P, _P, _P, _P],
     "pivco_exclusive_scan": [_P, _I32, _P, _P, _SZ, _P, _P],
     "pivco_encode_blocks": [_P, _P, _I32, _P, _P, _P, _P, _P, _P],
+    "pivco_histogram_chunks": [_P, _P, _I32, _P, _P, _P],
+    "pivco_encode_blocks_chunked": [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _P],
     "pivco_ans_encode_blocks": [_P, _I32, _P, _P, _P, _P, _SZ, _P, _P],
     "pivco_decode_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
     "pivco_decode_blocks": [_P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
@@ -150,6 +152,21 @@ def exclusive_scan(values, n, out, ws, status=None, stream=None):
 def encode_blocks(data, blk_off, nblk, layout, out, out_off, rec_bytes, status, stream=None):
     _check(lib().pivco_encode_blocks(_ptr(data), _ptr(blk_off), nblk, _ptr(layout), _ptr(out), _ptr(out_off),
                                      _ptr(rec_bytes), _ptr(status), _stream(stream)), "pivco_encode_blocks")
+
+
+CHUNKS = 8
+
+
+def histogram_chunks(data, blk_off, hist, chunk_hist, stream=None):
+    """Block histograms plus the encoder's warp-chunk histograms ([nblk][8][256])."""
+    _check(lib().pivco_histogram_chunks(_ptr(data), _ptr(blk_off), blk_off.numel() - 1, _ptr(hist), _ptr(chunk_hist),
+                                        _stream(stream)), "pivco_histogram_chunks")
+
+
+def encode_blocks_chunked(data, blk_off, nblk, layout, chunk_hist, out, out_off, rec_bytes, status, stream=None):
+    _check(lib().pivco_encode_blocks_chunked(_ptr(data), _ptr(blk_off), nblk, _ptr(layout), _ptr(chunk_hist),
+                                             _ptr(out), _ptr(out_off), _ptr(rec_bytes), _ptr(status),
+                                             _stream(stream)), "pivco_encode_blocks_chunked")
 
 
 def ans_encode_blocks(layout, nblk, out, out_off, rec_bytes, ws, status, stream=None):
@@ -376,6 +393,7 @@ class Encoder:
         import torch
         self.nblk, self.prm, self.dev = nblk, prm or params(), device
         self.hist = torch.empty(nblk * 256, dtype=torch.int32, device=device)
+        self.chunk_hist = torch.empty(nblk * CHUNKS * 256, dtype=torch.int32, device=device)
         self.lens = torch.empty(nblk * 256, dtype=torch.uint8, device=device)
         self.layout = torch.empty(nblk * layout_bytes(), dtype=torch.uint8, device=device)
         self.bound = torch.empty(nblk, dtype=torch.int64, device=device)
@@ -389,7 +407,7 @@ class Encoder:
     def plan(self, data, blk_off, stream=None):
         """Statistics, code and layout; returns the total output bytes (synchronises)."""
         n = self.nblk
-        histogram(data, blk_off, self.hist, stream)
+        histogram_chunks(data, blk_off, self.hist, self.chunk_hist, stream)
         code_lengths(self.hist, n, self.prm.max_len, self.lens, self.status, stream)
         build_layout(self.hist, self.lens, n, self.prm, self.layout, self.bound, self.status, stream)
         exclusive_scan(self.bound, n, self.off, self.scan_ws, self.status, stream)
@@ -406,11 +424,12 @@ class Encoder:
         """Full encode without host synchronisation (buffers must be sized)."""
         n = self.nblk
         if replan:
-            histogram(data, blk_off, self.hist, stream)
+            histogram_chunks(data, blk_off, self.hist, self.chunk_hist, stream)
             code_lengths(self.hist, n, self.prm.max_len, self.lens, self.status, stream)
             build_layout(self.hist, self.lens, n, self.prm, self.layout, self.bound, self.status, stream)
             exclusive_scan(self.bound, n, self.off, self.scan_ws, self.status, stream)
-        encode_blocks(data, blk_off, n, self.layout, self.comp, self.off, self.rec_bytes, self.status, stream)
+        encode_blocks_chunked(data, blk_off, n, self.layout, self.chunk_hist, self.comp, self.off, self.rec_bytes,
+                              self.status, stream)
         if self.prm.ans_enable:
             ans_encode_blocks(self.layout, n, self.comp, self.off, self.rec_bytes, self.ans_ws, self.status, stream)
         return Encoded(self.comp, self.off, self.rec_bytes, self.status)

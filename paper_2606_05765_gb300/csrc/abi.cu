@@ -157,8 +157,24 @@ pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int
                                  void *stream) {
     if (nblk < 0 || (nblk > 0 && (!blk_off || !layout || !out || !out_off || !rec_bytes || !status)))
         return PIVCO_ERR_INVALID_ARG;
-    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), out, out_off,
-                                    rec_bytes, status, S(stream)));
+    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), nullptr, out,
+                                    out_off, rec_bytes, status, S(stream)));
+}
+
+pivco_status pivco_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, uint32_t *hist,
+                                    uint32_t *chunk_hist, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!blk_off || !hist || !chunk_hist))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    return ok_or_cuda(launch_histogram_chunks(in, blk_off, nblk, hist, chunk_hist, S(stream)));
+}
+
+pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, const void *layout,
+                                         const uint32_t *chunk_hist, uint8_t *out, const uint64_t *out_off,
+                                         uint64_t *rec_bytes, int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!blk_off || !layout || !chunk_hist || !out || !out_off || !rec_bytes || !status)))
+        return PIVCO_ERR_INVALID_ARG;
+    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), chunk_hist, out,
+                                    out_off, rec_bytes, status, S(stream)));
 }
 
 pivco_status pivco_ans_encode_blocks(const void *layout, int32_t nblk, uint8_t *out, const uint64_t *out_off,

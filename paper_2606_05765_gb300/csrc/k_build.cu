@@ -118,6 +118,76 @@ cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nbl
     return cudaGetLastError();
 }
 
+// Chunked histogram: CTA (b, w) counts chunk w of block b (the encoder's warp
+// chunks), writes it to chunk_hist[b][w] and adds it into hist[b].  Chunks a
+// block does not have are written as zeros.
+__global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const uint8_t *__restrict__ in,
+                                                                        const uint64_t *__restrict__ blk_off,
+                                                                        uint32_t *__restrict__ hist,
+                                                                        uint32_t *__restrict__ chunk_hist) {
+    __shared__ uint32_t wh[kHistWarps][256];
+    const int b = blockIdx.x, w = blockIdx.y;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint64_t n = blk_off[b + 1] - blk_off[b];
+    const uint32_t nw = enc_nchunks(n);
+    const uint64_t lo = blk_off[b] + enc_chunk_start(n, w, nw), hi = blk_off[b] + enc_chunk_start(n, w + 1, nw);
+    for (int i = t; i < kHistWarps * 256; i += kHistThreads) (&wh[0][0])[i] = 0;
+    uint32_t hot = 0;
+    if (hi > lo) {
+        const uint64_t pos = lo + ((uint64_t)lane * 2654435761u) % (hi - lo);
+        const uint32_t v = in[pos];
+        const uint32_t peers = __match_any_sync(0xffffffffu, v);
+        int best = __popc(peers), bl = lane;
+        for (int o = 16; o; o >>= 1) {
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
+        }
+        hot = __shfl_sync(0xffffffffu, v, bl);
+    }
+    const uint32_t hot4 = hot * 0x01010101u;
+    uint32_t hot_cnt = 0;
+    __syncthreads();
+    uint32_t *my = wh[warp];
+    uint64_t a = (lo + 15) & ~uint64_t(15);
+    if (a > hi) a = hi;
+    for (uint64_t i = lo + t; i < a; i += kHistThreads) {
+        const uint32_t v = in[i];
+        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
+    }
+    const uint64_t nvec = (hi - a) / 16;
+    const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
+    for (uint64_t i = t; i < nvec; i += kHistThreads) {
+        const uint4 q = __ldg(vp + i);
+        hist_add_word(q.x, hot4, hot, my, hot_cnt);
+        hist_add_word(q.y, hot4, hot, my, hot_cnt);
+        hist_add_word(q.z, hot4, hot, my, hot_cnt);
+        hist_add_word(q.w, hot4, hot, my, hot_cnt);
+    }
+    for (uint64_t i = a + nvec * 16 + t; i < hi; i += kHistThreads) {
+        const uint32_t v = in[i];
+        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
+    }
+    for (int o = 16; o; o >>= 1) hot_cnt += __shfl_xor_sync(0xffffffffu, hot_cnt, o);
+    if (lane == 0 && hot_cnt) atomicAdd(&my[hot], hot_cnt);
+    __syncthreads();
+    for (int s = t; s < 256; s += kHistThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < kHistWarps; k++) sum += wh[k][s];
+        chunk_hist[((size_t)b * kEncChunks + w) * 256 + s] = sum;
+        if (sum) atomicAdd(&hist[(size_t)b * 256 + s], sum);
+    }
+}
+
+cudaError_t launch_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
+                                    uint32_t *chunk_hist, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    zero_u32_kernel<<<min(1024, div_up((long long)nblk * 256, 256)), 256, 0, st>>>(hist, (size_t)nblk * 256);
+    histogram_chunks_kernel<<<dim3(nblk, kEncChunks), kHistThreads, 0, st>>>(in, blk_off, hist, chunk_hist);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Code lengths by package-merge, one CTA (256 threads) per block.
 // Lists are built from the deepest level L up to level 1.  Level L is the

@@ -27,7 +27,6 @@ constexpr int kEncWarps = kEncThreads / 32;
 constexpr int kEncCtasPerSm = 2;
 constexpr int kEBufE = kEncCtasPerSm == 1 ? 5376 : 2304;   // symbols per level buffer of a warp
 constexpr int kESlack = 48;                                  // over-read room (symbols)
-constexpr uint32_t kEMinChunk = 4096;                        // shortest warp chunk (symbols)
 
 struct __align__(16) EncWarp {
     uint16_t buf[2][kEBufE + kESlack];   // depth d >= 1 reads buf[d & 1], writes its children to the other
@@ -37,6 +36,8 @@ struct __align__(16) EncWarp {
     uint16_t sp[256];                    // first symbol of node v's span in its level buffer
     uint16_t gs[256];                    // first 32-symbol group of node v within its level
     uint16_t lg[16];                     // groups of each level
+    uint32_t bad;                        // a level held more symbols than its counts
+    uint32_t pad[3];
 };
 static_assert(sizeof(EncWarp) % 16 == 0 && ((kEBufE + kESlack) * 2) % 16 == 0, "16-byte aligned level buffers");
 
@@ -255,6 +256,7 @@ __device__ inline void enc_split(uint32_t la, uint32_t ra, bool i0, bool i1, con
 __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(const uint8_t *__restrict__ in,
                                                                             const uint64_t *__restrict__ blk_off,
                                                                             const BlockLayout *__restrict__ layout,
+                                                                            const uint32_t *__restrict__ chunk_hist,
                                                                             uint8_t *__restrict__ out,
                                                                             const uint64_t *__restrict__ out_off,
                                                                             uint64_t *__restrict__ rec_bytes,
@@ -364,17 +366,22 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     __syncthreads();
     const uint32_t hot = S.hot & 0xFFu;
     // ---- warp chunks and their histograms ----
-    const uint32_t nw = (uint32_t)min((uint64_t)kEncWarps, max((uint64_t)1, n / kEMinChunk));
-    const uint32_t Q0 = (uint32_t)(((uint64_t)n * warp / nw) & ~31ull);
-    const uint32_t Q1 = warp + 1 >= (int)nw ? (uint32_t)n : (uint32_t)(((uint64_t)n * (warp + 1) / nw) & ~31ull);
+    static_assert(kEncChunks == kEncWarps, "one warp per chunk");
+    const uint32_t nw = enc_nchunks(n);
+    const uint32_t Q0 = enc_chunk_start(n, warp, nw), Q1 = enc_chunk_start(n, warp + 1, nw);
     const uint8_t *src = in + blk_off[b];
     const uint8_t *src_end = in + blk_off[b + 1];
     EncWarp &E = S.w[warp];
+    if (lane == 0) E.bad = 0;
     // histograms live in the first level buffer until the levels need it
     uint32_t *hist = reinterpret_cast<uint32_t *>(E.buf[0]);
     for (int s = lane; s < 256; s += 32) hist[s] = 0;
     __syncwarp();
-    if ((uint32_t)warp < nw) {
+    if (chunk_hist) {
+        // counted by the chunked histogram pass
+        const uint32_t *ch = chunk_hist + ((size_t)b * kEncChunks + warp) * 256;
+        for (int s = lane; s < 256; s += 32) hist[s] = __ldg(ch + s);
+    } else if ((uint32_t)warp < nw) {
         // two input loads in flight per lane
         for (uint32_t kb = Q0; kb < Q1; kb += 2048) {
             const uint32_t k0 = kb + 32 * lane, k1 = k0 + 1024;
@@ -414,12 +421,16 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         enc_node_counts(S, E.start, E.pos);
         for (int v = lane; v < V; v += 32) E.pos[v] += S.bitsrc[v];
         __syncwarp();
+        // the symbols before this chunk are exactly its start: every chunk's
+        // counts then total its length, so the root's bits stay in its span
+        const bool start_ok = E.pos[0] == S.bitsrc[0] + Q0;
+        if (!start_ok && lane == 0) E.bad = 1;
         // the whole chunk at once when its levels fit; else equal sub-chunks
         // sized from the chunk's busiest level (each with its own histogram)
         const uint32_t Q = Q1 - Q0;
         uint32_t C = Q;
         bool whole = true;
-        for (uint32_t P = Q0; P < Q1;) {
+        for (uint32_t P = start_ok ? Q0 : Q1; P < Q1;) {
             C = min(C, Q1 - P);
             if (whole) {
                 for (int s = lane; s < 256; s += 32)
@@ -438,6 +449,26 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             enc_node_counts(S, hist, E.dem);
             uint64_t maxlvl = 0;
             if (!enc_layout(S, E, maxlvl)) {
+                if (whole && chunk_hist) {
+                    // sub-chunks advance the cursors by their own counts: the
+                    // given chunk counts must be this chunk's bytes' counts
+                    for (int s = lane; s < 256; s += 32) hist[s] = 0;
+                    __syncwarp();
+                    for (uint32_t kb = Q0; kb < Q1; kb += 1024) {
+                        const uint32_t k = kb + 32 * lane;
+                        uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                        if (k < Q1) ldg32(src + k, src_end, x);
+                        hist_add32(hist, x, k < Q1 ? min(32u, Q1 - k) : 0u, hot);
+                    }
+                    __syncwarp();
+                    uint32_t diff = 0;
+                    for (int s = lane; s < 256; s += 32)
+                        diff |= hist[s] ^ (((uint32_t)warp + 1 < nw ? S.w[warp + 1].start[s] : S.htot[s]) - E.start[s]);
+                    if (__any_sync(0xffffffffu, diff != 0)) {
+                        if (lane == 0) E.bad = 1;
+                        break;
+                    }
+                }
                 uint32_t nc = C / 2;
                 if (whole) {
                     const uint64_t room = kEBufE - 2 * 128;
@@ -481,7 +512,10 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     const uint32_t r1 = carry + inc - pc;
                     carry += __shfl_sync(0xffffffffu, inc, 31);
                     enc_put_bits(rec32, act, 0u, E.pos[0] + kk, bw, vl);
-                    if (act) enc_split(lp0 + 2u * (kk - r1), rp0 + 2u * r1, i0, i1, y, bw, vl);
+                    // a chunk whose symbols do not match its counts must not write past the spans
+                    if (act && ((i1 && r1 + pc > E.dem[c1 & 0xFFu]) || (i0 && kk + vl - r1 - pc > E.dem[c0 & 0xFFu])))
+                        E.bad = 1;
+                    else if (act) enc_split(lp0 + 2u * (kk - r1), rp0 + 2u * r1, i0, i1, y, bw, vl);
                 }
             }
             __syncwarp();
@@ -539,7 +573,10 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                         const uint32_t ob = smem_addr(bout);
                         const uint32_t lp = ob + 2u * ((i0 ? E.sp[c0 & 0xFFu] : 0u) + (kk - r1));
                         const uint32_t rp = ob + 2u * ((i1 ? E.sp[c1 & 0xFFu] : 0u) + r1);
-                        enc_split(lp, rp, i0, i1, y, bw, vl);
+                        if ((i1 && r1 + pc > E.dem[c1 & 0xFFu]) || (i0 && kk + vl - r1 - pc > E.dem[c0 & 0xFFu]))
+                            E.bad = 1;
+                        else
+                            enc_split(lp, rp, i0, i1, y, bw, vl);
                     }
                 }
                 __syncwarp();
@@ -551,19 +588,21 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     }
     __syncthreads();
     if (t == 0) {
-        status[b] = PIVCO_OK;
-        rec_bytes[b] = rec_bound;
+        uint32_t bad = 0;
+        for (int w = 0; w < kEncWarps; w++) bad |= S.w[w].bad;
+        status[b] = bad ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
+        rec_bytes[b] = bad ? 0 : rec_bound;
     }
 }
 
 cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, const BlockLayout *layout,
-                          uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status,
-                          cudaStream_t st) {
+                          const uint32_t *chunk_hist, uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes,
+                          int32_t *status, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     const int smem = (int)sizeof(EncSmem);
     cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    encode_kernel<<<nblk, kEncThreads, smem, st>>>(in, blk_off, layout, out, out_off, rec_bytes, status);
+    encode_kernel<<<nblk, kEncThreads, smem, st>>>(in, blk_off, layout, chunk_hist, out, out_off, rec_bytes, status);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -202,6 +202,22 @@ void count_launches(int n);
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Launchers implemented in the kernel translation units.
+// Warp chunks of an encoded block: a block of n symbols is cut into
+// nw = min(8, max(1, n / 4096)) contiguous chunks, chunk w starting at
+// floor(n w / nw) rounded down to a multiple of 32.  The encoder gives chunk w
+// to its warp w; the chunked histogram counts each chunk on its own.
+constexpr uint32_t kEncChunks = 8;
+constexpr uint32_t kEncMinChunk = 4096;
+__host__ __device__ inline uint32_t enc_nchunks(uint64_t n) {
+    const uint64_t c = n / kEncMinChunk;
+    return (uint32_t)(c < 1 ? 1 : (c > kEncChunks ? kEncChunks : c));
+}
+__host__ __device__ inline uint32_t enc_chunk_start(uint64_t n, uint32_t w, uint32_t nw) {
+    return w >= nw ? (uint32_t)n : (uint32_t)((n * w / nw) & ~31ull);
+}
+cudaError_t launch_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
+                                    uint32_t *chunk_hist, cudaStream_t st);
+
 cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
                              int slices, cudaStream_t st);
 cudaError_t launch_code_lengths(const uint32_t *hist, int nblk, int max_len, uint8_t *lens, int32_t *status,
@@ -211,8 +227,8 @@ cudaError_t launch_build_layout(const uint32_t *hist, const uint8_t *lens, int n
 cudaError_t launch_scan(const uint64_t *in, int n, uint64_t *out, void *ws, int32_t *status, cudaStream_t st);
 size_t scan_ws_bytes(int n);
 cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, const BlockLayout *layout,
-                          uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status,
-                          cudaStream_t st);
+                          const uint32_t *chunk_hist, uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes,
+                          int32_t *status, cudaStream_t st);
 cudaError_t launch_ans_encode_blocks(const BlockLayout *layout, int nblk, uint8_t *out, const uint64_t *out_off,
                                      uint64_t *rec_bytes, uint8_t *ws, size_t ws_bytes, int32_t *status,
                                      cudaStream_t st);

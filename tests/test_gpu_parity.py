@@ -234,3 +234,109 @@ def test_exclusive_scan(P):
         ref = np.zeros(n + 1, np.int64); ref[1:] = np.cumsum(v)
         assert np.array_equal(out.cpu().numpy(), ref)
         assert int(st.cpu().numpy()[0]) == 0
+
+
+def _chunk_bounds(n):
+    """The encoder's warp chunks of an n-symbol block: min(8, max(1, n // 4096))
+    contiguous pieces, piece w starting at floor(n w / nw) rounded down to 32."""
+    nw = min(8, max(1, n // 4096))
+    starts = [(n * w // nw) & ~31 for w in range(nw)] + [n]
+    return list(zip(starts[:-1], starts[1:]))
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_histogram_chunks(P, oracle, name):
+    """Block histograms equal pivco_histogram's; each chunk's equals the
+    oracle's histogram of that slice; absent chunks are zero."""
+    import torch
+    w = WORKLOADS[name]()
+    hist = torch.empty(w.nblk * 256, dtype=torch.int32, device="cuda")
+    ch = torch.full((w.nblk * P.CHUNKS * 256,), -1, dtype=torch.int32, device="cuda")
+    P.histogram_chunks(dev(w.data), off64(w.blk_off), hist, ch)
+    got = hist.cpu().numpy().view(np.uint32).reshape(w.nblk, 256)
+    gch = ch.cpu().numpy().view(np.uint32).reshape(w.nblk, P.CHUNKS, 256)
+    for b in range(w.nblk):
+        blk = w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])]
+        assert np.array_equal(got[b], oracle.histogram(blk)), b
+        bounds = _chunk_bounds(blk.size)
+        for c in range(P.CHUNKS):
+            want = oracle.histogram(blk[bounds[c][0]:bounds[c][1]]) if c < len(bounds) else np.zeros(256, np.uint32)
+            assert np.array_equal(gch[b, c], want), (b, c)
+
+
+@pytest.mark.parametrize("name", ["shifting", "mixed_24", "edge"])
+def test_encode_plain_equals_chunked(P, name):
+    """pivco_encode_blocks (chunks counted in the encoder) and
+    pivco_encode_blocks_chunked write the same records."""
+    import torch
+    w = WORKLOADS[name]()
+    data, boff = dev(w.data), off64(w.blk_off)
+    enc = P.Encoder(w.nblk)
+    total = enc.plan(data, boff)
+    enc.ensure(total)
+    P.encode_blocks_chunked(data, boff, w.nblk, enc.layout, enc.chunk_hist, enc.comp, enc.off, enc.rec_bytes,
+                            enc.status)
+    a = enc.comp[:total].clone()
+    ra, sa = enc.rec_bytes.clone(), enc.status.clone()
+    enc.comp.fill_(0x5A)
+    P.encode_blocks(data, boff, w.nblk, enc.layout, enc.comp, enc.off, enc.rec_bytes, enc.status)
+    assert not sa.cpu().numpy().any() and not enc.status.cpu().numpy().any()
+    assert torch.equal(ra, enc.rec_bytes)
+    off, rb = enc.off.cpu().numpy(), ra.cpu().numpy()
+    ca, cb = a.cpu().numpy(), enc.comp[:total].cpu().numpy()
+    for b in range(w.nblk):
+        lo, hi = int(off[b]), int(off[b]) + int(rb[b])
+        assert np.array_equal(ca[lo:hi], cb[lo:hi]), b
+
+
+def _encode_with_chunks(P, enc, data, boff, ch, guard):
+    import torch
+    total = int(enc.off[-1].item())
+    comp = torch.full((total + 2 * guard,), 0xA5, dtype=torch.uint8, device="cuda")
+    P.encode_blocks_chunked(data, boff, enc.nblk, enc.layout, ch, comp, enc.off + guard, enc.rec_bytes, enc.status)
+    return comp.cpu().numpy(), enc.status.cpu().numpy(), enc.rec_bytes.cpu().numpy()
+
+
+def test_encode_chunked_stale_histograms(P):
+    """Chunk histograms that do not describe the input make an error status
+    for their blocks and never a write outside those blocks' records: chunk
+    histograms of other data (block totals differ), and of the same blocks
+    reversed (block totals agree, the chunks' do not; the shifting blocks
+    also take the sub-chunk path)."""
+    import torch
+    w = shifting_workload()
+    data, boff = dev(w.data), off64(w.blk_off)
+    enc = P.Encoder(w.nblk)
+    total = enc.plan(data, boff)
+    good = enc.chunk_hist.clone()
+    guard = 4096
+    ref, st, rb = _encode_with_chunks(P, enc, data, boff, good, guard)
+    assert not st.any()
+    off = enc.off.cpu().numpy()
+    h2 = torch.empty_like(enc.hist)
+    # other data of the same size
+    other = np.random.default_rng(3).integers(0, 256, w.data.size).astype(np.uint8)
+    stale = torch.empty_like(good)
+    P.histogram_chunks(dev(other), boff, h2, stale)
+    c, st2, _ = _encode_with_chunks(P, enc, data, boff, stale, guard)
+    assert (st2 == P.ERR_INVALID_ARG).all(), st2
+    assert (c[:guard] == 0xA5).all() and (c[guard + total:] == 0xA5).all()
+    # odd blocks get the chunk counts of their reversed bytes
+    rev = np.concatenate([w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])][::-1] for b in range(w.nblk)])
+    P.histogram_chunks(dev(rev), boff, h2, stale)
+    mixed = good.clone().view(w.nblk, -1)
+    mixed[1::2] = stale.view(w.nblk, -1)[1::2]
+    c, st3, rb3 = _encode_with_chunks(P, enc, data, boff, mixed.view(-1), guard)
+    assert (c[:guard] == 0xA5).all() and (c[guard + total:] == 0xA5).all()
+    for b in range(w.nblk):
+        if b % 2:
+            assert st3[b] == P.ERR_INVALID_ARG, (b, st3)
+        else:
+            assert st3[b] == 0 and rb3[b] == rb[b]
+            lo, hi = guard + int(off[b]), guard + int(off[b]) + int(rb[b])
+            assert np.array_equal(c[lo:hi], ref[lo:hi]), b
+    # the right counts again: the records decode
+    comp = torch.from_numpy(ref[guard:guard + total].copy()).cuda()
+    out, st4 = P.decode(comp, enc.off, boff)
+    assert not st4.cpu().numpy().any()
+    assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
