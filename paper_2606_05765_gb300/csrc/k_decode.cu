@@ -81,7 +81,13 @@ __device__ inline int find_block(const uint32_t *key, int n, uint32_t g) {
 // ---------------------------------------------------------------------------
 // Warp-level record parse (plan and ANS passes)
 // ---------------------------------------------------------------------------
-struct WarpRec {
+// bytes of a record staged in shared memory by the parse: the header, the
+// length nibbles, n_v, the markers and the alen table of any record
+constexpr uint32_t kStage = 2448;
+static_assert(kStage >= kNvOff + 5 * 255 + 3 + 4 * 255 && kStage % 16 == 0, "the stage holds a record's tables");
+
+struct __align__(16) WarpRec {
+    uint8_t stg[kStage];     // the record's first kStage bytes (zeros past its end)
     uint32_t nv[256];
     uint32_t body_off[256];
     uint32_t alen[256];
@@ -91,8 +97,26 @@ struct WarpRec {
     uint32_t V, n, kind, rb, scratch_bytes, nsegs;
 };
 
-__device__ inline bool warp_parse(const uint8_t *rec, uint64_t avail, WarpRec &R) {
+__device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &R) {
     const int lane = threadIdx.x & 31;
+    // one coalesced pass stages the tables; everything below reads shared memory
+    {
+        const uint32_t ns = (uint32_t)(avail < kStage ? avail : kStage);
+        if (!(reinterpret_cast<uintptr_t>(grec) & 15)) {
+#pragma unroll
+            for (uint32_t i = 16 * lane; i < kStage; i += 512) {
+                if (i + 16 <= ns) {
+                    *reinterpret_cast<uint4 *>(R.stg + i) = __ldg(reinterpret_cast<const uint4 *>(grec + i));
+                } else {
+                    for (uint32_t j = i; j < i + 16; j++) R.stg[j] = j < ns ? grec[j] : 0;
+                }
+            }
+        } else {
+            for (uint32_t i = lane; i < kStage; i += 32) R.stg[i] = i < ns ? grec[i] : 0;
+        }
+        __syncwarp();
+    }
+    const uint8_t *rec = R.stg;
     bool ok = avail >= kHdr;
     uint32_t rb = 0, n = 0, V = 0, kind = 0;
     if (ok) {
@@ -213,7 +237,7 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
     if (coded) {
         // canonical tree of the code lengths: a[d] prefixes of depth d are
         // leaves or under leaves, the others are internal nodes (Sec. 1.1)
-        const uint32_t x = ld_le32(rec + kLensOff + 4 * lane);
+        const uint32_t x = ld_le32(R.stg + kLensOff + 4 * lane);
         for (int j = 0; j < 8; j++) {
             const uint32_t l = (x >> (4 * j)) & 15u;
             if (l) atomicAdd(&Q.cntl[l], 1u);
@@ -248,7 +272,7 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         // symbols in canonical order (length, then value): rounds of 32 symbols
         for (int j = 0; j < 8; j++) {
             const int sym = 32 * j + lane;
-            const uint32_t l = (rec[kLensOff + (sym >> 1)] >> (4 * (sym & 1))) & 15u;
+            const uint32_t l = (R.stg[kLensOff + (sym >> 1)] >> (4 * (sym & 1))) & 15u;
             const uint32_t peers = __match_any_sync(0xffffffffu, l);
             const uint32_t r = __popc(peers & ((1u << lane) - 1u));
             if (l && good) Q.sorted[Q.start[l] + Q.run[l] + r] = (uint8_t)sym;
@@ -312,11 +336,10 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
     }
     const uint64_t sb = ok ? R.scratch_bytes : 0, sg = ok ? R.nsegs : 0;
     if (!ok) { ntile = 1; T = 0; dir_bytes = 0; }
-    uint64_t eb = 0;
+    int to = 0;
+    const uint64_t ea = lookback_exclusive_warp(W.states_a, b, (sb << 22) | sg, &to);
+    const uint64_t eb = lookback_exclusive_warp(W.states_b, b, (dir_bytes << 22) | ntile, &to);
     if (lane == 0) {
-        int to = 0;
-        const uint64_t ea = lookback_exclusive(W.states_a, b, (sb << 22) | sg, &to);
-        eb = lookback_exclusive(W.states_b, b, (dir_bytes << 22) | ntile, &to);
         W.blk_scratch[b] = ea >> 22;
         W.blk_seg[b] = (uint32_t)(ea & ((1u << 22) - 1));
         W.blk_dir[b] = eb >> 22;
@@ -331,7 +354,6 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
             hdr32[6] = (uint32_t)((eb & ((1u << 22) - 1)) + ntile);
         }
     }
-    eb = __shfl_sync(0xffffffffu, eb, 0);
     // the node table (only where the workspace holds it: a sizing run may not)
     const uint64_t nbase = decode_ws_fixed_bytes(nblk) + (eb >> 22);
     if (ok && coded && nbase + ntab_bytes(R.V) <= ws_bytes) {
@@ -552,6 +574,24 @@ __device__ inline uint32_t tile_bits(const TileSrc &s, uint32_t pos, uint32_t k)
     return __funnelshift_r(lo, hi, sh);
 }
 
+// The two words under 32 bits of a bitmap, loaded ahead of their use
+struct BitLd {
+    uint32_t lo, hi, sh;
+};
+__device__ inline BitLd tile_ld(const TileSrc &s, uint32_t pos, uint32_t k) {
+    const bool sc = (pos >> 31) != 0;
+    const uint64_t e = (uint64_t)(pos & 0x7FFFFFFFu) + k;
+    const uint64_t wi = e >> 5;
+    BitLd b;
+    b.sh = (uint32_t)e & 31u;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(sc ? s.scr : s.rec);
+    const uint64_t lim = sc ? s.scr_bytes : (uint64_t)s.rec_bytes;
+    b.lo = 4 * wi + 4 <= lim ? __ldcg(w + wi) : 0u;
+    b.hi = (b.sh && 4 * wi + 8 <= lim) ? __ldcg(w + wi + 1) : 0u;
+    return b;
+}
+__device__ inline uint32_t tile_word(const BitLd &b) { return __funnelshift_r(b.lo, b.hi, b.sh); }
+
 // popcount of bits [e, e + len) (len <= 256) of the bitmap at bit address
 // pos: the covering words are loaded together, then counted
 __device__ inline uint32_t tile_popc(const TileSrc &s, uint32_t pos, uint32_t e, uint32_t len) {
@@ -716,32 +756,72 @@ __device__ inline void wt_demand(WarpTile &S, const TileSrc &src, uint32_t V, ui
     }
 }
 
-// One level (depth d >= 1) of the current chunk into its buffer.
-__device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const uint32_t (*sel)[16]) {
+// The group of lane `lane` in the window of 32 groups at `base` of a level
+// (nodes f0 .. f1-1, G groups): its node counts the nodes that start in the
+// window at or before it, after node vcur.
+struct WtLoc {
+    uint32_t v, kk, dv, starts;
+    bool act;
+};
+__device__ inline WtLoc wt_locate(const WarpTile &S, uint32_t f1, uint32_t G, uint32_t base, uint32_t vcur) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
+    const uint32_t cand = vcur + 1 + lane;
+    uint32_t bit = 0;
+    if (cand < f1) {
+        const uint32_t s = (uint32_t)S.gs[cand] - base;
+        if (s < 32) bit = 1u << s;
+    }
+    WtLoc L;
+    L.starts = __reduce_or_sync(0xffffffffu, bit);
+    L.v = vcur + __popc(L.starts & le);
+    const uint32_t g = base + lane;
+    L.kk = (g - S.gs[L.v]) * 32u;
+    L.dv = S.dem[L.v];
+    L.act = g < G && L.kk < L.dv;
+    return L;
+}
+
+// The first window of level d (d >= 1), or of the root (d = 0), and its words
+__device__ inline void wt_first(const WarpTile &S, const TileSrc &src, int d, WtLoc &nx, BitLd &nld) {
+    const int lane = threadIdx.x & 31;
+    nld = BitLd{0u, 0u, 0u};
+    if (d >= 1) {
+        nx = wt_locate(S, S.first[d + 1], S.lg[d], 0, S.first[d]);
+        if (nx.act) nld = tile_ld(src, S.pos[nx.v], nx.kk);
+    } else if (32u * lane < S.dem[0]) {
+        nld = tile_ld(src, S.pos[0], 32u * lane);
+    }
+}
+
+// One level (depth d >= 1) of the current chunk into its buffer.  Windows of
+// 32 groups; the next window's bitmap words (the next level's first window
+// after the last one) are loaded while the current one is merged: nx / nld
+// hold this level's first window on entry and the next level's on return.
+__device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const uint32_t (*sel)[16], WtLoc &nx,
+                                BitLd &nld) {
     const int lane = threadIdx.x & 31;
     const uint8_t *bin = S.buf[(d + 1) & 1];
     uint8_t *bout = S.buf[d & 1];
-    const uint32_t f0 = S.first[d], f1 = S.first[d + 1], G = S.lg[d];
+    const uint32_t f1 = S.first[d + 1], G = S.lg[d];
     const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
-    uint32_t vcur = f0, carry = 0;
+    uint32_t carry = 0;
     bool bad = false;
-    for (uint32_t base = 0; base < G; base += 32) {
-        // node of this lane's group: count the nodes that start in the window at or before it
-        const uint32_t cand = vcur + 1 + lane;
-        uint32_t bit = 0;
-        if (cand < f1) {
-            const uint32_t s = (uint32_t)S.gs[cand] - base;
-            if (s < 32) bit = 1u << s;
+    for (uint32_t base = 0;; base += 32) {
+        const WtLoc L = nx;
+        const BitLd ld = nld;
+        if (base + 32 < G) {
+            nx = wt_locate(S, f1, G, base + 32, __shfl_sync(0xffffffffu, L.v, 31));
+            nld = BitLd{0u, 0u, 0u};
+            if (nx.act) nld = tile_ld(src, S.pos[nx.v], nx.kk);
+        } else {
+            wt_first(S, src, d - 1, nx, nld);
         }
-        const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
-        const uint32_t v = vcur + __popc(starts & le);
-        const uint32_t g = base + lane;
-        const uint32_t kk = (g - S.gs[v]) * 32u;
-        const uint32_t dv = S.dem[v];
-        const bool act = g < G && kk < dv;
+        const uint32_t starts = L.starts, v = L.v, kk = L.kk, dv = L.dv;
+        const bool act = L.act;
         uint32_t w = 0;
         if (act) {
-            w = tile_bits(src, S.pos[v], kk);
+            w = tile_word(ld);
             if (dv - kk < 32) w &= (1u << (dv - kk)) - 1u;
         }
         const uint32_t pc = __popc(w);
@@ -757,7 +837,6 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
         const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
         const uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u) + (s0 < 0 ? carry : 0u);
         carry = __shfl_sync(0xffffffffu, r1 + pc, 31);
-        vcur = __shfl_sync(0xffffffffu, v, 31);
         if (act) {
             const uint32_t chv = S.ch[v];
             if (kk + 32 >= dv && !children_ok(S, chv, dv, r1 + pc)) bad = true;
@@ -770,22 +849,27 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
             for (int j = 0; j < 8; j++)
                 if (4u * j < dv - kk) p4[j] = o[j];
         }
+        if (base + 32 >= G) break;
     }
     return !__any_sync(0xffffffffu, bad);
 }
 
 // The root level of the current chunk into the output.
-__device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, const uint32_t (*sel)[16]) {
+__device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, const uint32_t (*sel)[16], BitLd nld) {
     const int lane = threadIdx.x & 31;
     const uint8_t *bin = S.buf[1];
     const uint32_t dv = S.dem[0], chv = S.ch[0], p0 = S.pos[0];
     uint32_t carry = 0;
+    // nld: the first window's words; the next window's are loaded while the
+    // current one is merged
     for (uint32_t kb = 0; kb < dv; kb += 1024) {
         const uint32_t kk = kb + 32u * lane;
         const bool act = kk < dv;
+        const BitLd ld = nld;
+        if (kk + 1024 < dv) nld = tile_ld(src, p0, kk + 1024);
         uint32_t w = 0;
         if (act) {
-            w = tile_bits(src, p0, kk);
+            w = tile_word(ld);
             if (dv - kk < 32) w &= (1u << (dv - kk)) - 1u;
         }
         const uint32_t pc = __popc(w);
@@ -896,11 +980,14 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
             continue;
         }
         bool ok = true;
+        WtLoc nx;
+        BitLd nld;
+        wt_first(S, src, (int)S.maxd - 1, nx, nld);
         for (int d = (int)S.maxd - 1; d >= 1; d--) {
-            ok = wt_level(S, src, d, sel) && ok;
+            ok = wt_level(S, src, d, sel, nx, nld) && ok;
             __syncwarp();
         }
-        ok = wt_root(S, src, dst + P, sel) && ok;
+        ok = wt_root(S, src, dst + P, sel, nld) && ok;
         if (!ok) {
             if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
             return;
@@ -1107,7 +1194,8 @@ __device__ inline uint32_t dir_entries(int b, const uint8_t *comp, const uint64_
 
 __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
                                 int nblk, uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
-                                uint32_t *u, uint32_t *nvs, uint8_t *first, uint8_t &maxd) {
+                                uint32_t *u, uint32_t *nvs, uint8_t *first, uint8_t &maxd, uint32_t *sm,
+                                uint32_t sm_words) {
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(ws, nblk);
     const DecRegions G = dec_regions(nblk, ws);
@@ -1126,7 +1214,7 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
     }
     uint32_t *dirp = reinterpret_cast<uint32_t *>(ws + nbase + ntb);
     uint32_t *cur = dirp + ent;
-    const uint32_t *nsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr), *nch = nsrc + V;
+    const uint32_t *gsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr);
     const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
     const uint64_t sbase = G.scratch + W.blk_scratch[b];
     TileSrc src;
@@ -1136,8 +1224,18 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
     src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
     if (lane < 17) first[lane] = nt[lane];
     if (lane == 17) maxd = nt[17];
+    // the nodes' bitmap addresses and children in shared memory (sm[0..512),
+    // sm_words >= 512); the tile cursors too (sm[512..)) when they fit,
+    // copied out at the end
+    uint32_t *nsrc = sm, *nch = sm + 256;
+    const bool cur_sm = (uint64_t)(ntile + 1) * V + 512 <= sm_words;
     const uint32_t tot = warp_scan_loop_d((int)V, [&](int v) { return (__ldg(nv + v) + dir_bits - 1) / dir_bits; },
-                                          [&](int v, uint32_t p) { u[v] = p; nvs[v] = __ldg(nv + v); });
+                                          [&](int v, uint32_t p) {
+                                              u[v] = p;
+                                              nvs[v] = __ldg(nv + v);
+                                              nsrc[v] = gsrc[v];
+                                              nch[v] = gsrc[V + v];
+                                          });
     __syncwarp();
     if (tot != ent) {
         if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
@@ -1145,61 +1243,78 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
     }
     const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
     uint32_t vcur = 0, carry = 0;
-    for (uint32_t base = 0; base < ent; base += 32) {
-        const uint32_t cand = vcur + 1 + lane;
-        uint32_t bit = 0;
-        if (cand < V) {
-            const uint32_t sd = u[cand] - base;
-            if (sd < 32) bit = 1u << sd;
-        }
-        const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
-        const uint32_t v = vcur + __popc(starts & le);
-        const uint32_t g = base + lane;
-        uint32_t pc = 0;
-        if (g < ent) {
-            const uint32_t e0 = (g - u[v]) * dir_bits, nvv = nvs[v];
-            pc = tile_popc(src, nsrc[v], e0, min(dir_bits, nvv - e0));
-        }
-        uint32_t inc = pc;
+    // four windows of 32 superblocks per step: their nodes first (shared
+    // memory only), then all their bitmap loads, then the scans
+    constexpr int kU = 4;
+    for (uint32_t base = 0; base < ent; base += 32 * kU) {
+        uint32_t vv[kU], st[kU], pc[kU];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+        for (int r = 0; r < kU; r++) {
+            const uint32_t cand = vcur + 1 + lane, bb = base + 32 * r;
+            uint32_t bit = 0;
+            if (cand < V) {
+                const uint32_t sd = u[cand] - bb;
+                if (sd < 32) bit = 1u << sd;
+            }
+            st[r] = __reduce_or_sync(0xffffffffu, bit);
+            vv[r] = vcur + __popc(st[r] & le);
+            vcur = __shfl_sync(0xffffffffu, vv[r], 31);
         }
-        const uint32_t sl = starts & le;
-        const int sa = sl ? 31 - __clz(sl) : -1;
-        const uint32_t before = __shfl_sync(0xffffffffu, inc, sa > 0 ? sa - 1 : 0);
-        const uint32_t ex = inc - pc - (sa > 0 ? before : 0u) + (sa < 0 ? carry : 0u);
-        if (g < ent) dirp[g] = ex;
-        carry = __shfl_sync(0xffffffffu, ex + pc, 31);
-        vcur = __shfl_sync(0xffffffffu, v, 31);
+#pragma unroll
+        for (int r = 0; r < kU; r++) {
+            const uint32_t g = base + 32 * r + lane;
+            pc[r] = 0;
+            if (g < ent) {
+                const uint32_t v = vv[r], e0 = (g - u[v]) * dir_bits;
+                pc[r] = tile_popc(src, nsrc[v], e0, min(dir_bits, nvs[v] - e0));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kU; r++) {
+            const uint32_t g = base + 32 * r + lane;
+            uint32_t inc = pc[r];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t sl = st[r] & le;
+            const int sa = sl ? 31 - __clz(sl) : -1;
+            const uint32_t before = __shfl_sync(0xffffffffu, inc, sa > 0 ? sa - 1 : 0);
+            const uint32_t ex = inc - pc[r] - (sa > 0 ? before : 0u) + (sa < 0 ? carry : 0u);
+            if (g < ent) dirp[g] = ex;
+            carry = __shfl_sync(0xffffffffu, ex + pc[r], 31);
+        }
     }
-    for (uint32_t v = lane; v < V; v += 32) { cur[v] = 0; cur[(size_t)ntile * V + v] = nvs[v]; }
-    for (uint32_t k = 1 + lane; k < ntile; k += 32) cur[(size_t)k * V] = k * T;
+    uint32_t *cw = cur_sm ? sm + 512 : cur;
+    for (uint32_t v = lane; v < V; v += 32) { cw[v] = 0; cw[(size_t)ntile * V + v] = nvs[v]; }
+    for (uint32_t k = 1 + lane; k < ntile; k += 32) cw[(size_t)k * V] = k * T;
     __syncwarp();
     int bad = 0;
     for (int d = 0; d < (int)maxd; d++) {
         const uint32_t f0 = first[d], nd = first[d + 1] - f0;
         for (uint32_t i = lane; i < (ntile - 1) * nd; i += 32) {
             const uint32_t k = 1 + i / nd, v = f0 + i % nd;
-            const uint32_t c = cur[(size_t)k * V + v], nvv = nvs[v];
+            const uint32_t c = cw[(size_t)k * V + v], nvv = nvs[v];
             if (c > nvv) { bad = 1; continue; }
             const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
             uint32_t sb = c / dir_bits;
             if (sb >= nsb) sb = nsb - 1;
             const uint32_t ones = dirp[u[v] + sb] + tile_popc(src, nsrc[v], sb * dir_bits, c - sb * dir_bits);
             const uint32_t chv = nch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
-            if (!(c0 & 0x8000u)) cur[(size_t)k * V + c0] = c - ones;
-            if (!(c1 & 0x8000u)) cur[(size_t)k * V + c1] = ones;
+            if (!(c0 & 0x8000u)) cw[(size_t)k * V + c0] = c - ones;
+            if (!(c1 & 0x8000u)) cw[(size_t)k * V + c1] = ones;
         }
         __syncwarp();
     }
+    if (cur_sm)
+        for (uint32_t i = lane; i < (ntile + 1) * V; i += 32) cur[i] = cw[i];
     if (__any_sync(0xffffffffu, bad) && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
     __syncwarp();
 }
 
 struct DirWarpSmem {
-    uint32_t u[256], nv[256];
+    uint32_t u[256], nv[256], sm[512];
     uint8_t first[17];
     uint8_t maxd;
     uint8_t pad[14];
@@ -1228,7 +1343,8 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_
     DirWarpSmem &M = DW[warp];
     for (int b = gw; b < nblk; b += nw) {
         const uint32_t e = dir_entries(b, comp, comp_off, nblk, ws, ws_bytes);
-        if (e && e <= kDirWarpMax) dir_warp(b, comp, comp_off, nblk, ws, ws_bytes, status, M.u, M.nv, M.first, M.maxd);
+        if (e && e <= kDirWarpMax)
+            dir_warp(b, comp, comp_off, nblk, ws, ws_bytes, status, M.u, M.nv, M.first, M.maxd, M.sm, 512);
     }
 }
 
@@ -1260,8 +1376,8 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *_
 //   plans      8 blocks per item, one warp each (ticket order = block order,
 //              as the plan's look-back needs)
 //   ANS        8 segments per item, one warp each
-//   directory  one block per item, whole CTA, for blocks with many
-//              superblocks (other blocks skip it)
+//   directory  8 blocks per item; the blocks with many superblocks are
+//              taken one after another by the whole CTA (the others skip)
 // then warp items: the directories of the other multi-tile blocks, then the
 // tiles, one per warp.  A CTA turns to tiles once the CTA
 // items are all taken.  An item only waits (bounded) on items earlier in the
@@ -1287,6 +1403,7 @@ struct PlanAnsSmem {
     PlanScratch Q[kDecWarps];
     AnsSm T[kDecWarps];
 };
+static_assert(sizeof(PlanAnsSmem) <= sizeof(WarpTile) * kDecWarps, "plans fit the tiles' shared memory");
 union BatchUnion {
     PlanAnsSmem pa;
     DirSmem dir;
@@ -1313,7 +1430,7 @@ struct BatchQueue {
 __device__ inline uint32_t batch_items_total(const BatchQueue &q) {
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
     const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
-    return nplan + (hdr[2] + kDecWarps - 1) / kDecWarps + 2u * (uint32_t)q.nblk + hdr[6];
+    return 2u * nplan + (hdr[2] + kDecWarps - 1) / kDecWarps + (uint32_t)q.nblk + hdr[6];
 }
 
 enum : int { kItemDone = 0, kItemNone = 1, kItemStop = 2 };
@@ -1360,10 +1477,13 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
         return kItemDone;
     }
     it -= nseg_items;
-    if (it < (uint32_t)nblk) {
-        // ---- directory of block it ----
-        const int b = (int)it;
-        if (dir_entries(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes) > kDirWarpMax) {
+    if (it < nplan) {
+        // ---- directories of blocks 8 it .. 8 it + 7 that have many superblocks ----
+        const int bw = (int)(it * kDecWarps + warp);
+        const bool big = bw < nblk && dir_entries(bw, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes) > kDirWarpMax;
+        for (int w = 0; w < kDecWarps; w++) {
+            if (!__syncthreads_or(warp == w && big)) continue;
+            const int b = (int)(it * kDecWarps + w);
             const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
             int okw = 1;
             if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs);
@@ -1399,7 +1519,8 @@ __device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTil
             if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
         }
         if (__shfl_sync(0xffffffffu, okw, 0))
-            dir_warp(b, q.comp, q.comp_off, q.nblk, q.ws, q.ws_bytes, q.status, S.pos, S.dem, S.first, S.maxd);
+            dir_warp(b, q.comp, q.comp_off, q.nblk, q.ws, q.ws_bytes, q.status, S.pos, S.dem, S.first, S.maxd,
+                     reinterpret_cast<uint32_t *>(&S.buf[0][0]), (uint32_t)(sizeof(S.buf) / 4));
         __syncwarp();
         if (lane == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
         return;
