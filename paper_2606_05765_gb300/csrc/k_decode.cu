@@ -78,6 +78,31 @@ __device__ inline int find_block(const uint32_t *key, int n, uint32_t g) {
     return lo;
 }
 
+// The same search by a whole warp (all lanes, same arguments): 32 probes per
+// step, the first around `guess` (where g would sit if the items were spread
+// evenly), then 32-way splits of what is left.  key[0] <= g.
+__device__ inline int find_block_warp(const uint32_t *key, int n, uint32_t g, int guess) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n;   // the answer is in [lo, hi); key[lo] <= g
+    {
+        const int s = max(0, min(guess - 15, n - 32));
+        const int b = s + lane;
+        const uint32_t m = __ballot_sync(0xffffffffu, b < n && key[b] <= g);   // a prefix of the lanes
+        const int c = __popc(m), nv = min(32, n - s);
+        if (c > 0) lo = s + c - 1;
+        if (c < nv) hi = s + c;
+    }
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int b = lo + lane * step;
+        const uint32_t m = __ballot_sync(0xffffffffu, lane == 0 || (b < hi && key[b] <= g));
+        const int c = __popc(m);
+        lo += (c - 1) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // Warp-level record parse (plan and ANS passes)
 // ---------------------------------------------------------------------------
@@ -910,7 +935,8 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
     const DecRegions G = dec_regions(nblk, ws);
-    const int b = find_block(W.blk_tile, nblk, gt);
+    const uint32_t ttot = reinterpret_cast<const uint32_t *>(ws)[6];
+    const int b = find_block_warp(W.blk_tile, nblk, gt, (int)((uint64_t)gt * (uint32_t)nblk / max(ttot, 1u)));
     if (*reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
     const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
     const uint8_t *rec = comp + comp_off[b];
@@ -947,16 +973,35 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
     src.rec_bytes = rb;
     src.scr = ws + sbase;
     src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
-    int bad = 0;
-    for (uint32_t v = lane; v < V; v += 32) {
-        const uint32_t nvv = __ldg(nv + v);
-        const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
-        const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : nvv;
-        const uint32_t s0 = nsrc[v];
-        if (ce < cs || ce > nvv || (uint64_t)(s0 & 0x7FFFFFFFu) + nvv >= 0x80000000ull) bad = 1;
-        S.pos[v] = s0 + cs;
-        S.dem[v] = ce - cs;
-        S.ch[v] = nsrc[V + v];
+    int bad = V > 255;   // the plan has checked it
+    {
+        // all of the node loads first (V <= 255: 8 per lane), then the checks and stores
+        uint32_t nvv[8], cs[8], ce[8], s0[8], chv[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint32_t v = lane + 32u * i;
+            nvv[i] = cs[i] = ce[i] = s0[i] = chv[i] = 0u;
+            if (v < V) {
+                nvv[i] = __ldg(nv + v);
+                if (ntile > 1) {
+                    cs[i] = cursors[(size_t)k * V + v];
+                    ce[i] = cursors[(size_t)(k + 1) * V + v];
+                }
+                s0[i] = nsrc[v];
+                chv[i] = nsrc[V + v];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint32_t v = lane + 32u * i;
+            if (v < V) {
+                const uint32_t e = ntile > 1 ? ce[i] : nvv[i];
+                if (e < cs[i] || e > nvv[i] || (uint64_t)(s0[i] & 0x7FFFFFFFu) + nvv[i] >= 0x80000000ull) bad = 1;
+                S.pos[v] = s0[i] + cs[i];
+                S.dem[v] = e - cs[i];
+                S.ch[v] = chv[i];
+            }
+        }
     }
     __syncwarp();
     if (lane == 0 && S.dem[0] != P1 - P0) bad = 1;
@@ -1526,7 +1571,7 @@ __device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTil
         return;
     }
     it -= (uint32_t)q.nblk;
-    const int b = find_block(W.blk_tile, q.nblk, it);
+    const int b = find_block_warp(W.blk_tile, q.nblk, it, (int)((uint64_t)it * (uint32_t)q.nblk / max(hdr[6], 1u)));
     const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
     int okw = 1;
     if (lane == 0) {
