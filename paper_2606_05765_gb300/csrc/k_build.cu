@@ -118,20 +118,24 @@ cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nbl
     return cudaGetLastError();
 }
 
-// Chunked histogram: CTA (b, w) counts chunk w of block b (the encoder's warp
-// chunks), writes it to chunk_hist[b][w] and adds it into hist[b].  Chunks a
-// block does not have are written as zeros.
+// Chunked histogram: one CTA per block, warp w counting chunk w of it (the
+// encoder's warp chunks) into its own shared histogram.  The chunk
+// histograms are written as they are (zeros for chunks the block does not
+// have), the block histogram is their sum: no global atomics.
 __global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const uint8_t *__restrict__ in,
                                                                         const uint64_t *__restrict__ blk_off,
                                                                         uint32_t *__restrict__ hist,
                                                                         uint32_t *__restrict__ chunk_hist) {
+    static_assert(kHistWarps == kEncChunks, "one warp per encoder chunk");
     __shared__ uint32_t wh[kHistWarps][256];
-    const int b = blockIdx.x, w = blockIdx.y;
+    const int b = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint64_t n = blk_off[b + 1] - blk_off[b];
     const uint32_t nw = enc_nchunks(n);
-    const uint64_t lo = blk_off[b] + enc_chunk_start(n, w, nw), hi = blk_off[b] + enc_chunk_start(n, w + 1, nw);
-    for (int i = t; i < kHistWarps * 256; i += kHistThreads) (&wh[0][0])[i] = 0;
+    const uint64_t lo = blk_off[b] + enc_chunk_start(n, warp, nw), hi = blk_off[b] + enc_chunk_start(n, warp + 1, nw);
+    uint32_t *my = wh[warp];
+    for (int i = lane; i < 256; i += 32) my[i] = 0;
+    // hot byte: the most frequent of 32 samples of the chunk (warp-uniform)
     uint32_t hot = 0;
     if (hi > lo) {
         const uint64_t pos = lo + ((uint64_t)lane * 2654435761u) % (hi - lo);
@@ -146,24 +150,37 @@ __global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const ui
     }
     const uint32_t hot4 = hot * 0x01010101u;
     uint32_t hot_cnt = 0;
-    __syncthreads();
-    uint32_t *my = wh[warp];
+    __syncwarp();
+    // head bytes up to 16-byte alignment, then 16-byte loads (four in flight per lane), then the tail
     uint64_t a = (lo + 15) & ~uint64_t(15);
     if (a > hi) a = hi;
-    for (uint64_t i = lo + t; i < a; i += kHistThreads) {
+    for (uint64_t i = lo + lane; i < a; i += 32) {
         const uint32_t v = in[i];
         if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
     }
     const uint64_t nvec = (hi - a) / 16;
     const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
-    for (uint64_t i = t; i < nvec; i += kHistThreads) {
+    uint64_t i = lane;
+    for (; i + 96 < nvec; i += 128) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = __ldg(vp + i + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            hist_add_word(q[u].x, hot4, hot, my, hot_cnt);
+            hist_add_word(q[u].y, hot4, hot, my, hot_cnt);
+            hist_add_word(q[u].z, hot4, hot, my, hot_cnt);
+            hist_add_word(q[u].w, hot4, hot, my, hot_cnt);
+        }
+    }
+    for (; i < nvec; i += 32) {
         const uint4 q = __ldg(vp + i);
         hist_add_word(q.x, hot4, hot, my, hot_cnt);
         hist_add_word(q.y, hot4, hot, my, hot_cnt);
         hist_add_word(q.z, hot4, hot, my, hot_cnt);
         hist_add_word(q.w, hot4, hot, my, hot_cnt);
     }
-    for (uint64_t i = a + nvec * 16 + t; i < hi; i += kHistThreads) {
+    for (uint64_t i = a + nvec * 16 + lane; i < hi; i += 32) {
         const uint32_t v = in[i];
         if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
     }
@@ -173,18 +190,19 @@ __global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const ui
     for (int s = t; s < 256; s += kHistThreads) {
         uint32_t sum = 0;
 #pragma unroll
-        for (int k = 0; k < kHistWarps; k++) sum += wh[k][s];
-        chunk_hist[((size_t)b * kEncChunks + w) * 256 + s] = sum;
-        if (sum) atomicAdd(&hist[(size_t)b * 256 + s], sum);
+        for (int w = 0; w < kHistWarps; w++) {
+            chunk_hist[((size_t)b * kEncChunks + w) * 256 + s] = wh[w][s];
+            sum += wh[w][s];
+        }
+        hist[(size_t)b * 256 + s] = sum;
     }
 }
 
 cudaError_t launch_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
                                     uint32_t *chunk_hist, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    zero_u32_kernel<<<min(1024, div_up((long long)nblk * 256, 256)), 256, 0, st>>>(hist, (size_t)nblk * 256);
-    histogram_chunks_kernel<<<dim3(nblk, kEncChunks), kHistThreads, 0, st>>>(in, blk_off, hist, chunk_hist);
-    count_launches(2);
+    histogram_chunks_kernel<<<nblk, kHistThreads, 0, st>>>(in, blk_off, hist, chunk_hist);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -558,24 +558,27 @@ struct WarpTile {
 };
 static_assert(sizeof(WarpTile) % 16 == 0, "warp tiles must stay 16-byte aligned");
 
-// Byte-permute selectors by (children kind, 4 bitmap bits): a one takes the
-// next byte of the right window (bytes 4..7), a zero the next byte of the
-// left window (bytes 0..3); a leaf side always takes its constant.  Kind bit
-// 0: the left child is a node, bit 1: the right child is.
-__device__ inline void sel_init(uint32_t (*sel)[16]) {
+// Byte-permute selectors of a bitmap byte (low 16 bits: its low nibble,
+// high 16 bits: its high nibble): a one takes the next byte of the right
+// window (bytes 4..7), a zero the next byte of the left window (bytes 0..3).
+// A leaf side's window is its symbol in all four bytes, so one table serves
+// every kind of children.
+__device__ inline void sel_init(uint32_t *sel) {
     const int t = threadIdx.x;
-    if (t < 64) {
-        const int kd = t >> 4, nib = t & 15;
-        const bool lint = kd & 1, rint = kd & 2;
-        uint32_t s = 0, ones = 0, zeros = 0;
-        for (int j = 0; j < 4; j++) {
-            const uint32_t bit = (nib >> j) & 1u;
-            const uint32_t idx = bit ? (rint ? 4 + ones : 4) : (lint ? zeros : 0);
-            s |= idx << (4 * j);
-            ones += bit;
-            zeros += 1 - bit;
+    for (int b8 = t; b8 < 256; b8 += blockDim.x) {
+        uint32_t pair = 0;
+        for (int h = 0; h < 2; h++) {
+            const uint32_t nib = (b8 >> (4 * h)) & 15u;
+            uint32_t s = 0, ones = 0, zeros = 0;
+            for (int j = 0; j < 4; j++) {
+                const uint32_t bit = (nib >> j) & 1u;
+                s |= (bit ? 4 + ones : zeros) << (4 * j);
+                ones += bit;
+                zeros += 1 - bit;
+            }
+            pair |= s << (16 * h);
         }
-        sel[kd][nib] = s;
+        sel[b8] = pair;
     }
 }
 
@@ -657,25 +660,24 @@ __device__ inline void win8(const uint8_t *buf, uint32_t a, uint32_t &x0, uint32
 // 32 output symbols of a node from bitmap word w: r0 / r1 zeros / ones of the
 // node before this word, i.e. the start of its left / right window.
 __device__ inline void merge32(const WarpTile &S, const uint8_t *bin, uint32_t chv, uint32_t r0, uint32_t r1,
-                               uint32_t w, const uint32_t (*sel)[16], uint32_t (&o)[8]) {
+                               uint32_t w, const uint32_t *sel, uint32_t (&o)[8]) {
     const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
     const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-    const uint32_t *sk = sel[(i0 ? 1 : 0) | (i1 ? 2 : 0)];
     uint32_t la = i0 ? min((uint32_t)S.sp[c0 & 0xFFu] + r0, (uint32_t)kWBuf) : 0u;
     uint32_t ra = i1 ? min((uint32_t)S.sp[c1 & 0xFFu] + r1, (uint32_t)kWBuf) : 0u;
     const uint32_t kl = (c0 & 0xFFu) * 0x01010101u, kr = (c1 & 0xFFu) * 0x01010101u;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         const uint32_t b8 = (w >> (8 * q)) & 0xFFu;
-        const uint32_t n0 = b8 & 15u, n1 = b8 >> 4;
-        const uint32_t p0 = __popc(n0), p8 = __popc(b8);
+        const uint32_t p0 = __popc(b8 & 15u), p8 = __popc(b8);
         uint32_t L0 = kl, L1 = kl, R0 = kr, R1 = kr;
         if (i0) win8(bin, la, L0, L1);
         if (i1) win8(bin, ra, R0, R1);
         const uint32_t Lh = __funnelshift_rc(L0, L1, 8u * (4u - p0));
         const uint32_t Rh = __funnelshift_rc(R0, R1, 8u * p0);
-        o[2 * q] = __byte_perm(L0, R0, sk[n0]);
-        o[2 * q + 1] = __byte_perm(Lh, Rh, sk[n1]);
+        const uint32_t sp = sel[b8];
+        o[2 * q] = __byte_perm(L0, R0, sp);
+        o[2 * q + 1] = __byte_perm(Lh, Rh, sp >> 16);
         la += 8u - p8;
         ra += p8;
     }
@@ -823,7 +825,7 @@ __device__ inline void wt_first(const WarpTile &S, const TileSrc &src, int d, Wt
 // 32 groups; the next window's bitmap words (the next level's first window
 // after the last one) are loaded while the current one is merged: nx / nld
 // hold this level's first window on entry and the next level's on return.
-__device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const uint32_t (*sel)[16], WtLoc &nx,
+__device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const uint32_t *sel, WtLoc &nx,
                                 BitLd &nld) {
     const int lane = threadIdx.x & 31;
     const uint8_t *bin = S.buf[(d + 1) & 1];
@@ -880,7 +882,7 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
 }
 
 // The root level of the current chunk into the output.
-__device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, const uint32_t (*sel)[16], BitLd nld) {
+__device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, const uint32_t *sel, BitLd nld) {
     const int lane = threadIdx.x & 31;
     const uint8_t *bin = S.buf[1];
     const uint32_t dv = S.dem[0], chv = S.ch[0], p0 = S.pos[0];
@@ -931,7 +933,7 @@ __device__ inline void warp_fill(uint8_t *p, uint32_t n, uint8_t x) {
 __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
                                  int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
                                  const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
-                                 WarpTile &S, const uint32_t (*sel)[16]) {
+                                 WarpTile &S, const uint32_t *sel) {
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
     const DecRegions G = dec_regions(nblk, ws);
@@ -1366,7 +1368,7 @@ struct DirWarpSmem {
 };
 
 struct TileSmem {
-    uint32_t sel[4][16];
+    uint32_t sel[256];
     WarpTile w[kDecWarps];
 };
 
@@ -1455,7 +1457,7 @@ union BatchUnion {
     WarpTile tw[kDecWarps];
 };
 struct BatchSmem {
-    uint32_t sel[4][16];
+    uint32_t sel[256];
     BatchUnion u;
 };
 
@@ -1549,7 +1551,7 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
 // blocks with few superblocks (after the block's ANS segments), then the
 // tiles (after the block's ANS segments and directory).  Waits are bounded;
 // an expired one marks the block.
-__device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTile &S, const uint32_t (*sel)[16]) {
+__device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTile &S, const uint32_t *sel) {
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(q.ws, q.nblk);
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
