@@ -116,9 +116,10 @@ pivco_status pivco_exclusive_scan(const uint64_t *in, int32_t n, uint64_t *out, 
 /* Encode blocks (Sec. 4, Table 11: per node, write the bitmap and stably
  * partition the symbols to the non-leaf children).  Writes block b's record at
  * out + out_off[b]; its capacity is out_off[b+1] - out_off[b] and must be at
- * least rec_bound[b].  Nodes selected for ANS are written raw with marker
- * 0xFF; pivco_ans_encode_blocks then codes them.  rec_bytes[b] (device)
- * receives the record size.  status[b] (device). */
+ * least rec_bound[b], and out + out_off[b] must be 16-byte aligned (else
+ * status[b] = PIVCO_ERR_INVALID_ARG and nothing is written).  Nodes selected
+ * for ANS are written raw with marker 0xFF; pivco_ans_encode_blocks then codes
+ * them.  rec_bytes[b] (device) receives the record size.  status[b] (device). */
 pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
                                  const void *layout, uint8_t *out, const uint64_t *out_off,
                                  uint64_t *rec_bytes, int32_t *status, void *stream);
@@ -166,9 +167,12 @@ pivco_status pivco_decode_workspace_size(const uint8_t *comp, const uint64_t *co
  * decoded first).  Record b starts at comp + comp_off[b] (device; at most
  * comp_off[b+1] - comp_off[b] bytes are read).  Symbols go to
  * out + out_off[b]; the capacity out_off[b+1] - out_off[b] must equal the
- * record's n.  ws: device workspace (pivco_decode_workspace_size).
+ * record's n.  ws: device workspace (pivco_decode_workspace_size).  A record
+ * must start on a 16-byte boundary (its sizes are multiples of 16, so records
+ * placed back to back from an aligned buffer do); one that does not gets
+ * PIVCO_ERR_INVALID_ARG and is not read as words.
  * status[b] (device): PIVCO_OK, PIVCO_ERR_CORRUPT, PIVCO_ERR_CAPACITY,
- * PIVCO_ERR_TIMEOUT. */
+ * PIVCO_ERR_TIMEOUT, PIVCO_ERR_INVALID_ARG. */
 pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
                                  uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
                                  int32_t *status, void *stream);

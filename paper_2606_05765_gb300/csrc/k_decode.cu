@@ -254,7 +254,9 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
     if (lane < 16) { Q.cntl[lane] = 0; Q.lvl[lane] = 0; Q.run[lane] = 0; }
     __syncwarp();
     const uint8_t *rec = comp + comp_off[b];
-    bool ok = warp_parse(rec, comp_off[b + 1] - comp_off[b], R);
+    // a record starts on a 16-byte boundary (its words are read as words)
+    const bool misal = (reinterpret_cast<uintptr_t>(rec) & 15) != 0;
+    bool ok = warp_parse(rec, comp_off[b + 1] - comp_off[b], R) && !misal;
     __syncwarp();
     uint32_t ntile = 1, T = ok ? R.n : 0, ent = 0;
     uint64_t dir_bytes = 0;
@@ -371,7 +373,7 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         W.blk_tile[b] = (uint32_t)(eb & ((1u << 22) - 1));
         W.blk_T[b] = T;
         W.blk_ntile[b] = ntile;
-        status[b] = !ok ? PIVCO_ERR_CORRUPT : (to ? PIVCO_ERR_TIMEOUT : PIVCO_OK);
+        status[b] = !ok ? (misal ? PIVCO_ERR_INVALID_ARG : PIVCO_ERR_CORRUPT) : (to ? PIVCO_ERR_TIMEOUT : PIVCO_OK);
         if (b == nblk - 1) {
             hdr64[0] = (ea >> 22) + sb;
             hdr32[2] = (uint32_t)((ea & ((1u << 22) - 1)) + sg);

@@ -264,11 +264,19 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     extern __shared__ __align__(128) uint8_t smem_raw[];
     EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // the block's input is read by the chunk histograms and again by the
-    // root pass: ask L2 for it now, so those reads overlap the setup below
+    // global reads the setup needs, issued first so their latencies overlap
+    const uint64_t i0 = blk_off[b], i1 = blk_off[b + 1], o0 = out_off[b], o1 = out_off[b + 1];
+    uint32_t chv[8];   // this warp's chunk histogram (symbol lane + 32 i)
+    if (chunk_hist) {
+        const uint32_t *ch = chunk_hist + ((size_t)b * kEncChunks + warp) * 256;
+#pragma unroll
+        for (int i = 0; i < 8; i++) chv[i] = __ldg(ch + lane + 32 * i);
+    }
+    // the block's input is read by the root pass: ask L2 for it now, so
+    // those reads find it there
     {
-        const uint8_t *p0 = in + blk_off[b];
-        const uint64_t nb = blk_off[b + 1] - blk_off[b];
+        const uint8_t *p0 = in + i0;
+        const uint64_t nb = i1 - i0;
         for (uint64_t i = 128ull * t; i < nb; i += 128ull * kEncThreads)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + i));
     }
@@ -283,13 +291,13 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     }
     __syncthreads();
     const BlockLayout &L = *reinterpret_cast<const BlockLayout *>(S.w[kEncWarps - 1].buf[1]);
-    const uint64_t n = blk_off[b + 1] - blk_off[b];
-    uint8_t *rec = out + out_off[b];
-    const uint64_t cap = out_off[b + 1] - out_off[b];
+    const uint64_t n = i1 - i0;
+    uint8_t *rec = out + o0;
+    const uint64_t cap = o1 - o0;
     const uint32_t kind = L.kind;
     int st = PIVCO_OK;
     if (L.status != 0) st = L.status;
-    else if (L.n != n) st = PIVCO_ERR_INVALID_ARG;
+    else if (L.n != n || (reinterpret_cast<uintptr_t>(rec) & 15)) st = PIVCO_ERR_INVALID_ARG;
     else if (cap < L.rec_bound) st = PIVCO_ERR_CAPACITY;
     if (st != PIVCO_OK) {
         if (t == 0) { status[b] = st; rec_bytes[b] = 0; }
@@ -314,8 +322,14 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         if (t == 0) { status[b] = PIVCO_OK; rec_bytes[b] = kHdr; }
         return;
     }
-    if (t < 128) rec[kLensOff + t] = (uint8_t)(L.len[2 * t] | (L.len[2 * t + 1] << 4));
-    for (int i = t; i < 4 * V; i += kEncThreads) rec[kNvOff + i] = (uint8_t)(L.nv[i >> 2] >> (8 * (i & 3)));
+    // the record start is 16-byte aligned: the length nibbles and n_v as words
+    if (t < 32) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) x |= (uint32_t)(L.len[8 * t + j] & 15u) << (4 * j);
+        reinterpret_cast<uint32_t *>(rec + kLensOff)[t] = x;
+    }
+    if (t < V) reinterpret_cast<uint32_t *>(rec + kNvOff)[t] = L.nv[t];
     if (t < V) rec[kNvOff + 4 * V + t] = L.sel[t] ? kMarkRawSel : 0;
     {
         const uint32_t pad_lo = kNvOff + 5 * V, alen_off = (pad_lo + 3) & ~3u;
@@ -369,8 +383,8 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     static_assert(kEncChunks == kEncWarps, "one warp per chunk");
     const uint32_t nw = enc_nchunks(n);
     const uint32_t Q0 = enc_chunk_start(n, warp, nw), Q1 = enc_chunk_start(n, warp + 1, nw);
-    const uint8_t *src = in + blk_off[b];
-    const uint8_t *src_end = in + blk_off[b + 1];
+    const uint8_t *src = in + i0;
+    const uint8_t *src_end = in + i1;
     EncWarp &E = S.w[warp];
     if (lane == 0) E.bad = 0;
     // histograms live in the first level buffer until the levels need it
@@ -378,9 +392,9 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     for (int s = lane; s < 256; s += 32) hist[s] = 0;
     __syncwarp();
     if (chunk_hist) {
-        // counted by the chunked histogram pass
-        const uint32_t *ch = chunk_hist + ((size_t)b * kEncChunks + warp) * 256;
-        for (int s = lane; s < 256; s += 32) hist[s] = __ldg(ch + s);
+        // counted by the chunked histogram pass (loaded at the start)
+#pragma unroll
+        for (int i = 0; i < 8; i++) hist[lane + 32 * i] = chv[i];
     } else if ((uint32_t)warp < nw) {
         // two input loads in flight per lane
         for (uint32_t kb = Q0; kb < Q1; kb += 2048) {
@@ -405,22 +419,32 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         if (run && !L.len[t]) S.tot[255] = 0xFFFFFFFFu;   // a symbol the code does not have: mismatch below
     }
     __syncthreads();
-    if (warp == 0) enc_node_counts(S, S.htot, S.tot);
+    // node counts of the symbols before each chunk's end (the histograms are
+    // dead: their buffers take the counts), all warps at once; the last
+    // chunk's are the block's totals, checked against the layout.  A chunk's
+    // start counts are the previous chunk's end counts, its demands the
+    // difference.
+    auto endc = [&](uint32_t w) { return reinterpret_cast<uint32_t *>(S.w[w].buf[0]); };
+    if ((uint32_t)warp < nw) enc_node_counts(S, (uint32_t)warp + 1 < nw ? S.w[warp + 1].start : S.htot, endc(warp));
     __syncthreads();
     {
-        int bad = t < V && S.tot[t] != L.nv[t];
-        if (t == 255 && V < 256 && S.tot[255] == 0xFFFFFFFFu) bad = 1;
+        int bad = t < V && endc(nw - 1)[t] != L.nv[t];
+        if (t == 255 && S.tot[255] == 0xFFFFFFFFu) bad = 1;
         if (__syncthreads_or(bad)) {
             if (t == 0) { status[b] = PIVCO_ERR_INVALID_ARG; rec_bytes[b] = 0; }
             return;
         }
     }
+    if ((uint32_t)warp < nw) {
+        for (int v = lane; v < V; v += 32) {
+            const uint32_t s0 = warp ? endc(warp - 1)[v] : 0u;
+            E.pos[v] = s0 + S.bitsrc[v];
+            E.dem[v] = endc(warp)[v] - s0;
+        }
+    }
+    __syncthreads();   // the count buffers are level buffers again
     uint32_t *rec32 = reinterpret_cast<uint32_t *>(rec);
     if ((uint32_t)warp < nw) {
-        // start cursors of this warp's chunk
-        enc_node_counts(S, E.start, E.pos);
-        for (int v = lane; v < V; v += 32) E.pos[v] += S.bitsrc[v];
-        __syncwarp();
         // the symbols before this chunk are exactly its start: every chunk's
         // counts then total its length, so the root's bits stay in its span
         const bool start_ok = E.pos[0] == S.bitsrc[0] + Q0;
@@ -432,10 +456,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         bool whole = true;
         for (uint32_t P = start_ok ? Q0 : Q1; P < Q1;) {
             C = min(C, Q1 - P);
-            if (whole) {
-                for (int s = lane; s < 256; s += 32)
-                    hist[s] = ((uint32_t)warp + 1 < nw ? S.w[warp + 1].start[s] : S.htot[s]) - E.start[s];
-            } else {
+            if (!whole) {   // (the whole chunk's demands were set above)
                 for (int s = lane; s < 256; s += 32) hist[s] = 0;
                 __syncwarp();
                 for (uint32_t kb = P; kb < P + C; kb += 1024) {
@@ -444,9 +465,9 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     if (k < P + C) ldg32(src + k, src_end, x);
                     hist_add32(hist, x, k < P + C ? min(32u, P + C - k) : 0u, hot);
                 }
+                __syncwarp();
+                enc_node_counts(S, hist, E.dem);
             }
-            __syncwarp();
-            enc_node_counts(S, hist, E.dem);
             uint64_t maxlvl = 0;
             if (!enc_layout(S, E, maxlvl)) {
                 if (whole && chunk_hist) {

@@ -340,3 +340,30 @@ def test_encode_chunked_stale_histograms(P):
     out, st4 = P.decode(comp, enc.off, boff)
     assert not st4.cpu().numpy().any()
     assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
+
+
+def test_misaligned_records_rejected(P):
+    """A record placed off a 16-byte boundary is an argument error, for the
+    encoder (nothing written) and for every decode path (not read as words)."""
+    import torch
+    w = workloads.skew80(nblk=4, bs=65536)
+    data, boff = dev(w.data), off64(w.blk_off)
+    enc = P.Encoder(w.nblk)
+    total = enc.plan(data, boff)
+    enc.ensure(total)
+    comp = torch.full((total + 64,), 0x77, dtype=torch.uint8, device="cuda")
+    P.encode_blocks_chunked(data, boff, w.nblk, enc.layout, enc.chunk_hist, comp, enc.off + 4, enc.rec_bytes,
+                            enc.status)
+    assert (enc.status.cpu().numpy() == P.ERR_INVALID_ARG).all()
+    assert (comp.cpu().numpy() == 0x77).all()
+    # good records, then the same bytes 4 bytes further on
+    good = P.encode(data, boff)
+    rec = good.comp[:total]
+    shifted = torch.zeros(total + 64, dtype=torch.uint8, device="cuda")
+    shifted[4:4 + total] = rec
+    for batched in (False, True):
+        out, st = P.decode(shifted, good.off + 4, boff, batched=batched)
+        assert (st.cpu().numpy() == P.ERR_INVALID_ARG).all(), (batched, st)
+        out, st = P.decode(rec.contiguous(), good.off, boff, batched=batched)
+        assert not st.cpu().numpy().any()
+        assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
