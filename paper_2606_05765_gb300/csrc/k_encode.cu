@@ -45,8 +45,13 @@ struct EncSmem {
     uint16_t code16[256];    // code of symbol s, most significant bit at bit 15 (0: absent)
     uint32_t ch[256];        // children: 0x8000 | symbol for a leaf, else the node index
     uint32_t bitsrc[256];    // bit address of node v's bitmap in the record
-    uint32_t tot[256];       // symbols of node v in the block (checked against the layout)
     uint32_t htot[256];      // the block's histogram
+    uint32_t pmask[8];       // symbols that have a code
+    uint8_t ci[256];         // canonical index of symbol s (its place in (length, symbol) order)
+    uint8_t nlo[256];        // node v's leaves are canonical indices nlo[v] .. nhi1[v]
+    uint8_t nhi1[256];
+    uint16_t lcnt[8][16];    // symbols of each length per warp of symbols, then their prefix
+    uint32_t nocode;         // a symbol without a code has a count
     int32_t a[17];           // d-bit prefixes under leaves of length <= d
     uint8_t first[17];       // first node of each depth
     uint8_t maxd;
@@ -118,23 +123,35 @@ __device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32
     if (lane == 0 && hot) atomicAdd(&hist[h], hot);
 }
 
-// node symbol counts of a histogram, bottom-up one depth at a time: a node
-// counts its children (a leaf child: its symbol's count).  One warp.
-__device__ inline void enc_node_counts(const EncSmem &S, const uint32_t *hist, uint32_t *cnt) {
+// Node symbol counts of a histogram h by prefix sums in canonical order: the
+// leaves under a node are the contiguous canonical range nlo .. nhi1, so its
+// count is a difference of two prefix sums.  One warp; hc (256) and ps (257)
+// are scratch.
+__device__ inline void enc_counts(const EncSmem &S, const uint32_t *h, uint32_t *cnt, uint32_t *hc, uint32_t *ps) {
     const int lane = threadIdx.x & 31;
-    for (int d = (int)S.maxd - 1; d >= 0; d--) {
-        for (int v = S.first[d] + lane; v < (int)S.first[d + 1]; v += 32) {
-            const uint32_t chv = S.ch[v];
-            uint32_t c = 0;
+    const int V = S.first[S.maxd];
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const uint32_t code = (chv >> (16 * k)) & 0xFFFFu;
-                c += (code & 0x8000u) ? hist[code & 0xFFu] : cnt[code];
-            }
-            cnt[v] = c;
-        }
-        __syncwarp();
+    for (int i = 0; i < 8; i++) {
+        const int s = lane + 32 * i;
+        if ((S.pmask[i] >> lane) & 1u) hc[S.ci[s]] = h[s];
     }
+    __syncwarp();
+    uint32_t x[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) { x[j] = hc[8 * lane + j]; sum += x[j]; }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    uint32_t run = inc - sum;
+    if (lane == 0) ps[0] = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) { run += x[j]; ps[8 * lane + j + 1] = run; }
+    __syncwarp();
+    for (int v = lane; v < V; v += 32) cnt[v] = ps[S.nhi1[v] + 1] - ps[S.nlo[v]];
+    __syncwarp();
 }
 
 // Spans and groups of every level for the current demands; false when a
@@ -334,7 +351,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     {
         const uint32_t pad_lo = kNvOff + 5 * V, alen_off = (pad_lo + 3) & ~3u;
         if (pad_lo + t < alen_off) rec[pad_lo + t] = 0;
-        if (warp == 0) {
+        if (warp == 0 && L.n_sel) {
             // the alen table: raw sizes of the selected nodes, in node order
             warp_scan_loop(V, [&](int v) { return (uint32_t)(L.sel[v] != 0); }, [&](int v, uint32_t p) {
                 if (L.sel[v]) {
@@ -367,18 +384,73 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             S.ch[t] = code2;
             S.bitsrc[t] = 8u * L.body_off[t];
         }
-        S.tot[t] = 0;
         if (t < 17) { S.a[t] = L.tree_a[t]; S.first[t] = L.depth_first[t]; }
-        if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; }
+        if (t < 8 * 16) (&S.lcnt[0][0])[t] = 0;
+        if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; S.nocode = 0; }
     }
     __syncthreads();
+    // canonical order (length, symbol) of the symbols with a code: per warp
+    // of symbols, the count of each length and each symbol's rank in it
+    const uint32_t my_len = L.len[t];
+    const uint32_t len_peers = __match_any_sync(0xffffffffu, my_len);
+    const uint32_t len_rank = __popc(len_peers & ((1u << lane) - 1u));
     {
-        const uint32_t l = L.len[t];
-        const uint32_t key = __reduce_min_sync(0xffffffffu, l ? (l << 8) | (uint32_t)t : 0xFFFFu);
+        const uint32_t key = __reduce_min_sync(0xffffffffu, my_len ? (my_len << 8) | (uint32_t)t : 0xFFFFu);
         if (lane == 0) atomicMin(&S.hot, key);
+        if (len_rank == 0) S.lcnt[warp][my_len] = (uint16_t)__popc(len_peers);
+        const uint32_t pm = __ballot_sync(0xffffffffu, my_len != 0);
+        if (lane == 0) S.pmask[warp] = pm;
     }
     __syncthreads();
     const uint32_t hot = S.hot & 0xFFu;
+    if (t < 32) {
+        // lane l < 16: symbols of length l before each warp of symbols, in canonical order
+        const uint32_t l = (uint32_t)t;
+        uint32_t tot = 0;
+        if (l >= 1 && l < 16)
+            for (int w = 0; w < kEncWarps; w++) tot += S.lcnt[w][l];
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (l >= 1 && l < 16) {
+            uint32_t run = inc - tot;
+            for (int w = 0; w < kEncWarps; w++) {
+                const uint32_t c = S.lcnt[w][l];
+                S.lcnt[w][l] = (uint16_t)run;
+                run += c;
+            }
+        }
+    }
+    __syncthreads();
+    // the codes in canonical order (left-aligned, increasing), in warp 0's
+    // second level buffer until the node ranges are known
+    uint16_t *acode = reinterpret_cast<uint16_t *>(S.w[0].buf[1]);
+    int K = 0;
+    if (my_len) {
+        const uint32_t c = S.lcnt[warp][my_len] + len_rank;
+        S.ci[t] = (uint8_t)c;
+        acode[c] = S.code16[t];
+    }
+    K = __syncthreads_count(my_len != 0);
+    if (t < V) {
+        // node t: depth d, prefix p; its leaves have codes in [p, p + 1) << (16 - d)
+        int d = 0;
+        while (d + 1 < 17 && S.first[d + 1] <= t) d++;
+        const uint32_t p = (uint32_t)S.a[d] + (uint32_t)(t - S.first[d]);
+        const uint32_t x0 = p << (16 - d), x1 = (p + 1) << (16 - d);
+        int lo = 0, hi = 0;
+#pragma unroll
+        for (int step = 256; step >= 1; step >>= 1) {
+            const int q0 = lo + step, q1 = hi + step;
+            if (q0 <= K && acode[q0 - 1] < x0) lo = q0;
+            if (q1 <= K && acode[q1 - 1] < x1) hi = q1;
+        }
+        S.nlo[t] = (uint8_t)lo;
+        S.nhi1[t] = (uint8_t)(hi - 1);
+    }
     // ---- warp chunks and their histograms ----
     static_assert(kEncChunks == kEncWarps, "one warp per chunk");
     const uint32_t nw = enc_nchunks(n);
@@ -416,7 +488,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             run += h;
         }
         S.htot[t] = run;
-        if (run && !L.len[t]) S.tot[255] = 0xFFFFFFFFu;   // a symbol the code does not have: mismatch below
+        if (run && !L.len[t]) S.nocode = 1;   // a symbol the code does not have: mismatch below
     }
     __syncthreads();
     // node counts of the symbols before each chunk's end (the histograms are
@@ -425,11 +497,13 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     // start counts are the previous chunk's end counts, its demands the
     // difference.
     auto endc = [&](uint32_t w) { return reinterpret_cast<uint32_t *>(S.w[w].buf[0]); };
-    if ((uint32_t)warp < nw) enc_node_counts(S, (uint32_t)warp + 1 < nw ? S.w[warp + 1].start : S.htot, endc(warp));
+    if ((uint32_t)warp < nw)
+        enc_counts(S, (uint32_t)warp + 1 < nw ? S.w[warp + 1].start : S.htot, endc(warp), endc(warp) + 256,
+                   endc(warp) + 512);
     __syncthreads();
     {
         int bad = t < V && endc(nw - 1)[t] != L.nv[t];
-        if (t == 255 && S.tot[255] == 0xFFFFFFFFu) bad = 1;
+        if (t == 0 && S.nocode) bad = 1;
         if (__syncthreads_or(bad)) {
             if (t == 0) { status[b] = PIVCO_ERR_INVALID_ARG; rec_bytes[b] = 0; }
             return;
@@ -466,7 +540,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                     hist_add32(hist, x, k < P + C ? min(32u, P + C - k) : 0u, hot);
                 }
                 __syncwarp();
-                enc_node_counts(S, hist, E.dem);
+                enc_counts(S, hist, E.dem, hist + 256, hist + 512);
             }
             uint64_t maxlvl = 0;
             if (!enc_layout(S, E, maxlvl)) {
