@@ -104,6 +104,15 @@ pivco_status pivco_build_layout(const uint32_t *hist, const uint8_t *lens, int32
                                 const pivco_params *params, void *layout, uint64_t *rec_bound,
                                 int32_t *status, void *stream);
 
+/* pivco_histogram_chunks, pivco_code_lengths and pivco_build_layout in one
+ * launch (one CTA per block; the block's counts and lengths stay on chip
+ * between the steps).  Writes exactly what the three calls write: hist,
+ * chunk_hist, lens, layout, rec_bound and status (the layout step's). */
+pivco_status pivco_plan_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
+                               const pivco_params *params, uint32_t *hist, uint32_t *chunk_hist,
+                               uint8_t *lens, void *layout, uint64_t *rec_bound, int32_t *status,
+                               void *stream);
+
 /* Device-wide exclusive scan of n uint64 values (single pass, decoupled
  * look-back): out[0] = 0, out[i+1] = in[0] + ... + in[i] (device arrays,
  * out has n + 1 entries).  Used to place records from their sizes.  ws:

@@ -31,6 +31,7 @@ _SIGS = {
     "pivco_exclusive_scan": [_P, _I32, _P, _P, _SZ, _P, _P],
     "pivco_encode_blocks": [_P, _P, _I32, _P, _P, _P, _P, _P, _P],
     "pivco_histogram_chunks": [_P, _P, _I32, _P, _P, _P],
+    "pivco_plan_blocks": [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P],
     "pivco_encode_blocks_chunked": [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _P],
     "pivco_ans_encode_blocks": [_P, _I32, _P, _P, _P, _P, _SZ, _P, _P],
     "pivco_decode_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
@@ -161,6 +162,13 @@ def histogram_chunks(data, blk_off, hist, chunk_hist, stream=None):
     """Block histograms plus the encoder's warp-chunk histograms ([nblk][8][256])."""
     _check(lib().pivco_histogram_chunks(_ptr(data), _ptr(blk_off), blk_off.numel() - 1, _ptr(hist), _ptr(chunk_hist),
                                         _stream(stream)), "pivco_histogram_chunks")
+
+
+def plan_blocks(data, blk_off, prm, hist, chunk_hist, lens, layout, rec_bound, status, stream=None):
+    """Chunk histograms, code lengths and layout of every block in one launch."""
+    _check(lib().pivco_plan_blocks(_ptr(data), _ptr(blk_off), blk_off.numel() - 1, C.byref(prm), _ptr(hist),
+                                   _ptr(chunk_hist), _ptr(lens), _ptr(layout), _ptr(rec_bound), _ptr(status),
+                                   _stream(stream)), "pivco_plan_blocks")
 
 
 def encode_blocks_chunked(data, blk_off, nblk, layout, chunk_hist, out, out_off, rec_bytes, status, stream=None):
@@ -407,9 +415,8 @@ class Encoder:
     def plan(self, data, blk_off, stream=None):
         """Statistics, code and layout; returns the total output bytes (synchronises)."""
         n = self.nblk
-        histogram_chunks(data, blk_off, self.hist, self.chunk_hist, stream)
-        code_lengths(self.hist, n, self.prm.max_len, self.lens, self.status, stream)
-        build_layout(self.hist, self.lens, n, self.prm, self.layout, self.bound, self.status, stream)
+        plan_blocks(data, blk_off, self.prm, self.hist, self.chunk_hist, self.lens, self.layout, self.bound,
+                    self.status, stream)
         exclusive_scan(self.bound, n, self.off, self.scan_ws, self.status, stream)
         return int(self.off[-1].item())
 
@@ -424,9 +431,8 @@ class Encoder:
         """Full encode without host synchronisation (buffers must be sized)."""
         n = self.nblk
         if replan:
-            histogram_chunks(data, blk_off, self.hist, self.chunk_hist, stream)
-            code_lengths(self.hist, n, self.prm.max_len, self.lens, self.status, stream)
-            build_layout(self.hist, self.lens, n, self.prm, self.layout, self.bound, self.status, stream)
+            plan_blocks(data, blk_off, self.prm, self.hist, self.chunk_hist, self.lens, self.layout, self.bound,
+                        self.status, stream)
             exclusive_scan(self.bound, n, self.off, self.scan_ws, self.status, stream)
         encode_blocks_chunked(data, blk_off, n, self.layout, self.chunk_hist, self.comp, self.off, self.rec_bytes,
                               self.status, stream)

@@ -144,6 +144,20 @@ pivco_status pivco_build_layout(const uint32_t *hist, const uint8_t *lens, int32
                                           S(stream)));
 }
 
+pivco_status pivco_plan_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, const pivco_params *params,
+                               uint32_t *hist, uint32_t *chunk_hist, uint8_t *lens, void *layout, uint64_t *rec_bound,
+                               int32_t *status, void *stream) {
+    if (nblk < 0 || !params ||
+        (nblk > 0 && (!blk_off || !hist || !chunk_hist || !lens || !layout || !rec_bound || !status)))
+        return PIVCO_ERR_INVALID_ARG;
+    const pivco_params &p = *params;
+    if (p.max_len < 1 || p.max_len > (int32_t)kMaxLen || p.ans_min_bytes < 0 || p.ans_skew_den <= 0 ||
+        p.ans_skew_num < 0 || p.ans_ratio_pct < 0)
+        return PIVCO_ERR_INVALID_ARG;
+    return ok_or_cuda(launch_block_plan(in, blk_off, nblk, p, hist, chunk_hist, lens,
+                                        reinterpret_cast<BlockLayout *>(layout), rec_bound, status, S(stream)));
+}
+
 size_t pivco_scan_workspace_size(int32_t n) { return scan_ws_bytes(n); }
 
 pivco_status pivco_exclusive_scan(const uint64_t *in, int32_t n, uint64_t *out, void *ws, size_t ws_bytes,

@@ -122,13 +122,13 @@ cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nbl
 // encoder's warp chunks) into its own shared histogram.  The chunk
 // histograms are written as they are (zeros for chunks the block does not
 // have), the block histogram is their sum: no global atomics.
-__global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const uint8_t *__restrict__ in,
-                                                                        const uint64_t *__restrict__ blk_off,
-                                                                        uint32_t *__restrict__ hist,
-                                                                        uint32_t *__restrict__ chunk_hist) {
+// One block by one CTA (256 threads): wh is shared scratch; the block
+// histogram also goes to h_sm (shared) when given.
+__device__ inline void histogram_chunks_block(int b, const uint8_t *__restrict__ in,
+                                              const uint64_t *__restrict__ blk_off, uint32_t *__restrict__ hist,
+                                              uint32_t *__restrict__ chunk_hist, uint32_t (*wh)[256],
+                                              uint32_t *h_sm) {
     static_assert(kHistWarps == kEncChunks, "one warp per encoder chunk");
-    __shared__ uint32_t wh[kHistWarps][256];
-    const int b = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint64_t n = blk_off[b + 1] - blk_off[b];
     const uint32_t nw = enc_nchunks(n);
@@ -195,7 +195,16 @@ __global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const ui
             sum += wh[w][s];
         }
         hist[(size_t)b * 256 + s] = sum;
+        if (h_sm) h_sm[s] = sum;
     }
+}
+
+__global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const uint8_t *__restrict__ in,
+                                                                        const uint64_t *__restrict__ blk_off,
+                                                                        uint32_t *__restrict__ hist,
+                                                                        uint32_t *__restrict__ chunk_hist) {
+    __shared__ uint32_t wh[kHistWarps][256];
+    histogram_chunks_block(blockIdx.x, in, blk_off, hist, chunk_hist, wh, nullptr);
 }
 
 cudaError_t launch_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
@@ -244,21 +253,26 @@ __device__ inline int count_le_u64(const uint64_t *a, int n, uint64_t x) {
     return pos;
 }
 
-__global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t *__restrict__ hist, int max_len,
-                                                                  uint8_t *__restrict__ lens_out,
-                                                                  int32_t *__restrict__ status) {
-    __shared__ uint64_t leafw[256];
-    __shared__ uint8_t leafsym[256];
-    __shared__ uint64_t lw[2][512];
-    __shared__ uint64_t pw[256];
-    __shared__ uint16_t leafpos[kMaxLen + 1][256];
-    __shared__ uint32_t h[256];
-    __shared__ int32_t s_len[kMaxLen + 2];
-    const int b = blockIdx.x, t = threadIdx.x;
-    h[t] = hist[(size_t)b * 256 + t];
-    __syncthreads();
+struct ClSmem {
+    uint64_t leafw[256];
+    uint8_t leafsym[256];
+    uint64_t lw[2][512];
+    uint64_t pw[256];
+    uint16_t leafpos[kMaxLen + 1][256];
+    int32_t s_len[kMaxLen + 2];
+};
+
+// Code lengths of the histogram h (shared, 256) into lens (shared, 256) by
+// one CTA of 256 threads; returns the status (every thread).
+__device__ inline int code_lengths_block(const uint32_t *h, int max_len, ClSmem &C, uint8_t *lens) {
+    uint64_t *leafw = C.leafw, *pw = C.pw;
+    uint8_t *leafsym = C.leafsym;
+    uint64_t (*lw)[512] = C.lw;
+    uint16_t (*leafpos)[256] = C.leafpos;
+    int32_t *s_len = C.s_len;
+    const int t = threadIdx.x;
+    lens[t] = 0;
     const int K = __syncthreads_count(h[t] != 0);
-    uint8_t my_len = 0;
     if (K >= 2 && K <= (1 << max_len)) {
         // present symbols sorted by (count, symbol): bitonic sort of one key per
         // thread (absent symbols sort last); in-warp steps exchange by shuffle
@@ -325,13 +339,25 @@ __global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t
         if (t < K) {
             int l = 0;
             for (int lvl = 1; lvl <= max_len; lvl++) l += (t < s_len[lvl]);
-            h[leafsym[t]] = 0x80000000u | (uint32_t)l;   // reuse as output staging
+            lens[leafsym[t]] = (uint8_t)l;
         }
-        __syncthreads();
-        my_len = (h[t] & 0x80000000u) ? (uint8_t)(h[t] & 0xFF) : 0;
     }
-    lens_out[(size_t)b * 256 + t] = my_len;
-    if (t == 0 && status) status[b] = (K > (1 << max_len)) ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
+    __syncthreads();
+    return (K > (1 << max_len)) ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
+}
+
+__global__ void __launch_bounds__(kPmThreads) code_lengths_kernel(const uint32_t *__restrict__ hist, int max_len,
+                                                                  uint8_t *__restrict__ lens_out,
+                                                                  int32_t *__restrict__ status) {
+    __shared__ ClSmem C;
+    __shared__ uint32_t h[256];
+    __shared__ uint8_t lens[256];
+    const int b = blockIdx.x, t = threadIdx.x;
+    h[t] = hist[(size_t)b * 256 + t];
+    __syncthreads();
+    const int st = code_lengths_block(h, max_len, C, lens);
+    lens_out[(size_t)b * 256 + t] = lens[t];
+    if (t == 0 && status) status[b] = st;
 }
 
 cudaError_t launch_code_lengths(const uint32_t *hist, int nblk, int max_len, uint8_t *lens, int32_t *status,
@@ -372,21 +398,26 @@ __device__ inline uint8_t ans_select(uint64_t nv, uint64_t n1, int depth, const 
 
 constexpr int kLayThreads = 256;
 
-__global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_t *__restrict__ hist,
-                                                                   const uint8_t *__restrict__ lens_in,
-                                                                   const __grid_constant__ SelectParams sp,
-                                                                   BlockLayout *__restrict__ layout,
-                                                                   uint64_t *__restrict__ rec_bound,
-                                                                   int32_t *__restrict__ status) {
-    __shared__ BlockLayout L;
-    __shared__ uint8_t lens[256], sorted[256];
-    __shared__ uint16_t codes[256];
-    __shared__ int32_t scratch[256];
-    __shared__ uint32_t h[256];
-    __shared__ TreeShape ts;
-    const int b = blockIdx.x, t = threadIdx.x;
-    h[t] = hist[(size_t)b * 256 + t];
-    lens[t] = lens_in[(size_t)b * 256 + t];
+struct LaySmem {
+    BlockLayout L;
+    uint8_t sorted[256];
+    uint16_t codes[256];
+    int32_t scratch[256];
+    TreeShape ts;
+    unsigned long long s_part[kLayThreads / 32];
+};
+
+// Layout of block b from its histogram h and lengths lens (both shared, 256)
+// by one CTA of 256 threads: written to layout[b], rec_bound[b], status[b].
+__device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_t *lens, const SelectParams &sp,
+                                          LaySmem &Y, BlockLayout *__restrict__ layout,
+                                          uint64_t *__restrict__ rec_bound, int32_t *__restrict__ status) {
+    BlockLayout &L = Y.L;
+    uint8_t *sorted = Y.sorted;
+    uint16_t *codes = Y.codes;
+    int32_t *scratch = Y.scratch;
+    TreeShape &ts = Y.ts;
+    const int t = threadIdx.x;
     // zero the shared layout
     for (int i = t; i < (int)(sizeof(BlockLayout) / 4); i += kLayThreads) reinterpret_cast<uint32_t *>(&L)[i] = 0;
     __syncthreads();
@@ -394,7 +425,7 @@ __global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_
     uint64_t n = 0;
     {
         // block total: warp sums, then the 8 partial sums (no same-address atomics)
-        __shared__ unsigned long long s_part[kLayThreads / 32];
+        unsigned long long *s_part = Y.s_part;
         uint64_t x = h[t];
 #pragma unroll
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -500,6 +531,68 @@ __global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_
         rec_bound[b] = L.rec_bound;
         if (status) status[b] = st;
     }
+}
+
+__global__ void __launch_bounds__(kLayThreads) build_layout_kernel(const uint32_t *__restrict__ hist,
+                                                                   const uint8_t *__restrict__ lens_in,
+                                                                   const __grid_constant__ SelectParams sp,
+                                                                   BlockLayout *__restrict__ layout,
+                                                                   uint64_t *__restrict__ rec_bound,
+                                                                   int32_t *__restrict__ status) {
+    __shared__ LaySmem Y;
+    __shared__ uint32_t h[256];
+    __shared__ uint8_t lens[256];
+    const int b = blockIdx.x, t = threadIdx.x;
+    h[t] = hist[(size_t)b * 256 + t];
+    lens[t] = lens_in[(size_t)b * 256 + t];
+    build_layout_block(b, h, lens, sp, Y, layout, rec_bound, status);
+}
+
+// The encoder's planning in one launch, one CTA per block: chunk histograms,
+// code lengths, layout.  The block's statistics stay in shared memory from
+// one step to the next, and blocks in different steps share the SMs.
+struct PlanSmem {
+    uint32_t h[256];
+    uint8_t lens[256];
+    union {
+        uint32_t wh[kHistWarps][256];
+        ClSmem cl;
+        LaySmem lay;
+    } u;
+};
+
+__global__ void __launch_bounds__(kHistThreads) block_plan_kernel(const uint8_t *__restrict__ in,
+                                                                  const uint64_t *__restrict__ blk_off, int max_len,
+                                                                  const __grid_constant__ SelectParams sp,
+                                                                  uint32_t *__restrict__ hist,
+                                                                  uint32_t *__restrict__ chunk_hist,
+                                                                  uint8_t *__restrict__ lens_out,
+                                                                  BlockLayout *__restrict__ layout,
+                                                                  uint64_t *__restrict__ rec_bound,
+                                                                  int32_t *__restrict__ status) {
+    static_assert(kHistThreads == kPmThreads && kPmThreads == kLayThreads, "one CTA shape for the three steps");
+    __shared__ PlanSmem P;
+    const int b = blockIdx.x, t = threadIdx.x;
+    histogram_chunks_block(b, in, blk_off, hist, chunk_hist, P.u.wh, P.h);
+    __syncthreads();
+    code_lengths_block(P.h, max_len, P.u.cl, P.lens);   // (its status is the layout's too)
+    lens_out[(size_t)b * 256 + t] = P.lens[t];
+    __syncthreads();
+    build_layout_block(b, P.h, P.lens, sp, P.u.lay, layout, rec_bound, status);
+}
+
+cudaError_t launch_block_plan(const uint8_t *in, const uint64_t *blk_off, int nblk, const pivco_params &p,
+                              uint32_t *hist, uint32_t *chunk_hist, uint8_t *lens, BlockLayout *layout,
+                              uint64_t *rec_bound, int32_t *status, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    SelectParams sp;
+    sp.p = p;
+    const AnsTables &T = host_ans_tables();
+    for (int i = 0; i < 50; i++) sp.fseh_q16[i] = T.fseh_q16[i];
+    block_plan_kernel<<<nblk, kHistThreads, 0, st>>>(in, blk_off, p.max_len, sp, hist, chunk_hist, lens, layout,
+                                                     rec_bound, status);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_layout(const uint32_t *hist, const uint8_t *lens, int nblk, const pivco_params &p,

@@ -217,6 +217,10 @@ __host__ __device__ inline uint32_t enc_chunk_start(uint64_t n, uint32_t w, uint
 }
 cudaError_t launch_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
                                     uint32_t *chunk_hist, cudaStream_t st);
+struct BlockLayout;
+cudaError_t launch_block_plan(const uint8_t *in, const uint64_t *blk_off, int nblk, const pivco_params &p,
+                              uint32_t *hist, uint32_t *chunk_hist, uint8_t *lens, BlockLayout *layout,
+                              uint64_t *rec_bound, int32_t *status, cudaStream_t st);
 
 cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nblk, uint32_t *hist,
                              int slices, cudaStream_t st);

@@ -367,3 +367,32 @@ def test_misaligned_records_rejected(P):
         out, st = P.decode(rec.contiguous(), good.off, boff, batched=batched)
         assert not st.cpu().numpy().any()
         assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+@pytest.mark.parametrize("ans", [False, True])
+def test_plan_blocks_equals_steps(P, name, ans):
+    """The one-launch plan writes what the histogram, code-length and layout
+    calls write one after another."""
+    import torch
+    w = WORKLOADS[name]()
+    n = w.nblk
+    data, boff = dev(w.data), off64(w.blk_off)
+    prm = P.params(ans=ans)
+
+    def bufs():
+        return (torch.zeros(n * 256, dtype=torch.int32, device="cuda"),
+                torch.zeros(n * P.CHUNKS * 256, dtype=torch.int32, device="cuda"),
+                torch.zeros(n * 256, dtype=torch.uint8, device="cuda"),
+                torch.zeros(n * P.layout_bytes(), dtype=torch.uint8, device="cuda"),
+                torch.zeros(n, dtype=torch.int64, device="cuda"),
+                torch.full((n,), 77, dtype=torch.int32, device="cuda"))
+
+    h1, c1, l1, y1, r1, s1 = bufs()
+    P.histogram_chunks(data, boff, h1, c1)
+    P.code_lengths(h1, n, prm.max_len, l1, s1)
+    P.build_layout(h1, l1, n, prm, y1, r1, s1)
+    h2, c2, l2, y2, r2, s2 = bufs()
+    P.plan_blocks(data, boff, prm, h2, c2, l2, y2, r2, s2)
+    for a, b in [(h1, h2), (c1, c2), (l1, l2), (y1, y2), (r1, r2), (s1, s2)]:
+        assert torch.equal(a, b)
