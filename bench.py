@@ -45,6 +45,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="skew80", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-segments", type=int, default=8)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default decode tuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load time per arrival rate")
@@ -469,32 +470,30 @@ def main(argv=None):
     dom = max(["decode_batch_kernel", "encode_kernel"], key=lambda k: kernels[k]["ms"])
     ach = kernels[dom]["gbs"]
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public host-buffer API (pivco_host_compress /
+    # pivco_host_decompress) with pinned host buffers: every step copies the
+    # raw bytes in and the records out, then the records in and the bytes out
     e2e = None
     if args.e2e_steps > 0:
+        torch.cuda.synchronize()
         h_in = torch.from_numpy(w.data).pin_memory()
-        h_comp = torch.empty(enc.comp.numel(), dtype=torch.uint8).pin_memory()
         h_out = torch.empty(raw, dtype=torch.uint8).pin_memory()
-        d_in = torch.empty_like(data)
-        d_comp = torch.empty_like(enc.comp)
-        e2e_t = []
-        with torch.cuda.stream(stream):
+        with P.HostCodec(w.blk_off, P.params(ans=w.ans), segments=args.e2e_segments) as hc:
+            h_comp = torch.empty(max(hc.capacity, 1), dtype=torch.uint8).pin_memory()
+            e2e_t = []
+            e2e_ok = True
             for i in range(args.e2e_steps + 1):
-                stream.synchronize()
                 t0 = time.perf_counter()
-                d_in.copy_(h_in, non_blocking=True)
-                enc.run(d_in, blk_off, stream)
-                h_comp.copy_(enc.comp, non_blocking=True)
-                d_comp.copy_(h_comp, non_blocking=True)
-                P.decode_batched(d_comp, enc.off, nblk, out, blk_off, dec.ws, dec.status, stream)
-                h_out.copy_(out, non_blocking=True)
-                stream.synchronize()
+                comp_off, st_c = hc.compress(h_in, h_comp)
+                comp_bytes = int(comp_off[-1])
+                st_d = hc.decompress(h_comp, comp_off, h_out)
                 if i:
                     e2e_t.append(time.perf_counter() - t0)
-        ok = ok and (not enc.status.cpu().numpy().any()) and (not dec.status.cpu().numpy().any()) \
-            and bool(torch.equal(h_out, h_in))
+                e2e_ok = e2e_ok and not st_c.any() and not st_d.any()
+        ok = ok and e2e_ok and bool(torch.equal(h_out, h_in))
         e2e = {"value": round(raw / statistics.mean(e2e_t) / 1e9 * world, 3), "unit": "GB/s",
-               "h2d_bytes_per_step": raw + enc.comp.numel(), "d2h_bytes_per_step": enc.comp.numel() + raw}
+               "h2d_bytes_per_step": raw + comp_bytes, "d2h_bytes_per_step": comp_bytes + raw,
+               "api": "pivco_host_compress + pivco_host_decompress, %d pieces" % args.e2e_segments}
 
     serving = None
     if world == 1 and not args.no_serving:

@@ -98,7 +98,8 @@ pivco_status pivco_code_lengths(const uint32_t *hist, int32_t nblk, int32_t max_
  * From lens and hist builds the canonical codes, the breadth-first node
  * table with per-node counts n_v, the ANS selection of each node, and the
  * record's byte layout.  layout: device buffer of nblk * pivco_layout_bytes()
- * bytes (opaque).  rec_bound[b] (device, uint64): the record size with every
+ * bytes (opaque), 16-byte aligned (else PIVCO_ERR_INVALID_ARG, here and in
+ * every call that takes a layout).  rec_bound[b] (device, uint64): the record size with every
  * node stored raw; the final record is never larger.  params: host. */
 pivco_status pivco_build_layout(const uint32_t *hist, const uint8_t *lens, int32_t nblk,
                                 const pivco_params *params, void *layout, uint64_t *rec_bound,
@@ -288,6 +289,35 @@ uint64_t pivco_launch_count(void);
 pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
                                   uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
                                   int32_t *status, void *stream);
+
+/* Host-buffer codec: compress and decompress a batch of blocks that lives in
+ * host memory, the host<->device copies overlapped with the kernels (no
+ * counterpart in the paper: a transport convenience of this library).  The
+ * blocks (blk_off: host, nblk + 1 offsets, blk_off[0] = 0) are cut into
+ * `segments` pieces of about equal raw size; while one piece is coded, the
+ * next is copied in and the previous one out.  All buffers below are host
+ * memory; page-locked buffers let the copies run asynchronously.
+ *   create: device buffers for every piece (about 2x the raw bytes for
+ *     records, 2x for input and output); params as for pivco_build_layout.
+ *   comp_capacity: the largest compressed size any input can have.
+ *   compress: records of in[] into comp[0 .. comp_cap) back to back (the same
+ *     bytes pivco_encode_blocks and pivco_ans_encode_blocks write, each
+ *     record in its bound-sized slot), comp_off[nblk + 1] their offsets,
+ *     status[nblk] per block.  PIVCO_ERR_CAPACITY if comp_cap is too small.
+ *   decompress: blocks of comp[] (records at comp_off[b], 16-byte aligned
+ *     relative to comp_off[0]) into out[blk_off[b] ..]; status[nblk] as for
+ *     pivco_decode_blocks.
+ * One call at a time per codec; each call returns when its output is in
+ * host memory. */
+typedef struct pivco_host_codec pivco_host_codec;
+pivco_status pivco_host_codec_create(const uint64_t *blk_off, int32_t nblk, const pivco_params *params,
+                                     int32_t segments, pivco_host_codec **codec);
+pivco_status pivco_host_codec_destroy(pivco_host_codec *codec);
+uint64_t pivco_host_codec_comp_capacity(const pivco_host_codec *codec);
+pivco_status pivco_host_compress(pivco_host_codec *codec, const uint8_t *in, uint8_t *comp, uint64_t comp_cap,
+                                 uint64_t *comp_off, int32_t *status);
+pivco_status pivco_host_decompress(pivco_host_codec *codec, const uint8_t *comp, const uint64_t *comp_off,
+                                   uint8_t *out, int32_t *status);
 
 /* Launch tuning of the decode (process-wide).  None of it changes any output.
  * tile_max: longest root tile in symbols (a multiple of 128, 128..65536);

@@ -32,6 +32,10 @@ _SIGS = {
     "pivco_encode_blocks": [_P, _P, _I32, _P, _P, _P, _P, _P, _P],
     "pivco_histogram_chunks": [_P, _P, _I32, _P, _P, _P],
     "pivco_plan_blocks": [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P],
+    "pivco_host_codec_create": [_P, _I32, _P, _I32, _P],
+    "pivco_host_codec_destroy": [_P],
+    "pivco_host_compress": [_P, _P, _P, C.c_uint64, _P, _P],
+    "pivco_host_decompress": [_P, _P, _P, _P, _P],
     "pivco_encode_blocks_chunked": [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _P],
     "pivco_ans_encode_blocks": [_P, _I32, _P, _P, _P, _P, _SZ, _P, _P],
     "pivco_decode_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
@@ -64,6 +68,7 @@ _OTHER = {
     "pivco_scan_workspace_size": ([_I32], _SZ),
     "pivco_decode_plan_bytes": ([_I32], _SZ),
     "pivco_launch_count": ([], C.c_uint64),
+    "pivco_host_codec_comp_capacity": ([_P], C.c_uint64),
 }
 
 
@@ -293,6 +298,59 @@ class Graph:
             self.handle = C.c_void_p()
 
 
+# --------------------------------------------------------- host buffers ----
+class HostCodec:
+    """pivco_host_codec: compress / decompress batches held in host memory,
+    copies overlapped with the kernels piece by piece.  blk_off: the blocks'
+    offsets (nblk + 1 integers, host).  Host buffers should be pinned CPU
+    tensors (or numpy arrays)."""
+
+    def __init__(self, blk_off, prm=None, segments=8):
+        self.blk_off = np.ascontiguousarray(np.asarray(blk_off), np.uint64)
+        self.nblk = self.blk_off.size - 1
+        self.prm = prm or params()
+        self.handle = C.c_void_p()
+        _check(lib().pivco_host_codec_create(C.c_void_p(self.blk_off.ctypes.data), self.nblk, C.byref(self.prm),
+                                             segments, C.byref(self.handle)), "pivco_host_codec_create")
+        self.capacity = int(lib().pivco_host_codec_comp_capacity(self.handle))
+        self.comp_off = np.zeros(self.nblk + 1, np.uint64)
+        self.status = np.zeros(max(self.nblk, 1), np.int32)
+
+    def compress(self, data, comp):
+        """Records of `data` into `comp` (capacity >= self.capacity is always
+        enough); returns (comp_off, status) as numpy arrays (views, valid
+        until the next call)."""
+        n = comp.numel() if hasattr(comp, "numel") else comp.size
+        _check(lib().pivco_host_compress(self.handle, _host_ptr(data), _host_ptr(comp), n,
+                                         C.c_void_p(self.comp_off.ctypes.data), C.c_void_p(self.status.ctypes.data)),
+               "pivco_host_compress")
+        return self.comp_off, self.status[: self.nblk]
+
+    def decompress(self, comp, comp_off, out):
+        """Blocks of `comp` (records at comp_off) into `out`; returns status."""
+        co = np.ascontiguousarray(comp_off, np.uint64)
+        _check(lib().pivco_host_decompress(self.handle, _host_ptr(comp), C.c_void_p(co.ctypes.data), _host_ptr(out),
+                                           C.c_void_p(self.status.ctypes.data)), "pivco_host_decompress")
+        return self.status[: self.nblk]
+
+    def close(self):
+        if self.handle:
+            _check(lib().pivco_host_codec_destroy(self.handle), "pivco_host_codec_destroy")
+            self.handle = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # -------------------------------------------------------------- serving ----
 class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("idle_us", C.c_int32), ("epoch_us", C.c_int32)]
@@ -305,7 +363,7 @@ def _host_ptr(a):
     """Address of a host buffer: a CPU torch tensor (pinned or not) or a numpy array."""
     if hasattr(a, "data_ptr"):
         if a.is_cuda:
-            raise PivcoError("server buffers are host memory")
+            raise PivcoError("these buffers are host memory")
         return C.c_void_p(a.data_ptr())
     return C.c_void_p(a.ctypes.data)
 

@@ -127,6 +127,9 @@ pivco_status pivco_histogram(const uint8_t *in, const uint64_t *blk_off, int32_t
     return ok_or_cuda(launch_histogram(in, blk_off, nblk, hist, slices, S(stream)));
 }
 
+// the layout buffer is read with 16-byte loads
+static bool layout_aligned(const void *layout) { return !(reinterpret_cast<uintptr_t>(layout) & 15); }
+
 pivco_status pivco_code_lengths(const uint32_t *hist, int32_t nblk, int32_t max_len, uint8_t *lens, int32_t *status,
                                 void *stream) {
     if (nblk < 0 || max_len < 1 || max_len > (int32_t)kMaxLen || (nblk > 0 && (!hist || !lens))) return PIVCO_ERR_INVALID_ARG;
@@ -140,6 +143,7 @@ pivco_status pivco_build_layout(const uint32_t *hist, const uint8_t *lens, int32
     if (p.max_len < 1 || p.max_len > (int32_t)kMaxLen || p.ans_min_bytes < 0 || p.ans_skew_den <= 0 ||
         p.ans_skew_num < 0 || p.ans_ratio_pct < 0)
         return PIVCO_ERR_INVALID_ARG;
+    if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_build_layout(hist, lens, nblk, p, reinterpret_cast<BlockLayout *>(layout), rec_bound, status,
                                           S(stream)));
 }
@@ -154,6 +158,7 @@ pivco_status pivco_plan_blocks(const uint8_t *in, const uint64_t *blk_off, int32
     if (p.max_len < 1 || p.max_len > (int32_t)kMaxLen || p.ans_min_bytes < 0 || p.ans_skew_den <= 0 ||
         p.ans_skew_num < 0 || p.ans_ratio_pct < 0)
         return PIVCO_ERR_INVALID_ARG;
+    if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_block_plan(in, blk_off, nblk, p, hist, chunk_hist, lens,
                                         reinterpret_cast<BlockLayout *>(layout), rec_bound, status, S(stream)));
 }
@@ -171,6 +176,7 @@ pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int
                                  void *stream) {
     if (nblk < 0 || (nblk > 0 && (!blk_off || !layout || !out || !out_off || !rec_bytes || !status)))
         return PIVCO_ERR_INVALID_ARG;
+    if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), nullptr, out,
                                     out_off, rec_bytes, status, S(stream)));
 }
@@ -187,6 +193,7 @@ pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_
                                          uint64_t *rec_bytes, int32_t *status, void *stream) {
     if (nblk < 0 || (nblk > 0 && (!blk_off || !layout || !chunk_hist || !out || !out_off || !rec_bytes || !status)))
         return PIVCO_ERR_INVALID_ARG;
+    if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), chunk_hist, out,
                                     out_off, rec_bytes, status, S(stream)));
 }
@@ -194,6 +201,7 @@ pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_
 pivco_status pivco_ans_encode_blocks(const void *layout, int32_t nblk, uint8_t *out, const uint64_t *out_off,
                                      uint64_t *rec_bytes, void *ws, size_t ws_bytes, int32_t *status, void *stream) {
     if (nblk < 0 || (nblk > 0 && (!layout || !out || !out_off || !rec_bytes || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_ans_encode_blocks(reinterpret_cast<const BlockLayout *>(layout), nblk, out, out_off,
                                                rec_bytes, reinterpret_cast<uint8_t *>(ws), ws_bytes, status,
                                                S(stream)));

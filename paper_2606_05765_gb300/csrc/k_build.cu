@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kHistThreads) histogram_kernel(const uint8_t *
     __syncthreads();
     uint32_t *my = wh[warp];
     // head bytes up to 16-byte alignment, then 16-byte vector loads, then tail
-    uint64_t a = (lo + 15) & ~uint64_t(15);
+    // (the 16-byte boundary of the address: `in` itself may be unaligned)
+    uint64_t a = lo + ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(in + lo) & 15u)) & 15u);
     if (a > hi) a = hi;
     for (uint64_t i = lo + t; i < a; i += kHistThreads) {
         const uint32_t v = in[i];
@@ -152,7 +153,8 @@ __device__ inline void histogram_chunks_block(int b, const uint8_t *__restrict__
     uint32_t hot_cnt = 0;
     __syncwarp();
     // head bytes up to 16-byte alignment, then 16-byte loads (four in flight per lane), then the tail
-    uint64_t a = (lo + 15) & ~uint64_t(15);
+    // (the 16-byte boundary of the address: `in` itself may be unaligned)
+    uint64_t a = lo + ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(in + lo) & 15u)) & 15u);
     if (a > hi) a = hi;
     for (uint64_t i = lo + lane; i < a; i += 32) {
         const uint32_t v = in[i];

@@ -1776,6 +1776,27 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
     return ((decode_ws_fixed_bytes(nblk) + dir + 255) & ~(size_t)255) + scratch + 256;
 }
 
+// Host: an upper bound of the same workspace from the blocks' sizes alone
+// (no record is read): every block taken as 255 nodes carrying at most 15
+// bits per symbol, all of them ANS-coded.  For callers that place records
+// they have not seen yet.
+size_t decode_ws_size_bound(const uint64_t *blk_off, int nblk, const DecTuning &tu) {
+    const uint64_t t_fit = ((uint64_t)(kWBuf - 4 * 128 - 32) / 5 * 4) & ~127ull;
+    uint64_t t_min = tu.tile_max < t_fit ? tu.tile_max : t_fit;
+    if (t_min < 128) t_min = 128;
+    uint64_t dir = 0, scratch = 0;
+    for (int b = 0; b < nblk; b++) {
+        const uint64_t n = blk_off[b + 1] - blk_off[b];
+        if (n < 2) continue;   // empty and one-symbol blocks have no nodes
+        const uint64_t ent = 15 * n / tu.dir_bits + 255;
+        uint64_t ntile = (n + t_min - 1) / t_min;
+        if (ntile > (1u << 21)) ntile = 1u << 21;
+        dir += ntab_bytes(255) + ((4 * ent + 4 * (ntile + 1) * 255 + 15) & ~(uint64_t)15);
+        scratch += 15 * n / 8 + 255ull * 48;
+    }
+    return ((decode_ws_fixed_bytes(nblk) + dir + 255) & ~(size_t)255) + scratch + 256;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------

@@ -324,6 +324,7 @@ struct ServeFlags {                         // pinned host memory mapped into th
 cudaError_t launch_serve_loop(ServeCtl *ctl, const ServeDesc *ring, ServeFlags *flags, uint64_t idle_ns,
                               uint64_t life_ns, cudaStream_t st);
 size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, const DecTuning &tu);
+size_t decode_ws_size_bound(const uint64_t *blk_off, int nblk, const DecTuning &tu);
 
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                size_t ws_bytes, int32_t *status, cudaStream_t st);

@@ -396,3 +396,30 @@ def test_plan_blocks_equals_steps(P, name, ans):
     P.plan_blocks(data, boff, prm, h2, c2, l2, y2, r2, s2)
     for a, b in [(h1, h2), (c1, c2), (l1, l2), (y1, y2), (r1, r2), (s1, s2)]:
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("shift", [1, 3, 8, 13])
+def test_unaligned_input(P, oracle, shift):
+    """Blocks read through an input pointer at any byte offset: histograms,
+    plan and records are the same as from an aligned buffer."""
+    import torch
+    w = WORKLOADS["mixed_24"]()
+    buf = torch.zeros(w.data.size + 32, dtype=torch.uint8, device="cuda")
+    buf[shift:shift + w.data.size] = dev(w.data)
+    data = buf[shift:shift + w.data.size]
+    assert data.data_ptr() % 16 == shift % 16
+    boff = off64(w.blk_off)
+    h = torch.empty(w.nblk * 256, dtype=torch.int32, device="cuda")
+    P.histogram(data, boff, h)
+    got = h.cpu().numpy().view(np.uint32).reshape(w.nblk, 256)
+    for b in range(w.nblk):
+        assert np.array_equal(got[b], oracle.histogram(w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])])), b
+    enc = P.encode(data, boff, P.params(ans=True))
+    ref = P.encode(dev(w.data), boff, P.params(ans=True))
+    assert not enc.status.cpu().numpy().any()
+    assert torch.equal(enc.off, ref.off) and torch.equal(enc.rec_bytes, ref.rec_bytes)
+    off, rb = ref.off.cpu().numpy(), ref.rec_bytes.cpu().numpy()
+    a, r = enc.comp.cpu().numpy(), ref.comp.cpu().numpy()
+    for b in range(w.nblk):
+        lo = int(off[b])
+        assert np.array_equal(a[lo:lo + int(rb[b])], r[lo:lo + int(rb[b])]), b
