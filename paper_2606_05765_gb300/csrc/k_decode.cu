@@ -309,8 +309,8 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         }
         // children of every internal node and the symbols of each depth
         bool okn = good;
+        int d = 0;   // depth of node v (v grows, so the search goes on from the last one)
         for (int v = lane; v < (int)R.V && good; v += 32) {
-            int d = 0;
             while (d < 15 && Q.first[d + 1] <= v) d++;
             if (d >= 1) atomicAdd(&Q.lvl[d], R.nv[v]);
             const int32_t p = Q.a[d] + (v - Q.first[d]);
@@ -364,8 +364,8 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
     const uint64_t sb = ok ? R.scratch_bytes : 0, sg = ok ? R.nsegs : 0;
     if (!ok) { ntile = 1; T = 0; dir_bytes = 0; }
     int to = 0;
-    const uint64_t ea = lookback_exclusive_warp(W.states_a, b, (sb << 22) | sg, &to);
-    const uint64_t eb = lookback_exclusive_warp(W.states_b, b, (dir_bytes << 22) | ntile, &to);
+    uint64_t ea = 0, eb = 0;
+    lookback2_exclusive_warp(W.states_a, W.states_b, b, (sb << 22) | sg, (dir_bytes << 22) | ntile, ea, eb, &to);
     if (lane == 0) {
         W.blk_scratch[b] = ea >> 22;
         W.blk_seg[b] = (uint32_t)(ea & ((1u << 22) - 1));

@@ -93,4 +93,57 @@ __device__ inline uint64_t lookback_exclusive_warp(uint64_t *states, int tile, u
     return excl;
 }
 
+// Two chains at once (the same tile in both): lanes 0-15 walk chain A and
+// lanes 16-31 chain B, 16 predecessors per step each; a half that has met
+// its inclusive prefix stops reading while the other goes on.  Called by all
+// 32 lanes; returns both exclusive prefixes in every lane.
+__device__ inline void lookback2_exclusive_warp(uint64_t *states_a, uint64_t *states_b, int tile, uint64_t agg_a,
+                                                uint64_t agg_b, uint64_t &excl_a, uint64_t &excl_b,
+                                                int *timed_out) {
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    uint64_t *states = half ? states_b : states_a;
+    const uint64_t agg = half ? agg_b : agg_a;
+    if (tile == 0) {
+        if (hl == 0) lb_store(&states[0], kLbFlagInc | (agg & kLbValMask));
+        excl_a = excl_b = 0;
+        return;
+    }
+    if (hl == 0) lb_store(&states[tile], kLbFlagAgg | (agg & kLbValMask));
+    uint64_t excl = 0;
+    int j = tile - 1;
+    bool done = false;   // (the same in all lanes of a half)
+    const uint64_t t0 = globaltimer_ns();
+    unsigned ns = 32;
+    for (;;) {
+        const int k = j - hl;
+        uint64_t v = kLbFlagInc;   // before tile 0: an inclusive zero
+        if (!done && k >= 0) v = lb_load(&states[k]);
+        const uint64_t f = v & ~kLbValMask;
+        const uint32_t inc = (__ballot_sync(0xffffffffu, f == kLbFlagInc) >> (16 * half)) & 0xFFFFu;
+        const uint32_t unset = (__ballot_sync(0xffffffffu, f == 0) >> (16 * half)) & 0xFFFFu;
+        const uint32_t upto = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFu;   // lanes up to the nearest one
+        if (__any_sync(0xffffffffu, !done && (unset & upto))) {
+            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > kWaitLimitNs)) {
+                *timed_out = 1;
+                break;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+            continue;
+        }
+        uint64_t x = (!done && ((upto >> hl) & 1u)) ? (v & kLbValMask) : 0ull;
+#pragma unroll
+        for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);   // within the half
+        if (!done) {
+            excl += x;
+            if (inc) done = true;
+            else j -= 16;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+    }
+    if (hl == 0) lb_store(&states[tile], kLbFlagInc | ((excl + agg) & kLbValMask));
+    excl_a = __shfl_sync(0xffffffffu, excl, 0);
+    excl_b = __shfl_sync(0xffffffffu, excl, 16);
+}
+
 }  // namespace pv
