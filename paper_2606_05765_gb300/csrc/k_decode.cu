@@ -635,18 +635,17 @@ __device__ inline uint32_t tile_popc(const TileSrc &s, uint32_t pos, uint32_t e,
     uint32_t x[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) x[i] = ((uint32_t)i < nw && 4 * (w0 + i) + 4 <= lim) ? __ldcg(w + w0 + i) : 0u;
-    uint32_t c = 0;
+    // all bits of the loaded words, less those before sh in the first and
+    // those from sh + len on in the last
+    uint32_t c = 0, xl = 0;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        // bits of word i inside [sh, sh + len)
-        const int lo = 32 * i, hi = lo + 32;
-        const int b0 = max(lo, (int)sh), b1 = min(hi, (int)(sh + len));
-        if (b1 > b0) {
-            const uint32_t n = (uint32_t)(b1 - b0), st = (uint32_t)(b0 - lo);
-            const uint32_t m = n >= 32 ? 0xFFFFFFFFu : (((1u << n) - 1u) << st);
-            c += __popc(x[i] & m);
-        }
+        c += __popc(x[i]);
+        xl = (uint32_t)i + 1 == nw ? x[i] : xl;
     }
+    c -= __popc(x[0] & ((1u << sh) - 1u));
+    const uint32_t eb = (sh + len) & 31u;
+    if (eb) c -= __popc(xl >> eb);
     return c;
 }
 
