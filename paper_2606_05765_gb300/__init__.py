@@ -305,7 +305,7 @@ class HostCodec:
     offsets (nblk + 1 integers, host).  Host buffers should be pinned CPU
     tensors (or numpy arrays)."""
 
-    def __init__(self, blk_off, prm=None, segments=8):
+    def __init__(self, blk_off, prm=None, segments=4):
         self.blk_off = np.ascontiguousarray(np.asarray(blk_off), np.uint64)
         self.nblk = self.blk_off.size - 1
         self.prm = prm or params()
