@@ -82,3 +82,44 @@ def test_tuning_validation(built_lib):
         P.set_tuning()
     t = P.get_tuning()
     assert (t.tile_max, t.dir_bits, t.ctas_per_sm) == (65536, 128, 0)
+
+
+def test_host_codec_and_plan_argument_errors(built_lib):
+    """The host-buffer codec and the one-launch plan reject bad arguments on
+    the host, before any CUDA call (so this runs without a GPU)."""
+    import ctypes as C
+    import numpy as np
+    import paper_2606_05765_gb300 as P
+    L = P.lib()
+    prm = P.params()
+    off = np.array([0, 10, 30], np.uint64)
+    h = C.c_void_p()
+    p_off = C.c_void_p(off.ctypes.data)
+    assert L.pivco_host_codec_create(p_off, 2, C.byref(prm), 0, C.byref(h)) == P.ERR_INVALID_ARG   # no pieces
+    assert L.pivco_host_codec_create(p_off, -1, C.byref(prm), 4, C.byref(h)) == P.ERR_INVALID_ARG
+    assert L.pivco_host_codec_create(None, 2, C.byref(prm), 4, C.byref(h)) == P.ERR_INVALID_ARG
+    assert L.pivco_host_codec_create(p_off, 2, None, 4, C.byref(h)) == P.ERR_INVALID_ARG
+    bad_off = np.array([0, 10, 5], np.uint64)                                                   # decreasing
+    assert L.pivco_host_codec_create(C.c_void_p(bad_off.ctypes.data), 2, C.byref(prm), 4, C.byref(h)) == \
+        P.ERR_INVALID_ARG
+    shifted = np.array([3, 10, 30], np.uint64)                                                  # must start at 0
+    assert L.pivco_host_codec_create(C.c_void_p(shifted.ctypes.data), 2, C.byref(prm), 4, C.byref(h)) == \
+        P.ERR_INVALID_ARG
+    bad = P.params()
+    bad.max_len = 16
+    assert L.pivco_host_codec_create(p_off, 2, C.byref(bad), 4, C.byref(h)) == P.ERR_INVALID_ARG
+    assert not h.value
+    assert L.pivco_host_compress(None, None, None, 0, None, None) == P.ERR_INVALID_ARG
+    assert L.pivco_host_decompress(None, None, None, None, None) == P.ERR_INVALID_ARG
+    assert L.pivco_host_codec_destroy(None) == P.ERR_INVALID_ARG
+    assert L.pivco_host_codec_comp_capacity(None) == 0
+    # the plan: missing buffers, bad parameters, a layout buffer off a 16-byte boundary
+    assert L.pivco_plan_blocks(None, None, 1, C.byref(prm), None, None, None, None, None, None, None) == \
+        P.ERR_INVALID_ARG
+    assert L.pivco_plan_blocks(None, None, 0, C.byref(bad), None, None, None, None, None, None, None) == \
+        P.ERR_INVALID_ARG
+    fake = C.c_void_p(0x1000)
+    odd = C.c_void_p(0x1008)
+    assert L.pivco_plan_blocks(fake, fake, 1, C.byref(prm), fake, fake, fake, odd, fake, fake, None) == \
+        P.ERR_INVALID_ARG
+    assert L.pivco_encode_blocks(fake, fake, 1, odd, fake, fake, fake, fake, None) == P.ERR_INVALID_ARG
