@@ -468,8 +468,11 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                 L.child[t][0] = (int16_t)node_child(ts, sorted, t, d, 0);
                 L.child[t][1] = (int16_t)node_child(ts, sorted, t, d, 1);
             }
+            if (t < K) L.ci[sorted[t]] = (uint8_t)t;
             __syncthreads();
-            // n_v bottom-up, one depth at a time: a node's count is its children's
+            // n_v bottom-up, one depth at a time: a node's count is its
+            // children's; its leaves (a contiguous run of the canonical order)
+            // start at its left child's and end at its right child's
             for (int d = ts.max_len - 1; d >= 0; d--) {
                 const int v = ts.first[d] + t;
                 if (v < ts.first[d + 1]) {
@@ -479,6 +482,9 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                         c += ch >= 0 ? L.nv[ch] : h[-ch - 1];
                     }
                     L.nv[v] = c;
+                    const int c0 = L.child[v][0], c1 = L.child[v][1];
+                    L.nlo[v] = c0 >= 0 ? L.nlo[c0] : L.ci[-c0 - 1];
+                    L.nhi1[v] = c1 >= 0 ? L.nhi1[c1] : L.ci[-c1 - 1];
                 }
                 __syncthreads();
             }

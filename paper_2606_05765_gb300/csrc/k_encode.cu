@@ -47,10 +47,9 @@ struct EncSmem {
     uint32_t bitsrc[256];    // bit address of node v's bitmap in the record
     uint32_t htot[256];      // the block's histogram
     uint32_t pmask[8];       // symbols that have a code
-    uint8_t ci[256];         // canonical index of symbol s (its place in (length, symbol) order)
+    __align__(16) uint8_t ci[256];   // canonical index of symbol s (its place in (length, symbol) order)
     uint8_t nlo[256];        // node v's leaves are canonical indices nlo[v] .. nhi1[v]
     uint8_t nhi1[256];
-    uint16_t lcnt[8][16];    // symbols of each length per warp of symbols, then their prefix
     uint32_t nocode;         // a symbol without a code has a count
     int32_t a[17];           // d-bit prefixes under leaves of length <= d
     uint8_t first[17];       // first node of each depth
@@ -60,7 +59,8 @@ struct EncSmem {
     EncWarp w[kEncWarps];
 };
 static_assert(offsetof(EncSmem, w) % 16 == 0, "16-byte aligned warp areas");
-static_assert(((sizeof(BlockLayout) + 15) / 16) * 16 <= sizeof(EncWarp::buf[1]), "the staged layout fits a level buffer");
+static_assert(offsetof(BlockLayout, ci) <= sizeof(EncWarp::buf[1]) && offsetof(BlockLayout, ci) % 16 == 0,
+              "the staged part of the layout fits a level buffer");
 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop(int n, F f, G out) {
@@ -304,7 +304,10 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         const uint4 *g = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(layout) +
                                                           (size_t)b * kLayoutBytes);
         uint4 *d = reinterpret_cast<uint4 *>(S.w[kEncWarps - 1].buf[1]);
-        for (int i = t; i < (int)((sizeof(BlockLayout) + 15) / 16); i += kEncThreads) d[i] = __ldg(g + i);
+        constexpr int kStaged = (int)(offsetof(BlockLayout, ci) / 16), kTab = 768 / 16;
+        for (int i = t; i < kStaged; i += kEncThreads) d[i] = __ldg(g + i);
+        // the canonical order and the nodes' leaf ranges, straight into their tables
+        if (t < kTab) reinterpret_cast<uint4 *>(S.ci)[t] = __ldg(g + kStaged + t);
     }
     __syncthreads();
     const BlockLayout &L = *reinterpret_cast<const BlockLayout *>(S.w[kEncWarps - 1].buf[1]);
@@ -385,72 +388,18 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             S.bitsrc[t] = 8u * L.body_off[t];
         }
         if (t < 17) { S.a[t] = L.tree_a[t]; S.first[t] = L.depth_first[t]; }
-        if (t < 8 * 16) (&S.lcnt[0][0])[t] = 0;
         if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; S.nocode = 0; }
     }
     __syncthreads();
-    // canonical order (length, symbol) of the symbols with a code: per warp
-    // of symbols, the count of each length and each symbol's rank in it
-    const uint32_t my_len = L.len[t];
-    const uint32_t len_peers = __match_any_sync(0xffffffffu, my_len);
-    const uint32_t len_rank = __popc(len_peers & ((1u << lane) - 1u));
     {
+        const uint32_t my_len = L.len[t];
         const uint32_t key = __reduce_min_sync(0xffffffffu, my_len ? (my_len << 8) | (uint32_t)t : 0xFFFFu);
         if (lane == 0) atomicMin(&S.hot, key);
-        if (len_rank == 0) S.lcnt[warp][my_len] = (uint16_t)__popc(len_peers);
         const uint32_t pm = __ballot_sync(0xffffffffu, my_len != 0);
         if (lane == 0) S.pmask[warp] = pm;
     }
     __syncthreads();
     const uint32_t hot = S.hot & 0xFFu;
-    if (t < 32) {
-        // lane l < 16: symbols of length l before each warp of symbols, in canonical order
-        const uint32_t l = (uint32_t)t;
-        uint32_t tot = 0;
-        if (l >= 1 && l < 16)
-            for (int w = 0; w < kEncWarps; w++) tot += S.lcnt[w][l];
-        uint32_t inc = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (l >= 1 && l < 16) {
-            uint32_t run = inc - tot;
-            for (int w = 0; w < kEncWarps; w++) {
-                const uint32_t c = S.lcnt[w][l];
-                S.lcnt[w][l] = (uint16_t)run;
-                run += c;
-            }
-        }
-    }
-    __syncthreads();
-    // the codes in canonical order (left-aligned, increasing), in warp 0's
-    // second level buffer until the node ranges are known
-    uint16_t *acode = reinterpret_cast<uint16_t *>(S.w[0].buf[1]);
-    int K = 0;
-    if (my_len) {
-        const uint32_t c = S.lcnt[warp][my_len] + len_rank;
-        S.ci[t] = (uint8_t)c;
-        acode[c] = S.code16[t];
-    }
-    K = __syncthreads_count(my_len != 0);
-    if (t < V) {
-        // node t: depth d, prefix p; its leaves have codes in [p, p + 1) << (16 - d)
-        int d = 0;
-        while (d + 1 < 17 && S.first[d + 1] <= t) d++;
-        const uint32_t p = (uint32_t)S.a[d] + (uint32_t)(t - S.first[d]);
-        const uint32_t x0 = p << (16 - d), x1 = (p + 1) << (16 - d);
-        int lo = 0, hi = 0;
-#pragma unroll
-        for (int step = 256; step >= 1; step >>= 1) {
-            const int q0 = lo + step, q1 = hi + step;
-            if (q0 <= K && acode[q0 - 1] < x0) lo = q0;
-            if (q1 <= K && acode[q1 - 1] < x1) hi = q1;
-        }
-        S.nlo[t] = (uint8_t)lo;
-        S.nhi1[t] = (uint8_t)(hi - 1);
-    }
     // ---- warp chunks and their histograms ----
     static_assert(kEncChunks == kEncWarps, "one warp per chunk");
     const uint32_t nw = enc_nchunks(n);

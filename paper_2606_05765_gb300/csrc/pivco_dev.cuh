@@ -68,7 +68,14 @@ struct BlockLayout {
     int16_t child[256][2];     // >= 0 internal id; < 0 leaf, symbol = -c - 1
     uint8_t sel[256];          // ANS candidate marker (table id | 0x80 XOR), 0 if not selected
     uint8_t depth[256];
+    uint8_t pad3[8];
+    // (from here on not staged by the encoder, which loads it straight into its tables)
+    uint8_t ci[256];           // canonical index of symbol s: its place in (length, symbol) order
+    uint8_t nlo[256];          // the leaves under node v are canonical indices nlo[v] .. nhi1[v]
+    uint8_t nhi1[256];
 };
+static_assert(offsetof(BlockLayout, ci) % 16 == 0 && offsetof(BlockLayout, nhi1) + 256 == offsetof(BlockLayout, ci) + 768,
+              "the canonical tables are one 16-byte aligned run");
 static_assert(sizeof(BlockLayout) <= 8192, "layout too large");
 constexpr int32_t kLayoutBytes = 8192;
 
