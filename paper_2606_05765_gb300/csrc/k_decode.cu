@@ -45,6 +45,30 @@ __host__ __device__ inline uint32_t scratch_stride(uint32_t raw) { return ((raw 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop_d(int n, F f, G out) {
     const int lane = threadIdx.x & 31;
+    if (n <= 256) {
+        // lane l takes items 8l .. 8l + 7: one warp scan of the lanes' sums
+        uint32_t x[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int i = 8 * lane + j;
+            x[j] = i < n ? f(i) : 0u;
+            sum += x[j];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int i = 8 * lane + j;
+            if (i < n) out(i, run);
+            run += x[j];
+        }
+        return __shfl_sync(0xffffffffu, inc, 31);
+    }
     uint32_t carry = 0;
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
