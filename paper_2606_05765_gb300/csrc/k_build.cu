@@ -233,7 +233,8 @@ constexpr int kPmThreads = 256;
 
 // # of a[0..n) below x (a sorted, n <= 256): a fixed 9-step search with no
 // data-dependent branch
-__device__ inline int count_less_u64(const uint64_t *a, int n, uint64_t x) {
+template <typename W>
+__device__ inline int count_less_w(const W *a, int n, W x) {
     int pos = 0;
 #pragma unroll
     for (int step = 256; step >= 1; step >>= 1) {
@@ -244,7 +245,8 @@ __device__ inline int count_less_u64(const uint64_t *a, int n, uint64_t x) {
     return pos;
 }
 // # of a[0..n) not above x
-__device__ inline int count_le_u64(const uint64_t *a, int n, uint64_t x) {
+template <typename W>
+__device__ inline int count_le_w(const W *a, int n, W x) {
     int pos = 0;
 #pragma unroll
     for (int step = 256; step >= 1; step >>= 1) {
@@ -253,6 +255,33 @@ __device__ inline int count_le_u64(const uint64_t *a, int n, uint64_t x) {
         pos = ok ? q : pos;
     }
     return pos;
+}
+
+// Levels max_len - 1 .. 1 of package-merge: each level merges the sorted
+// leaves with the packages of the level below; leafpos[l][i] is leaf i's
+// place at level l.  W: the weight type (32 bits when no package can reach
+// 2^32, which halves the shared-memory traffic of the searches).
+template <typename W>
+__device__ inline void pm_levels(const W *leafw, W *pw, W (*lw)[512], uint16_t (*leafpos)[256], int K, int max_len) {
+    const int t = threadIdx.x;
+    for (int i = t; i < K; i += kPmThreads) { lw[max_len & 1][i] = leafw[i]; leafpos[max_len][i] = (uint16_t)i; }
+    int len_prev = K;
+    __syncthreads();
+    for (int lvl = max_len - 1; lvl >= 1; lvl--) {
+        const W *prev = lw[(lvl + 1) & 1];
+        W *cur = lw[lvl & 1];
+        const int P = len_prev / 2;
+        for (int j = t; j < P; j += kPmThreads) pw[j] = prev[2 * j] + prev[2 * j + 1];
+        __syncthreads();
+        for (int i = t; i < K; i += kPmThreads) {
+            const int pos = i + count_less_w(pw, P, leafw[i]);
+            cur[pos] = leafw[i];
+            leafpos[lvl][i] = (uint16_t)pos;
+        }
+        for (int j = t; j < P; j += kPmThreads) cur[j + count_le_w(leafw, K, pw[j])] = pw[j];
+        len_prev = K + P;
+        __syncthreads();
+    }
 }
 
 struct ClSmem {
@@ -302,24 +331,18 @@ __device__ inline int code_lengths_block(const uint32_t *h, int max_len, ClSmem 
             }
         }
         __syncthreads();
-        // level L: leaves only
-        for (int i = t; i < K; i += kPmThreads) { lw[max_len & 1][i] = leafw[i]; leafpos[max_len][i] = (uint16_t)i; }
-        int len_prev = K;
-        __syncthreads();
-        for (int lvl = max_len - 1; lvl >= 1; lvl--) {
-            const uint64_t *prev = lw[(lvl + 1) & 1];
-            uint64_t *cur = lw[lvl & 1];
-            const int P = len_prev / 2;
-            for (int j = t; j < P; j += kPmThreads) pw[j] = prev[2 * j] + prev[2 * j + 1];
+        // an item of a level holds at most one copy of a leaf per level
+        // below, so no weight exceeds max_len * K * (largest count)
+        if ((uint64_t)max_len * (uint64_t)K * leafw[K - 1] < (1ull << 32)) {
+            uint32_t *leafw32 = reinterpret_cast<uint32_t *>(pw), *pw32 = leafw32 + 256;
+            uint32_t (*lw32)[512] = reinterpret_cast<uint32_t (*)[512]>(&lw[0][0]);
+            const uint32_t w = t < K ? (uint32_t)leafw[t] : 0u;
             __syncthreads();
-            for (int i = t; i < K; i += kPmThreads) {
-                const int pos = i + count_less_u64(pw, P, leafw[i]);
-                cur[pos] = leafw[i];
-                leafpos[lvl][i] = (uint16_t)pos;
-            }
-            for (int j = t; j < P; j += kPmThreads) cur[j + count_le_u64(leafw, K, pw[j])] = pw[j];
-            len_prev = K + P;
+            if (t < K) leafw32[t] = w;
             __syncthreads();
+            pm_levels<uint32_t>(leafw32, pw32, lw32, leafpos, K, max_len);
+        } else {
+            pm_levels<uint64_t>(leafw, pw, lw, leafpos, K, max_len);
         }
         // selection, top-down (one warp): at each level the selected items are
         // the first m; count the leaves among them (their positions increase
