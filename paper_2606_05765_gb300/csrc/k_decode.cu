@@ -958,12 +958,14 @@ __device__ inline void warp_fill(uint8_t *p, uint32_t n, uint8_t x) {
 __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
                                  int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
                                  const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
-                                 WarpTile &S, const uint32_t *sel) {
+                                 WarpTile &S, const uint32_t *sel, int b = -1) {
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
     const DecRegions G = dec_regions(nblk, ws);
-    const uint32_t ttot = reinterpret_cast<const uint32_t *>(ws)[6];
-    const int b = find_block_warp(W.blk_tile, nblk, gt, (int)((uint64_t)gt * (uint32_t)nblk / max(ttot, 1u)));
+    if (b < 0) {   // (the batched path has found the tile's block already)
+        const uint32_t ttot = reinterpret_cast<const uint32_t *>(ws)[6];
+        b = find_block_warp(W.blk_tile, nblk, gt, (int)((uint64_t)gt * (uint32_t)nblk / max(ttot, 1u)));
+    }
     if (*reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
     const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
     const uint8_t *rec = comp + comp_off[b];
@@ -1607,7 +1609,7 @@ __device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTil
         if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
     }
     if (!__shfl_sync(0xffffffffu, okw, 0)) return;
-    warp_tile(it, q.comp, q.comp_off, q.nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, S, sel);
+    warp_tile(it, q.comp, q.comp_off, q.nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, S, sel, b);
 }
 
 __global__ void __launch_bounds__(kDecThreads, 2) decode_batch_kernel(const uint8_t *__restrict__ comp,
