@@ -530,12 +530,17 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 const uint32_t nb = smem_addr(E.buf[1]);
                 const uint32_t lp0 = nb + 2u * (i0 ? E.sp[c0 & 0xFFu] : 0u), rp0 = nb + 2u * (i1 ? E.sp[c1 & 0xFFu] : 0u);
                 uint32_t carry = 0;
+                // the next window's 32 bytes are loaded while this one is coded
+                uint32_t xn[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (32u * lane < C) ldg32(src + P + 32u * lane, src_end, xn);
                 for (uint32_t kb = 0; kb < C; kb += 1024) {
                     const uint32_t kk = kb + 32u * lane;
                     const bool act = kk < C;
                     const uint32_t vl = act ? min(32u, C - kk) : 0u;
-                    uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    if (act) ldg32(src + P + kk, src_end, x);
+                    uint32_t x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) { x[q] = xn[q]; xn[q] = 0u; }
+                    if (kk + 1024 < C) ldg32(src + P + kk + 1024, src_end, xn);
                     uint32_t y[16];
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
