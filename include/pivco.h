@@ -306,7 +306,9 @@ pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off,
  *     status[nblk] per block.  PIVCO_ERR_CAPACITY if comp_cap is too small.
  *   decompress: blocks of comp[] (records at comp_off[b], 16-byte aligned
  *     relative to comp_off[0]) into out[blk_off[b] ..]; status[nblk] as for
- *     pivco_decode_blocks.
+ *     pivco_decode_blocks.  The first call allocates each piece's decode
+ *     workspace, sized from the block sizes alone (no record is read on the
+ *     host; up to about 3x the piece's raw bytes), and later calls reuse it.
  * One call at a time per codec; each call returns when its output is in
  * host memory. */
 typedef struct pivco_host_codec pivco_host_codec;
