@@ -17,8 +17,12 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *     stream).  Work is enqueued asynchronously on it; nothing here
  *     synchronises unless the comment says "synchronous".
- *   - The library allocates no device memory in any call of this header:
- *     scratch space is a caller-provided workspace sized by a query call.
+ *   - The device-buffer calls allocate no device memory: scratch space is a
+ *     caller-provided workspace sized by a query call (or, for
+ *     pivco_decode_blocks_static, an array the library's module holds).  The
+ *     exception is the host-buffer codec (pivco_host_codec_*), which owns
+ *     device buffers for its pieces: pivco_host_codec_create allocates them
+ *     and the first pivco_host_decompress allocates its decode workspaces.
  *   - Blocks are described by `blk_off[nblk + 1]` (device, uint64): block b is
  *     bytes [blk_off[b], blk_off[b+1]) of a flat buffer.
  *   - The return value reports host-side argument errors and launch errors.
@@ -196,8 +200,12 @@ pivco_status pivco_decode_blocks(const uint8_t *comp, const uint64_t *comp_off, 
  * device memory of PIVCO_DECODE_STATIC_WS_BYTES (16 MiB), created with the
  * library's module; nothing is allocated per call.
  *   - The first call on each device looks up that array's address (the
- *     module loads then) with that device current.  Make that first call
- *     before any stream capture.
+ *     module loads then) with that device current, and keeps it for the
+ *     life of the process.  Make that first call before any stream capture:
+ *     a first call on a stream that is capturing returns
+ *     PIVCO_ERR_INVALID_ARG.  The kept address does not survive
+ *     cudaDeviceReset; do not call this function after resetting a device
+ *     it was called on.
  *   - nblk whose fixed plan part alone (pivco_decode_plan_bytes) exceeds the
  *     array returns PIVCO_ERR_CAPACITY without launching anything.  Blocks
  *     whose ANS scratch or rank directories do not fit in what remains get
@@ -278,6 +286,18 @@ pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
 
 /* Number of kernels this library has launched in this process (host). */
 uint64_t pivco_launch_count(void);
+
+/* Bound of the library's device-side waits (process-wide, host).  Every
+ * wait a kernel makes on work of another CTA (the decoupled look-backs of
+ * pivco_exclusive_scan and of the decode plan, the batched decode's and the
+ * serving loop's waits on earlier queue items) gives up after `ns`
+ * nanoseconds of device time.  The blocks concerned then report
+ * PIVCO_ERR_TIMEOUT (pivco_exclusive_scan: its status_out) and the kernel
+ * returns; no block whose work was abandoned reports PIVCO_OK.  Applies to
+ * calls issued after it is set (a server takes it at each submit).  Default
+ * 10^9 (1 s).  pivco_get_wait_limit returns the current bound. */
+pivco_status pivco_set_wait_limit(uint64_t ns);
+uint64_t pivco_get_wait_limit(void);
 
 /* ---- Batching (not in the paper: the GPU scheduling of many blocks) ----
  * pivco_decode_batched decodes the same records as pivco_decode_blocks (same

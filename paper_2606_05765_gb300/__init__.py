@@ -61,6 +61,7 @@ _SIGS = {
     "pivco_server_drain": [_P, _I32],
     "pivco_server_forget": [_P, C.c_uint64],
     "pivco_server_destroy": [_P],
+    "pivco_set_wait_limit": [C.c_uint64],
 }
 _OTHER = {
     "pivco_version": ([], C.c_char_p),
@@ -69,6 +70,7 @@ _OTHER = {
     "pivco_decode_plan_bytes": ([_I32], _SZ),
     "pivco_launch_count": ([], C.c_uint64),
     "pivco_host_codec_comp_capacity": ([_P], C.c_uint64),
+    "pivco_get_wait_limit": ([], C.c_uint64),
 }
 
 
@@ -233,6 +235,15 @@ def decode_merge(comp, comp_off, nblk, out, out_off, ws, status, stream=None):
 
 def launch_count():
     return int(lib().pivco_launch_count())
+
+
+def set_wait_limit(ns=10 ** 9):
+    """Bound (ns) of the library's device-side waits; expired waits report TIMEOUT."""
+    _check(lib().pivco_set_wait_limit(int(ns)), "pivco_set_wait_limit")
+
+
+def get_wait_limit():
+    return int(lib().pivco_get_wait_limit())
 
 
 # ------------------------------------------------------------- batching ----

@@ -55,8 +55,7 @@ def build(verbose=False, force=False, extra=()):
                 print(out)
     if jobs or not os.path.exists(OUT):
         tmp = OUT + ".tmp%d" % os.getpid()
-        run([nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart_static"] if False else
-            [nvcc, "-shared", "-o", tmp] + objs + ARCH)
+        run([nvcc, "-shared", "-o", tmp] + objs + ARCH)
         os.replace(tmp, OUT)
     return OUT
 

@@ -65,12 +65,18 @@ static std::atomic<uint64_t> g_launches{0};
 // launch tuning of the decode (process-wide; set by pivco_set_tuning / the autotuner)
 static DecTuning g_tuning = {65536, 128, 0};
 static std::mutex g_tuning_mu;
-const DecTuning &current_tuning() { return g_tuning; }
+DecTuning current_tuning() {
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    return g_tuning;
+}
 void set_tuning(const DecTuning &t) {
     std::lock_guard<std::mutex> lk(g_tuning_mu);
     g_tuning = t;
 }
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+static std::atomic<uint64_t> g_wait_limit{kWaitLimitNs};
+uint64_t wait_limit_ns() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 const AnsTables &host_ans_tables() {
     std::call_once(g_tab_once, build_tables);
@@ -81,6 +87,8 @@ const AnsTables &host_ans_tables() {
 
 using namespace pv;
 
+static inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
 // Library-owned decode workspace for pivco_decode_blocks_static: one array
 // per device, part of this module (no allocation call ever makes it).  Its
 // address is looked up once per device, with that device current.
@@ -90,13 +98,19 @@ static constexpr int kMaxDevices = 64;
 static uint8_t *g_static_ws_ptr[kMaxDevices];
 static std::mutex g_static_ws_mu;
 
-static cudaError_t static_ws_address(uint8_t **ptr) {
+// cudaErrorStreamCaptureUnsupported when the address is not known yet and
+// `st` is capturing (the lookup may load the module, which a capture forbids)
+static cudaError_t static_ws_address(uint8_t **ptr, cudaStream_t st) {
     int d = 0;
     cudaError_t e = cudaGetDevice(&d);
     if (e != cudaSuccess) return e;
     if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_static_ws_mu);
     if (!g_static_ws_ptr[d]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) return e;
+        if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_ws);
         if (e != cudaSuccess) return e;
@@ -106,7 +120,6 @@ static cudaError_t static_ws_address(uint8_t **ptr) {
     return cudaSuccess;
 }
 
-static inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 static inline pivco_status ok_or_cuda(cudaError_t e) { return e == cudaSuccess ? PIVCO_OK : PIVCO_ERR_CUDA; }
 
 extern "C" {
@@ -235,7 +248,9 @@ pivco_status pivco_decode_blocks_static(const uint8_t *comp, const uint64_t *com
     if (nblk == 0) return PIVCO_OK;
     if (decode_ws_fixed_bytes(nblk) > kStaticWsBytes) return PIVCO_ERR_CAPACITY;
     uint8_t *ws = nullptr;
-    if (static_ws_address(&ws) != cudaSuccess) return PIVCO_ERR_CUDA;
+    const cudaError_t e = static_ws_address(&ws, S(stream));
+    if (e == cudaErrorStreamCaptureUnsupported) return PIVCO_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return PIVCO_ERR_CUDA;
     // the plan step's first launch zeroes the header, look-back states and
     // counters; scratch and directories need no clearing
     return ok_or_cuda(launch_decode(comp, comp_off, nblk, out, out_off, ws, kStaticWsBytes, status, S(stream)));
@@ -269,6 +284,13 @@ pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
 }
 
 uint64_t pivco_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pivco_status pivco_set_wait_limit(uint64_t ns) {
+    g_wait_limit.store(ns, std::memory_order_relaxed);
+    return PIVCO_OK;
+}
+
+uint64_t pivco_get_wait_limit(void) { return wait_limit_ns(); }
 
 pivco_status pivco_ans_tables(int32_t *fse_h_q16, uint32_t *class_freq) {
     const AnsTables &T = host_ans_tables();
@@ -309,7 +331,7 @@ pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off,
 
 pivco_status pivco_get_tuning(pivco_tuning *t) {
     if (!t) return PIVCO_ERR_INVALID_ARG;
-    const DecTuning &c = current_tuning();
+    const DecTuning c = current_tuning();
     t->tile_max = (int32_t)c.tile_max;
     t->dir_bits = (int32_t)c.dir_bits;
     t->ctas_per_sm = (int32_t)c.ctas_per_sm;
@@ -386,6 +408,7 @@ pivco_status pivco_autotune_decode(const uint8_t *comp, const uint64_t *comp_off
     for (uint32_t tm : tiles)
         for (uint32_t db : dirs)
             for (uint32_t cs : ctas) {
+                if (rc != PIVCO_OK) break;   // a CUDA error ends the whole search
                 set_tuning(DecTuning{tm, db, cs});
                 // the workspace this tuning needs (tile cursors and directories grow as
                 // tiles shrink): a candidate that does not fit is skipped, not timed

@@ -389,7 +389,8 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
     if (!ok) { ntile = 1; T = 0; dir_bytes = 0; }
     int to = 0;
     uint64_t ea = 0, eb = 0;
-    lookback2_exclusive_warp(W.states_a, W.states_b, b, (sb << 22) | sg, (dir_bytes << 22) | ntile, ea, eb, &to);
+    lookback2_exclusive_warp(W.states_a, W.states_b, b, (sb << 22) | sg, (dir_bytes << 22) | ntile, ea, eb, &to,
+                             hdr64[7]);
     if (lane == 0) {
         W.blk_scratch[b] = ea >> 22;
         W.blk_seg[b] = (uint32_t)(ea & ((1u << 22) - 1));
@@ -403,6 +404,9 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
             hdr32[2] = (uint32_t)((ea & ((1u << 22) - 1)) + sg);
             hdr64[2] = (eb >> 22) + dir_bytes;
             hdr32[6] = (uint32_t)((eb & ((1u << 22) - 1)) + ntile);
+            // totals from a partial prefix are unusable: every later pass
+            // gives the whole batch up (abandoned_batch)
+            if (to) atomicExch(&hdr32[13], 1u);
         }
     }
     // the node table (only where the workspace holds it: a sizing run may not)
@@ -437,8 +441,9 @@ __global__ void __launch_bounds__(32) decode_plan_kernel(const uint8_t *__restri
     plan_block(s_tile, comp, comp_off, nblk, ws, ws_bytes, status, R, Q);
 }
 
-// zero the header, the look-back states and the batch counters; set the tuning
-__global__ void dec_ws_init_kernel(uint8_t *ws, int nblk, uint32_t dir_bits, uint32_t tile_max) {
+// zero the header, the look-back states and the batch counters; set the
+// tuning and the wait bound
+__global__ void dec_ws_init_kernel(uint8_t *ws, int nblk, uint32_t dir_bits, uint32_t tile_max, uint64_t limit_ns) {
     const DecWs W = dec_ws(ws, nblk);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nblk; i += gridDim.x * blockDim.x) {
         W.states_a[i] = 0;
@@ -449,14 +454,30 @@ __global__ void dec_ws_init_kernel(uint8_t *ws, int nblk, uint32_t dir_bits, uin
     if (blockIdx.x == 0 && threadIdx.x < 16) {
         uint32_t *h = reinterpret_cast<uint32_t *>(ws);
         h[threadIdx.x] = threadIdx.x == 7 ? dir_bits : (threadIdx.x == 8 ? tile_max : 0u);
+        if (threadIdx.x == 14) h[14] = (uint32_t)limit_ns;
+        if (threadIdx.x == 15) h[15] = (uint32_t)(limit_ns >> 32);
     }
+}
+
+// True when the plan could not place the batch (a look-back wait ran out
+// before the last block's prefix was known) or a CTA of the batched queue
+// gave up: the workspace totals and offsets are not to be used.  The caller
+// marks every block that still reads OK as timed out (grid-stride, all CTAs
+// of a pass may do it) and leaves.  A uniform decision: the flag is set
+// before the pass starts, or (batched) before all plans are counted done.
+__device__ inline bool abandoned_batch(const uint8_t *ws, int32_t *status, int nblk) {
+    if (!*reinterpret_cast<const volatile uint32_t *>(ws + 52)) return false;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
+        if (*reinterpret_cast<volatile int32_t *>(&status[b]) == PIVCO_OK) status[b] = PIVCO_ERR_TIMEOUT;
+    return true;
 }
 
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
                                int32_t *status, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    const DecTuning &tu = current_tuning();
-    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max);
+    const DecTuning tu = current_tuning();
+    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max,
+                                                                      wait_limit_ns());
     decode_plan_kernel<<<nblk, 32, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
     count_launches(2);
     return cudaGetLastError();
@@ -547,6 +568,7 @@ __global__ void __launch_bounds__(32 * kAnsDecWarps) ans_decode_planned_kernel(c
                                                                                const __grid_constant__ AnsTables A) {
     __shared__ WarpRec R[kAnsDecWarps];
     __shared__ AnsSm T[kAnsDecWarps];
+    if (abandoned_batch(ws, status, nblk)) return;
     const int w = threadIdx.x >> 5;
     const uint32_t total = reinterpret_cast<const uint32_t *>(ws)[2];
     int last_b = -1;
@@ -1408,6 +1430,7 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_
                                                                     int32_t *__restrict__ status) {
     __shared__ DirSmem D;
     __shared__ DirWarpSmem DW[kDecWarps];
+    if (abandoned_batch(ws, status, nblk)) return;
     for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
         const uint32_t e = dir_entries(b, comp, comp_off, nblk, ws, ws_bytes);
         if (e > kDirWarpMax) dir_cta(b, comp, comp_off, nblk, ws, ws_bytes, status, D);
@@ -1430,6 +1453,7 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *_
                                                                 int32_t *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
+    if (abandoned_batch(ws, status, nblk)) return;
     sel_init(S.sel);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1459,12 +1483,12 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *_
 // segments; a tile on its block's ANS segments and directory.  The CTAs that
 // took those items are running, so every wait ends.
 // ---------------------------------------------------------------------------
-__device__ inline bool wait_geq(const uint32_t *p, uint32_t want) {
+__device__ inline bool wait_geq(const uint32_t *p, uint32_t want, uint64_t limit_ns) {
     if (*reinterpret_cast<const volatile uint32_t *>(p) >= want) { __threadfence(); return true; }
     const uint64_t t0 = globaltimer_ns();
     unsigned ns = 64;
     while (*reinterpret_cast<const volatile uint32_t *>(p) < want) {
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
         __nanosleep(ns);
         if (ns < 2048) ns <<= 1;
     }
@@ -1500,6 +1524,9 @@ struct BatchQueue {
     int nblk;
 };
 
+// the wait bound of a batch's queue (workspace header)
+__device__ inline uint64_t wait_bound(const BatchQueue &q) { return reinterpret_cast<const uint64_t *>(q.ws)[7]; }
+
 // Items of a batch's queue once all plans are done (header written by the last plan).
 __device__ inline uint32_t batch_items_total(const BatchQueue &q) {
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
@@ -1522,16 +1549,37 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
     if (item < nplan) {
         // ---- plans ----
         const int b = (int)(item * kDecWarps + warp);
-        if (b < nblk) plan_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.pa.R[warp], B.u.pa.Q[warp]);
+        if (b < nblk) {
+            plan_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.pa.R[warp], B.u.pa.Q[warp]);
+            // a CTA that has given up on the queue (below) may have marked
+            // the blocks before this plan wrote its status: re-mark it, so a
+            // block whose later items may never run does not read as done
+            __threadfence();
+            if (lane == 0 && *reinterpret_cast<volatile uint32_t *>(&hdr[13]) &&
+                *reinterpret_cast<volatile int32_t *>(&q.status[b]) == PIVCO_OK)
+                q.status[b] = PIVCO_ERR_TIMEOUT;
+        }
         __syncthreads();
         if (t == 0) { __threadfence(); atomicAdd(&hdr[10], 1u); }
         return kItemDone;
     }
     // everything after the plans needs all plans
     int ok = 1;
-    if (t == 0) ok = wait_geq(&hdr[10], nplan);
+    if (t == 0) {
+        ok = wait_geq(&hdr[10], nplan, wait_bound(q));
+        // the last plan could not place the batch: nothing after the plans runs
+        if (ok && *reinterpret_cast<volatile uint32_t *>(&hdr[13])) ok = 0;
+    }
     if (__syncthreads_or(!ok)) {
-        if (t == 0) for (int b = 0; b < nblk; b++) if (q.status[b] == PIVCO_OK) q.status[b] = PIVCO_ERR_TIMEOUT;
+        // this CTA leaves the queue: every block not yet failed is marked, as
+        // its items may now never run (the flag makes plans still running
+        // mark theirs, the fences order the flag against their status writes)
+        if (t == 0) {
+            atomicExch(&hdr[13], 1u);
+            __threadfence();
+            for (int b = 0; b < nblk; b++)
+                if (*reinterpret_cast<volatile int32_t *>(&q.status[b]) == PIVCO_OK) q.status[b] = PIVCO_ERR_TIMEOUT;
+        }
         __syncthreads();
         return kItemStop;
     }
@@ -1560,7 +1608,7 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
             const int b = (int)(it * kDecWarps + w);
             const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
             int okw = 1;
-            if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs);
+            if (t == 0) okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
             if (__syncthreads_or(!okw)) {
                 if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
             } else {
@@ -1589,7 +1637,7 @@ __device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTil
         const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
         int okw = 1;
         if (lane == 0) {
-            okw = wait_geq(&W.segs_done[b], nsegs);
+            okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
             if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
         }
         if (__shfl_sync(0xffffffffu, okw, 0))
@@ -1604,8 +1652,8 @@ __device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTil
     const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
     int okw = 1;
     if (lane == 0) {
-        okw = wait_geq(&W.segs_done[b], nsegs);
-        if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u);
+        okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
+        if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u, wait_bound(q));
         if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
     }
     if (!__shfl_sync(0xffffffffu, okw, 0)) return;
@@ -1888,8 +1936,9 @@ cudaError_t launch_decode_batch(const uint8_t *comp, const uint64_t *comp_off, i
                                 const uint64_t *out_off, uint8_t *ws, size_t ws_bytes, int32_t *status,
                                 cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    const DecTuning &tu = current_tuning();
-    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max);
+    const DecTuning tu = current_tuning();
+    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max,
+                                                                      wait_limit_ns());
     const int smem = (int)sizeof(BatchSmem);
     cudaError_t e = cudaFuncSetAttribute(decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -19,7 +19,7 @@ __global__ void zero_bytes_kernel(uint8_t *p, size_t n) {
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint64_t *__restrict__ in, int n,
                                                             uint64_t *__restrict__ out, uint8_t *ws,
-                                                            int32_t *status) {
+                                                            int32_t *status, uint64_t limit_ns) {
     __shared__ int s_tile;
     __shared__ uint64_t s_warp[kScanThreads / 32];
     __shared__ uint64_t s_excl;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint64_t *__re
     const uint64_t total = s_warp[kScanThreads / 32 - 1];
     if (t == 0) {
         int to = 0;
-        s_excl = lookback_exclusive(states, tile, total, &to);
+        s_excl = lookback_exclusive(states, tile, total, &to, limit_ns);
         s_to = to;
     }
     __syncthreads();
@@ -84,7 +84,7 @@ cudaError_t launch_scan(const uint64_t *in, int n, uint64_t *out, void *ws, int3
     const size_t wsb = scan_ws_bytes(n);
     zero_bytes_kernel<<<min(256, div_up((long long)wsb, 256)), 256, 0, st>>>(reinterpret_cast<uint8_t *>(ws), wsb);
     count_launches(1);
-    scan_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, out, reinterpret_cast<uint8_t *>(ws), status);
+    scan_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, out, reinterpret_cast<uint8_t *>(ws), status, wait_limit_ns());
     count_launches(1);
     return cudaGetLastError();
 }

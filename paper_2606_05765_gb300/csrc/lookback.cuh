@@ -1,8 +1,11 @@
 // Decoupled look-back (single-pass prefix over CTAs in ticket order).
 // Each tile publishes its aggregate, then walks back over its predecessors
 // until it meets an inclusive prefix, and publishes its own inclusive prefix.
-// Every wait is bounded by a 1 s device-clock limit; on expiry the caller's
-// timeout flag is set and the partial prefix is used (the status reports it).
+// Every wait is bounded by a device-clock limit (limit_ns); on expiry the
+// caller's timeout flag is set and the tile publishes its partial prefix
+// marked as poisoned.  A tile that meets a poisoned prefix sets its own
+// timeout flag and passes the poison on, so every tile after an expired wait
+// reports it and no tile takes a partial prefix for a final one.
 #pragma once
 #include "pivco_dev.cuh"
 
@@ -10,7 +13,8 @@ namespace pv {
 
 constexpr uint64_t kLbFlagAgg = 1ull << 62;
 constexpr uint64_t kLbFlagInc = 2ull << 62;
-constexpr uint64_t kLbValMask = (1ull << 62) - 1;
+constexpr uint64_t kLbPoison = 1ull << 61;
+constexpr uint64_t kLbValMask = (1ull << 61) - 1;
 
 __device__ inline void lb_store(uint64_t *p, uint64_t v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -23,7 +27,8 @@ __device__ inline uint64_t lb_load(const uint64_t *p) {
 
 // Called by ONE thread.  Returns the exclusive prefix of `agg` over tiles
 // 0 .. tile-1.  states[] must be zero before the launch.
-__device__ inline uint64_t lookback_exclusive(uint64_t *states, int tile, uint64_t agg, int *timed_out) {
+__device__ inline uint64_t lookback_exclusive(uint64_t *states, int tile, uint64_t agg, int *timed_out,
+                                              uint64_t limit_ns) {
     if (tile == 0) {
         lb_store(&states[0], kLbFlagInc | (agg & kLbValMask));
         return 0;
@@ -31,22 +36,27 @@ __device__ inline uint64_t lookback_exclusive(uint64_t *states, int tile, uint64
     lb_store(&states[tile], kLbFlagAgg | (agg & kLbValMask));
     uint64_t excl = 0;
     int j = tile - 1;
+    bool bad = false;
     const uint64_t t0 = globaltimer_ns();
     unsigned ns = 32;
     while (j >= 0) {
         const uint64_t v = lb_load(&states[j]);
-        const uint64_t f = v & ~kLbValMask;
+        const uint64_t f = v & (kLbFlagAgg | kLbFlagInc);
         if (f == 0) {
-            if (globaltimer_ns() - t0 > kWaitLimitNs) { *timed_out = 1; break; }
+            if (globaltimer_ns() - t0 > limit_ns) { bad = true; break; }
             __nanosleep(ns);
             if (ns < 1024) ns <<= 1;
             continue;
         }
         excl += v & kLbValMask;
-        if (f == kLbFlagInc) break;
+        if (f == kLbFlagInc) {
+            bad = (v & kLbPoison) != 0;
+            break;
+        }
         j--;
     }
-    lb_store(&states[tile], kLbFlagInc | ((excl + agg) & kLbValMask));
+    if (bad) *timed_out = 1;
+    lb_store(&states[tile], kLbFlagInc | (bad ? kLbPoison : 0ull) | ((excl + agg) & kLbValMask));
     return excl;
 }
 
@@ -55,7 +65,8 @@ __device__ inline uint64_t lookback_exclusive(uint64_t *states, int tile, uint64
 // nearest inclusive prefix, so a walk over many published aggregates takes
 // one load latency per 32 predecessors.  Called by all 32 lanes with the
 // same arguments; returns the exclusive prefix in every lane.
-__device__ inline uint64_t lookback_exclusive_warp(uint64_t *states, int tile, uint64_t agg, int *timed_out) {
+__device__ inline uint64_t lookback_exclusive_warp(uint64_t *states, int tile, uint64_t agg, int *timed_out,
+                                                   uint64_t limit_ns) {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
         if (lane == 0) lb_store(&states[0], kLbFlagInc | (agg & kLbValMask));
@@ -64,18 +75,19 @@ __device__ inline uint64_t lookback_exclusive_warp(uint64_t *states, int tile, u
     if (lane == 0) lb_store(&states[tile], kLbFlagAgg | (agg & kLbValMask));
     uint64_t excl = 0;
     int j = tile - 1;
+    bool bad = false;
     const uint64_t t0 = globaltimer_ns();
     unsigned ns = 32;
     for (;;) {
         const int k = j - lane;
         const uint64_t v = k >= 0 ? lb_load(&states[k]) : kLbFlagInc;   // before tile 0: an inclusive zero
-        const uint64_t f = v & ~kLbValMask;
+        const uint64_t f = v & (kLbFlagAgg | kLbFlagInc);
         const uint32_t inc = __ballot_sync(0xffffffffu, f == kLbFlagInc);
         const uint32_t unset = __ballot_sync(0xffffffffu, f == 0);
         const uint32_t upto = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;   // lanes up to the nearest one
         if (unset & upto) {
-            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > kWaitLimitNs)) {
-                *timed_out = 1;
+            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > limit_ns)) {
+                bad = true;
                 break;
             }
             __nanosleep(ns);
@@ -86,10 +98,14 @@ __device__ inline uint64_t lookback_exclusive_warp(uint64_t *states, int tile, u
 #pragma unroll
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         excl += x;
-        if (inc) break;
+        if (inc) {
+            bad = (__ballot_sync(0xffffffffu, (v & kLbPoison) != 0) & inc & (0u - inc)) != 0;
+            break;
+        }
         j -= 32;
     }
-    if (lane == 0) lb_store(&states[tile], kLbFlagInc | ((excl + agg) & kLbValMask));
+    if (bad) *timed_out = 1;
+    if (lane == 0) lb_store(&states[tile], kLbFlagInc | (bad ? kLbPoison : 0ull) | ((excl + agg) & kLbValMask));
     return excl;
 }
 
@@ -99,7 +115,7 @@ __device__ inline uint64_t lookback_exclusive_warp(uint64_t *states, int tile, u
 // 32 lanes; returns both exclusive prefixes in every lane.
 __device__ inline void lookback2_exclusive_warp(uint64_t *states_a, uint64_t *states_b, int tile, uint64_t agg_a,
                                                 uint64_t agg_b, uint64_t &excl_a, uint64_t &excl_b,
-                                                int *timed_out) {
+                                                int *timed_out, uint64_t limit_ns) {
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     uint64_t *states = half ? states_b : states_a;
     const uint64_t agg = half ? agg_b : agg_a;
@@ -112,19 +128,21 @@ __device__ inline void lookback2_exclusive_warp(uint64_t *states_a, uint64_t *st
     uint64_t excl = 0;
     int j = tile - 1;
     bool done = false;   // (the same in all lanes of a half)
+    bool bad = false;    // an expired wait, or a poisoned prefix met (the same in all lanes)
     const uint64_t t0 = globaltimer_ns();
     unsigned ns = 32;
     for (;;) {
         const int k = j - hl;
         uint64_t v = kLbFlagInc;   // before tile 0: an inclusive zero
         if (!done && k >= 0) v = lb_load(&states[k]);
-        const uint64_t f = v & ~kLbValMask;
+        const uint64_t f = v & (kLbFlagAgg | kLbFlagInc);
         const uint32_t inc = (__ballot_sync(0xffffffffu, f == kLbFlagInc) >> (16 * half)) & 0xFFFFu;
         const uint32_t unset = (__ballot_sync(0xffffffffu, f == 0) >> (16 * half)) & 0xFFFFu;
+        const uint32_t pois = (__ballot_sync(0xffffffffu, (v & kLbPoison) != 0) >> (16 * half)) & 0xFFFFu;
         const uint32_t upto = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFu;   // lanes up to the nearest one
         if (__any_sync(0xffffffffu, !done && (unset & upto))) {
-            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > kWaitLimitNs)) {
-                *timed_out = 1;
+            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > limit_ns)) {
+                bad = true;
                 break;
             }
             __nanosleep(ns);
@@ -134,6 +152,7 @@ __device__ inline void lookback2_exclusive_warp(uint64_t *states_a, uint64_t *st
         uint64_t x = (!done && ((upto >> hl) & 1u)) ? (v & kLbValMask) : 0ull;
 #pragma unroll
         for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);   // within the half
+        if (__any_sync(0xffffffffu, !done && (pois & inc & (0u - inc)) != 0)) bad = true;
         if (!done) {
             excl += x;
             if (inc) done = true;
@@ -141,7 +160,10 @@ __device__ inline void lookback2_exclusive_warp(uint64_t *states_a, uint64_t *st
         }
         if (__all_sync(0xffffffffu, done)) break;
     }
-    if (hl == 0) lb_store(&states[tile], kLbFlagInc | ((excl + agg) & kLbValMask));
+    // a poisoned or partial prefix in either chain makes both chains' prefixes
+    // unusable downstream (the block's offsets come from both)
+    if (bad) *timed_out = 1;
+    if (hl == 0) lb_store(&states[tile], kLbFlagInc | (bad ? kLbPoison : 0ull) | ((excl + agg) & kLbValMask));
     excl_a = __shfl_sync(0xffffffffu, excl, 0);
     excl_b = __shfl_sync(0xffffffffu, excl, 16);
 }

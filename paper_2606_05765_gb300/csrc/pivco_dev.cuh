@@ -201,7 +201,8 @@ __device__ inline uint64_t globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-constexpr uint64_t kWaitLimitNs = 1000000000ull;   // bounded device waits: 1 s
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // default bound of a device wait: 1 s
+uint64_t wait_limit_ns();                          // the current bound (pivco_set_wait_limit)
 
 __host__ __device__ inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 // kernels launched by this library (reported through pivco_launch_count)
@@ -253,7 +254,10 @@ cudaError_t launch_ans_decode(const uint8_t *bodies, const uint64_t *body_off, c
 //   header (64 B): u64 scratch bytes @0, u32 ANS segments @8, u32 ticket @12,
 //                  u64 directory+cursor bytes @16, u32 tiles @24,
 //                  u32 directory granularity (bits) @28, u32 longest tile @32,
-//                  u32 batch queue ticket @36, u32 batch plans done @40
+//                  u32 batch queue ticket @36, u32 batch plans done @40,
+//                  u32 items done (serving) @44, u32 tile ticket @48,
+//                  u32 abandoned @52 (a CTA gave up on the queue),
+//                  u64 wait bound in ns @56
 //   per block: u64 look-back states A[nblk], B[nblk]; u64 scratch offset[nblk];
 //              u64 directory offset[nblk]; u32 first segment[nblk];
 //              u32 first tile[nblk]; u32 tile length[nblk]; u32 tiles[nblk];
@@ -275,7 +279,7 @@ struct DecTuning {
     uint32_t dir_bits;      // rank directory granularity (bits), a multiple of 32, <= 1024
     uint32_t ctas_per_sm;   // persistent merge CTAs per SM (0: as many as fit)
 };
-const DecTuning &current_tuning();
+DecTuning current_tuning();   // a copy, taken under the tuning lock
 void set_tuning(const DecTuning &t);
 __host__ __device__ inline DecWs dec_ws(uint8_t *ws, int nblk) {
     DecWs w;

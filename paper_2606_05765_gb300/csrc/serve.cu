@@ -407,6 +407,8 @@ pivco_status pivco_server_submit(pivco_server *s, const uint8_t *comp, const uin
     r->hdr.assign(64, 0);
     memcpy(r->hdr.data() + 28, &tu.dir_bits, 4);
     memcpy(r->hdr.data() + 32, &tu.tile_max, 4);
+    const uint64_t lim = pv::wait_limit_ns();
+    memcpy(r->hdr.data() + 56, &lim, 8);
     r->t_submit = pv::now_ms();
     std::lock_guard<std::mutex> lk(s->mu);
     r->seq = s->next_id++;

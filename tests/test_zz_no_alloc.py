@@ -68,3 +68,31 @@ def test_static_rejects_oversized_batch(P):
     with pytest.raises(P.PivcoError, match="CAPACITY"):
         P.decode_blocks_static(comp, offs, n, comp, offs, st)
     assert P.decode_plan_bytes(n) > P.DECODE_STATIC_WS_BYTES
+
+
+def test_static_reports_capacity_per_block(P):
+    """Blocks whose ANS scratch or rank directories do not fit in what is left
+    of the 16 MiB array report PIVCO_ERR_CAPACITY; the others decode exactly
+    as pivco_decode_blocks decodes them."""
+    import torch
+    # 160 blocks of 1 MiB with an ANS-coded 128 KiB root bitmap each, split
+    # into several tiles: about 180 KiB of workspace per block, 28 MiB in all
+    w = workloads.skew95(nblk=160, bs=1 << 20, seed=23)
+    data = _dev(w.data)
+    boff = _dev(w.blk_off.astype(np.int64))
+    enc = P.encode(data, boff, P.params(ans=True))
+    assert not enc.status.cpu().numpy().any()
+    ref_out, ref_st = P.decode(enc.comp, enc.off, boff)
+    assert not ref_st.cpu().numpy().any()
+    for _ in range(2):
+        out = torch.full((w.data.size,), 0xA5, dtype=torch.uint8, device="cuda")
+        st = torch.full((w.nblk,), -7, dtype=torch.int32, device="cuda")
+        P.decode_blocks_static(enc.comp, enc.off, w.nblk, out, boff, st)
+        torch.cuda.synchronize()
+        s = st.cpu().numpy()
+        assert set(np.unique(s)) <= {0, 2}, np.unique(s)       # OK or CAPACITY
+        assert (s == 2).any() and (s == 0).any()
+        o = out.cpu().numpy()
+        for b in np.nonzero(s == 0)[0]:
+            lo, hi = int(w.blk_off[b]), int(w.blk_off[b + 1])
+            assert np.array_equal(o[lo:hi], w.data[lo:hi])
