@@ -342,7 +342,9 @@ pivco_status pivco_host_decompress(pivco_host_codec *codec, const uint8_t *comp,
                                    uint8_t *out, int32_t *status);
 
 /* Launch tuning of the decode (process-wide).  None of it changes any output.
- * tile_max: longest root tile in symbols (a multiple of 128, 128..65536);
+ * tile_max: longest root tile in symbols (a multiple of 128, 128..2^20;
+ *   the plan also caps a tile so that each of its levels fits the CTA's
+ *   level buffer; default 2^20);
  * dir_bits: rank-directory granularity in bits (a multiple of 32, 32..256);
  * ctas_per_sm: persistent CTAs per SM (0 = as many as fit, at most 32). */
 typedef struct pivco_tuning {

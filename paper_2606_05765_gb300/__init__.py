@@ -268,7 +268,7 @@ def get_tuning():
     return t
 
 
-def set_tuning(tile_max=65536, dir_bits=128, ctas_per_sm=0):
+def set_tuning(tile_max=1 << 20, dir_bits=128, ctas_per_sm=0):
     t = Tuning(tile_max, dir_bits, ctas_per_sm, 0)
     _check(lib().pivco_set_tuning(C.byref(t)), "pivco_set_tuning")
 

@@ -63,7 +63,7 @@ static void build_tables() {
 static std::atomic<uint64_t> g_launches{0};
 
 // launch tuning of the decode (process-wide; set by pivco_set_tuning / the autotuner)
-static DecTuning g_tuning = {65536, 128, 0};
+static DecTuning g_tuning = {1u << 20, 128, 0};
 static std::mutex g_tuning_mu;
 DecTuning current_tuning() {
     std::lock_guard<std::mutex> lk(g_tuning_mu);
@@ -340,7 +340,7 @@ pivco_status pivco_get_tuning(pivco_tuning *t) {
 }
 
 pivco_status pivco_set_tuning(const pivco_tuning *t) {
-    if (!t || t->tile_max < 128 || t->tile_max > 65536 || (t->tile_max & 127) || t->dir_bits < 32 ||
+    if (!t || t->tile_max < 128 || t->tile_max > (1 << 20) || (t->tile_max & 127) || t->dir_bits < 32 ||
         t->dir_bits > 256 || (t->dir_bits & 31) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
         return PIVCO_ERR_INVALID_ARG;
     set_tuning(DecTuning{(uint32_t)t->tile_max, (uint32_t)t->dir_bits, (uint32_t)t->ctas_per_sm});
@@ -395,7 +395,7 @@ pivco_status pivco_autotune_decode(const uint8_t *comp, const uint64_t *comp_off
                                    const uint64_t *out_off, void *ws, size_t ws_bytes, int32_t *status, int32_t reps,
                                    void *stream, pivco_tuning *best, float *best_ms) {
     if (nblk <= 0 || !comp || !comp_off || !out_off || !ws || !status || !best || reps < 1) return PIVCO_ERR_INVALID_ARG;
-    static const uint32_t tiles[] = {16384, 32768, 65536};
+    static const uint32_t tiles[] = {16384, 65536, 1u << 20};
     static const uint32_t dirs[] = {64, 128, 256};
     static const uint32_t ctas[] = {0, 2};
     const DecTuning saved = current_tuning();

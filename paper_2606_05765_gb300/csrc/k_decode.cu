@@ -33,8 +33,9 @@ namespace pv {
 
 constexpr int kDecThreads = 256;
 constexpr int kDecWarps = kDecThreads / 32;
-constexpr int kWBuf = 4864;                  // one level buffer of a warp tile (bytes)
+constexpr int kLvlBuf = 24576;               // one level buffer of a tile (bytes)
 constexpr int kWSlack = 64;                  // over-read room of the byte windows
+constexpr int kTileCtas = 4;                 // tile CTAs per SM the kernels are built for
 constexpr uint32_t kNtabHdr = 32;            // node table header (see plan_block)
 
 // bytes of a block's node table: header, u32 source and u32 children per node
@@ -358,13 +359,13 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         __syncwarp();
         ok = __all_sync(0xffffffffu, okn);
         if (ok) {
-            // root symbols per tile: every level of a tile must fit one warp's
+            // root symbols per tile: every level of a tile must fit one level
             // buffer (with 4-byte rounding per node), with 20 % headroom
             uint64_t tfit = ~0ull;
             for (int d = 1; d < 16; d++) {
                 if (!Q.lvl[d]) continue;
                 const uint32_t nodes = (uint32_t)(Q.first[d + 1] - Q.first[d]);
-                const uint64_t room = (uint64_t)kWBuf > 4ull * nodes + 32 ? kWBuf - 4ull * nodes - 32 : 0;
+                const uint64_t room = (uint64_t)kLvlBuf > 4ull * nodes + 32 ? kLvlBuf - 4ull * nodes - 32 : 0;
                 const uint64_t t = room * R.n / Q.lvl[d] / 5 * 4;
                 tfit = t < tfit ? t : tfit;
             }
@@ -590,21 +591,44 @@ cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_
 }
 
 // ---------------------------------------------------------------------------
-// Warp tiles (the bottom-up merge, Sec. 3)
+// CTA tiles (the bottom-up merge, Sec. 3)
+//
+// A tile is decoded by one CTA.  Its levels live in two shared-memory level
+// buffers; bottom-up, each level is split into windows of 32 groups (a group
+// is 32 consecutive symbols of one node, one lane each), and the CTA's warps
+// take the windows of a level in rounds, one window per warp per round.  A
+// group needs the ones of its node before it: within a window they come from
+// a segmented warp scan, across the windows of a round from the windows'
+// summaries (one barrier per round), across rounds from a carry every
+// thread keeps.  Large tiles (a whole 64 KiB block when its levels fit) need
+// no rank directory and amortise the tile's set-up over many symbols.
 // ---------------------------------------------------------------------------
-struct WarpTile {
-    uint8_t buf[2][kWBuf + kWSlack];   // level buffers: depth d writes buf[d & 1]
-    uint32_t pos[256];                 // bit address of node v's next bit (bit 31: in the ANS scratch)
-    uint32_t dem[256];                 // bits of node v in the current chunk
-    uint32_t ch[256];                  // children (node table format)
-    uint16_t sp[256];                  // byte offset of node v's sequence in its level buffer
-    uint16_t gs[256];                  // first 32-symbol group of node v within its level
-    uint16_t lg[16];                   // groups of each level
+constexpr int kTileWarps = kDecWarps;
+constexpr int kWnodeMax = 512;                 // window-node entries of all levels below the root
+
+struct WinSum {                                // one window of a round
+    uint32_t sum;                              // ones of its last node from that node's start in the window
+    uint32_t flags;                            // 1 its first node starts at its first group,
+};                                             //   2 a node starts in it, 4 active
+
+struct __align__(16) CtaTile {
+    uint8_t buf[2][kLvlBuf + kWSlack];         // level buffers: depth d writes buf[d & 1]
+    uint32_t pos[256];                         // bit address of node v's next bit (bit 31: in the ANS scratch)
+    uint32_t dem[256];                         // bits of node v in the current chunk
+    uint32_t ch[256];                          // children (node table format)
+    uint16_t sp[256];                          // byte offset of node v's sequence in its level buffer
+    uint16_t gs[256];                          // first 32-symbol group of node v within its level
+    uint16_t lg[16];                           // groups of each level
+    uint16_t wn_off[16];                       // first window-node entry of each level
+    WinSum win[2][kTileWarps];                 // window summaries, two rounds deep
+    uint8_t wnode[kWnodeMax];                  // node holding the first group of each window
     uint8_t first[17];
     uint8_t maxd;
-    uint8_t pad[14];
+    uint8_t pad[2];
+    int32_t blk, flag;
+    uint32_t pad2[2];
 };
-static_assert(sizeof(WarpTile) % 16 == 0, "warp tiles must stay 16-byte aligned");
+static_assert(sizeof(CtaTile) % 16 == 0, "tiles must stay 16-byte aligned");
 
 // Byte-permute selectors of a bitmap byte (low 16 bits: its low nibble,
 // high 16 bits: its high nibble): a one takes the next byte of the right
@@ -706,12 +730,12 @@ __device__ inline void win8(const uint8_t *buf, uint32_t a, uint32_t &x0, uint32
 
 // 32 output symbols of a node from bitmap word w: r0 / r1 zeros / ones of the
 // node before this word, i.e. the start of its left / right window.
-__device__ inline void merge32(const WarpTile &S, const uint8_t *bin, uint32_t chv, uint32_t r0, uint32_t r1,
+__device__ inline void merge32(const CtaTile &S, const uint8_t *bin, uint32_t chv, uint32_t r0, uint32_t r1,
                                uint32_t w, const uint32_t *sel, uint32_t (&o)[8]) {
     const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
     const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-    uint32_t la = i0 ? min((uint32_t)S.sp[c0 & 0xFFu] + r0, (uint32_t)kWBuf) : 0u;
-    uint32_t ra = i1 ? min((uint32_t)S.sp[c1 & 0xFFu] + r1, (uint32_t)kWBuf) : 0u;
+    uint32_t la = i0 ? min((uint32_t)S.sp[c0 & 0xFFu] + r0, (uint32_t)kLvlBuf) : 0u;
+    uint32_t ra = i1 ? min((uint32_t)S.sp[c1 & 0xFFu] + r1, (uint32_t)kLvlBuf) : 0u;
     const uint32_t kl = (c0 & 0xFFu) * 0x01010101u, kr = (c1 & 0xFFu) * 0x01010101u;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -731,7 +755,7 @@ __device__ inline void merge32(const WarpTile &S, const uint8_t *bin, uint32_t c
 }
 
 // the children's demands must be the node's zeros and ones
-__device__ inline bool children_ok(const WarpTile &S, uint32_t chv, uint32_t dv, uint32_t ones) {
+__device__ inline bool children_ok(const CtaTile &S, uint32_t chv, uint32_t dv, uint32_t ones) {
     const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
     bool ok = true;
     if (!(c0 & 0x8000u)) ok = ok && S.dem[c0] == dv - ones;
@@ -765,11 +789,12 @@ __device__ inline void st_out32(uint8_t *p, const uint32_t (&o)[8], uint32_t val
     }
 }
 
-// Spans and groups of every level for the current demands.  False when a
-// level (depth >= 1) does not fit a buffer.
-__device__ inline bool wt_layout(WarpTile &S) {
+// Spans, groups and window nodes of every level for the current demands
+// (one warp).  False when a level (depth >= 1) does not fit a buffer.
+__device__ inline bool ct_layout(CtaTile &S) {
     const int lane = threadIdx.x & 31;
     bool fits = true;
+    uint32_t wn = 0;   // window-node entries so far
     for (int d = 0; d < (int)S.maxd; d++) {
         const int f0 = S.first[d], f1 = S.first[d + 1];
         uint64_t carry = 0;
@@ -778,8 +803,8 @@ __device__ inline bool wt_layout(WarpTile &S) {
             uint64_t x = 0;
             if (v < f1) {
                 const uint32_t dv = S.dem[v];
-                if (d && dv > (uint32_t)kWBuf) fits = false;
-                const uint32_t by = d ? ((min(dv, (uint32_t)kWBuf) + 3u) & ~3u) : 0u;
+                if (d && dv > (uint32_t)kLvlBuf) fits = false;
+                const uint32_t by = d ? ((min(dv, (uint32_t)kLvlBuf) + 3u) & ~3u) : 0u;
                 x = ((uint64_t)by << 32) | max(1u, (dv + 31u) >> 5);
             }
             uint64_t inc = x;
@@ -790,22 +815,40 @@ __device__ inline bool wt_layout(WarpTile &S) {
             }
             const uint64_t ex = carry + inc - x;
             if (v < f1) {
-                S.sp[v] = (uint16_t)min((uint64_t)kWBuf, ex >> 32);
+                S.sp[v] = (uint16_t)min((uint64_t)kLvlBuf, ex >> 32);
                 S.gs[v] = (uint16_t)ex;
             }
             carry += __shfl_sync(0xffffffffu, inc, 31);
         }
-        if (d && (carry >> 32) > (uint64_t)kWBuf) fits = false;
+        if (d && (carry >> 32) > (uint64_t)kLvlBuf) fits = false;
         if ((uint32_t)carry > 0xFFFFu) fits = false;
-        if (lane == 0) S.lg[d] = (uint16_t)carry;
+        const uint32_t G = (uint32_t)carry & 0xFFFFu;
+        if (lane == 0) { S.lg[d] = (uint16_t)G; S.wn_off[d] = (uint16_t)wn; }
+        __syncwarp();
+        if (d) {
+            // the node holding the first group of each window of the level:
+            // the last node whose first group is at or before it
+            const uint32_t nwin = (G + 31) >> 5;
+            if (wn + nwin > (uint32_t)kWnodeMax) fits = false;
+            for (uint32_t i = lane; i < nwin && wn + i < (uint32_t)kWnodeMax; i += 32) {
+                int lo = f0, hi = f1;
+                while (hi - lo > 1) {
+                    const int m = (lo + hi) >> 1;
+                    if ((uint32_t)S.gs[m] <= 32u * i) lo = m; else hi = m;
+                }
+                S.wnode[wn + i] = (uint8_t)lo;
+            }
+            wn += nwin;
+        }
     }
     __syncwarp();
     return __all_sync(0xffffffffu, fits);
 }
 
 // Demands of a chunk of C root symbols from the current cursors, top-down:
-// a node's popcount over its range splits its demand between its children.
-__device__ inline void wt_demand(WarpTile &S, const TileSrc &src, uint32_t V, uint32_t C) {
+// a node's popcount over its range splits its demand between its children
+// (one warp).
+__device__ inline void ct_demand(CtaTile &S, const TileSrc &src, uint32_t V, uint32_t C) {
     const int lane = threadIdx.x & 31;
     for (uint32_t v = lane; v < V; v += 32) S.dem[v] = 0;
     __syncwarp();
@@ -837,7 +880,7 @@ struct WtLoc {
     uint32_t v, kk, dv, starts;
     bool act;
 };
-__device__ inline WtLoc wt_locate(const WarpTile &S, uint32_t f1, uint32_t G, uint32_t base, uint32_t vcur) {
+__device__ inline WtLoc wt_locate(const CtaTile &S, uint32_t f1, uint32_t G, uint32_t base, uint32_t vcur) {
     const int lane = threadIdx.x & 31;
     const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
     const uint32_t cand = vcur + 1 + lane;
@@ -856,41 +899,45 @@ __device__ inline WtLoc wt_locate(const WarpTile &S, uint32_t f1, uint32_t G, ui
     return L;
 }
 
-// The first window of level d (d >= 1), or of the root (d = 0), and its words
-__device__ inline void wt_first(const WarpTile &S, const TileSrc &src, int d, WtLoc &nx, BitLd &nld) {
+// The window at group `base` of level d (a warp's window of a round): its
+// groups' nodes and the two bitmap words under each group, loaded ahead.
+__device__ inline void ct_fetch(const CtaTile &S, const TileSrc &src, int d, uint32_t base, WtLoc &L, BitLd &ld) {
     const int lane = threadIdx.x & 31;
-    nld = BitLd{0u, 0u, 0u};
+    ld = BitLd{0u, 0u, 0u};
+    L = WtLoc{0u, 0u, 0u, 0u, false};
     if (d >= 1) {
-        nx = wt_locate(S, S.first[d + 1], S.lg[d], 0, S.first[d]);
-        if (nx.act) nld = tile_ld(src, S.pos[nx.v], nx.kk);
-    } else if (32u * lane < S.dem[0]) {
-        nld = tile_ld(src, S.pos[0], 32u * lane);
+        const uint32_t G = S.lg[d];
+        if (base < G) {
+            const uint32_t u = S.wnode[S.wn_off[d] + (base >> 5)];
+            L = wt_locate(S, S.first[d + 1], G, base, (uint32_t)S.gs[u] == base ? u - 1 : u);
+            if (L.act) ld = tile_ld(src, S.pos[L.v], L.kk);
+        }
+    } else if (d == 0) {
+        L.dv = S.dem[0];
+        L.kk = 32u * (base + lane);
+        L.act = L.kk < L.dv;
+        if (L.act) ld = tile_ld(src, S.pos[0], L.kk);
     }
 }
 
-// One level (depth d >= 1) of the current chunk into its buffer.  Windows of
-// 32 groups; the next window's bitmap words (the next level's first window
-// after the last one) are loaded while the current one is merged: nx / nld
-// hold this level's first window on entry and the next level's on return.
-__device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const uint32_t *sel, WtLoc &nx,
-                                BitLd &nld) {
-    const int lane = threadIdx.x & 31;
+// One level (depth d >= 1) of the current chunk into its buffer.  nx / nld
+// hold the warp's window of this level's first round on entry and of the
+// next level's first round on return; par alternates the summary slots.
+__device__ inline bool ct_level(CtaTile &S, const TileSrc &src, int d, const uint32_t *sel, WtLoc &nx, BitLd &nld,
+                                uint32_t &par) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t *bin = S.buf[(d + 1) & 1];
     uint8_t *bout = S.buf[d & 1];
-    const uint32_t f1 = S.first[d + 1], G = S.lg[d];
+    const uint32_t G = S.lg[d];
     const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
-    uint32_t carry = 0;
+    uint32_t rc_sum = 0;   // carry into the round: the ones so far of the node running into it
     bool bad = false;
-    for (uint32_t base = 0;; base += 32) {
+    for (uint32_t r0 = 0; r0 < G; r0 += 32 * kTileWarps) {
+        const uint32_t base = r0 + 32 * warp;
         const WtLoc L = nx;
         const BitLd ld = nld;
-        if (base + 32 < G) {
-            nx = wt_locate(S, f1, G, base + 32, __shfl_sync(0xffffffffu, L.v, 31));
-            nld = BitLd{0u, 0u, 0u};
-            if (nx.act) nld = tile_ld(src, S.pos[nx.v], nx.kk);
-        } else {
-            wt_first(S, src, d - 1, nx, nld);
-        }
+        if (r0 + 32 * kTileWarps < G) ct_fetch(S, src, d, base + 32 * kTileWarps, nx, nld);
+        else ct_fetch(S, src, d - 1, 32 * warp, nx, nld);
         const uint32_t starts = L.starts, v = L.v, kk = L.kk, dv = L.dv;
         const bool act = L.act;
         uint32_t w = 0;
@@ -899,7 +946,7 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
             if (dv - kk < 32) w &= (1u << (dv - kk)) - 1u;
         }
         const uint32_t pc = __popc(w);
-        // ones of the node before this word: segmented scan over the window
+        // ones of the node before this word within the window: segmented scan
         uint32_t inc = pc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -909,8 +956,33 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
         const uint32_t sl = starts & le;
         const int s0 = sl ? 31 - __clz(sl) : -1;
         const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
-        const uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u) + (s0 < 0 ? carry : 0u);
-        carry = __shfl_sync(0xffffffffu, r1 + pc, 31);
+        uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u);
+        if (lane == 31) S.win[par][warp] = WinSum{r1 + pc, (starts & 1u) | (starts ? 2u : 0u) | (base < G ? 4u : 0u)};
+        __syncthreads();
+        // the carry into each window of the round: lane p takes window p's
+        // summary; the carry out of a window is a segmented inclusive sum of
+        // the windows' sums (a segment starts at a window where a node
+        // starts), the first segment continuing the previous round's carry
+        uint32_t cin;
+        {
+            const WinSum x = lane < kTileWarps ? S.win[par][lane] : WinSum{0u, 0u};
+            uint32_t val = x.sum, seg = (x.flags >> 1) & 1u;
+#pragma unroll
+            for (int o = 1; o < kTileWarps; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, val, o), f = __shfl_up_sync(0xffffffffu, seg, o);
+                if (lane >= o && !seg) { val += y; seg |= f; }
+            }
+            if (!seg) val += rc_sum;
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, val, 1);
+            // the head node runs in from the window before unless it starts here
+            const uint32_t c = (x.flags & 1u) ? 0u : (lane ? prev : rc_sum);
+            cin = __shfl_sync(0xffffffffu, c, warp);
+            const uint32_t act = __ballot_sync(0xffffffffu, (x.flags & 4u) != 0);   // window 0 always is
+            const int last = 31 - __clz(act);
+            rc_sum = __shfl_sync(0xffffffffu, val, last);
+        }
+        par ^= 1u;
+        if (s0 < 0) r1 += cin;   // groups of the node that runs in from the previous window
         if (act) {
             const uint32_t chv = S.ch[v];
             if (kk + 32 >= dv && !children_ok(S, chv, dv, r1 + pc)) bad = true;
@@ -923,24 +995,25 @@ __device__ inline bool wt_level(WarpTile &S, const TileSrc &src, int d, const ui
             for (int j = 0; j < 8; j++)
                 if (4u * j < dv - kk) p4[j] = o[j];
         }
-        if (base + 32 >= G) break;
     }
-    return !__any_sync(0xffffffffu, bad);
+    return !__syncthreads_or(bad);   // (also: the level's output is complete)
 }
 
 // The root level of the current chunk into the output.
-__device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, const uint32_t *sel, BitLd nld) {
-    const int lane = threadIdx.x & 31;
+__device__ inline bool ct_root(CtaTile &S, const TileSrc &src, uint8_t *out, const uint32_t *sel, WtLoc nx,
+                               BitLd nld, uint32_t &par) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t *bin = S.buf[1];
-    const uint32_t dv = S.dem[0], chv = S.ch[0], p0 = S.pos[0];
-    uint32_t carry = 0;
-    // nld: the first window's words; the next window's are loaded while the
-    // current one is merged
-    for (uint32_t kb = 0; kb < dv; kb += 1024) {
-        const uint32_t kk = kb + 32u * lane;
-        const bool act = kk < dv;
+    const uint32_t dv = S.dem[0], chv = S.ch[0];
+    const uint32_t G = (dv + 31) >> 5;
+    uint32_t rc = 0;   // ones of the root before the round
+    for (uint32_t r0 = 0; r0 < G; r0 += 32 * kTileWarps) {
+        const uint32_t base = r0 + 32 * warp;
+        const WtLoc L = nx;
         const BitLd ld = nld;
-        if (kk + 1024 < dv) nld = tile_ld(src, p0, kk + 1024);
+        if (r0 + 32 * kTileWarps < G) ct_fetch(S, src, 0, base + 32 * kTileWarps, nx, nld);
+        const uint32_t kk = L.kk;
+        const bool act = L.act;
         uint32_t w = 0;
         if (act) {
             w = tile_word(ld);
@@ -953,42 +1026,68 @@ __device__ inline bool wt_root(WarpTile &S, const TileSrc &src, uint8_t *out, co
             const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
-        const uint32_t r1 = carry + inc - pc;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
+        if (lane == 31) S.win[par][warp].sum = inc;
+        __syncthreads();
+        // the windows' sums (lane p: window p; an empty window's is 0): the
+        // ones before this warp's window and the round's total
+        uint32_t cin;
+        {
+            const uint32_t ws = lane < kTileWarps ? S.win[par][lane].sum : 0u;
+            uint32_t wi = ws;
+#pragma unroll
+            for (int o = 1; o < kTileWarps; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            cin = rc + __shfl_sync(0xffffffffu, wi - ws, warp);
+            rc += __shfl_sync(0xffffffffu, wi, kTileWarps - 1);
+        }
+        par ^= 1u;
         if (act) {
+            const uint32_t r1 = cin + inc - pc;
             uint32_t o[8];
             merge32(S, bin, chv, kk - r1, r1, w, sel, o);
             st_out32(out + kk, o, min(32u, dv - kk));
         }
     }
-    return children_ok(S, chv, dv, carry);
+    return children_ok(S, chv, dv, rc);
 }
 
-// fills n bytes at p with x (whole warp)
-__device__ inline void warp_fill(uint8_t *p, uint32_t n, uint8_t x) {
-    const int lane = threadIdx.x & 31;
+// fills n bytes at p with x (whole CTA)
+__device__ inline void cta_fill(uint8_t *p, uint32_t n, uint8_t x) {
+    const int t = threadIdx.x;
     const uint32_t head = min(n, (uint32_t)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15));
-    if (lane < (int)head) p[lane] = x;
+    if (t < (int)head) p[t] = x;
     const uint32_t body = (n - head) / 16;
     const uint32_t x4 = x * 0x01010101u;
     uint4 *q = reinterpret_cast<uint4 *>(p + head);
-    for (uint32_t i = lane; i < body; i += 32) q[i] = make_uint4(x4, x4, x4, x4);
-    for (uint32_t i = head + 16 * body + lane; i < n; i += 32) p[i] = x;
+    for (uint32_t i = t; i < body; i += blockDim.x) q[i] = make_uint4(x4, x4, x4, x4);
+    for (uint32_t i = head + 16 * body + t; i < n; i += blockDim.x) p[i] = x;
 }
 
-// Decodes tile gt of the queue with one warp.
-__device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
-                                 int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
-                                 const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
-                                 WarpTile &S, const uint32_t *sel, int b = -1) {
-    const int lane = threadIdx.x & 31;
+// Decodes tile gt of the queue with the whole CTA (every thread calls it
+// with the same arguments).  b: the tile's block when the caller knows it.
+__device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
+                                int nblk, uint8_t *__restrict__ out, const uint64_t *__restrict__ out_off,
+                                const uint8_t *__restrict__ ws, uint64_t ws_bytes, int32_t *__restrict__ status,
+                                CtaTile &S, const uint32_t *sel, int b = -1) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
     const DecRegions G = dec_regions(nblk, ws);
-    if (b < 0) {   // (the batched path has found the tile's block already)
-        const uint32_t ttot = reinterpret_cast<const uint32_t *>(ws)[6];
-        b = find_block_warp(W.blk_tile, nblk, gt, (int)((uint64_t)gt * (uint32_t)nblk / max(ttot, 1u)));
+    // one block and one status for the whole CTA (every decision below that
+    // chooses a path with barriers is the same in every thread)
+    if (warp == 0) {
+        if (b < 0) {
+            const uint32_t ttot = reinterpret_cast<const uint32_t *>(ws)[6];
+            b = find_block_warp(W.blk_tile, nblk, gt, (int)((uint64_t)gt * (uint32_t)nblk / max(ttot, 1u)));
+        }
+        if (lane == 0) { S.blk = b; S.flag = *reinterpret_cast<volatile int32_t *>(&status[b]); }
     }
-    if (*reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
+    __syncthreads();
+    b = S.blk;
+    const int32_t st0 = S.flag;
+    __syncthreads();
+    if (st0 != PIVCO_OK) return;
     const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
     const uint8_t *rec = comp + comp_off[b];
     uint8_t *dst = out + out_off[b];
@@ -996,13 +1095,13 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
     const uint32_t rb = ld_le32(rec), n = ld_le32(rec + 4);
     const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8), kind = rec[10], aux = rec[11];
     if (n != ocap) {                     // the plan validated magic / size / layout
-        if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
+        if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
         return;
     }
     if (kind == 0) return;
     const uint32_t P0 = k * T, P1 = min(n, P0 + T);
     if (kind == 1) {
-        warp_fill(dst + P0, P1 - P0, (uint8_t)aux);
+        cta_fill(dst + P0, P1 - P0, (uint8_t)aux);
         return;
     }
     const uint64_t nbase = G.dir + W.blk_dir[b], ntb = ntab_bytes(V);
@@ -1011,13 +1110,13 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
     const uint32_t *cursors = reinterpret_cast<const uint32_t *>(nt + ntb) + ent;
     if (nbase + ntb > ws_bytes ||
         (ntile > 1 && nbase + ntb + 4ull * ent + 4ull * (ntile + 1) * V > ws_bytes)) {
-        if (lane == 0) status[b] = PIVCO_ERR_CAPACITY;
+        if (t == 0) status[b] = PIVCO_ERR_CAPACITY;
         return;
     }
     const uint32_t *nsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr);
     const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
-    if (lane < 17) S.first[lane] = nt[lane];
-    if (lane == 17) S.maxd = nt[17];
+    if (t < 17) S.first[t] = nt[t];
+    if (t == 17) S.maxd = nt[17];
     const uint64_t sbase = G.scratch + W.blk_scratch[b];
     TileSrc src;
     src.rec = rec;
@@ -1025,52 +1124,44 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
     src.scr = ws + sbase;
     src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
     int bad = V > 255;   // the plan has checked it
-    {
-        // all of the node loads first (V <= 255: 8 per lane), then the checks and stores
-        uint32_t nvv[8], cs[8], ce[8], s0[8], chv[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const uint32_t v = lane + 32u * i;
-            nvv[i] = cs[i] = ce[i] = s0[i] = chv[i] = 0u;
-            if (v < V) {
-                nvv[i] = __ldg(nv + v);
-                if (ntile > 1) {
-                    cs[i] = cursors[(size_t)k * V + v];
-                    ce[i] = cursors[(size_t)(k + 1) * V + v];
-                }
-                s0[i] = nsrc[v];
-                chv[i] = nsrc[V + v];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const uint32_t v = lane + 32u * i;
-            if (v < V) {
-                const uint32_t e = ntile > 1 ? ce[i] : nvv[i];
-                if (e < cs[i] || e > nvv[i] || (uint64_t)(s0[i] & 0x7FFFFFFFu) + nvv[i] >= 0x80000000ull) bad = 1;
-                S.pos[v] = s0[i] + cs[i];
-                S.dem[v] = e - cs[i];
-                S.ch[v] = chv[i];
-            }
-        }
+    if ((uint32_t)t < V) {
+        const uint32_t v = t;
+        const uint32_t nvv = __ldg(nv + v);
+        const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
+        const uint32_t e = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : nvv;
+        const uint32_t s0 = nsrc[v];
+        if (e < cs || e > nvv || (uint64_t)(s0 & 0x7FFFFFFFu) + nvv >= 0x80000000ull) bad = 1;
+        S.pos[v] = s0 + cs;
+        S.dem[v] = e - cs;
+        S.ch[v] = nsrc[V + v];
     }
-    __syncwarp();
-    if (lane == 0 && S.dem[0] != P1 - P0) bad = 1;
-    for (uint32_t v = lane; v < V; v += 32) {   // a child never has more symbols than its parent
-        const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
+    __syncthreads();
+    if (t == 0 && S.dem[0] != P1 - P0) bad = 1;
+    if ((uint32_t)t < V) {   // a child never has more symbols than its parent
+        const uint32_t chv = S.ch[t], c0 = chv & 0xFFFFu, c1 = chv >> 16;
         const uint32_t dc = ((c0 & 0x8000u) ? 0u : S.dem[c0]) + ((c1 & 0x8000u) ? 0u : S.dem[c1]);
-        if (dc > S.dem[v]) bad = 1;
+        if (dc > S.dem[t]) bad = 1;
     }
-    if (__any_sync(0xffffffffu, bad)) {
-        if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+    if (__syncthreads_or(bad)) {
+        if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
         return;
     }
     // the whole tile at once when its levels fit, else chunks found top-down
-    uint32_t P = P0, C = P1 - P0;
+    uint32_t P = P0, C = P1 - P0, par = 0;
     bool chunked = false;
     while (P < P1) {
-        if (chunked) wt_demand(S, src, V, C);
-        if (!wt_layout(S)) {
+        if (chunked) {
+            if (warp == 0) ct_demand(S, src, V, C);
+            __syncthreads();
+        }
+        if (warp == 0) {
+            const bool f = ct_layout(S);
+            if (lane == 0) S.flag = f;
+        }
+        __syncthreads();
+        const bool fits = S.flag != 0;
+        __syncthreads();
+        if (!fits) {
             chunked = true;
             C = max(32u, (C / 2) & ~31u);
             continue;
@@ -1078,36 +1169,28 @@ __device__ inline void warp_tile(uint32_t gt, const uint8_t *__restrict__ comp, 
         bool ok = true;
         WtLoc nx;
         BitLd nld;
-        wt_first(S, src, (int)S.maxd - 1, nx, nld);
-        for (int d = (int)S.maxd - 1; d >= 1; d--) {
-            ok = wt_level(S, src, d, sel, nx, nld) && ok;
-            __syncwarp();
-        }
-        ok = wt_root(S, src, dst + P, sel, nld) && ok;
-        if (!ok) {
-            if (lane == 0) status[b] = PIVCO_ERR_CORRUPT;
+        ct_fetch(S, src, (int)S.maxd - 1, 32 * warp, nx, nld);
+        for (int d = (int)S.maxd - 1; d >= 1; d--) ok = ct_level(S, src, d, sel, nx, nld, par) && ok;
+        ok = ct_root(S, src, dst + P, sel, nx, nld, par) && ok;
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
             return;
         }
-        for (uint32_t v = lane; v < V; v += 32) S.pos[v] += S.dem[v];
-        __syncwarp();
+        if ((uint32_t)t < V) S.pos[t] += S.dem[t];
+        __syncthreads();
         P += C;
         C = min(C, P1 - P);
     }
-    if (chunked) {   // the chunks must end exactly at the tile's end cursors
-        for (uint32_t v = lane; v < V; v += 32) {
-            const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : __ldg(nv + v);
-            if (S.pos[v] != nsrc[v] + ce) bad = 1;
-        }
+    if (chunked && (uint32_t)t < V) {   // the chunks must end exactly at the tile's end cursors
+        const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + t] : __ldg(nv + t);
+        if (S.pos[t] != nsrc[t] + ce) bad = 1;
     }
     // the last tile checks the pad bits of every bitmap
-    if (k + 1 == ntile) {
-        for (uint32_t v = lane; v < V; v += 32) {
-            const uint32_t nvv = __ldg(nv + v);
-            if ((nvv & 7) && (tile_bits(src, nsrc[v], nvv & ~7u) & 0xFFu) >> (nvv & 7)) bad = 1;
-        }
+    if (k + 1 == ntile && (uint32_t)t < V) {
+        const uint32_t nvv = __ldg(nv + t);
+        if ((nvv & 7) && (tile_bits(src, nsrc[t], nvv & ~7u) & 0xFFu) >> (nvv & 7)) bad = 1;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) status[b] = PIVCO_ERR_CORRUPT;
-    __syncwarp();
+    if (__syncthreads_or(bad) && t == 0) status[b] = PIVCO_ERR_CORRUPT;
 }
 
 // ---------------------------------------------------------------------------
@@ -1418,10 +1501,10 @@ struct DirWarpSmem {
 
 struct TileSmem {
     uint32_t sel[256];
-    WarpTile w[kDecWarps];
+    CtaTile tile;
 };
 
-// Plain tile pass: every warp takes tiles by ticket (workspace header word 12).
+// Plain tile pass: every CTA takes tiles by ticket (workspace header word 12).
 // Plain directory pass: CTAs take the blocks with many superblocks, then
 // every warp takes the blocks with few.
 __global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_t *__restrict__ comp,
@@ -1445,43 +1528,43 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_dir_kernel(const uint8_
     }
 }
 
-__global__ void __launch_bounds__(kDecThreads, 2) decode_kernel(const uint8_t *__restrict__ comp,
-                                                                const uint64_t *__restrict__ comp_off,
-                                                                int nblk, uint8_t *__restrict__ out,
-                                                                const uint64_t *__restrict__ out_off,
-                                                                uint8_t *__restrict__ ws, uint64_t ws_bytes,
-                                                                int32_t *__restrict__ status) {
+__global__ void __launch_bounds__(kDecThreads, kTileCtas) decode_kernel(const uint8_t *__restrict__ comp,
+                                                                        const uint64_t *__restrict__ comp_off,
+                                                                        int nblk, uint8_t *__restrict__ out,
+                                                                        const uint64_t *__restrict__ out_off,
+                                                                        uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                                        int32_t *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
+    __shared__ uint32_t s_it;
     if (abandoned_batch(ws, status, nblk)) return;
     sel_init(S.sel);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
     const uint32_t total_tiles = hdr[6];
     for (;;) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&hdr[12], 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
+        if (threadIdx.x == 0) s_it = atomicAdd(&hdr[12], 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        __syncthreads();
         if (it >= total_tiles) break;
-        warp_tile(it, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S.w[warp], S.sel);
+        cta_tile(it, comp, comp_off, nblk, out, out_off, ws, ws_bytes, status, S.tile, S.sel);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Batched decode: one persistent launch over a work queue keyed by
-// (block, stage).  CTA items, in queue order:
-//   plans      8 blocks per item, one warp each (ticket order = block order,
+// (block, stage).  Every item is taken by a whole CTA, in queue order:
+//   plans      4 blocks per item, one warp each (ticket order = block order,
 //              as the plan's look-back needs)
-//   ANS        8 segments per item, one warp each
-//   directory  8 blocks per item; the blocks with many superblocks are
-//              taken one after another by the whole CTA (the others skip)
-// then warp items: the directories of the other multi-tile blocks, then the
-// tiles, one per warp.  A CTA turns to tiles once the CTA
-// items are all taken.  An item only waits (bounded) on items earlier in the
-// queue: the ANS and later items on all plans; a directory on its block's ANS
-// segments; a tile on its block's ANS segments and directory.  The CTAs that
-// took those items are running, so every wait ends.
+//   ANS        4 segments per item, one warp each
+//   directory  8 blocks per item: each warp builds its block's directory if
+//              it has few superblocks, then the whole CTA builds those of the
+//              blocks with many, one after another
+//   tiles      one tile per item (cta_tile)
+// An item only waits (bounded) on items earlier in the queue: the ANS and
+// later items on all plans; a directory on its block's ANS segments; a tile
+// on its block's ANS segments and directory.  The CTAs that took those items
+// are running, so every wait ends.
 // ---------------------------------------------------------------------------
 __device__ inline bool wait_geq(const uint32_t *p, uint32_t want, uint64_t limit_ns) {
     if (*reinterpret_cast<const volatile uint32_t *>(p) >= want) { __threadfence(); return true; }
@@ -1496,21 +1579,28 @@ __device__ inline bool wait_geq(const uint32_t *p, uint32_t want, uint64_t limit
     return true;
 }
 
+constexpr int kPlanWarps = 4;   // warps per plan or ANS item (their shared memory bounds the CTA's)
 struct PlanAnsSmem {
-    WarpRec R[kDecWarps];
-    PlanScratch Q[kDecWarps];
-    AnsSm T[kDecWarps];
+    WarpRec R[kPlanWarps];
+    PlanScratch Q[kPlanWarps];
+    AnsSm T[kPlanWarps];
 };
-static_assert(sizeof(PlanAnsSmem) <= sizeof(WarpTile) * kDecWarps, "plans fit the tiles' shared memory");
+struct DirAllSmem {
+    DirSmem dir;
+    DirWarpSmem dw[kDecWarps];
+};
 union BatchUnion {
     PlanAnsSmem pa;
-    DirSmem dir;
-    WarpTile tw[kDecWarps];
+    DirAllSmem d;
+    CtaTile tile;
 };
 struct BatchSmem {
     uint32_t sel[256];
     BatchUnion u;
+    int32_t blk, ok;
+    uint32_t pad[2];
 };
+static_assert(sizeof(PlanAnsSmem) <= sizeof(CtaTile), "plans fit the tiles' shared memory");
 
 // One request's (batch's) queue: where its records, output and workspace are.
 struct BatchQueue {
@@ -1527,29 +1617,32 @@ struct BatchQueue {
 // the wait bound of a batch's queue (workspace header)
 __device__ inline uint64_t wait_bound(const BatchQueue &q) { return reinterpret_cast<const uint64_t *>(q.ws)[7]; }
 
+__device__ inline uint32_t batch_nplan(int nblk) { return (uint32_t)((nblk + kPlanWarps - 1) / kPlanWarps); }
+__device__ inline uint32_t batch_ndir(int nblk) { return (uint32_t)((nblk + kDecWarps - 1) / kDecWarps); }
+
 // Items of a batch's queue once all plans are done (header written by the last plan).
 __device__ inline uint32_t batch_items_total(const BatchQueue &q) {
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
-    const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
-    return 2u * nplan + (hdr[2] + kDecWarps - 1) / kDecWarps + (uint32_t)q.nblk + hdr[6];
+    return batch_nplan(q.nblk) + (hdr[2] + kPlanWarps - 1) / kPlanWarps + batch_ndir(q.nblk) + hdr[6];
 }
 
 enum : int { kItemDone = 0, kItemNone = 1, kItemStop = 2 };
 
-// Runs CTA item `item` of the queue with the whole CTA.  kItemDone: processed;
-// kItemNone: no CTA items left (tiles follow); kItemStop: the wait for the
-// plans expired (every block is marked), the CTA must stop.
+// Runs item `item` of the queue with the whole CTA.  kItemDone: processed;
+// kItemNone: past the last item; kItemStop: the wait for the plans expired
+// or the plans could not place the batch (every block is marked), the CTA
+// must stop.
 __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &B, const AnsTables &A, int &last_b,
                                  bool &last_ok) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int nblk = q.nblk;
     uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
     const DecWs W = dec_ws(q.ws, nblk);
-    const uint32_t nplan = (uint32_t)((nblk + kDecWarps - 1) / kDecWarps);
+    const uint32_t nplan = batch_nplan(nblk);
     if (item < nplan) {
         // ---- plans ----
-        const int b = (int)(item * kDecWarps + warp);
-        if (b < nblk) {
+        const int b = (int)(item * kPlanWarps + warp);
+        if (warp < kPlanWarps && b < nblk) {
             plan_block(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.pa.R[warp], B.u.pa.Q[warp]);
             // a CTA that has given up on the queue (below) may have marked
             // the blocks before this plan wrote its status: re-mark it, so a
@@ -1584,12 +1677,12 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
         return kItemStop;
     }
     const uint32_t total_segs = hdr[2];
-    const uint32_t nseg_items = (total_segs + kDecWarps - 1) / kDecWarps;
+    const uint32_t nseg_items = (total_segs + kPlanWarps - 1) / kPlanWarps;
     uint32_t it = item - nplan;
     if (it < nseg_items) {
         // ---- ANS segments ----
-        const uint32_t g = it * kDecWarps + warp;
-        if (g < total_segs) {
+        const uint32_t g = it * kPlanWarps + warp;
+        if (warp < kPlanWarps && g < total_segs) {
             const int b = ans_item(g, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, A, B.u.pa.R[warp],
                                    B.u.pa.T[warp], last_b, last_ok);
             if (lane == 0) { __threadfence(); atomicAdd(&W.segs_done[b], 1u); }
@@ -1599,10 +1692,27 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
         return kItemDone;
     }
     it -= nseg_items;
-    if (it < nplan) {
-        // ---- directories of blocks 8 it .. 8 it + 7 that have many superblocks ----
+    const uint32_t ndir = batch_ndir(nblk);
+    if (it < ndir) {
+        // ---- directories of blocks 8 it .. 8 it + 7 ----
         const int bw = (int)(it * kDecWarps + warp);
-        const bool big = bw < nblk && dir_entries(bw, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes) > kDirWarpMax;
+        const uint32_t e = bw < nblk ? dir_entries(bw, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes) : 0u;
+        if (e && e <= kDirWarpMax) {
+            const uint32_t nsegs = (bw + 1 < nblk ? W.blk_seg[bw + 1] : total_segs) - W.blk_seg[bw];
+            int okw = 1;
+            if (lane == 0) {
+                okw = wait_geq(&W.segs_done[bw], nsegs, wait_bound(q));
+                if (!okw) q.status[bw] = PIVCO_ERR_TIMEOUT;
+            }
+            if (__shfl_sync(0xffffffffu, okw, 0)) {
+                DirWarpSmem &M = B.u.d.dw[warp];
+                dir_warp(bw, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, M.u, M.nv, M.first, M.maxd, M.sm,
+                         512);
+            }
+            __syncwarp();
+            if (lane == 0) { __threadfence(); atomicExch(&W.dir_done[bw], 1u); }
+        }
+        const bool big = e > kDirWarpMax;
         for (int w = 0; w < kDecWarps; w++) {
             if (!__syncthreads_or(warp == w && big)) continue;
             const int b = (int)(it * kDecWarps + w);
@@ -1612,67 +1722,48 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
             if (__syncthreads_or(!okw)) {
                 if (t == 0) q.status[b] = PIVCO_ERR_TIMEOUT;
             } else {
-                dir_cta(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.dir);
+                dir_cta(b, q.comp, q.comp_off, nblk, q.ws, q.ws_bytes, q.status, B.u.d.dir);
             }
             __syncthreads();
             if (t == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
         }
+        __syncthreads();
         return kItemDone;
     }
-    return kItemNone;
-}
-
-// Warp item `it` of the queue: items 0..nblk-1 are the directories of the
-// blocks with few superblocks (after the block's ANS segments), then the
-// tiles (after the block's ANS segments and directory).  Waits are bounded;
-// an expired one marks the block.
-__device__ inline void batch_warp_item(const BatchQueue &q, uint32_t it, WarpTile &S, const uint32_t *sel) {
-    const int lane = threadIdx.x & 31;
-    const DecWs W = dec_ws(q.ws, q.nblk);
-    const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
-    if (it < (uint32_t)q.nblk) {
-        const int b = (int)it;
-        const uint32_t e = dir_entries(b, q.comp, q.comp_off, q.nblk, q.ws, q.ws_bytes);
-        if (!e || e > kDirWarpMax) return;
-        const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
-        int okw = 1;
+    it -= ndir;
+    if (it >= hdr[6]) return kItemNone;
+    // ---- tile it: after its block's ANS segments and directory ----
+    if (warp == 0) {
+        const int b = find_block_warp(W.blk_tile, nblk, it, (int)((uint64_t)it * (uint32_t)nblk / max(hdr[6], 1u)));
         if (lane == 0) {
-            okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
+            const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
+            int okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
+            if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u, wait_bound(q));
             if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
+            B.blk = b;
+            B.ok = okw;
         }
-        if (__shfl_sync(0xffffffffu, okw, 0))
-            dir_warp(b, q.comp, q.comp_off, q.nblk, q.ws, q.ws_bytes, q.status, S.pos, S.dem, S.first, S.maxd,
-                     reinterpret_cast<uint32_t *>(&S.buf[0][0]), (uint32_t)(sizeof(S.buf) / 4));
-        __syncwarp();
-        if (lane == 0) { __threadfence(); atomicExch(&W.dir_done[b], 1u); }
-        return;
     }
-    it -= (uint32_t)q.nblk;
-    const int b = find_block_warp(W.blk_tile, q.nblk, it, (int)((uint64_t)it * (uint32_t)q.nblk / max(hdr[6], 1u)));
-    const uint32_t nsegs = (b + 1 < q.nblk ? W.blk_seg[b + 1] : hdr[2]) - W.blk_seg[b];
-    int okw = 1;
-    if (lane == 0) {
-        okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
-        if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u, wait_bound(q));
-        if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
-    }
-    if (!__shfl_sync(0xffffffffu, okw, 0)) return;
-    warp_tile(it, q.comp, q.comp_off, q.nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, S, sel, b);
+    __syncthreads();
+    const int b = B.blk, okw = B.ok;
+    __syncthreads();
+    if (okw) cta_tile(it, q.comp, q.comp_off, nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status, B.u.tile, B.sel, b);
+    __syncthreads();
+    return kItemDone;
 }
 
-__global__ void __launch_bounds__(kDecThreads, 2) decode_batch_kernel(const uint8_t *__restrict__ comp,
-                                                                      const uint64_t *__restrict__ comp_off, int nblk,
-                                                                      uint8_t *__restrict__ out,
-                                                                      const uint64_t *__restrict__ out_off,
-                                                                      uint8_t *__restrict__ ws, uint64_t ws_bytes,
-                                                                      int32_t *__restrict__ status,
-                                                                      const __grid_constant__ AnsTables A) {
+__global__ void __launch_bounds__(kDecThreads, kTileCtas) decode_batch_kernel(const uint8_t *__restrict__ comp,
+                                                                              const uint64_t *__restrict__ comp_off,
+                                                                              int nblk, uint8_t *__restrict__ out,
+                                                                              const uint64_t *__restrict__ out_off,
+                                                                              uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                                              int32_t *__restrict__ status,
+                                                                              const __grid_constant__ AnsTables A) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
     __shared__ uint32_t s_item;
     const BatchQueue q{comp, comp_off, out, out_off, ws, ws_bytes, status, nblk};
     uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     sel_init(B.sel);
     int last_b = -1;
     bool last_ok = false;
@@ -1682,17 +1773,7 @@ __global__ void __launch_bounds__(kDecThreads, 2) decode_batch_kernel(const uint
         const uint32_t item = s_item;
         __syncthreads();
         const int r = batch_item(q, item, B, A, last_b, last_ok);
-        if (r == kItemStop) return;
-        if (r == kItemNone) break;
-    }
-    // warp items (small directories, tiles): every warp on its own
-    const uint32_t total = (uint32_t)nblk + hdr[6];
-    for (;;) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&hdr[12], 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= total) break;
-        batch_warp_item(q, it, B.u.tw[warp], B.sel);
+        if (r != kItemDone) return;
     }
 }
 
@@ -1727,8 +1808,7 @@ __device__ inline void serve_item_done(const BatchQueue &q, uint32_t r, ServeFla
     uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
     __threadfence();
     const uint32_t n = atomicAdd(&hdr[11], 1u) + 1;
-    const uint32_t nplan = (uint32_t)((q.nblk + kDecWarps - 1) / kDecWarps);
-    if (*reinterpret_cast<volatile uint32_t *>(&hdr[10]) < nplan) return;   // totals not known yet: not the last
+    if (*reinterpret_cast<volatile uint32_t *>(&hdr[10]) < batch_nplan(q.nblk)) return;   // totals not known yet
     __threadfence();
     if (n != batch_items_total(q)) return;
     int32_t worst = PIVCO_OK;
@@ -1738,16 +1818,16 @@ __device__ inline void serve_item_done(const BatchQueue &q, uint32_t r, ServeFla
     st_release_sys_u32(&flags->done[r % kServeRing], r + 1);
 }
 
-__global__ void __launch_bounds__(kDecThreads, 2) serve_loop_kernel(ServeCtl *__restrict__ ctl,
-                                                                    const ServeDesc *__restrict__ ring,
-                                                                    ServeFlags *flags, uint64_t idle_ns,
-                                                                    uint64_t life_ns,
-                                                                    const __grid_constant__ AnsTables A) {
+__global__ void __launch_bounds__(kDecThreads, kTileCtas) serve_loop_kernel(ServeCtl *__restrict__ ctl,
+                                                                            const ServeDesc *__restrict__ ring,
+                                                                            ServeFlags *flags, uint64_t idle_ns,
+                                                                            uint64_t life_ns,
+                                                                            const __grid_constant__ AnsTables A) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     BatchSmem &B = *reinterpret_cast<BatchSmem *>(smem_raw);
     __shared__ ServeDesc D;
     __shared__ uint32_t s_cmd, s_item, s_r;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     sel_init(B.sel);
     int last_b = -1;
     bool last_ok = false;
@@ -1797,19 +1877,7 @@ __global__ void __launch_bounds__(kDecThreads, 2) serve_loop_kernel(ServeCtl *__
             __syncthreads();
             continue;
         }
-        // the request's CTA items are all taken: its tiles, every warp on its own
-        uint32_t *hdr = reinterpret_cast<uint32_t *>(q.ws);
-        const uint32_t total = (uint32_t)q.nblk + hdr[6];
-        for (;;) {
-            uint32_t it = 0;
-            if (lane == 0) it = atomicAdd(&hdr[12], 1u);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= total) break;
-            batch_warp_item(q, it, B.u.tw[warp], B.sel);
-            if (lane == 0) serve_item_done(q, r, flags);
-            __syncwarp();
-        }
-        __syncthreads();
+        // the request has no items left: move on to the next one
         if (t == 0) atomicCAS(&ctl->cur, r, r + 1);
         __syncthreads();
     }
@@ -1824,7 +1892,7 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
     uint64_t dir = 0, scratch = 0;
     // the shortest tile the plan can choose: a level of at most 128 nodes and
     // at most n symbols in a buffer, 20 % headroom, a multiple of 128
-    const uint64_t t_fit = ((uint64_t)(kWBuf - 4 * 128 - 32) / 5 * 4) & ~127ull;
+    const uint64_t t_fit = ((uint64_t)(kLvlBuf - 4 * 128 - 32) / 5 * 4) & ~127ull;
     uint64_t t_min = tu.tile_max < t_fit ? tu.tile_max : t_fit;
     if (t_min < 128) t_min = 128;
     for (int b = 0; b < nblk; b++) {
@@ -1854,7 +1922,7 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
 // bits per symbol, all of them ANS-coded.  For callers that place records
 // they have not seen yet.
 size_t decode_ws_size_bound(const uint64_t *blk_off, int nblk, const DecTuning &tu) {
-    const uint64_t t_fit = ((uint64_t)(kWBuf - 4 * 128 - 32) / 5 * 4) & ~127ull;
+    const uint64_t t_fit = ((uint64_t)(kLvlBuf - 4 * 128 - 32) / 5 * 4) & ~127ull;
     uint64_t t_min = tu.tile_max < t_fit ? tu.tile_max : t_fit;
     if (t_min < 128) t_min = 128;
     uint64_t dir = 0, scratch = 0;

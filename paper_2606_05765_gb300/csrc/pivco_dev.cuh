@@ -275,7 +275,7 @@ __host__ __device__ inline size_t decode_ws_fixed_bytes(int nblk) {
 
 // Launch tuning of the decode (never changes the decoded bytes)
 struct DecTuning {
-    uint32_t tile_max;      // longest root tile (symbols), a multiple of 128, <= 65536
+    uint32_t tile_max;      // longest root tile (symbols), a multiple of 128, <= 2^20
     uint32_t dir_bits;      // rank directory granularity (bits), a multiple of 32, <= 1024
     uint32_t ctas_per_sm;   // persistent merge CTAs per SM (0: as many as fit)
 };

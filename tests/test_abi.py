@@ -72,7 +72,7 @@ def test_tuning_validation(built_lib):
     """Host-side checks of the decode tuning (no device work)."""
     import paper_2606_05765_gb300 as P
     try:
-        for bad in [(65536, 512, 0), (65536, 100, 0), (100, 128, 0), (65536, 128, 33), (131072, 128, 0)]:
+        for bad in [(65536, 512, 0), (65536, 100, 0), (100, 128, 0), (65536, 128, 33), ((1 << 20) + 128, 128, 0)]:
             with pytest.raises(P.PivcoError):
                 P.set_tuning(*bad)
         P.set_tuning(16384, 256, 2)
@@ -81,7 +81,7 @@ def test_tuning_validation(built_lib):
     finally:
         P.set_tuning()
     t = P.get_tuning()
-    assert (t.tile_max, t.dir_bits, t.ctas_per_sm) == (65536, 128, 0)
+    assert (t.tile_max, t.dir_bits, t.ctas_per_sm) == (1 << 20, 128, 0)
 
 
 def test_host_codec_and_plan_argument_errors(built_lib):

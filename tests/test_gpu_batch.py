@@ -44,7 +44,7 @@ def test_batched_equals_input(P, encoded, name):
     assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
 
 
-@pytest.mark.parametrize("tuning", [(128, 32, 1), (4096, 256, 0), (16384, 96, 2), (65536, 160, 3)])
+@pytest.mark.parametrize("tuning", [(128, 32, 1), (4096, 256, 0), (16384, 96, 2), (65536, 160, 3), (1 << 20, 64, 0)])
 def test_tunings_do_not_change_output(P, encoded, tuning):
     P.set_tuning(*tuning)
     try:
