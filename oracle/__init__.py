@@ -65,6 +65,9 @@ def lib():
             "ref_decode_block": [P, u64, P, u64, P],
             "ref_encode_batch": [P, P, C.c_int, P, P, P, P, P],
             "ref_decode_batch": [P, P, P, C.c_int, P, P, P],
+            "ref_golomb_bound": [P, u64, P],
+            "ref_golomb_encode": [P, u64, P, u64, P],
+            "ref_golomb_decode": [P, u64, P, u64, P],
         }
         for name, args in sig.items():
             fn = getattr(_lib, name)
@@ -231,3 +234,28 @@ def decode_batch(buf, rec_off, rec_avail, out_off):
                            _p(np.ascontiguousarray(rec_avail, np.uint64)), nblk, _p(out),
                            _p(np.ascontiguousarray(out_off, np.uint64)), _p(st))
     return st, out[: int(out_off[-1])]
+
+
+# ---------------------------------------------------------------- PivCo-Golomb
+def golomb_encode(x):
+    """PivCo-Golomb record of the values x (App. G; see the C header)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    bound = np.zeros(1, np.uint64)
+    _check(lib().ref_golomb_bound(_p(x), x.size, _p(bound)), "golomb_bound")
+    rec = np.zeros(int(bound[0]), np.uint8)
+    nb = np.zeros(1, np.uint64)
+    _check(lib().ref_golomb_encode(_p(x), x.size, _p(rec), rec.size, _p(nb)), "golomb_encode")
+    return rec[: int(nb[0])]
+
+
+def golomb_decode(rec, cap=None):
+    """(status, values) of a PivCo-Golomb record."""
+    rec = np.ascontiguousarray(rec, dtype=np.uint8)
+    cap = (1 << 32) - 1 if cap is None else cap
+    n = np.zeros(1, np.uint64)
+    rc = lib().ref_golomb_decode(_p(rec), rec.size, None, 0, _p(n))
+    if rc not in (OK, ERR_CAPACITY):
+        return rc, None
+    out = np.zeros(max(int(n[0]), 1), np.uint8)
+    rc = lib().ref_golomb_decode(_p(rec), rec.size, _p(out), min(cap, out.size), _p(n))
+    return rc, out[: int(n[0])] if rc == OK else None

@@ -20,6 +20,8 @@
  *   7. the block record (wire format)              (App. D, adapted: see below)
  *   8. decode by the definition: a per-node cursor walk (Listing 1 applied to
  *      the pivoted layout, Sec. 2)
+ *   9. PivCo-Golomb: the unary (Golomb parameter 1) code pivoted into a list
+ *      of bitmaps, its record and its decode by the definition (App. G)
  *
  * Readings where the paper is silent or loose (each is part of the format):
  *   R1  code lengths: optimal package-merge; leaves ordered by (count, symbol),
@@ -42,10 +44,16 @@
  *       stored with marker 0xFF.
  *   R7  record: u32 widths, a node directory of u32 counts, ANS bodies after
  *       all raw bodies, records padded to 16 bytes.
+ *   R8  PivCo-Golomb (App. G names Golomb coding and a list of bitmaps, and
+ *       decodes a 1 bit to 0x00 and a 0 bit to the child's value plus 1):
+ *       Golomb parameter 1, i.e. unary codes with stop bit 1; values are
+ *       bytes; bitmap j holds the bit of every value >= j; a "PVG1" record
+ *       with u32 counts n_j like R7.
  *
  * Parity status: every function above is pinned by the oracle tests (worked
  * examples of Sec. 1.1 and 2.2, brute-force optimality, Kraft, closed forms
- * of Sec. 5.1, round trips).  The exact bytes of an ANS stream are pinned
+ * of Sec. 5.1, round trips; for PivCo-Golomb a hand-derived record, the plain
+ * unary stream, closed forms of the counts and App. G's bottom-up merge).  The exact bytes of an ANS stream are pinned
  * only by this definition and the round trip: "parity unpinned" beyond that.
  */
 #include <stdint.h>
@@ -718,4 +726,113 @@ int ref_decode_batch(const uint8_t *rec, const uint64_t *rec_off, const uint64_t
         if (status[b]) bad++;
     }
     return bad ? REF_ERR_CORRUPT : REF_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PivCo-Golomb (App. G).                                                    */
+/*                                                                          */
+/* Reading: App. G applies pivoted coding to Golomb coding with a LIST of    */
+/* bitmaps in place of a tree.  Here the Golomb parameter is 1, i.e. the     */
+/* unary code: value v is written as v "continue" bits then one "stop" bit,   */
+/* and stop = 1 (App. G: a 1 bit yields output 0x00, a 0 bit the child's      */
+/* value plus 1).  Pivoted: bitmap j holds, in sequence order, the j-th code  */
+/* bit of every value with at least j+1 code bits, i.e. of every v >= j: 1    */
+/* if v == j, 0 if v > j.  There are m = (largest value) + 1 bitmaps.         */
+/*                                                                          */
+/* Record (byte-aligned like App. D; u32 widths as in the PivCo record):      */
+/*    0 u32 rec_bytes (multiple of 16)   4 u32 n   8 u16 m   10 u8 kind = 4   */
+/*   11 u8 0   12 "PVG1"   16 u32 n_j[m] (values >= j; n_0 = n)               */
+/*   then the bitmaps B_0 .. B_{m-1}, ceil(n_j / 8) bytes each, back to back, */
+/*   bit i of B_j in byte i >> 3 at bit (i & 7), pad bits 0; zero pad to 16.  */
+/* An empty sequence is a 16-byte record with n = m = 0.                     */
+/* ------------------------------------------------------------------------ */
+#define REF_GOLOMB_KIND 4u
+
+int ref_golomb_bound(const uint8_t *x, uint64_t n, uint64_t *bound) {
+    if (!bound || n > 0xFFFFFFFFull || (n && !x)) return REF_ERR_ARG;
+    uint64_t cnt[257];
+    memset(cnt, 0, sizeof cnt);
+    int m = 0;
+    for (uint64_t i = 0; i < n; i++) { cnt[x[i]]++; if ((int)x[i] + 1 > m) m = (int)x[i] + 1; }
+    /* n_j = values >= j: a suffix sum of the counts */
+    uint64_t ge = 0, bytes = 16 + 4ull * (uint64_t)m;
+    for (int j = 255; j >= 0; j--) { ge += cnt[j]; if (j < m) bytes += (ge + 7) / 8; }
+    *bound = pad16(bytes);
+    return REF_OK;
+}
+
+int ref_golomb_encode(const uint8_t *x, uint64_t n, uint8_t *rec, uint64_t cap, uint64_t *rec_bytes) {
+    uint64_t size = 0;
+    int rc = ref_golomb_bound(x, n, &size);
+    if (rc != REF_OK) return rc;
+    if (!rec || cap < size) return REF_ERR_CAPACITY;
+    memset(rec, 0, size);
+    int m = 0;
+    for (uint64_t i = 0; i < n; i++) if ((int)x[i] + 1 > m) m = (int)x[i] + 1;
+    put32(rec, (uint32_t)size);
+    put32(rec + 4, (uint32_t)n);
+    put16(rec + 8, (uint32_t)m);
+    rec[10] = (uint8_t)REF_GOLOMB_KIND;
+    rec[11] = 0;
+    memcpy(rec + 12, "PVG1", 4);
+    /* n_j and the bitmap starts */
+    uint64_t nj[256], start[256], off = 16 + 4ull * (uint64_t)m;
+    for (int j = 0; j < m; j++) {
+        nj[j] = 0;
+        for (uint64_t i = 0; i < n; i++) nj[j] += x[i] >= j;
+        put32(rec + 16 + 4 * j, (uint32_t)nj[j]);
+        start[j] = off;
+        off += (nj[j] + 7) / 8;
+    }
+    /* value by value, code bit by code bit: bit j of value v goes to the next
+       free position of bitmap j */
+    uint64_t cur[256];
+    memset(cur, 0, sizeof cur);
+    for (uint64_t i = 0; i < n; i++) {
+        for (int j = 0; j <= x[i]; j++) {
+            const uint64_t pos = cur[j]++;
+            if (j == x[i]) rec[start[j] + (pos >> 3)] |= (uint8_t)(1u << (pos & 7));
+        }
+    }
+    if (rec_bytes) *rec_bytes = size;
+    return REF_OK;
+}
+
+/* Decode by the definition: for each output, read bitmaps 0, 1, ... at their
+   own cursors until a stop bit; the value is the number of continue bits. */
+int ref_golomb_decode(const uint8_t *rec, uint64_t avail, uint8_t *out, uint64_t cap, uint64_t *n_out) {
+    if (!rec || avail < 16) return REF_ERR_CORRUPT;
+    const uint32_t size = get32(rec), n = get32(rec + 4), m = get16(rec + 8);
+    if (memcmp(rec + 12, "PVG1", 4) != 0 || rec[10] != REF_GOLOMB_KIND || rec[11] != 0 || size % 16 || size > avail ||
+        m > 256 || (n == 0) != (m == 0) || 16ull + 4ull * m > size)
+        return REF_ERR_CORRUPT;
+    if (n_out) *n_out = n;
+    if (n > cap || (n && !out)) return REF_ERR_CAPACITY;
+    uint64_t nj[256], start[256], off = 16 + 4ull * m;
+    for (uint32_t j = 0; j < m; j++) {
+        nj[j] = get32(rec + 16 + 4 * j);
+        if ((j == 0 && nj[j] != n) || (j && nj[j] > nj[j - 1])) return REF_ERR_CORRUPT;
+        start[j] = off;
+        off += (nj[j] + 7) / 8;
+    }
+    if (pad16(off) != size) return REF_ERR_CORRUPT;
+    uint64_t cur[256];
+    memset(cur, 0, sizeof cur);
+    for (uint32_t i = 0; i < n; i++) {
+        uint32_t j = 0;
+        for (;;) {
+            if (j >= m || cur[j] >= nj[j]) return REF_ERR_CORRUPT;
+            const uint64_t pos = cur[j]++;
+            if ((rec[start[j] + (pos >> 3)] >> (pos & 7)) & 1u) break;
+            j++;
+        }
+        out[i] = (uint8_t)j;
+    }
+    /* every bitmap read exactly to its end; pad bits zero */
+    for (uint32_t j = 0; j < m; j++) {
+        if (cur[j] != nj[j]) return REF_ERR_CORRUPT;
+        if ((nj[j] & 7) && (rec[start[j] + (nj[j] >> 3)] >> (nj[j] & 7))) return REF_ERR_CORRUPT;
+    }
+    for (uint64_t i = off; i < size; i++) if (rec[i]) return REF_ERR_CORRUPT;
+    return REF_OK;
 }

@@ -16,6 +16,8 @@ float64 CDF; the rank-k symbol is byte k-1 unless ``permute`` is given):
              alphabet A ~ U{2..256} and exponent s ~ U(0.5, 2.0), P(k) ~ k^-s, seed 3
   serving    Poisson request stream, sizes floor(exp(U(ln 1 KiB, ln 16 MiB))),
              each request drawn from skew80 / skew95 / mixed, seed 4
+  golomb     PivCo-Golomb values: 4096 blocks x 32 KiB, i.i.d. geometric with
+             mean unary code length 1.25 .. 5 (App. G, Table 18), seed 5
 """
 import hashlib
 from dataclasses import dataclass, field
@@ -163,5 +165,17 @@ def serving_requests(n_req, rate_per_s, seed=4, lo=KiB, hi=16 * MiB):
     return reqs
 
 
+def golomb(nblk=4096, bs=32 * KiB, avg_len=2.0, seed=5):
+    """PivCo-Golomb values (App. G, Table 18's sweep of average code lengths):
+    i.i.d. geometric values v >= 0 with P(v) = p (1 - p)^v, p = 1 / avg_len,
+    so the unary code length v + 1 has mean avg_len; capped at 255."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = nblk * bs
+    data = np.minimum(rng.geometric(1.0 / avg_len, n) - 1, 255).astype(np.uint8)
+    return Workload("golomb", data, _uniform_blocks(nblk, bs), False,
+                    "%d blocks x %d values, geometric with mean code length %.2f, seed %d" % (nblk, bs, avg_len, seed),
+                    {"avg_len": avg_len})
+
+
 def by_name(name, **kw):
-    return {"zipf1": zipf1, "skew80": skew80, "skew95": skew95, "mixed": mixed}[name](**kw)
+    return {"zipf1": zipf1, "skew80": skew80, "skew95": skew95, "mixed": mixed, "golomb": golomb}[name](**kw)
