@@ -146,10 +146,15 @@ pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int
  * each chunk's histogram to chunk_hist[nblk][8][256] (device; the chunks a
  * block does not have are zeros).  pivco_encode_blocks_chunked is
  * pivco_encode_blocks reading those chunk histograms instead of counting the
- * chunks again; the records are byte-identical.  Chunk histograms that do not
- * describe `in` (another input, or stale) make status[b] =
- * PIVCO_ERR_INVALID_ARG for the blocks they do not fit; nothing is written
- * outside each block's record. */
+ * chunks again; the records are byte-identical.  The encoder codes a block
+ * in runs of consecutive chunks whose levels fit its buffers, taking each
+ * run's node counts from the summed chunk histograms (a chunk too large for
+ * the buffers is coded in parts counted from `in`, and the parts' counts
+ * must add up to its histogram).  Chunk histograms that do not describe
+ * `in` (another input, or stale) never give a wrong record with an OK
+ * status: a block is either refused (status[b] = PIVCO_ERR_INVALID_ARG) or,
+ * when the sums it used are right after all, encoded exactly; nothing is
+ * written outside each block's record. */
 pivco_status pivco_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
                                     uint32_t *hist, uint32_t *chunk_hist, void *stream);
 pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
@@ -283,6 +288,66 @@ pivco_status pivco_decode_ans(const uint8_t *comp, const uint64_t *comp_off, int
 pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,
                                 uint8_t *out, const uint64_t *out_off, void *ws, size_t ws_bytes,
                                 int32_t *status, void *stream);
+
+/* Random access (Sec. 2.1's top-down traversal, answered per position the
+ * way a wavelet tree answers access, Sec. 7.2): the symbol at position
+ * qpos[i] of block qblk[i] (device arrays of nq uint32), by a walk from the
+ * root in which the position's bit at node v picks the child and its rank
+ * among the positions of that bit (rank directory + popcount) becomes the
+ * position at the child.  Gives the bytes pivco_decode_blocks gives, one
+ * position at a time, without decoding the rest of the block.
+ *   pivco_access_workspace_size (synchronous): as
+ *     pivco_decode_workspace_size, for a workspace that holds a rank
+ *     directory for every coded block;
+ *   pivco_access_prepare: plans the records, decodes the ANS-coded bitmaps
+ *     and builds the directories in `ws` (asynchronous; status[b] as for
+ *     pivco_decode_blocks);
+ *   pivco_access: the queries, any number of times on a prepared `ws` (the
+ *     records and `status` must be those of the prepare).  sym[i] (device
+ *     uint8) receives the symbol; qstatus[i] (device int32, may be NULL):
+ *     PIVCO_OK, PIVCO_ERR_INVALID_ARG (block index or position out of
+ *     range, or a workspace not prepared for access), or the block's
+ *     non-OK status, or PIVCO_ERR_CORRUPT (the walk left the tree). */
+pivco_status pivco_access_workspace_size(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws,
+                                         size_t ws_bytes, int32_t *status, size_t *bytes, void *stream);
+pivco_status pivco_access_prepare(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws,
+                                  size_t ws_bytes, int32_t *status, void *stream);
+pivco_status pivco_access(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, const uint32_t *qblk,
+                          const uint32_t *qpos, int32_t nq, uint8_t *sym, int32_t *qstatus, const void *ws,
+                          size_t ws_bytes, const int32_t *status, void *stream);
+
+/* ---- PivCo-Golomb (App. G): pivoted coding of Golomb codes ----
+ * Values are Golomb-coded with parameter 1 (the unary code): value v is v
+ * continue bits then one stop bit, stop = 1.  Pivoted, the code is a list of
+ * bitmaps instead of a tree: bitmap j holds, in order, the j-th code bit of
+ * every value >= j (1 where the value is j, 0 where it is larger), and the
+ * decoder merges the list bottom-up with App. G's merge_vec_cst_plus1
+ * (cst 0xFF): out_j[i] = B_j[i] ? 0x00 : out_{j+1}[rank0(B_j, i)] + 1.
+ * Record of a block (16-byte aligned, like the PivCo-Huffman record):
+ *    0 u32 rec_bytes (multiple of 16)   4 u32 n   8 u16 m (largest value + 1;
+ *    0 for an empty block)   10 u8 kind = 4   11 u8 0   12 "PVG1"
+ *   16 u32 n_j[m] (values >= j; n_0 = n), then the bitmaps B_0 .. B_{m-1} of
+ *      ceil(n_j / 8) bytes each, back to back (bit i in byte i >> 3 at bit
+ *      i & 7, pad bits 0), zero pad to 16.
+ * Blocks hold at most PIVCO_GOLOMB_MAX_BLOCK values (one CTA keeps a block's
+ * levels in shared memory); larger ones get status[b] = PIVCO_ERR_INVALID_ARG.
+ *   pivco_golomb_plan: rec_size[b] (device uint64) = the exact record size
+ *     of block b of `in` (device values, blocks by blk_off); place records by
+ *     an exclusive scan of the sizes (pivco_exclusive_scan);
+ *   pivco_golomb_encode: block b's record at out + out_off[b] (capacity
+ *     out_off[b+1] - out_off[b], else PIVCO_ERR_CAPACITY), its size in
+ *     rec_bytes[b];
+ *   pivco_golomb_decode: block b's values at out + out_off[b] (capacity must
+ *     equal the record's n, else PIVCO_ERR_CAPACITY); a record that fails
+ *     validation gives PIVCO_ERR_CORRUPT.
+ * status[b] (device int32) as for the PivCo-Huffman calls. */
+#define PIVCO_GOLOMB_MAX_BLOCK 32768u
+pivco_status pivco_golomb_plan(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, uint64_t *rec_size,
+                               int32_t *status, void *stream);
+pivco_status pivco_golomb_encode(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, uint8_t *out,
+                                 const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status, void *stream);
+pivco_status pivco_golomb_decode(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, uint8_t *out,
+                                 const uint64_t *out_off, int32_t *status, void *stream);
 
 /* Number of kernels this library has launched in this process (host). */
 uint64_t pivco_launch_count(void);

@@ -62,6 +62,12 @@ _SIGS = {
     "pivco_server_forget": [_P, C.c_uint64],
     "pivco_server_destroy": [_P],
     "pivco_set_wait_limit": [C.c_uint64],
+    "pivco_access_workspace_size": [_P, _P, _I32, _P, _SZ, _P, C.POINTER(C.c_size_t), _P],
+    "pivco_access_prepare": [_P, _P, _I32, _P, _SZ, _P, _P],
+    "pivco_access": [_P, _P, _I32, _P, _P, _I32, _P, _P, _P, _SZ, _P, _P],
+    "pivco_golomb_plan": [_P, _P, _I32, _P, _P, _P],
+    "pivco_golomb_encode": [_P, _P, _I32, _P, _P, _P, _P, _P],
+    "pivco_golomb_decode": [_P, _P, _I32, _P, _P, _P, _P],
 }
 _OTHER = {
     "pivco_version": ([], C.c_char_p),
@@ -231,6 +237,67 @@ def decode_ans(comp, comp_off, nblk, ws, status, stream=None):
 def decode_merge(comp, comp_off, nblk, out, out_off, ws, status, stream=None):
     _check(lib().pivco_decode_merge(_ptr(comp), _ptr(comp_off), nblk, _ptr(out), _ptr(out_off), _ptr(ws),
                                     ws.numel(), _ptr(status), _stream(stream)), "pivco_decode_merge")
+
+
+class Access:
+    """Random access to the symbols of a batch of records (pivco_access_*):
+    prepare once (plans, ANS bitmaps, a rank directory per block), then
+    query (block, position) pairs any number of times."""
+
+    def __init__(self, comp, comp_off, nblk, stream=None):
+        import torch
+        dev = comp.device
+        self.comp, self.comp_off, self.nblk = comp, comp_off, nblk
+        self.status = torch.empty(max(nblk, 1), dtype=torch.int32, device=dev)
+        self.ws = torch.empty(decode_plan_bytes(nblk), dtype=torch.uint8, device=dev)
+        need = C.c_size_t(0)
+        _check(lib().pivco_access_workspace_size(_ptr(comp), _ptr(comp_off), nblk, _ptr(self.ws), self.ws.numel(),
+                                                 _ptr(self.status), C.byref(need), _stream(stream)),
+               "pivco_access_workspace_size")
+        if need.value > self.ws.numel():
+            self.ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
+        _check(lib().pivco_access_prepare(_ptr(comp), _ptr(comp_off), nblk, _ptr(self.ws), self.ws.numel(),
+                                          _ptr(self.status), _stream(stream)), "pivco_access_prepare")
+
+    def __call__(self, qblk, qpos, sym=None, qstatus=None, stream=None):
+        """qblk, qpos: int32/uint32 CUDA tensors of equal length; returns (sym, qstatus)."""
+        import torch
+        nq = qblk.numel()
+        sym = torch.empty(max(nq, 1), dtype=torch.uint8, device=qblk.device) if sym is None else sym
+        qstatus = torch.empty(max(nq, 1), dtype=torch.int32, device=qblk.device) if qstatus is None else qstatus
+        _check(lib().pivco_access(_ptr(self.comp), _ptr(self.comp_off), self.nblk, _ptr(qblk), _ptr(qpos), nq,
+                                  _ptr(sym), _ptr(qstatus), _ptr(self.ws), self.ws.numel(), _ptr(self.status),
+                                  _stream(stream)), "pivco_access")
+        return sym[:nq], qstatus[:nq]
+
+
+GOLOMB_MAX_BLOCK = 32768
+
+
+def golomb_encode(data, blk_off, stream=None):
+    """PivCo-Golomb records of the blocks of `data` (uint8 values): plan,
+    place by an exclusive scan, encode.  Returns Encoded(comp, off, rec_bytes, status)."""
+    import torch
+    nblk = blk_off.numel() - 1
+    dev = data.device
+    size = torch.empty(max(nblk, 1), dtype=torch.int64, device=dev)
+    status = torch.empty(max(nblk, 1), dtype=torch.int32, device=dev)
+    _check(lib().pivco_golomb_plan(_ptr(data), _ptr(blk_off), nblk, _ptr(size), _ptr(status), _stream(stream)),
+           "pivco_golomb_plan")
+    off = torch.empty(nblk + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(scan_workspace_size(nblk), dtype=torch.uint8, device=dev)
+    exclusive_scan(size, nblk, off, ws, None, stream)
+    total = int(off[-1].item()) if nblk else 0
+    comp = torch.empty(max(total, 16), dtype=torch.uint8, device=dev)
+    rec_bytes = torch.empty(max(nblk, 1), dtype=torch.int64, device=dev)
+    _check(lib().pivco_golomb_encode(_ptr(data), _ptr(blk_off), nblk, _ptr(comp), _ptr(off), _ptr(rec_bytes),
+                                     _ptr(status), _stream(stream)), "pivco_golomb_encode")
+    return Encoded(comp, off, rec_bytes[:nblk], status[:nblk])
+
+
+def golomb_decode(comp, comp_off, out, out_off, status, stream=None):
+    _check(lib().pivco_golomb_decode(_ptr(comp), _ptr(comp_off), comp_off.numel() - 1, _ptr(out), _ptr(out_off),
+                                     _ptr(status), _stream(stream)), "pivco_golomb_decode")
 
 
 def launch_count():

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpivco.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["abi.cu", "k_build.cu", "k_scan.cu", "k_encode.cu", "k_ans.cu", "k_decode.cu", "serve.cu", "host_codec.cu"]
+SOURCES = ["abi.cu", "k_build.cu", "k_scan.cu", "k_encode.cu", "k_ans.cu", "k_decode.cu", "k_golomb.cu", "serve.cu",
+           "host_codec.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

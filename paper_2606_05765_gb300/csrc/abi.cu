@@ -283,6 +283,55 @@ pivco_status pivco_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
                                           ws_bytes, status, S(stream)));
 }
 
+pivco_status pivco_access_workspace_size(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws,
+                                         size_t ws_bytes, int32_t *status, size_t *bytes, void *stream) {
+    if (nblk < 0 || !bytes || (nblk > 0 && (!comp || !comp_off || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) { *bytes = 0; return PIVCO_OK; }
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    cudaError_t e = launch_decode_plan(comp, comp_off, nblk, reinterpret_cast<uint8_t *>(ws), ws_bytes, status, S(stream),
+                                       true);
+    if (e != cudaSuccess) return PIVCO_ERR_CUDA;
+    return ok_or_cuda(read_decode_ws_need(reinterpret_cast<const uint8_t *>(ws), nblk, bytes, S(stream)));
+}
+
+pivco_status pivco_access_prepare(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, void *ws,
+                                  size_t ws_bytes, int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !ws || !status))) return PIVCO_ERR_INVALID_ARG;
+    if (nblk == 0) return PIVCO_OK;
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    return ok_or_cuda(launch_access_prepare(comp, comp_off, nblk, reinterpret_cast<uint8_t *>(ws), ws_bytes, status,
+                                            S(stream)));
+}
+
+pivco_status pivco_access(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, const uint32_t *qblk,
+                          const uint32_t *qpos, int32_t nq, uint8_t *sym, int32_t *qstatus, const void *ws,
+                          size_t ws_bytes, const int32_t *status, void *stream) {
+    if (nblk < 0 || nq < 0 || (nq > 0 && (!comp || !comp_off || !qblk || !qpos || !sym || !ws || !status)))
+        return PIVCO_ERR_INVALID_ARG;
+    if (nq == 0) return PIVCO_OK;
+    if (ws_bytes < decode_ws_fixed_bytes(nblk)) return PIVCO_ERR_CAPACITY;
+    return ok_or_cuda(launch_access(comp, comp_off, nblk, qblk, qpos, nq, sym, qstatus,
+                                    reinterpret_cast<const uint8_t *>(ws), ws_bytes, status, S(stream)));
+}
+
+pivco_status pivco_golomb_plan(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, uint64_t *rec_size,
+                               int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!blk_off || !rec_size || !status))) return PIVCO_ERR_INVALID_ARG;
+    return ok_or_cuda(launch_golomb_plan(in, blk_off, nblk, rec_size, status, S(stream)));
+}
+
+pivco_status pivco_golomb_encode(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, uint8_t *out,
+                                 const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!blk_off || !out || !out_off || !rec_bytes || !status))) return PIVCO_ERR_INVALID_ARG;
+    return ok_or_cuda(launch_golomb_encode(in, blk_off, nblk, out, out_off, rec_bytes, status, S(stream)));
+}
+
+pivco_status pivco_golomb_decode(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk, uint8_t *out,
+                                 const uint64_t *out_off, int32_t *status, void *stream) {
+    if (nblk < 0 || (nblk > 0 && (!comp || !comp_off || !out_off || !status))) return PIVCO_ERR_INVALID_ARG;
+    return ok_or_cuda(launch_golomb_decode(comp, comp_off, nblk, out, out_off, status, S(stream)));
+}
+
 uint64_t pivco_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 pivco_status pivco_set_wait_limit(uint64_t ns) {
@@ -357,7 +406,7 @@ pivco_status pivco_graph_begin(void *stream) {
     // kernel attributes and the ANS tables are set up outside the capture
     host_ans_tables();
     if (prepare_decode_kernels() != cudaSuccess || prepare_encode_kernels() != cudaSuccess ||
-        prepare_ans_kernels() != cudaSuccess)
+        prepare_ans_kernels() != cudaSuccess || prepare_golomb_kernels() != cudaSuccess)
         return PIVCO_ERR_CUDA;
     return ok_or_cuda(cudaStreamBeginCapture(S(stream), cudaStreamCaptureModeThreadLocal));
 }

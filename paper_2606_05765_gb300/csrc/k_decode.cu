@@ -38,8 +38,15 @@ constexpr int kWSlack = 64;                  // over-read room of the byte windo
 constexpr int kTileCtas = 4;                 // tile CTAs per SM the kernels are built for
 constexpr uint32_t kNtabHdr = 32;            // node table header (see plan_block)
 
-// bytes of a block's node table: header, u32 source and u32 children per node
-__host__ __device__ inline uint32_t ntab_bytes(uint32_t V) { return (kNtabHdr + 8u * V + 15u) & ~15u; }
+// bytes of a block's node table: header, then per node u32 bitmap source,
+// u32 children and u32 first rank-directory entry
+__host__ __device__ inline uint32_t ntab_bytes(uint32_t V) { return (kNtabHdr + 12u * V + 15u) & ~15u; }
+
+// rank-directory granularity, and whether every coded block gets a directory
+// (random access) rather than only those split into several tiles: header
+// word 7, the flag in bit 31
+__device__ inline uint32_t dec_dir_bits(const uint8_t *ws) { return reinterpret_cast<const uint32_t *>(ws)[7] & 0xFFFFu; }
+__device__ inline bool dec_all_dirs(const uint8_t *ws) { return (reinterpret_cast<const uint32_t *>(ws)[7] >> 31) != 0; }
 
 __host__ __device__ inline uint32_t scratch_stride(uint32_t raw) { return ((raw + 15u) & ~15u) + 16u; }
 
@@ -259,12 +266,14 @@ __device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &
 //                     or 8 x block scratch offset | 2^31 for ANS-coded nodes
 //      u32 ch[V]      children: child c in bits [16c, 16c + 16), 0x8000 |
 //                     symbol for a leaf, else the child's node index
+//      u32 u[V]       node v's first rank-directory entry (blocks with one)
 // ---------------------------------------------------------------------------
 struct PlanScratch {
     uint32_t cntl[16], lvl[16], run[16];
     int32_t a[17], first[18], start[17];
     int32_t good, maxd;
     uint32_t ch[256];
+    uint32_t u[256];
     uint8_t sorted[256];
 };
 
@@ -275,7 +284,8 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
     uint32_t *hdr32 = reinterpret_cast<uint32_t *>(ws);
     uint64_t *hdr64 = reinterpret_cast<uint64_t *>(ws);
     const DecWs W = dec_ws(ws, nblk);
-    const uint32_t dir_bits = hdr32[7], tile_max = hdr32[8];
+    const uint32_t dir_bits = dec_dir_bits(ws), tile_max = hdr32[8];
+    const bool all_dirs = dec_all_dirs(ws);
     if (lane < 16) { Q.cntl[lane] = 0; Q.lvl[lane] = 0; Q.run[lane] = 0; }
     __syncwarp();
     const uint8_t *rec = comp + comp_off[b];
@@ -380,10 +390,11 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
                 T = (uint32_t)t2;
                 ntile = (R.n + T - 1) / T;
             }
-            if (ntile > 1)
+            if (ntile > 1 || all_dirs)
                 ent = warp_scan_loop_d((int)R.V, [&](int v) { return (R.nv[v] + dir_bits - 1) / dir_bits; },
-                                       [&](int, uint32_t) {});
-            dir_bytes = ntab_bytes(R.V) + (ntile > 1 ? ((4ull * ent + 4ull * (ntile + 1) * R.V + 15) & ~15ull) : 0ull);
+                                       [&](int v, uint32_t p) { Q.u[v] = p; });
+            dir_bytes = ntab_bytes(R.V) +
+                        (ent ? ((4ull * ent + 4ull * (ntile + 1) * R.V + 15) & ~15ull) : 0ull);
         }
     }
     const uint64_t sb = ok ? R.scratch_bytes : 0, sg = ok ? R.nsegs : 0;
@@ -425,6 +436,7 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
             const uint8_t m = R.marker[v];
             src[v] = (m && m != kMarkRawSel) ? (8u * R.soff[v]) | 0x80000000u : 8u * R.body_off[v];
             src[R.V + v] = Q.ch[v];
+            src[2 * R.V + v] = ent ? Q.u[v] : 0u;
         }
     }
     __syncwarp();
@@ -474,11 +486,11 @@ __device__ inline bool abandoned_batch(const uint8_t *ws, int32_t *status, int n
 }
 
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
-                               int32_t *status, cudaStream_t st) {
+                               int32_t *status, cudaStream_t st, bool all_dirs) {
     if (nblk <= 0) return cudaSuccess;
     const DecTuning tu = current_tuning();
-    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits, tu.tile_max,
-                                                                      wait_limit_ns());
+    dec_ws_init_kernel<<<min(1024, div_up(nblk, 256)), 256, 0, st>>>(ws, nblk, tu.dir_bits | (all_dirs ? 1u << 31 : 0u),
+                                                                      tu.tile_max, wait_limit_ns());
     decode_plan_kernel<<<nblk, 32, 0, st>>>(comp, comp_off, nblk, ws, ws_bytes, status);
     count_launches(2);
     return cudaGetLastError();
@@ -1221,9 +1233,9 @@ __device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const ui
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const DecWs W = dec_ws(ws, nblk);
     const DecRegions G = dec_regions(nblk, ws);
-    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
+    const uint32_t dir_bits = dec_dir_bits(ws);
     const uint32_t ntile = W.blk_ntile[b], T = W.blk_T[b];
-    if (ntile <= 1) return;
+    if (ntile <= 1 && !dec_all_dirs(ws)) return;
     // one decision for the whole CTA (every thread reaches the same barriers)
     if (__syncthreads_or(*reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK)) return;
     const uint8_t *rec = comp + comp_off[b];
@@ -1359,15 +1371,21 @@ __device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const ui
 // first / maxd are the warp's scratch.
 constexpr uint32_t kDirWarpMax = 8192;
 
-// superblock count of block b's rank directory (0: the block has one tile)
+// superblock count of block b's rank directory (0: the block has none: one
+// tile, and no directory asked for every block; or no node table at all: a
+// block that is not coded, or whose plan failed, has an empty region, and
+// its record is not read)
 __device__ inline uint32_t dir_entries(int b, const uint8_t *comp, const uint64_t *comp_off, int nblk,
                                        const uint8_t *ws, uint64_t ws_bytes) {
     const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
-    if (W.blk_ntile[b] <= 1) return 0;
+    if (W.blk_ntile[b] <= 1 && !dec_all_dirs(ws)) return 0;
+    const uint64_t d0 = W.blk_dir[b];
+    const uint64_t d1 = b + 1 < nblk ? W.blk_dir[b + 1] : reinterpret_cast<const uint64_t *>(ws)[2];
+    if (d1 <= d0) return 0;
     const DecRegions G = dec_regions(nblk, ws);
     const uint8_t *rec = comp + comp_off[b];
     const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
-    const uint64_t nbase = G.dir + W.blk_dir[b];
+    const uint64_t nbase = G.dir + d0;
     return nbase + ntab_bytes(V) <= ws_bytes ? *reinterpret_cast<const uint32_t *>(ws + nbase + 20) : 0xFFFFFFFFu;
 }
 
@@ -1378,9 +1396,9 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
     const int lane = threadIdx.x & 31;
     const DecWs W = dec_ws(ws, nblk);
     const DecRegions G = dec_regions(nblk, ws);
-    const uint32_t dir_bits = reinterpret_cast<const uint32_t *>(ws)[7];
+    const uint32_t dir_bits = dec_dir_bits(ws);
     const uint32_t ntile = W.blk_ntile[b], T = W.blk_T[b];
-    if (ntile <= 1 || *reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
+    if ((ntile <= 1 && !dec_all_dirs(ws)) || *reinterpret_cast<volatile int32_t *>(&status[b]) != PIVCO_OK) return;
     const uint8_t *rec = comp + comp_off[b];
     const uint32_t rb = ld_le32(rec);
     const uint32_t V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
@@ -1881,6 +1899,103 @@ __global__ void __launch_bounds__(kDecThreads, kTileCtas) serve_loop_kernel(Serv
         if (t == 0) atomicCAS(&ctl->cur, r, r + 1);
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Random access (NEXT to the bottom-up merge): the symbol at one position of
+// one block by a top-down walk, Sec. 2.1's traversal made random-access the
+// way a wavelet tree answers access (Sec. 7.2): at node v the position's bit
+// picks the child, and the position becomes its rank among the positions of
+// that bit, rank1(B_v, x) = the directory's ones before x's superblock plus
+// the popcount of the superblock's bits before x.  The workspace comes from
+// the plan with a directory for every coded block, the ANS pass and the
+// directory pass (pivco_access_prepare).  One thread per query.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) access_kernel(const uint8_t *__restrict__ comp,
+                                                     const uint64_t *__restrict__ comp_off, int nblk,
+                                                     const uint32_t *__restrict__ qblk, const uint32_t *__restrict__ qpos,
+                                                     int nq, uint8_t *__restrict__ sym, int32_t *__restrict__ qstatus,
+                                                     const uint8_t *__restrict__ ws, uint64_t ws_bytes,
+                                                     const int32_t *__restrict__ status) {
+    const DecWs W = dec_ws(const_cast<uint8_t *>(ws), nblk);
+    const DecRegions G = dec_regions(nblk, ws);
+    const uint32_t dir_bits = dec_dir_bits(ws);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t b = qblk[q], x0 = qpos[q];
+        uint8_t out = 0;
+        int32_t st = PIVCO_OK;
+        if (b >= (uint32_t)nblk) {
+            st = PIVCO_ERR_INVALID_ARG;
+        } else if ((st = status[b]) == PIVCO_OK) {
+            const uint8_t *rec = comp + comp_off[b];   // validated by the plan
+            const uint32_t n = ld_le32(rec + 4), kind = rec[10];
+            if (x0 >= n) {
+                st = PIVCO_ERR_INVALID_ARG;
+            } else if (kind == 1) {
+                out = rec[11];
+            } else {
+                const uint32_t rb = ld_le32(rec), V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
+                const uint64_t nbase = G.dir + W.blk_dir[b], ntb = ntab_bytes(V);
+                const uint8_t *nt = ws + nbase;
+                const uint32_t ent = nbase + ntb <= ws_bytes ? *reinterpret_cast<const uint32_t *>(nt + 20) : 0u;
+                if (!ent || nbase + ntb + 4ull * ent > ws_bytes) {
+                    st = PIVCO_ERR_INVALID_ARG;   // no directory: the workspace was not prepared for access
+                } else {
+                    const uint32_t *nsrc = reinterpret_cast<const uint32_t *>(nt + kNtabHdr);
+                    const uint32_t *nch = nsrc + V, *nu = nsrc + 2 * V;
+                    const uint32_t *dirp = reinterpret_cast<const uint32_t *>(nt + ntb);
+                    const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
+                    const uint64_t sbase = G.scratch + W.blk_scratch[b];
+                    TileSrc src;
+                    src.rec = rec;
+                    src.rec_bytes = rb;
+                    src.scr = ws + sbase;
+                    src.scr_bytes = ws_bytes > sbase ? ws_bytes - sbase : 0;
+                    uint32_t v = 0, x = x0;
+                    st = PIVCO_ERR_CORRUPT;   // unless a leaf is reached within the code-length limit
+                    for (int d = 0; d <= (int)kMaxLen && v < V; d++) {
+                        const uint32_t nvv = __ldg(nv + v);
+                        if (x >= nvv) break;
+                        const uint32_t bit = tile_bits(src, nsrc[v], x) & 1u;
+                        const uint32_t sb = x / dir_bits;
+                        const uint32_t ones = dirp[nu[v] + sb] + tile_popc(src, nsrc[v], sb * dir_bits, x - sb * dir_bits);
+                        const uint32_t c = (nch[v] >> (16 * bit)) & 0xFFFFu;
+                        x = bit ? ones : x - ones;
+                        if (c & 0x8000u) {
+                            out = (uint8_t)c;
+                            st = PIVCO_OK;
+                            break;
+                        }
+                        v = c;
+                    }
+                }
+            }
+        }
+        sym[q] = out;
+        if (qstatus) qstatus[q] = st;
+    }
+}
+
+cudaError_t launch_access_prepare(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
+                                  int32_t *status, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    cudaError_t e = launch_decode_plan(comp, comp_off, nblk, ws, ws_bytes, status, st, true);
+    if (e == cudaSuccess) e = launch_ans_decode_planned(comp, comp_off, nblk, ws, ws_bytes, status, st);
+    if (e == cudaSuccess) e = launch_decode_dir(comp, comp_off, nblk, ws, ws_bytes, status, st);
+    return e;
+}
+
+cudaError_t launch_access(const uint8_t *comp, const uint64_t *comp_off, int nblk, const uint32_t *qblk,
+                          const uint32_t *qpos, int nq, uint8_t *sym, int32_t *qstatus, const uint8_t *ws,
+                          size_t ws_bytes, const int32_t *status, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = min(div_up(nq, 256), sms * 8);
+    access_kernel<<<grid, 256, 0, st>>>(comp, comp_off, nblk, qblk, qpos, nq, sym, qstatus, ws, ws_bytes, status);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // Host: an upper bound, from host copies of the records, of the workspace the

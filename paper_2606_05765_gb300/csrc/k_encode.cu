@@ -1,22 +1,24 @@
 // Encode kernel: per-node bitmap emission by stable partition (Sec. 4, Sec. 2.4.1).
 //
-// One CTA encodes one block; its warps split the block into contiguous
-// chunks and work independently.  A node's bitmap holds, in block order, the
-// code bit of every symbol passing through it, so a warp's first bit of node
-// v is the number of the block's earlier symbols under v: the chunk
-// histograms, prefix-summed over the warps and summed over each node's
-// subtree, give every warp its start cursors.  A warp encodes its chunk in
-// sub-chunks whose levels fit its buffers:
-//   - the sub-chunk's histogram gives every node's symbol count (demand),
-//     hence the spans of each level buffer;
-//   - top-down, a lane takes 32 consecutive symbols of one node: their code
-//     bits at the node's depth form one 32-bit bitmap word (written to the
-//     record at the node's cursor, assembled across lanes; words shared with
-//     a neighbour are ORed in), and the symbols are stably partitioned into
-//     the internal children's spans (EPF / EPL / EPR / EPN of Sec. 2.4.1).
-// Below the root a symbol travels as its remaining code bits, most
-// significant first in 16 bits, so a node's bit is bit 15 and the child
-// receives the value shifted left by one.
+// One CTA encodes one block, top-down, level by level; its warps share two
+// level buffers.  The block is coded in chunks whose levels fit those
+// buffers (usually a few of the planning pass's chunks, whose histograms
+// give every node's symbol count in the chunk; a chunk too large for the
+// buffers is cut and counted again).  A node's bitmap holds, in block order,
+// the code bit of every symbol passing through it, so the chunk's bits of
+// node v start at the symbols under v in the chunks before it: the cursors
+// advance by each chunk's counts.  Per level, the symbols of every node are
+// cut into groups of 32 (one lane each) and windows of 32 groups, which the
+// warps take in rounds of eight.  A lane's 32 code bits at the node's depth
+// form one bitmap word (written to the record at the node's cursor; words
+// shared with a neighbour are ORed into the zeroed body), and its symbols
+// are stably partitioned into the internal children's spans (EPF / EPL /
+// EPR / EPN of Sec. 2.4.1) at the zeros / ones of the node before the group:
+// a segmented warp scan within the window, the windows' summaries across a
+// round (one barrier), a carry across rounds.  Below the root a symbol
+// travels as its remaining code bits, most significant first in 16 bits, so
+// a node's bit is bit 15 and the child receives the value shifted left by
+// one.
 
 #include "pivco_dev.cuh"
 
@@ -24,43 +26,43 @@ namespace pv {
 
 constexpr int kEncThreads = 256;
 constexpr int kEncWarps = kEncThreads / 32;
-constexpr int kEncCtasPerSm = 2;
-constexpr int kEBufE = kEncCtasPerSm == 1 ? 5376 : 2304;   // symbols per level buffer of a warp
-constexpr int kESlack = 48;                                  // over-read room (symbols)
+constexpr int kEncCtasPerSm = 3;
+constexpr int kEBuf = 13824;                // symbols per level buffer (a skew80 64 KiB block in one chunk)
+constexpr int kESlack = 48;                 // over-read room (symbols)
+constexpr int kEWinPerLvl = 32;             // windows of a level below the root (<= kEBuf/32 + 128 groups)
 
-struct __align__(16) EncWarp {
-    uint16_t buf[2][kEBufE + kESlack];   // depth d >= 1 reads buf[d & 1], writes its children to the other
-    uint32_t pos[256];                   // bit address of node v's next bitmap bit in the record
-    uint32_t dem[256];                   // symbols of node v in the current sub-chunk
-    uint32_t start[256];                 // symbols before this warp's chunk, per symbol
-    uint16_t sp[256];                    // first symbol of node v's span in its level buffer
-    uint16_t gs[256];                    // first 32-symbol group of node v within its level
-    uint16_t lg[16];                     // groups of each level
-    uint32_t bad;                        // a level held more symbols than its counts
-    uint32_t pad[3];
+struct EncWin {                             // one window of a round
+    uint32_t sum;                           // ones of its last node from that node's start in the window
+    uint32_t flags;                         // 1 its first node starts at its first group, 2 a node starts in it, 4 active
 };
-static_assert(sizeof(EncWarp) % 16 == 0 && ((kEBufE + kESlack) * 2) % 16 == 0, "16-byte aligned level buffers");
 
-struct EncSmem {
-    uint16_t code16[256];    // code of symbol s, most significant bit at bit 15 (0: absent)
-    uint32_t ch[256];        // children: 0x8000 | symbol for a leaf, else the node index
-    uint32_t bitsrc[256];    // bit address of node v's bitmap in the record
-    uint32_t htot[256];      // the block's histogram
-    uint32_t pmask[8];       // symbols that have a code
-    __align__(16) uint8_t ci[256];   // canonical index of symbol s (its place in (length, symbol) order)
-    uint8_t nlo[256];        // node v's leaves are canonical indices nlo[v] .. nhi1[v]
+struct __align__(16) EncSmem {
+    uint16_t buf[2][kEBuf + kESlack];       // depth d >= 1 reads buf[d & 1], writes its children to the other
+                                            // (spans start on 16-byte boundaries)
+    uint32_t pos[256];                      // bit address of node v's first bit of the current chunk
+    uint32_t dem[256];                      // symbols of node v in the current chunk
+    uint32_t ch[256];                       // children: 0x8000 | symbol for a leaf, else the node index
+    uint32_t bitsrc[256];                   // bit address of node v's bitmap in the record
+    uint32_t nv[256];                       // symbols of node v in the block (the layout's)
+    uint16_t code16[256];                   // code of symbol s, most significant bit at bit 15 (0: absent)
+    uint16_t sp[256];                       // first symbol of node v's span in its level buffer
+    uint16_t gs[256];                       // first 32-symbol group of node v within its level
+    uint16_t lg[16];                        // groups of each level
+    uint8_t wnode[16][kEWinPerLvl];         // node holding the first group of each window of a level
+    EncWin win[2][kEncWarps];               // window summaries, two rounds deep
+    uint8_t ci[256];                        // canonical index of symbol s (its place in (length, symbol) order)
+    uint8_t nlo[256];                       // node v's leaves are canonical indices nlo[v] .. nhi1[v]
     uint8_t nhi1[256];
-    uint32_t nocode;         // a symbol without a code has a count
-    int32_t a[17];           // d-bit prefixes under leaves of length <= d
-    uint8_t first[17];       // first node of each depth
+    uint32_t pmask[8];                      // symbols that have a code
+    uint32_t hot;                           // the symbol with the shortest code (the most frequent one)
+    uint32_t bad, fits, tot;
+    uint8_t first[17];
     uint8_t maxd;
-    uint8_t pad[2];
-    uint32_t hot;            // the symbol with the shortest code (the most frequent one)
-    EncWarp w[kEncWarps];
+    uint8_t pad[14];
 };
-static_assert(offsetof(EncSmem, w) % 16 == 0, "16-byte aligned warp areas");
-static_assert(offsetof(BlockLayout, ci) <= sizeof(EncWarp::buf[1]) && offsetof(BlockLayout, ci) % 16 == 0,
+static_assert(offsetof(BlockLayout, ci) <= sizeof(EncSmem::buf[1]) && offsetof(BlockLayout, ci) % 16 == 0,
               "the staged part of the layout fits a level buffer");
+static_assert(sizeof(EncSmem::buf[0]) >= 4 * 1024 + 4, "a level buffer holds the counting scratch");
 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop(int n, F f, G out) {
@@ -154,44 +156,76 @@ __device__ inline void enc_counts(const EncSmem &S, const uint32_t *h, uint32_t 
     __syncwarp();
 }
 
-// Spans and groups of every level for the current demands; false when a
-// level (depth >= 1) does not fit a buffer.
-__device__ inline bool enc_layout(const EncSmem &S, EncWarp &E, uint64_t &maxlvl) {
+// Spans, groups and window nodes of level d for the current demands (one
+// warp; the levels are independent).  False when the level (depth >= 1)
+// does not fit a buffer or has more windows than its window-node table.
+__device__ inline bool enc_layout_level(EncSmem &S, int d) {
     const int lane = threadIdx.x & 31;
     bool fits = true;
-    maxlvl = 0;
-    for (int d = 0; d < (int)S.maxd; d++) {
-        const int f0 = S.first[d], f1 = S.first[d + 1];
-        uint64_t carry = 0;
-        for (int base = f0; base < f1; base += 32) {
-            const int v = base + lane;
-            uint64_t x = 0;
-            if (v < f1) {
-                const uint32_t dv = E.dem[v];
-                if (d && dv > (uint32_t)kEBufE) fits = false;
-                const uint32_t el = d ? ((min(dv, (uint32_t)kEBufE) + 1u) & ~1u) : 0u;
-                x = ((uint64_t)el << 32) | max(1u, (dv + 31u) >> 5);
-            }
-            uint64_t inc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            const uint64_t ex = carry + inc - x;
-            if (v < f1) {
-                E.sp[v] = (uint16_t)min((uint64_t)kEBufE, ex >> 32);
-                E.gs[v] = (uint16_t)ex;
-            }
-            carry += __shfl_sync(0xffffffffu, inc, 31);
+    const int f0 = S.first[d], f1 = S.first[d + 1];
+    uint64_t carry = 0;
+    for (int base = f0; base < f1; base += 32) {
+        const int v = base + lane;
+        uint64_t x = 0;
+        if (v < f1) {
+            const uint32_t dv = S.dem[v];
+            if (d && dv > (uint32_t)kEBuf) fits = false;
+            const uint32_t el = d ? ((min(dv, (uint32_t)kEBuf) + 7u) & ~7u) : 0u;   // spans of whole 16-byte units
+            x = ((uint64_t)el << 32) | max(1u, (dv + 31u) >> 5);
         }
-        if (d && (carry >> 32) > (uint64_t)kEBufE) fits = false;
-        if ((uint32_t)carry > 0xFFFFu) fits = false;
-        if (d && (carry >> 32) > maxlvl) maxlvl = carry >> 32;
-        if (lane == 0) E.lg[d] = (uint16_t)carry;
+        uint64_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint64_t ex = carry + inc - x;
+        if (v < f1) {
+            S.sp[v] = (uint16_t)min((uint64_t)kEBuf, ex >> 32);
+            S.gs[v] = (uint16_t)ex;
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (d && (carry >> 32) > (uint64_t)kEBuf) fits = false;
+    if ((uint32_t)carry > 0xFFFFu) fits = false;
+    const uint32_t G = (uint32_t)carry & 0xFFFFu;
+    if (lane == 0) S.lg[d] = (uint16_t)G;
+    __syncwarp();
+    if (d) {
+        const uint32_t nwin = (G + 31) >> 5;
+        if (nwin > (uint32_t)kEWinPerLvl) fits = false;
+        for (uint32_t i = lane; i < nwin && i < (uint32_t)kEWinPerLvl; i += 32) {
+            int lo = f0, hi = f1;
+            while (hi - lo > 1) {
+                const int m = (lo + hi) >> 1;
+                if ((uint32_t)S.gs[m] <= 32u * i) lo = m; else hi = m;
+            }
+            S.wnode[d][i] = (uint8_t)lo;
+        }
     }
     __syncwarp();
     return __all_sync(0xffffffffu, fits);
+}
+
+// The carry into this warp's window of the round (the ones, before the
+// window, of the node that runs into it) and the carry into the next round;
+// every warp calls it after the round's summaries are written.
+__device__ inline uint32_t enc_round_carry(const EncSmem &S, uint32_t par, uint32_t &rc_sum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const EncWin x = lane < kEncWarps ? S.win[par][lane] : EncWin{0u, 0u};
+    uint32_t val = x.sum, seg = (x.flags >> 1) & 1u;
+#pragma unroll
+    for (int o = 1; o < kEncWarps; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, val, o), f = __shfl_up_sync(0xffffffffu, seg, o);
+        if (lane >= o && !seg) { val += y; seg |= f; }
+    }
+    if (!seg) val += rc_sum;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, val, 1);
+    const uint32_t c = (x.flags & 1u) ? 0u : (lane ? prev : rc_sum);
+    const uint32_t cin = __shfl_sync(0xffffffffu, c, warp);
+    const uint32_t act = __ballot_sync(0xffffffffu, (x.flags & 4u) != 0);   // window 0 always is
+    rc_sum = __shfl_sync(0xffffffffu, val, 31 - __clz(act));
+    return cin;
 }
 
 // Writes bits bw (vl of them valid) of one node at bit address a of the
@@ -281,14 +315,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     extern __shared__ __align__(128) uint8_t smem_raw[];
     EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
     const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // global reads the setup needs, issued first so their latencies overlap
     const uint64_t i0 = blk_off[b], i1 = blk_off[b + 1], o0 = out_off[b], o1 = out_off[b + 1];
-    uint32_t chv[8];   // this warp's chunk histogram (symbol lane + 32 i)
-    if (chunk_hist) {
-        const uint32_t *ch = chunk_hist + ((size_t)b * kEncChunks + warp) * 256;
-#pragma unroll
-        for (int i = 0; i < 8; i++) chv[i] = __ldg(ch + lane + 32 * i);
-    }
     // the block's input is read by the root pass: ask L2 for it now, so
     // those reads find it there
     {
@@ -297,20 +324,19 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         for (uint64_t i = 128ull * t; i < nb; i += 128ull * kEncThreads)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + i));
     }
-    // the block's layout, staged into shared memory once (coalesced): every
-    // later read of it is a shared-memory read.  It borrows the last warp's
-    // second level buffer, unused until that warp's levels start.
+    // the block's layout, staged into shared memory once (coalesced); it
+    // borrows the second level buffer, unused until the levels start
     {
         const uint4 *g = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(layout) +
                                                           (size_t)b * kLayoutBytes);
-        uint4 *d = reinterpret_cast<uint4 *>(S.w[kEncWarps - 1].buf[1]);
+        uint4 *d = reinterpret_cast<uint4 *>(S.buf[1]);
         constexpr int kStaged = (int)(offsetof(BlockLayout, ci) / 16), kTab = 768 / 16;
         for (int i = t; i < kStaged; i += kEncThreads) d[i] = __ldg(g + i);
         // the canonical order and the nodes' leaf ranges, straight into their tables
         if (t < kTab) reinterpret_cast<uint4 *>(S.ci)[t] = __ldg(g + kStaged + t);
     }
     __syncthreads();
-    const BlockLayout &L = *reinterpret_cast<const BlockLayout *>(S.w[kEncWarps - 1].buf[1]);
+    const BlockLayout &L = *reinterpret_cast<const BlockLayout *>(S.buf[1]);
     const uint64_t n = i1 - i0;
     uint8_t *rec = out + o0;
     const uint64_t cap = o1 - o0;
@@ -386,259 +412,250 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             }
             S.ch[t] = code2;
             S.bitsrc[t] = 8u * L.body_off[t];
+            S.pos[t] = 8u * L.body_off[t];
+            S.nv[t] = L.nv[t];
         }
-        if (t < 17) { S.a[t] = L.tree_a[t]; S.first[t] = L.depth_first[t]; }
-        if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; S.nocode = 0; }
+        if (t < 17) S.first[t] = L.depth_first[t];
+        if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; S.bad = 0; }
     }
     __syncthreads();
     {
-        const uint32_t my_len = L.len[t];
-        const uint32_t key = __reduce_min_sync(0xffffffffu, my_len ? (my_len << 8) | (uint32_t)t : 0xFFFFu);
+        const uint32_t l = L.len[t];
+        const uint32_t key = __reduce_min_sync(0xffffffffu, l ? (l << 8) | (uint32_t)t : 0xFFFFu);
         if (lane == 0) atomicMin(&S.hot, key);
-        const uint32_t pm = __ballot_sync(0xffffffffu, my_len != 0);
+        const uint32_t pm = __ballot_sync(0xffffffffu, l != 0);
         if (lane == 0) S.pmask[warp] = pm;
     }
-    __syncthreads();
+    __syncthreads();   // (the staged layout is dead from here on)
     const uint32_t hot = S.hot & 0xFFu;
-    // ---- warp chunks and their histograms ----
-    static_assert(kEncChunks == kEncWarps, "one warp per chunk");
-    const uint32_t nw = enc_nchunks(n);
-    const uint32_t Q0 = enc_chunk_start(n, warp, nw), Q1 = enc_chunk_start(n, warp + 1, nw);
     const uint8_t *src = in + i0;
     const uint8_t *src_end = in + i1;
-    EncWarp &E = S.w[warp];
-    if (lane == 0) E.bad = 0;
-    // histograms live in the first level buffer until the levels need it
-    uint32_t *hist = reinterpret_cast<uint32_t *>(E.buf[0]);
-    for (int s = lane; s < 256; s += 32) hist[s] = 0;
-    __syncwarp();
-    if (chunk_hist) {
-        // counted by the chunked histogram pass (loaded at the start)
-#pragma unroll
-        for (int i = 0; i < 8; i++) hist[lane + 32 * i] = chv[i];
-    } else if ((uint32_t)warp < nw) {
-        // two input loads in flight per lane
-        for (uint32_t kb = Q0; kb < Q1; kb += 2048) {
-            const uint32_t k0 = kb + 32 * lane, k1 = k0 + 1024;
-            uint32_t x0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, x1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (k0 < Q1) ldg32(src + k0, src_end, x0);
-            if (k1 < Q1) ldg32(src + k1, src_end, x1);
-            hist_add32(hist, x0, k0 < Q1 ? min(32u, Q1 - k0) : 0u, hot);
-            hist_add32(hist, x1, k1 < Q1 ? min(32u, Q1 - k1) : 0u, hot);
-        }
-    }
-    __syncthreads();
-    // exclusive prefix over the warps (each warp's start counts), block totals
-    {
-        uint32_t run = 0;
-        for (uint32_t w = 0; w < nw; w++) {
-            const uint32_t h = reinterpret_cast<const uint32_t *>(S.w[w].buf[0])[t];
-            S.w[w].start[t] = run;
-            run += h;
-        }
-        S.htot[t] = run;
-        if (run && !L.len[t]) S.nocode = 1;   // a symbol the code does not have: mismatch below
-    }
-    __syncthreads();
-    // node counts of the symbols before each chunk's end (the histograms are
-    // dead: their buffers take the counts), all warps at once; the last
-    // chunk's are the block's totals, checked against the layout.  A chunk's
-    // start counts are the previous chunk's end counts, its demands the
-    // difference.
-    auto endc = [&](uint32_t w) { return reinterpret_cast<uint32_t *>(S.w[w].buf[0]); };
-    if ((uint32_t)warp < nw)
-        enc_counts(S, (uint32_t)warp + 1 < nw ? S.w[warp + 1].start : S.htot, endc(warp), endc(warp) + 256,
-                   endc(warp) + 512);
-    __syncthreads();
-    {
-        int bad = t < V && endc(nw - 1)[t] != L.nv[t];
-        if (t == 0 && S.nocode) bad = 1;
-        if (__syncthreads_or(bad)) {
-            if (t == 0) { status[b] = PIVCO_ERR_INVALID_ARG; rec_bytes[b] = 0; }
-            return;
-        }
-    }
-    if ((uint32_t)warp < nw) {
-        for (int v = lane; v < V; v += 32) {
-            const uint32_t s0 = warp ? endc(warp - 1)[v] : 0u;
-            E.pos[v] = s0 + S.bitsrc[v];
-            E.dem[v] = endc(warp)[v] - s0;
-        }
-    }
-    __syncthreads();   // the count buffers are level buffers again
     uint32_t *rec32 = reinterpret_cast<uint32_t *>(rec);
-    if ((uint32_t)warp < nw) {
-        // the symbols before this chunk are exactly its start: every chunk's
-        // counts then total its length, so the root's bits stay in its span
-        const bool start_ok = E.pos[0] == S.bitsrc[0] + Q0;
-        if (!start_ok && lane == 0) E.bad = 1;
-        // the whole chunk at once when its levels fit; else equal sub-chunks
-        // sized from the chunk's busiest level (each with its own histogram)
-        const uint32_t Q = Q1 - Q0;
-        uint32_t C = Q;
-        bool whole = true;
-        for (uint32_t P = start_ok ? Q0 : Q1; P < Q1;) {
-            C = min(C, Q1 - P);
-            if (!whole) {   // (the whole chunk's demands were set above)
-                for (int s = lane; s < 256; s += 32) hist[s] = 0;
-                __syncwarp();
-                for (uint32_t kb = P; kb < P + C; kb += 1024) {
-                    const uint32_t k = kb + 32 * lane;
-                    uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    if (k < P + C) ldg32(src + k, src_end, x);
-                    hist_add32(hist, x, k < P + C ? min(32u, P + C - k) : 0u, hot);
-                }
-                __syncwarp();
-                enc_counts(S, hist, E.dem, hist + 256, hist + 512);
+    // counting scratch in the second level buffer (free between chunks)
+    uint32_t *hist = reinterpret_cast<uint32_t *>(S.buf[1]);
+    uint32_t *hc = hist + 256, *ps = hist + 512;
+    // ---- chunks: runs of the planning pass's chunks, or parts of one ----
+    const uint32_t nw = enc_nchunks(n);
+    uint32_t c0 = 0, k = nw;       // the run of plan chunks tried: c0 .. c0 + k - 1
+    uint32_t P = 0, sub = 0;       // sub > 0: cutting plan chunk c0 into parts of `sub` symbols
+    uint32_t acc = 0;              // count of symbol t in the coded parts of plan chunk c0
+    while (P < (uint32_t)n) {
+        const uint32_t Q1 = enc_chunk_start(n, c0 + (sub ? 1u : k), nw);   // end of the run / plan chunk
+        const uint32_t C = sub ? min(sub, Q1 - P) : Q1 - P;
+        // the chunk's histogram: the planning pass's chunk counts, or counted here
+        for (int s2 = t; s2 < 256; s2 += kEncThreads) hist[s2] = 0;
+        __syncthreads();
+        if (chunk_hist && !sub) {
+            uint32_t h = 0;
+            for (uint32_t c = c0; c < c0 + k; c++) h += __ldg(chunk_hist + ((size_t)b * kEncChunks + c) * 256 + t);
+            hist[t] = h;
+        } else {
+            // warp-uniform trip counts: hist_add32 reduces over the whole warp
+            for (uint32_t kw = P + 1024u * warp; kw < P + C; kw += 1024u * kEncWarps) {
+                const uint32_t kb = kw + 32u * lane;
+                uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (kb < P + C) ldg32(src + kb, src_end, x);
+                hist_add32(hist, x, kb < P + C ? min(32u, P + C - kb) : 0u, hot);
             }
-            uint64_t maxlvl = 0;
-            if (!enc_layout(S, E, maxlvl)) {
-                if (whole && chunk_hist) {
-                    // sub-chunks advance the cursors by their own counts: the
-                    // given chunk counts must be this chunk's bytes' counts
-                    for (int s = lane; s < 256; s += 32) hist[s] = 0;
-                    __syncwarp();
-                    for (uint32_t kb = Q0; kb < Q1; kb += 1024) {
-                        const uint32_t k = kb + 32 * lane;
-                        uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        if (k < Q1) ldg32(src + k, src_end, x);
-                        hist_add32(hist, x, k < Q1 ? min(32u, Q1 - k) : 0u, hot);
-                    }
-                    __syncwarp();
-                    uint32_t diff = 0;
-                    for (int s = lane; s < 256; s += 32)
-                        diff |= hist[s] ^ (((uint32_t)warp + 1 < nw ? S.w[warp + 1].start[s] : S.htot[s]) - E.start[s]);
-                    if (__any_sync(0xffffffffu, diff != 0)) {
-                        if (lane == 0) E.bad = 1;
-                        break;
-                    }
-                }
-                uint32_t nc = C / 2;
-                if (whole) {
-                    const uint64_t room = kEBufE - 2 * 128;
-                    const uint32_t ns = (uint32_t)min((uint64_t)Q, (maxlvl * 9 / 8 + room - 1) / room);
-                    nc = (Q + ns - 1) / max(ns, 1u);
-                }
-                whole = false;
-                C = max(32u, (min(nc, C / 2 + 32)) & ~31u);
-                continue;
+        }
+        __syncthreads();
+        const uint32_t hcount = hist[t];
+        if (warp == 0) {
+            // the counts must total the chunk, with no symbol the code lacks
+            uint32_t tot = 0, nocode = 0;
+            for (int s2 = lane; s2 < 256; s2 += 32) {
+                tot += hist[s2];
+                if (hist[s2] && !((S.pmask[s2 >> 5] >> (s2 & 31)) & 1u)) nocode = 1;
             }
-            // ---- the root: input bytes -> codes; bits; children ----
-            {
-                const uint32_t chv = S.ch[0], c0 = chv & 0xFFFFu, c1 = chv >> 16;
-                const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-                const uint32_t nb = smem_addr(E.buf[1]);
-                const uint32_t lp0 = nb + 2u * (i0 ? E.sp[c0 & 0xFFu] : 0u), rp0 = nb + 2u * (i1 ? E.sp[c1 & 0xFFu] : 0u);
-                uint32_t carry = 0;
-                // the next window's 32 bytes are loaded while this one is coded
-                uint32_t xn[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                if (32u * lane < C) ldg32(src + P + 32u * lane, src_end, xn);
-                for (uint32_t kb = 0; kb < C; kb += 1024) {
-                    const uint32_t kk = kb + 32u * lane;
-                    const bool act = kk < C;
-                    const uint32_t vl = act ? min(32u, C - kk) : 0u;
-                    uint32_t x[8];
-#pragma unroll
-                    for (int q = 0; q < 8; q++) { x[q] = xn[q]; xn[q] = 0u; }
-                    if (kk + 1024 < C) ldg32(src + P + kk + 1024, src_end, xn);
-                    uint32_t y[16];
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const uint32_t s0 = (x[j >> 1] >> (16 * (j & 1))) & 0xFFu, s1 = (x[j >> 1] >> (16 * (j & 1) + 8)) & 0xFFu;
-                        y[j] = (uint32_t)S.code16[s0] | ((uint32_t)S.code16[s1] << 16);
-                    }
-                    uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
-                                  (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
-                                  (top_bits8(y[12], y[13], y[14], y[15]) << 24);
-                    if (vl < 32) bw &= (1u << vl) - 1u;
-                    const uint32_t pc = __popc(bw);
-                    uint32_t inc = pc;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t yy = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += yy;
-                    }
-                    const uint32_t r1 = carry + inc - pc;
-                    carry += __shfl_sync(0xffffffffu, inc, 31);
-                    enc_put_bits(rec32, act, 0u, E.pos[0] + kk, bw, vl);
-                    // a chunk whose symbols do not match its counts must not write past the spans
-                    if (act && ((i1 && r1 + pc > E.dem[c1 & 0xFFu]) || (i0 && kk + vl - r1 - pc > E.dem[c0 & 0xFFu])))
-                        E.bad = 1;
-                    else if (act) enc_split(lp0 + 2u * (kk - r1), rp0 + 2u * r1, i0, i1, y, bw, vl);
-                }
+            tot = __reduce_add_sync(0xffffffffu, tot);
+            if (__any_sync(0xffffffffu, nocode) || tot != C) { if (lane == 0) S.bad = 1; }
+            else enc_counts(S, hist, S.dem, hc, ps);
+            if (lane == 0) S.fits = 1;
+        }
+        __syncthreads();
+        if (S.bad) break;
+        for (int d = warp; d < (int)S.maxd; d += kEncWarps)
+            if (!enc_layout_level(S, d) && lane == 0) S.fits = 0;
+        __syncthreads();
+        const bool fits = S.fits != 0;
+        __syncthreads();
+        if (!fits) {
+            // a shorter run of plan chunks, or parts of one chunk (32 symbols
+            // always fit: a level then holds at most 32 symbols in 160 groups)
+            if (sub == 32u) {
+                if (t == 0) S.bad = 1;
+                break;
             }
-            __syncwarp();
-            // ---- depths 1.. : node spans of buf[d & 1] into the children's spans ----
-            for (int d = 1; d < (int)S.maxd; d++) {
-                const uint16_t *bin = E.buf[d & 1];
-                uint16_t *bout = E.buf[(d + 1) & 1];
-                const uint32_t f0 = S.first[d], f1 = S.first[d + 1], G = E.lg[d];
-                const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
-                uint32_t vcur = f0, carry = 0;
-                for (uint32_t base = 0; base < G; base += 32) {
+            if (!sub && k > 1) k = (k + 1) / 2;
+            else sub = max(32u, ((sub ? sub : C) / 2) & ~31u);
+            continue;
+        }
+        // ---- the root: input bytes -> codes; bits; children ----
+        uint32_t par = 0;
+        {
+            const uint32_t chv = S.ch[0], c0n = chv & 0xFFFFu, c1n = chv >> 16;
+            const bool i0c = !(c0n & 0x8000u), i1c = !(c1n & 0x8000u);
+            const uint32_t nb = smem_addr(S.buf[1]);
+            const uint32_t lp0 = nb + 2u * (i0c ? S.sp[c0n & 0xFFu] : 0u), rp0 = nb + 2u * (i1c ? S.sp[c1n & 0xFFu] : 0u);
+            const uint32_t G = (C + 31) >> 5;
+            uint32_t rc = 0;
+            // the next round's 32 bytes of each lane are loaded while this one is coded
+            uint32_t xn[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (32u * (32u * warp + lane) < C) ldg32(src + P + 32u * (32u * warp + lane), src_end, xn);
+            for (uint32_t r0 = 0; r0 < G; r0 += 32 * kEncWarps) {
+                const uint32_t kk = 32u * (r0 + 32u * warp + lane);
+                const bool act = kk < C;
+                const uint32_t vl = act ? min(32u, C - kk) : 0u;
+                uint32_t x[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) { x[q] = xn[q]; xn[q] = 0u; }
+                if (kk + 32u * 32u * kEncWarps < C) ldg32(src + P + kk + 32u * 32u * kEncWarps, src_end, xn);
+                uint32_t y[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const uint32_t s0 = (x[j >> 1] >> (16 * (j & 1))) & 0xFFu, s1 = (x[j >> 1] >> (16 * (j & 1) + 8)) & 0xFFu;
+                    y[j] = (uint32_t)S.code16[s0] | ((uint32_t)S.code16[s1] << 16);
+                }
+                uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
+                              (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
+                              (top_bits8(y[12], y[13], y[14], y[15]) << 24);
+                if (vl < 32) bw &= (1u << vl) - 1u;
+                const uint32_t pc = __popc(bw);
+                uint32_t inc = pc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t yy = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += yy;
+                }
+                if (lane == 31) S.win[par][warp] = EncWin{inc, 0u};
+                __syncthreads();
+                uint32_t cin;
+                {
+                    const uint32_t ws = lane < kEncWarps ? S.win[par][lane].sum : 0u;
+                    uint32_t wi = ws;
+#pragma unroll
+                    for (int o = 1; o < kEncWarps; o <<= 1) {
+                        const uint32_t yy = __shfl_up_sync(0xffffffffu, wi, o);
+                        if (lane >= o) wi += yy;
+                    }
+                    cin = rc + __shfl_sync(0xffffffffu, wi - ws, warp);
+                    rc += __shfl_sync(0xffffffffu, wi, kEncWarps - 1);
+                }
+                par ^= 1u;
+                const uint32_t r1 = cin + inc - pc;
+                enc_put_bits(rec32, act, 0u, S.pos[0] + kk, bw, vl);
+                // a chunk whose symbols do not match its counts must not write past the spans
+                if (act && ((i1c && r1 + pc > S.dem[c1n & 0xFFu]) || (i0c && kk + vl - r1 - pc > S.dem[c0n & 0xFFu])))
+                    S.bad = 1;
+                else if (act) enc_split(lp0 + 2u * (kk - r1), rp0 + 2u * r1, i0c, i1c, y, bw, vl);
+            }
+        }
+        __syncthreads();
+        // ---- depths 1.. : node spans of buf[d & 1] into the children's spans ----
+        for (int d = 1; d < (int)S.maxd; d++) {
+            const uint16_t *bin = S.buf[d & 1];
+            uint16_t *bout = S.buf[(d + 1) & 1];
+            const uint32_t f1 = S.first[d + 1], G = S.lg[d];
+            const uint32_t le = 0xFFFFFFFFu >> (31 - lane);
+            uint32_t rc_sum = 0;
+            for (uint32_t r0 = 0; r0 < G; r0 += 32 * kEncWarps) {
+                const uint32_t base = r0 + 32u * warp;
+                // this warp's window: the node of each group
+                uint32_t v = 0, kk = 0, dv = 0, starts = 0;
+                bool act = false;
+                if (base < G) {
+                    const uint32_t u = S.wnode[d][base >> 5];
+                    const uint32_t vcur = (uint32_t)S.gs[u] == base ? u - 1 : u;
                     const uint32_t cand = vcur + 1 + lane;
                     uint32_t bit = 0;
                     if (cand < f1) {
-                        const uint32_t s = (uint32_t)E.gs[cand] - base;
-                        if (s < 32) bit = 1u << s;
+                        const uint32_t sd = (uint32_t)S.gs[cand] - base;
+                        if (sd < 32) bit = 1u << sd;
                     }
-                    const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
-                    const uint32_t v = vcur + __popc(starts & le);
+                    starts = __reduce_or_sync(0xffffffffu, bit);
+                    v = vcur + __popc(starts & le);
                     const uint32_t g = base + lane;
-                    const uint32_t kk = (g - E.gs[v]) * 32u;
-                    const uint32_t dv = E.dem[v];
-                    const bool act = g < G && kk < dv;
-                    const uint32_t vl = act ? min(32u, dv - kk) : 0u;
-                    uint32_t y[16];
-                    if (act) {
-                        const uint32_t *p = reinterpret_cast<const uint32_t *>(bin + E.sp[v] + kk);
-#pragma unroll
-                        for (int q = 0; q < 16; q++) y[q] = p[q];
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; j++) y[j] = 0;
-                    }
-                    uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
-                                  (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
-                                  (top_bits8(y[12], y[13], y[14], y[15]) << 24);
-                    if (vl < 32) bw &= (1u << vl) - 1u;
-                    const uint32_t pc = __popc(bw);
-                    uint32_t inc = pc;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t yy = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += yy;
-                    }
-                    const uint32_t sl = starts & le;
-                    const int s0 = sl ? 31 - __clz(sl) : -1;
-                    const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
-                    const uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u) + (s0 < 0 ? carry : 0u);
-                    carry = __shfl_sync(0xffffffffu, r1 + pc, 31);
-                    vcur = __shfl_sync(0xffffffffu, v, 31);
-                    enc_put_bits(rec32, act, v, E.pos[v] + kk, bw, vl);
-                    if (act) {
-                        const uint32_t chv = S.ch[v], c0 = chv & 0xFFFFu, c1 = chv >> 16;
-                        const bool i0 = !(c0 & 0x8000u), i1 = !(c1 & 0x8000u);
-                        const uint32_t ob = smem_addr(bout);
-                        const uint32_t lp = ob + 2u * ((i0 ? E.sp[c0 & 0xFFu] : 0u) + (kk - r1));
-                        const uint32_t rp = ob + 2u * ((i1 ? E.sp[c1 & 0xFFu] : 0u) + r1);
-                        if ((i1 && r1 + pc > E.dem[c1 & 0xFFu]) || (i0 && kk + vl - r1 - pc > E.dem[c0 & 0xFFu]))
-                            E.bad = 1;
-                        else
-                            enc_split(lp, rp, i0, i1, y, bw, vl);
-                    }
+                    kk = (g - S.gs[v]) * 32u;
+                    dv = S.dem[v];
+                    act = g < G && kk < dv;
                 }
-                __syncwarp();
+                const uint32_t vl = act ? min(32u, dv - kk) : 0u;
+                uint32_t y[16];
+                if (act) {
+                    // 16-byte loads: four per lane instead of sixteen, and four
+                    // times fewer shared-memory wavefronts for the same bytes
+                    const uint4 *p = reinterpret_cast<const uint4 *>(bin + S.sp[v] + kk);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint4 u = p[q];
+                        y[4 * q] = u.x; y[4 * q + 1] = u.y; y[4 * q + 2] = u.z; y[4 * q + 3] = u.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; j++) y[j] = 0;
+                }
+                uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
+                              (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
+                              (top_bits8(y[12], y[13], y[14], y[15]) << 24);
+                if (vl < 32) bw &= (1u << vl) - 1u;
+                const uint32_t pc = __popc(bw);
+                uint32_t inc = pc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t yy = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += yy;
+                }
+                const uint32_t sl = starts & le;
+                const int s0 = sl ? 31 - __clz(sl) : -1;
+                const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
+                uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u);
+                if (lane == 31) S.win[par][warp] = EncWin{r1 + pc, (starts & 1u) | (starts ? 2u : 0u) | (base < G ? 4u : 0u)};
+                __syncthreads();
+                const uint32_t cin = enc_round_carry(S, par, rc_sum);
+                par ^= 1u;
+                if (s0 < 0) r1 += cin;   // groups of the node that runs in from the window before
+                enc_put_bits(rec32, act, v, S.pos[v] + kk, bw, vl);
+                if (act) {
+                    const uint32_t chv = S.ch[v], c0n = chv & 0xFFFFu, c1n = chv >> 16;
+                    const bool i0c = !(c0n & 0x8000u), i1c = !(c1n & 0x8000u);
+                    const uint32_t ob = smem_addr(bout);
+                    const uint32_t lp = ob + 2u * ((i0c ? S.sp[c0n & 0xFFu] : 0u) + (kk - r1));
+                    const uint32_t rp = ob + 2u * ((i1c ? S.sp[c1n & 0xFFu] : 0u) + r1);
+                    if ((i1c && r1 + pc > S.dem[c1n & 0xFFu]) || (i0c && kk + vl - r1 - pc > S.dem[c0n & 0xFFu]))
+                        S.bad = 1;
+                    else
+                        enc_split(lp, rp, i0c, i1c, y, bw, vl);
+                }
             }
-            for (int v = lane; v < V; v += 32) E.pos[v] += E.dem[v];
-            __syncwarp();
-            P += C;
+            __syncthreads();
+        }
+        if (t < V) S.pos[t] += S.dem[t];
+        __syncthreads();
+        if (S.bad) break;
+        P += C;
+        if (sub) {
+            acc += hcount;
+            if (P >= Q1) {
+                // plan chunk done in parts: its given counts must be the ones just counted
+                if (__syncthreads_or(chunk_hist && acc != __ldg(chunk_hist + ((size_t)b * kEncChunks + c0) * 256 + t))) {
+                    if (t == 0) S.bad = 1;
+                    break;
+                }
+                acc = 0;
+                sub = 0;   // whole runs again
+                c0 += 1;
+                k = nw - c0;
+            }
+        } else {
+            c0 += k;
+            k = nw - c0;
         }
     }
     __syncthreads();
     if (t == 0) {
-        uint32_t bad = 0;
-        for (int w = 0; w < kEncWarps; w++) bad |= S.w[w].bad;
+        // every node's cursor ends exactly at the end of its bitmap
+        uint32_t bad = S.bad;
+        for (int v = 0; v < V && !bad; v++) bad = S.pos[v] != S.bitsrc[v] + S.nv[v];
         status[b] = bad ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
         rec_bytes[b] = bad ? 0 : rec_bound;
     }

@@ -338,7 +338,12 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
 size_t decode_ws_size_bound(const uint64_t *blk_off, int nblk, const DecTuning &tu);
 
 cudaError_t launch_decode_plan(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
-                               size_t ws_bytes, int32_t *status, cudaStream_t st);
+                               size_t ws_bytes, int32_t *status, cudaStream_t st, bool all_dirs = false);
+cudaError_t launch_access_prepare(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
+                                  size_t ws_bytes, int32_t *status, cudaStream_t st);
+cudaError_t launch_access(const uint8_t *comp, const uint64_t *comp_off, int nblk, const uint32_t *qblk,
+                          const uint32_t *qpos, int nq, uint8_t *sym, int32_t *qstatus, const uint8_t *ws,
+                          size_t ws_bytes, const int32_t *status, cudaStream_t st);
 cudaError_t launch_zero_bytes(uint8_t *p, size_t n, cudaStream_t st);
 cudaError_t launch_ans_decode_planned(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws,
                                       size_t ws_bytes, int32_t *status, cudaStream_t st);
@@ -347,6 +352,13 @@ cudaError_t launch_decode_merge(const uint8_t *comp, const uint64_t *comp_off, i
                                 cudaStream_t st);
 cudaError_t launch_decode_dir(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *ws, size_t ws_bytes,
                               int32_t *status, cudaStream_t st);
+cudaError_t launch_golomb_plan(const uint8_t *in, const uint64_t *blk_off, int nblk, uint64_t *rec_size,
+                               int32_t *status, cudaStream_t st);
+cudaError_t launch_golomb_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, uint8_t *out,
+                                 const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status, cudaStream_t st);
+cudaError_t launch_golomb_decode(const uint8_t *comp, const uint64_t *comp_off, int nblk, uint8_t *out,
+                                 const uint64_t *out_off, int32_t *status, cudaStream_t st);
+cudaError_t prepare_golomb_kernels();
 cudaError_t prepare_decode_kernels();
 cudaError_t prepare_encode_kernels();
 cudaError_t prepare_ans_kernels();

@@ -298,11 +298,13 @@ def _encode_with_chunks(P, enc, data, boff, ch, guard):
 
 
 def test_encode_chunked_stale_histograms(P):
-    """Chunk histograms that do not describe the input make an error status
-    for their blocks and never a write outside those blocks' records: chunk
-    histograms of other data (block totals differ), and of the same blocks
-    reversed (block totals agree, the chunks' do not; the shifting blocks
-    also take the sub-chunk path)."""
+    """Chunk histograms that do not describe the input never give a wrong
+    record with an OK status, nor a write outside the blocks' records: chunk
+    histograms of other data (block totals differ: an error status), and of
+    the same blocks reversed (block totals agree, the chunks' do not; the
+    shifting blocks also take the part-by-part path): each such block either
+    reports PIVCO_ERR_INVALID_ARG or, where the encoder coded together the
+    chunks whose summed counts are right, gives the exact record."""
     import torch
     w = shifting_workload()
     data, boff = dev(w.data), off64(w.blk_off)
@@ -328,13 +330,15 @@ def test_encode_chunked_stale_histograms(P):
     mixed[1::2] = stale.view(w.nblk, -1)[1::2]
     c, st3, rb3 = _encode_with_chunks(P, enc, data, boff, mixed.view(-1), guard)
     assert (c[:guard] == 0xA5).all() and (c[guard + total:] == 0xA5).all()
+    n_refused = 0
     for b in range(w.nblk):
-        if b % 2:
-            assert st3[b] == P.ERR_INVALID_ARG, (b, st3)
-        else:
-            assert st3[b] == 0 and rb3[b] == rb[b]
-            lo, hi = guard + int(off[b]), guard + int(off[b]) + int(rb[b])
-            assert np.array_equal(c[lo:hi], ref[lo:hi]), b
+        lo, hi = guard + int(off[b]), guard + int(off[b]) + int(rb[b])
+        if b % 2 and st3[b] == P.ERR_INVALID_ARG:
+            n_refused += 1
+            continue
+        assert st3[b] == 0 and rb3[b] == rb[b], (b, st3)
+        assert np.array_equal(c[lo:hi], ref[lo:hi]), b
+    assert n_refused >= 1    # (some odd block is cut where its chunk counts matter)
     # the right counts again: the records decode
     comp = torch.from_numpy(ref[guard:guard + total].copy()).cuda()
     out, st4 = P.decode(comp, enc.off, boff)
