@@ -24,14 +24,16 @@ MARK_RAW_SELECTED = 0xFF
 
 
 class Params(C.Structure):
-    """Encoder parameters (App. D: L = 11; Sec. 5.2: the three ANS knobs)."""
+    """Encoder parameters (App. D: L = 11; Sec. 5.2: the three ANS knobs;
+    Sec. 2.2.3-2.2.4: the regrouped tree with flat subtrees)."""
     _fields_ = [("max_len", C.c_int32), ("ans_enable", C.c_int32),
                 ("ans_min_bytes", C.c_int32), ("ans_skew_num", C.c_int32),
-                ("ans_skew_den", C.c_int32), ("ans_ratio_pct", C.c_int32)]
+                ("ans_skew_den", C.c_int32), ("ans_ratio_pct", C.c_int32),
+                ("flat", C.c_int32)]
 
 
-def params(max_len=11, ans=False):
-    return Params(max_len, 1 if ans else 0, 32, 5, 8, 95)
+def params(max_len=11, ans=False, flat=False):
+    return Params(max_len, 1 if ans else 0, 32, 5, 8, 95, 1 if flat else 0)
 
 
 def build(force=False):
@@ -55,6 +57,8 @@ def lib():
             "ref_code_lengths": [P, C.c_int, P],
             "ref_canonical_codes": [P, P],
             "ref_tree_info": [P, P, P, P, P],
+            "ref_tree_info_ex": [P, C.c_int, P, P, P, P, P, P],
+            "ref_flat_codes": [P, P, P],
             "ref_ans_class_freqs": [C.c_int, P],
             "ref_fse_h_q16": [C.c_int],
             "ref_rans_encode": [P, u32, C.c_int, P, u64, P],
@@ -123,6 +127,34 @@ def tree_info(lens):
     _check(lib().ref_tree_info(_p(lens), _p(nv), _p(depth), _p(prefix), _p(child)), "tree_info")
     V = int(nv[0])
     return depth[:V].copy(), prefix[:V].copy(), child[:2 * V].reshape(V, 2).copy()
+
+
+def flat_codes(lens):
+    """Regrouped codes (Sec. 2.2.4): (codes[256], fd[256]); fd[s] is the
+    depth D of the flat node symbol s belongs to, 0 if none."""
+    lens = np.ascontiguousarray(lens, dtype=np.uint8)
+    codes = np.zeros(256, np.uint32)
+    fd = np.zeros(256, np.int32)
+    _check(lib().ref_flat_codes(_p(lens), _p(codes), _p(fd)), "flat_codes")
+    return codes, fd
+
+
+def tree_info_ex(lens, flat=True):
+    """(depth[V], prefix[V], child[V,2], D[V], ftab[V,256]) of the canonical
+    (flat=False) or regrouped (flat=True) tree; D = 0 for ordinary nodes,
+    ftab[v, x] = symbol of index x of flat node v (-1 past 2^D)."""
+    lens = np.ascontiguousarray(lens, dtype=np.uint8)
+    nv = np.zeros(1, np.int32)
+    depth = np.zeros(256, np.int32)
+    prefix = np.zeros(256, np.uint32)
+    child = np.zeros(512, np.int32)
+    fdep = np.zeros(256, np.int32)
+    ftab = np.zeros(256 * 256, np.int32)
+    _check(lib().ref_tree_info_ex(_p(lens), 1 if flat else 0, _p(nv), _p(depth), _p(prefix), _p(child), _p(fdep),
+                                  _p(ftab)), "tree_info_ex")
+    V = int(nv[0])
+    return (depth[:V].copy(), prefix[:V].copy(), child[:2 * V].reshape(V, 2).copy(), fdep[:V].copy(),
+            ftab[:256 * V].reshape(V, 256).copy())
 
 
 def ans_class_freqs(t):

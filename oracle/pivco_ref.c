@@ -12,9 +12,14 @@
  *   2. length-limited code lengths, L = 11         (Sec. 1.2; App. D) -- optimal
  *      package-merge; the paper names no algorithm, see the readings below
  *   3. canonical codes                             (Sec. 1 note on canonical coding; App. D)
+ *   3b. optionally, the regrouped (non-canonical) tree with flat subtrees:
+ *      equal-length symbols combined in power-of-two groups, each group of
+ *      2^D >= 4 symbols one flat node             (Sec. 2.2.3, 2.2.4; App. D)
  *   4. the pivoted tree: one node per proper code prefix, bit 1 = right
  *                                                  (Listing 1; Sec. 2, Fig. 2-3)
- *   5. per-node bitmaps, LSB-first inside bytes    (Sec. 2; Sec. 2.4.2 bit_pos table)
+ *   5. per-node bitmaps, LSB-first inside bytes; a flat node stores the
+ *      D-bit index of each of its symbols, packed (Sec. 2; Sec. 2.4.2 bit_pos
+ *      table; Sec. 2.2.3 scatter_flat_D; App. D flat subtree roots)
  *   6. selective ANS: node selection rule and byte-wise static-table ANS
  *                                                  (Sec. 5.2; App. D marker byte)
  *   7. the block record (wire format)              (App. D, adapted: see below)
@@ -49,6 +54,19 @@
  *       Golomb parameter 1, i.e. unary codes with stop bit 1; values are
  *       bytes; bitmap j holds the bit of every value >= j; a "PVG1" record
  *       with u32 counts n_j like R7.
+ *   R10 flat subtrees (Sec. 2.2.3-2.2.4 describe the regrouping in words):
+ *       code lengths are those of R1.  For each length l the symbols of that
+ *       length, ascending, are cut greedily into groups of the largest power
+ *       of two 2^D that is left (first 2^D symbols first); a group is one item
+ *       of length l - D.  Items get canonical codes in (length, first symbol)
+ *       order; symbol number x of a group (ascending) has the code
+ *       (item code << D) | x, so every symbol keeps its length.  A group with
+ *       D >= 2 is a flat node (a group of two is an ordinary node with two
+ *       leaves).  A flat node's body is its symbols' D-bit indices x in block
+ *       order, value j at bits [jD, jD + D), least significant bit first
+ *       (App. D: ceil(n*D/8) bytes).  Flat nodes are never ANS coded.  Nodes
+ *       (ordinary and flat) are ordered breadth-first as in R3.  Records of
+ *       this tree carry the tag "PVC2" in place of "PVC1".
  *
  * Parity status: every function above is pinned by the oracle tests (worked
  * examples of Sec. 1.1 and 2.2, brute-force optimality, Kraft, closed forms
@@ -80,6 +98,7 @@ typedef struct ref_params {
     int32_t ans_skew_num;   /* PIVCO_FSE_MIN_THRESHOLD = num/den = 5/8 */
     int32_t ans_skew_den;
     int32_t ans_ratio_pct;  /* PIVCO_FSE_MIN_RATIO, 95 (%) */
+    int32_t flat;           /* regrouped tree with flat subtrees (R10) on/off */
 } ref_params;
 
 /* ------------------------------------------------------------------ */
@@ -202,14 +221,67 @@ int ref_canonical_codes(const uint8_t *lens, uint32_t *codes) {
 }
 
 /* ------------------------------------------------------------------ */
+/* 3b. Regrouped codes (Sec. 2.2.4; reading R10).  Each length class    */
+/*     is cut into power-of-two groups, largest first; the groups get   */
+/*     canonical codes as items of length l - D; a symbol's code is its */
+/*     group's code followed by its D-bit index in the group.           */
+/*     fd[s] = D when the symbol's group is a flat node (D >= 2), else 0 */
+/* ------------------------------------------------------------------ */
+int ref_flat_codes(const uint8_t *lens, uint32_t *codes, int32_t *fd) {
+    int glen[256], gD[256], gfirst[256], gsym[256], ng = 0, ns = 0;
+    for (int s = 0; s < 256; s++) { codes[s] = 0; fd[s] = 0; }
+    for (int l = 1; l <= REF_MAX_LEN_CAP; l++) {
+        int mem[256], m = 0;
+        for (int s = 0; s < 256; s++) if (lens[s] == l) mem[m++] = s;
+        int at = 0;
+        while (at < m) {
+            int D = 0;
+            while ((1 << (D + 1)) <= m - at) D++;
+            if (D > l) return REF_ERR_ARG;              /* more symbols than codes of length l */
+            glen[ng] = l - D; gD[ng] = D; gfirst[ng] = ns;
+            for (int k = 0; k < (1 << D); k++) gsym[ns++] = mem[at + k];
+            at += 1 << D;
+            ng++;
+        }
+    }
+    /* canonical codes of the items, ordered by (item length, first symbol) */
+    int order[256];
+    for (int i = 0; i < ng; i++) order[i] = i;
+    for (int i = 1; i < ng; i++) {
+        int g = order[i], j = i - 1;
+        while (j >= 0 && (glen[order[j]] > glen[g] ||
+                          (glen[order[j]] == glen[g] && gsym[gfirst[order[j]]] > gsym[gfirst[g]]))) {
+            order[j + 1] = order[j]; j--;
+        }
+        order[j + 1] = g;
+    }
+    uint32_t c = 0;
+    for (int i = 0; i < ng; i++) {
+        int g = order[i];
+        if (i > 0) c = (c + 1) << (glen[g] - glen[order[i - 1]]);
+        for (int x = 0; x < (1 << gD[g]); x++) {
+            int sy = gsym[gfirst[g] + x];
+            codes[sy] = (c << gD[g]) | (uint32_t)x;
+            fd[sy] = gD[g] >= 2 ? gD[g] : 0;
+        }
+    }
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* 4. The pivoted tree (Listing 1: bit 1 = right; Sec. 2: one bitmap   */
 /*    per internal node = per proper code prefix).  Node order R3.     */
+/*    With flat subtrees (R10) the prefixes at and below a flat group's */
+/*    item code are replaced by one flat node of depth D whose symbol   */
+/*    number x is the symbol coded (prefix << D) | x.                   */
 /* ------------------------------------------------------------------ */
 typedef struct ref_tree {
-    int n_int;
+    int n_int;                 /* nodes: ordinary and flat */
     int depth[256];
     uint32_t prefix[256];
-    int child[256][2];   /* >= 0: internal node id; < 0: leaf, symbol = -child-1 */
+    int flat[256];             /* D of a flat node, 0 for an ordinary node */
+    int child[256][2];         /* ordinary: >= 0 node id, < 0 leaf -(symbol+1) */
+    uint8_t ftab[256][256];    /* flat: symbol of index x */
 } ref_tree;
 
 static int tree_find(const ref_tree *t, int d, uint32_t p) {
@@ -217,34 +289,60 @@ static int tree_find(const ref_tree *t, int d, uint32_t p) {
     return -1;
 }
 
-static int build_tree(const uint8_t *lens, const uint32_t *codes, ref_tree *t) {
-    /* collect distinct proper prefixes (d, p), d < len(s) */
+/* the node a symbol's code bit d is read at (d below the flat depth), or
+   its flat node (d = lens - fd) */
+static int sym_node(const ref_tree *t, const uint8_t *lens, const uint32_t *codes, int s, int d) {
+    return tree_find(t, d, codes[s] >> (lens[s] - d));
+}
+
+static int build_tree(const uint8_t *lens, const uint32_t *codes, const int32_t *fd, ref_tree *t) {
+    /* collect the nodes (d, p, D): ordinary nodes are proper prefixes above
+       a symbol's flat node, flat nodes are the flat groups' item codes */
     int nd = 0;
-    int dd[4096]; uint32_t pp[4096];
+    int dd[4096], DD[4096]; uint32_t pp[4096];
     for (int s = 0; s < 256; s++) {
-        for (int d = 0; d < lens[s]; d++) {
+        if (!lens[s]) continue;
+        int top = lens[s] - fd[s];
+        for (int d = 0; d <= top; d++) {
+            int D = d < top ? 0 : fd[s];
+            if (d == top && fd[s] == 0) break;       /* a leaf, not a node */
             uint32_t p = codes[s] >> (lens[s] - d);
-            int seen = 0;
-            for (int k = 0; k < nd; k++) if (dd[k] == d && pp[k] == p) { seen = 1; break; }
-            if (!seen) { if (nd >= 4096) return REF_ERR_ARG; dd[nd] = d; pp[nd] = p; nd++; }
+            int seen = -1;
+            for (int k = 0; k < nd; k++) if (dd[k] == d && pp[k] == p) { seen = k; break; }
+            if (seen >= 0) { if (DD[seen] != D) return REF_ERR_CORRUPT; continue; }
+            if (nd >= 4096) return REF_ERR_ARG;
+            dd[nd] = d; pp[nd] = p; DD[nd] = D; nd++;
         }
     }
     if (nd > 255) return REF_ERR_ARG;
     /* breadth-first order: sort by (depth, prefix) */
     for (int i = 1; i < nd; i++) {
-        int d = dd[i]; uint32_t p = pp[i]; int j = i - 1;
-        while (j >= 0 && (dd[j] > d || (dd[j] == d && pp[j] > p))) { dd[j + 1] = dd[j]; pp[j + 1] = pp[j]; j--; }
-        dd[j + 1] = d; pp[j + 1] = p;
+        int d = dd[i], D = DD[i]; uint32_t p = pp[i]; int j = i - 1;
+        while (j >= 0 && (dd[j] > d || (dd[j] == d && pp[j] > p))) { dd[j + 1] = dd[j]; pp[j + 1] = pp[j]; DD[j + 1] = DD[j]; j--; }
+        dd[j + 1] = d; pp[j + 1] = p; DD[j + 1] = D;
     }
     t->n_int = nd;
-    for (int v = 0; v < nd; v++) { t->depth[v] = dd[v]; t->prefix[v] = pp[v]; }
+    for (int v = 0; v < nd; v++) { t->depth[v] = dd[v]; t->prefix[v] = pp[v]; t->flat[v] = DD[v]; }
     for (int v = 0; v < nd; v++) {
+        if (t->flat[v]) {
+            /* symbol x of the flat node: code (prefix << D) | x, length depth + D */
+            int D = t->flat[v];
+            t->child[v][0] = t->child[v][1] = 0;
+            for (int x = 0; x < (1 << D); x++) {
+                int sym = -1;
+                for (int s = 0; s < 256; s++)
+                    if (lens[s] == t->depth[v] + D && fd[s] == D && codes[s] == ((t->prefix[v] << D) | (uint32_t)x)) { sym = s; break; }
+                if (sym < 0) return REF_ERR_CORRUPT;
+                t->ftab[v][x] = (uint8_t)sym;
+            }
+            continue;
+        }
         for (int b = 0; b < 2; b++) {
             int cd = t->depth[v] + 1; uint32_t cp = (t->prefix[v] << 1) | (uint32_t)b;
             int id = tree_find(t, cd, cp);
             if (id >= 0) { t->child[v][b] = id; continue; }
             int leaf = -1;
-            for (int s = 0; s < 256; s++) if (lens[s] == cd && codes[s] == cp) { leaf = s; break; }
+            for (int s = 0; s < 256; s++) if (lens[s] == cd && fd[s] == 0 && codes[s] == cp) { leaf = s; break; }
             if (leaf < 0) return REF_ERR_CORRUPT;   /* not a full tree */
             t->child[v][b] = -leaf - 1;
         }
@@ -252,18 +350,40 @@ static int build_tree(const uint8_t *lens, const uint32_t *codes, ref_tree *t) {
     return REF_OK;
 }
 
-/* exported view of the tree for tests: depth, prefix, child ids */
-int ref_tree_info(const uint8_t *lens, int32_t *n_int, int32_t *depth, uint32_t *prefix, int32_t *child) {
-    uint32_t codes[256]; ref_tree t;
-    ref_canonical_codes(lens, codes);
-    int rc = build_tree(lens, codes, &t);
-    if (rc) return rc;
-    *n_int = t.n_int;
-    for (int v = 0; v < t.n_int; v++) {
-        depth[v] = t.depth[v]; prefix[v] = t.prefix[v];
-        child[2 * v] = t.child[v][0]; child[2 * v + 1] = t.child[v][1];
+/* codes and tree of a block: canonical (flat = 0) or regrouped (flat = 1) */
+static int make_tree(const uint8_t *lens, int flat, uint32_t *codes, int32_t *fd, ref_tree *t) {
+    if (flat) {
+        int rc = ref_flat_codes(lens, codes, fd);
+        if (rc) return rc;
+    } else {
+        ref_canonical_codes(lens, codes);
+        for (int s = 0; s < 256; s++) fd[s] = 0;
     }
+    return build_tree(lens, codes, fd, t);
+}
+
+/* exported view of the tree for tests: depth, prefix, child ids (ordinary
+   nodes), flat depth and symbol table (flat nodes, ftab[v * 256 + x]) */
+int ref_tree_info_ex(const uint8_t *lens, int flat, int32_t *n_int, int32_t *depth, uint32_t *prefix, int32_t *child,
+                     int32_t *fdepth, int32_t *ftab) {
+    uint32_t codes[256]; int32_t fd[256];
+    ref_tree *t = (ref_tree *)malloc(sizeof(ref_tree));
+    if (!t) return REF_ERR_ARG;
+    int rc = make_tree(lens, flat, codes, fd, t);
+    if (rc) { free(t); return rc; }
+    *n_int = t->n_int;
+    for (int v = 0; v < t->n_int; v++) {
+        depth[v] = t->depth[v]; prefix[v] = t->prefix[v];
+        child[2 * v] = t->child[v][0]; child[2 * v + 1] = t->child[v][1];
+        if (fdepth) fdepth[v] = t->flat[v];
+        if (ftab) for (int x = 0; x < 256; x++) ftab[256 * v + x] = (t->flat[v] && x < (1 << t->flat[v])) ? t->ftab[v][x] : -1;
+    }
+    free(t);
     return REF_OK;
+}
+
+int ref_tree_info(const uint8_t *lens, int32_t *n_int, int32_t *depth, uint32_t *prefix, int32_t *child) {
+    return ref_tree_info_ex(lens, 0, n_int, depth, prefix, child, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -463,11 +583,12 @@ int ref_ans_select(uint64_t n_v, uint64_t n1, int depth, const ref_params *p) {
 /* 7. Block record (App. D, adapted; reading R7)                        */
 /*  0  u32 rec_bytes (multiple of 16)   4 u32 n                         */
 /*  8  u16 n_int  10 u8 kind (0 empty, 1 constant, 2 coded)  11 u8 aux  */
-/*  12 "PVC1"                                                           */
+/*  12 "PVC1" (canonical tree) or "PVC2" (regrouped tree, R10)          */
 /*  kind 2: 16 lens[128] (symbol 2k low nibble of byte k)               */
 /*          144 nv[n_int] u32, marker[n_int] u8, pad to 4,              */
 /*          alen[n_sel] u32 (body bytes of each node with marker != 0), */
 /*          raw bodies of marker-0 nodes, then bodies of the others,    */
+/*          (a flat node's raw body is ceil(n_v * D / 8) bytes)         */
 /*          zero pad to 16                                              */
 /* ------------------------------------------------------------------ */
 #define HDR_BYTES 16u
@@ -476,91 +597,117 @@ int ref_ans_select(uint64_t n_v, uint64_t n1, int depth, const ref_params *p) {
 
 static uint64_t pad16(uint64_t x) { return (x + 15) & ~(uint64_t)15; }
 
-static void write_header(uint8_t *rec, uint32_t rec_bytes, uint32_t n, uint32_t n_int, uint32_t kind, uint32_t aux) {
+static void write_header(uint8_t *rec, uint32_t rec_bytes, uint32_t n, uint32_t n_int, uint32_t kind, uint32_t aux, int flat) {
     put32(rec, rec_bytes);
     put32(rec + 4, n);
     put16(rec + 8, n_int);
     rec[10] = (uint8_t)kind;
     rec[11] = (uint8_t)aux;
-    rec[12] = 'P'; rec[13] = 'V'; rec[14] = 'C'; rec[15] = '1';
+    rec[12] = 'P'; rec[13] = 'V'; rec[14] = 'C'; rec[15] = flat ? '2' : '1';
+}
+
+/* bits per element of node v's body: 1 for an ordinary node, D for a flat one */
+static int node_bits(const ref_tree *t, int v) { return t->flat[v] ? t->flat[v] : 1; }
+
+/* n_v of every node: the symbols whose code passes through it */
+static void node_counts(const ref_tree *t, const uint8_t *lens, const uint32_t *codes, const int32_t *fd,
+                        const uint32_t *hist, uint64_t *nv) {
+    for (int v = 0; v < 256; v++) nv[v] = 0;
+    for (int s = 0; s < 256; s++) {
+        if (!lens[s]) continue;
+        for (int d = 0; d < lens[s] - fd[s]; d++) nv[sym_node(t, lens, codes, s, d)] += hist[s];
+        if (fd[s]) nv[sym_node(t, lens, codes, s, lens[s] - fd[s])] += hist[s];
+    }
+}
+
+/* count of node v's right (bit 1) child, for the ANS rule */
+static uint64_t right_count(const ref_tree *t, const uint64_t *nv, const uint32_t *hist, int v) {
+    return t->child[v][1] >= 0 ? nv[t->child[v][1]] : hist[-t->child[v][1] - 1];
 }
 
 /* largest record the block can produce (every node stored raw) */
 int ref_record_bound(const uint32_t *hist, const ref_params *p, uint64_t *bound) {
-    uint8_t lens[256]; uint32_t codes[256]; ref_tree t;
-    uint64_t n = 0; int K = 0;
-    for (int s = 0; s < 256; s++) { n += hist[s]; if (hist[s]) K++; }
+    uint8_t lens[256]; uint32_t codes[256]; int32_t fd[256];
+    int K = 0;
+    for (int s = 0; s < 256; s++) if (hist[s]) K++;
     if (K <= 1) { *bound = HDR_BYTES; return REF_OK; }
     int rc = ref_code_lengths(hist, p->max_len, lens);
     if (rc) return rc;
-    ref_canonical_codes(lens, codes);
-    rc = build_tree(lens, codes, &t);
-    if (rc) return rc;
-    uint64_t nv[256]; memset(nv, 0, sizeof(nv));
-    for (int s = 0; s < 256; s++)
-        for (int d = 0; d < lens[s]; d++)
-            nv[tree_find(&t, d, codes[s] >> (lens[s] - d))] += hist[s];
-    uint64_t sz = NV_OFF + 5ull * (uint64_t)t.n_int;
+    ref_tree *t = (ref_tree *)malloc(sizeof(ref_tree));
+    if (!t) return REF_ERR_ARG;
+    rc = make_tree(lens, p->flat, codes, fd, t);
+    if (rc) { free(t); return rc; }
+    uint64_t nv[256];
+    node_counts(t, lens, codes, fd, hist, nv);
+    uint64_t sz = NV_OFF + 5ull * (uint64_t)t->n_int;
     sz = (sz + 3) & ~(uint64_t)3;
     int nsel_max = 0;
-    for (int v = 0; v < t.n_int; v++) {
-        sz += (nv[v] + 7) / 8;
-        uint64_t n1 = t.child[v][1] >= 0 ? nv[t.child[v][1]] : hist[-t.child[v][1] - 1];
-        if (ref_ans_select(nv[v], n1, t.depth[v], p)) nsel_max++;
+    for (int v = 0; v < t->n_int; v++) {
+        sz += (nv[v] * (uint64_t)node_bits(t, v) + 7) / 8;
+        if (!t->flat[v] && ref_ans_select(nv[v], right_count(t, nv, hist, v), t->depth[v], p)) nsel_max++;
     }
     sz += 4ull * (uint64_t)nsel_max;
-    (void)n;
+    free(t);
     *bound = pad16(sz);
     return REF_OK;
 }
 
 int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t *rec, uint64_t cap, uint64_t *rec_bytes) {
-    uint32_t hist[256]; uint8_t lens[256]; uint32_t codes[256]; ref_tree t;
+    uint32_t hist[256]; uint8_t lens[256]; uint32_t codes[256]; int32_t fd[256];
     if (n > 0xFFFFFFFFull) return REF_ERR_ARG;
     ref_histogram(x, n, hist);
     int K = 0, only = 0;
     for (int s = 0; s < 256; s++) if (hist[s]) { K++; only = s; }
     if (K <= 1) {
         if (cap < HDR_BYTES) return REF_ERR_CAPACITY;
-        write_header(rec, HDR_BYTES, (uint32_t)n, 0, K == 0 ? 0u : 1u, K == 0 ? 0u : (uint32_t)only);
+        write_header(rec, HDR_BYTES, (uint32_t)n, 0, K == 0 ? 0u : 1u, K == 0 ? 0u : (uint32_t)only, p->flat);
         *rec_bytes = HDR_BYTES;
         return REF_OK;
     }
     int rc = ref_code_lengths(hist, p->max_len, lens);
     if (rc) return rc;
-    ref_canonical_codes(lens, codes);
-    rc = build_tree(lens, codes, &t);
-    if (rc) return rc;
-    int V = t.n_int;
+    ref_tree *t = (ref_tree *)malloc(sizeof(ref_tree));
+    if (!t) return REF_ERR_ARG;
+    rc = make_tree(lens, p->flat, codes, fd, t);
+    if (rc) { free(t); return rc; }
+    int V = t->n_int;
 
-    /* 5. per-node bitmaps by the definition: append bit d of code(s) to the
-          bitmap of the node named by its first d bits, in block order */
-    uint64_t nv[256]; memset(nv, 0, sizeof(nv));
-    for (int s = 0; s < 256; s++)
-        for (int d = 0; d < lens[s]; d++)
-            nv[tree_find(&t, d, codes[s] >> (lens[s] - d))] += hist[s];
+    /* 5. per-node bodies by the definition: in block order, append bit d of
+          code(s) to the node named by its first d bits; a symbol that reaches
+          a flat node appends its D-bit index there (value j at bits jD..) */
+    uint64_t nv[256];
+    node_counts(t, lens, codes, fd, hist, nv);
     uint8_t *bm[256];
     uint64_t cur[256];
     int node_of[256][16];
     for (int s = 0; s < 256; s++)
-        for (int d = 0; d < lens[s]; d++) node_of[s][d] = tree_find(&t, d, codes[s] >> (lens[s] - d));
-    for (int v = 0; v < V; v++) { bm[v] = (uint8_t *)calloc((size_t)((nv[v] + 7) / 8) + 1, 1); cur[v] = 0; }
+        if (lens[s]) for (int d = 0; d <= lens[s] - fd[s] && d < lens[s]; d++) node_of[s][d] = sym_node(t, lens, codes, s, d);
+    for (int v = 0; v < V; v++) { bm[v] = (uint8_t *)calloc((size_t)((nv[v] * (uint64_t)node_bits(t, v) + 7) / 8) + 1, 1); cur[v] = 0; }
     for (uint64_t i = 0; i < n; i++) {
         int s = x[i];
-        for (int d = 0; d < lens[s]; d++) {
+        for (int d = 0; d < lens[s] - fd[s]; d++) {
             int v = node_of[s][d];
             uint32_t bit = (codes[s] >> (lens[s] - 1 - d)) & 1u;
             if (bit) bm[v][cur[v] >> 3] |= (uint8_t)(1u << (cur[v] & 7));
             cur[v]++;
         }
+        if (fd[s]) {
+            int v = node_of[s][lens[s] - fd[s]], D = fd[s];
+            uint32_t xv = codes[s] & ((1u << D) - 1u);
+            for (int k = 0; k < D; k++) {
+                uint64_t pos = cur[v] * (uint64_t)D + (uint64_t)k;
+                if ((xv >> k) & 1u) bm[v][pos >> 3] |= (uint8_t)(1u << (pos & 7));
+            }
+            cur[v]++;
+        }
     }
 
-    /* 6. selective ANS */
+    /* 6. selective ANS (ordinary nodes only) */
     int marker[256]; uint8_t *ans_body[256]; uint64_t ans_len[256];
     for (int v = 0; v < V; v++) {
         marker[v] = 0; ans_body[v] = NULL; ans_len[v] = 0;
-        uint64_t n1 = t.child[v][1] >= 0 ? nv[t.child[v][1]] : hist[-t.child[v][1] - 1];
-        int m = ref_ans_select(nv[v], n1, t.depth[v], p);
+        if (t->flat[v]) continue;
+        int m = ref_ans_select(nv[v], right_count(t, nv, hist, v), t->depth[v], p);
         if (!m) continue;
         uint64_t raw = (nv[v] + 7) / 8;
         uint8_t *src = (uint8_t *)malloc((size_t)raw);
@@ -570,7 +717,7 @@ int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t 
         uint64_t blen = 0;
         rc = ref_rans_encode(src, (uint32_t)raw, (m & 0x7F) + 49, body, bcap, &blen);
         free(src);
-        if (rc) { free(body); return rc; }
+        if (rc) { free(body); for (int u = 0; u < V; u++) { free(bm[u]); free(ans_body[u]); } free(t); return rc; }
         if (blen >= raw) { free(body); marker[v] = (int)REF_MARK_RAW_SEL; ans_len[v] = raw; }
         else { marker[v] = m; ans_body[v] = body; ans_len[v] = blen; }
     }
@@ -583,25 +730,30 @@ int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t 
     uint64_t alen_off = off;
     off += 4ull * (uint64_t)nsel;
     uint64_t total = off;
-    for (int v = 0; v < V; v++) total += marker[v] ? ans_len[v] : (nv[v] + 7) / 8;
+    for (int v = 0; v < V; v++) total += marker[v] ? ans_len[v] : (nv[v] * (uint64_t)node_bits(t, v) + 7) / 8;
     total = pad16(total);
     if (total > cap || total > 0xFFFFFFFFull) {
         for (int v = 0; v < V; v++) { free(bm[v]); free(ans_body[v]); }
+        free(t);
         return REF_ERR_CAPACITY;
     }
     memset(rec, 0, (size_t)total);
-    write_header(rec, (uint32_t)total, (uint32_t)n, (uint32_t)V, 2, 0);
+    write_header(rec, (uint32_t)total, (uint32_t)n, (uint32_t)V, 2, 0, p->flat);
     for (int k = 0; k < 128; k++) rec[LENS_OFF + k] = (uint8_t)(lens[2 * k] | (lens[2 * k + 1] << 4));
     for (int v = 0; v < V; v++) put32(rec + NV_OFF + 4ull * v, (uint32_t)nv[v]);
     for (int v = 0; v < V; v++) rec[NV_OFF + 4ull * V + v] = (uint8_t)marker[v];
     { int k = 0; for (int v = 0; v < V; v++) if (marker[v]) put32(rec + alen_off + 4ull * (k++), (uint32_t)ans_len[v]); }
-    for (int v = 0; v < V; v++) if (!marker[v]) { uint64_t b = (nv[v] + 7) / 8; memcpy(rec + off, bm[v], (size_t)b); off += b; }
+    for (int v = 0; v < V; v++) if (!marker[v]) {
+        uint64_t b = (nv[v] * (uint64_t)node_bits(t, v) + 7) / 8;
+        memcpy(rec + off, bm[v], (size_t)b); off += b;
+    }
     for (int v = 0; v < V; v++) if (marker[v]) {
         if (ans_body[v]) memcpy(rec + off, ans_body[v], (size_t)ans_len[v]);
         else memcpy(rec + off, bm[v], (size_t)ans_len[v]);
         off += ans_len[v];
     }
     for (int v = 0; v < V; v++) { free(bm[v]); free(ans_body[v]); }
+    free(t);
     *rec_bytes = total;
     return REF_OK;
 }
@@ -609,56 +761,48 @@ int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t 
 /* ------------------------------------------------------------------ */
 /* 8. Decode by the definition: for each output position walk from the */
 /*    root, reading the next unread bit of each visited node (Listing 1 */
-/*    on the pivoted layout of Sec. 2).                                 */
+/*    on the pivoted layout of Sec. 2); a flat node gives its next      */
+/*    D-bit index, the symbol of that index (Sec. 2.2.3).               */
 /* ------------------------------------------------------------------ */
-int ref_decode_block(const uint8_t *rec, uint64_t avail, uint8_t *out, uint64_t cap, uint64_t *n_out) {
-    if (avail < HDR_BYTES) return REF_ERR_CORRUPT;
-    uint32_t rb = get32(rec), n = get32(rec + 4), V = get16(rec + 8), kind = rec[10], aux = rec[11];
-    if (rec[12] != 'P' || rec[13] != 'V' || rec[14] != 'C' || rec[15] != '1') return REF_ERR_CORRUPT;
-    if (rb < HDR_BYTES || (rb & 15u) || rb > avail) return REF_ERR_CORRUPT;
-    if (n > cap) return REF_ERR_CAPACITY;
-    *n_out = n;
-    if (kind == 0) { if (n != 0 || V != 0 || aux != 0 || rb != HDR_BYTES) return REF_ERR_CORRUPT; return REF_OK; }
-    if (kind == 1) {
-        if (n == 0 || V != 0 || rb != HDR_BYTES) return REF_ERR_CORRUPT;
-        for (uint32_t i = 0; i < n; i++) out[i] = (uint8_t)aux;
-        return REF_OK;
-    }
-    if (kind != 2 || aux != 0 || n == 0 || V < 1 || V > 255) return REF_ERR_CORRUPT;
-    if (rb < NV_OFF + 5ull * V) return REF_ERR_CORRUPT;
-    uint8_t lens[256]; uint32_t codes[256]; ref_tree t;
+static int decode_coded(const uint8_t *rec, uint32_t rb, uint32_t n, uint32_t V, int flat, ref_tree *t, uint8_t *out) {
+    uint8_t lens[256]; uint32_t codes[256]; int32_t fd[256];
     int K = 0;
     for (int k = 0; k < 128; k++) { lens[2 * k] = rec[LENS_OFF + k] & 15; lens[2 * k + 1] = rec[LENS_OFF + k] >> 4; }
     /* Kraft equality (a full tree) is required */
     uint64_t kraft = 0;
     for (int s = 0; s < 256; s++) if (lens[s]) { K++; kraft += 1ull << (15 - lens[s]); }
-    if (K < 2 || kraft != (1ull << 15) || (uint32_t)(K - 1) != V) return REF_ERR_CORRUPT;
-    ref_canonical_codes(lens, codes);
-    if (build_tree(lens, codes, &t) || t.n_int != (int)V) return REF_ERR_CORRUPT;
-    uint64_t nv[256]; int marker[256];
+    if (K < 2 || kraft != (1ull << 15)) return REF_ERR_CORRUPT;
+    if (make_tree(lens, flat, codes, fd, t) || t->n_int != (int)V) return REF_ERR_CORRUPT;
+    uint64_t nv[256] = { 0 }; int marker[256];
     for (uint32_t v = 0; v < V; v++) { nv[v] = get32(rec + NV_OFF + 4ull * v); marker[v] = rec[NV_OFF + 4ull * V + v]; }
     if (nv[0] != n) return REF_ERR_CORRUPT;
     int nsel = 0;
     for (uint32_t v = 0; v < V; v++) {
         int m = marker[v];
-        if (m) { nsel++; if (m != (int)REF_MARK_RAW_SEL && ((m & 0x7F) < 1 || (m & 0x7F) > 50)) return REF_ERR_CORRUPT; }
-        if (nv[v] < 2) return REF_ERR_CORRUPT;
-        for (int b = 0; b < 2; b++) if (t.child[v][b] >= 0 && nv[t.child[v][b]] > nv[v]) return REF_ERR_CORRUPT;
+        if (m) {
+            if (t->flat[v]) return REF_ERR_CORRUPT;     /* flat nodes are never ANS coded */
+            nsel++;
+            if (m != (int)REF_MARK_RAW_SEL && ((m & 0x7F) < 1 || (m & 0x7F) > 50)) return REF_ERR_CORRUPT;
+        }
+        /* every symbol below a node occurs at least once */
+        if (nv[v] < (1ull << node_bits(t, (int)v))) return REF_ERR_CORRUPT;
+        if (!t->flat[v]) for (int b = 0; b < 2; b++) if (t->child[v][b] >= 0 && nv[t->child[v][b]] > nv[v]) return REF_ERR_CORRUPT;
     }
     uint64_t off = NV_OFF + 5ull * V;
     off = (off + 3) & ~(uint64_t)3;
     uint64_t alen_off = off;
     off += 4ull * (uint64_t)nsel;
     if (off > rb) return REF_ERR_CORRUPT;
-    /* bitmaps: raw ones point into the record, ANS ones are decoded */
+    /* bodies: raw ones point into the record, ANS ones are decoded */
     const uint8_t *bm[256]; uint8_t *owned[256];
+    uint64_t nbits[256];
     int k = 0;
-    for (uint32_t v = 0; v < V; v++) owned[v] = NULL;
+    for (uint32_t v = 0; v < V; v++) { owned[v] = NULL; nbits[v] = nv[v] * (uint64_t)node_bits(t, (int)v); }
     uint64_t alen[256];
     for (uint32_t v = 0; v < V; v++) alen[v] = marker[v] ? get32(rec + alen_off + 4ull * (k++)) : 0;
     int rc = REF_OK;
     for (uint32_t v = 0; v < V; v++) if (!marker[v]) {
-        uint64_t b = (nv[v] + 7) / 8;
+        uint64_t b = (nbits[v] + 7) / 8;
         if (off + b > rb) { rc = REF_ERR_CORRUPT; goto done; }
         bm[v] = rec + off; off += b;
     }
@@ -686,8 +830,18 @@ int ref_decode_block(const uint8_t *rec, uint64_t avail, uint8_t *out, uint64_t 
             for (;;) {
                 if (cursor[v] >= nv[v]) { rc = REF_ERR_CORRUPT; goto done; }
                 uint64_t j = cursor[v]++;
+                if (t->flat[v]) {
+                    int D = t->flat[v];
+                    uint32_t xv = 0;
+                    for (int q = 0; q < D; q++) {
+                        uint64_t pos = j * (uint64_t)D + (uint64_t)q;
+                        xv |= (uint32_t)((bm[v][pos >> 3] >> (pos & 7)) & 1u) << q;
+                    }
+                    out[i] = t->ftab[v][xv];
+                    break;
+                }
                 int bit = (bm[v][j >> 3] >> (j & 7)) & 1;
-                int c = t.child[v][bit];
+                int c = t->child[v][bit];
                 if (c < 0) { out[i] = (uint8_t)(-c - 1); break; }
                 v = c;
             }
@@ -695,11 +849,34 @@ int ref_decode_block(const uint8_t *rec, uint64_t avail, uint8_t *out, uint64_t 
         for (uint32_t v = 0; v < V; v++) {
             if (cursor[v] != nv[v]) { rc = REF_ERR_CORRUPT; goto done; }
             /* pad bits of the last byte are zero */
-            if (nv[v] & 7) { if (bm[v][nv[v] >> 3] >> (nv[v] & 7)) { rc = REF_ERR_CORRUPT; goto done; } }
+            if (nbits[v] & 7) { if (bm[v][nbits[v] >> 3] >> (nbits[v] & 7)) { rc = REF_ERR_CORRUPT; goto done; } }
         }
     }
 done:
     for (uint32_t v = 0; v < V; v++) free(owned[v]);
+    return rc;
+}
+
+int ref_decode_block(const uint8_t *rec, uint64_t avail, uint8_t *out, uint64_t cap, uint64_t *n_out) {
+    if (avail < HDR_BYTES) return REF_ERR_CORRUPT;
+    uint32_t rb = get32(rec), n = get32(rec + 4), V = get16(rec + 8), kind = rec[10], aux = rec[11];
+    if (rec[12] != 'P' || rec[13] != 'V' || rec[14] != 'C' || (rec[15] != '1' && rec[15] != '2')) return REF_ERR_CORRUPT;
+    int flat = rec[15] == '2';
+    if (rb < HDR_BYTES || (rb & 15u) || rb > avail) return REF_ERR_CORRUPT;
+    if (n > cap) return REF_ERR_CAPACITY;
+    *n_out = n;
+    if (kind == 0) { if (n != 0 || V != 0 || aux != 0 || rb != HDR_BYTES) return REF_ERR_CORRUPT; return REF_OK; }
+    if (kind == 1) {
+        if (n == 0 || V != 0 || rb != HDR_BYTES) return REF_ERR_CORRUPT;
+        for (uint32_t i = 0; i < n; i++) out[i] = (uint8_t)aux;
+        return REF_OK;
+    }
+    if (kind != 2 || aux != 0 || n == 0 || V < 1 || V > 255) return REF_ERR_CORRUPT;
+    if (rb < NV_OFF + 5ull * V) return REF_ERR_CORRUPT;
+    ref_tree *t = (ref_tree *)malloc(sizeof(ref_tree));
+    if (!t) return REF_ERR_ARG;
+    int rc = decode_coded(rec, rb, n, V, flat, t, out);
+    free(t);
     return rc;
 }
 
