@@ -64,7 +64,9 @@
  *       D >= 2 is a flat node (a group of two is an ordinary node with two
  *       leaves).  A flat node's body is its symbols' D-bit indices x in block
  *       order, value j at bits [jD, jD + D), least significant bit first
- *       (App. D: ceil(n*D/8) bytes).  Flat nodes are never ANS coded.  Nodes
+ *       (App. D: ceil(n*D/8) bytes).  Flat nodes are never ANS coded; their
+ *       marker byte is 0xF0 + D, so body sizes follow from the record's
+ *       tables alone, and their bodies sit with the raw ones.  Nodes
  *       (ordinary and flat) are ordered breadth-first as in R3.  Records of
  *       this tree carry the tag "PVC2" in place of "PVC1".
  *
@@ -90,6 +92,7 @@
 #define REF_ANS_L (1u << 16)
 #define REF_ANS_SEG 16384u
 #define REF_MARK_RAW_SEL 0xFFu
+#define REF_MARK_FLAT 0xF0u       /* flat node of depth D: marker 0xF0 + D (R10) */
 
 typedef struct ref_params {
     int32_t max_len;        /* L (App. D: 11) */
@@ -722,7 +725,7 @@ int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t 
         else { marker[v] = m; ans_body[v] = body; ans_len[v] = blen; }
     }
 
-    /* 7. serialise */
+    /* 7. serialise (marker[v] != 0: an ANS-coded or ANS-selected node) */
     int nsel = 0;
     for (int v = 0; v < V; v++) if (marker[v]) nsel++;
     uint64_t off = NV_OFF + 5ull * (uint64_t)V;
@@ -741,7 +744,7 @@ int ref_encode_block(const uint8_t *x, uint64_t n, const ref_params *p, uint8_t 
     write_header(rec, (uint32_t)total, (uint32_t)n, (uint32_t)V, 2, 0, p->flat);
     for (int k = 0; k < 128; k++) rec[LENS_OFF + k] = (uint8_t)(lens[2 * k] | (lens[2 * k + 1] << 4));
     for (int v = 0; v < V; v++) put32(rec + NV_OFF + 4ull * v, (uint32_t)nv[v]);
-    for (int v = 0; v < V; v++) rec[NV_OFF + 4ull * V + v] = (uint8_t)marker[v];
+    for (int v = 0; v < V; v++) rec[NV_OFF + 4ull * V + v] = (uint8_t)(t->flat[v] ? REF_MARK_FLAT + (uint32_t)t->flat[v] : (uint32_t)marker[v]);
     { int k = 0; for (int v = 0; v < V; v++) if (marker[v]) put32(rec + alen_off + 4ull * (k++), (uint32_t)ans_len[v]); }
     for (int v = 0; v < V; v++) if (!marker[v]) {
         uint64_t b = (nv[v] * (uint64_t)node_bits(t, v) + 7) / 8;
@@ -774,13 +777,21 @@ static int decode_coded(const uint8_t *rec, uint32_t rb, uint32_t n, uint32_t V,
     if (K < 2 || kraft != (1ull << 15)) return REF_ERR_CORRUPT;
     if (make_tree(lens, flat, codes, fd, t) || t->n_int != (int)V) return REF_ERR_CORRUPT;
     uint64_t nv[256] = { 0 }; int marker[256];
-    for (uint32_t v = 0; v < V; v++) { nv[v] = get32(rec + NV_OFF + 4ull * v); marker[v] = rec[NV_OFF + 4ull * V + v]; }
+    for (uint32_t v = 0; v < V; v++) {
+        nv[v] = get32(rec + NV_OFF + 4ull * v);
+        int m = rec[NV_OFF + 4ull * V + v];
+        /* a flat node's marker names its depth; it is never ANS coded */
+        if (t->flat[v]) {
+            if (m != (int)REF_MARK_FLAT + t->flat[v]) return REF_ERR_CORRUPT;
+            m = 0;
+        }
+        marker[v] = m;
+    }
     if (nv[0] != n) return REF_ERR_CORRUPT;
     int nsel = 0;
     for (uint32_t v = 0; v < V; v++) {
         int m = marker[v];
         if (m) {
-            if (t->flat[v]) return REF_ERR_CORRUPT;     /* flat nodes are never ANS coded */
             nsel++;
             if (m != (int)REF_MARK_RAW_SEL && ((m & 0x7F) < 1 || (m & 0x7F) > 50)) return REF_ERR_CORRUPT;
         }

@@ -24,11 +24,12 @@ def _header(rec):
 
 
 def _bodies(rec, D):
-    """Raw bodies of every node (records without ANS nodes)."""
+    """Raw bodies of every node (records without ANS nodes); a flat node's
+    marker byte is 0xF0 + D, an ordinary raw node's 0."""
     n, V = _header(rec)
     nv = rec[144:144 + 4 * V].view(np.uint32).astype(np.int64)
     marker = rec[144 + 4 * V:144 + 5 * V]
-    assert not marker.any()
+    assert list(marker) == [0xF0 + int(d) if d else 0 for d in D]
     off = (144 + 5 * V + 3) & ~3
     out = []
     for v in range(V):
@@ -51,6 +52,7 @@ def test_hand_derived_record(oracle):
         assert "".join(chr(c) for c in ftab[int(v)][: 1 << D[int(v)]]) == syms
     nv, bodies, end = _bodies(rec, D)
     assert list(nv) == g["n_v"]
+    assert list(rec[144 + 16:144 + 20]) == g["markers"]
     assert [list(b) for b in bodies] == g["bodies"]
     assert not rec[end:].any()
     st, y = oracle.decode_block(rec)
@@ -218,7 +220,7 @@ def test_round_trip_and_no_ans_on_flat_nodes(oracle, wl, ans):
         if V:
             D = oracle.tree_info_ex(lens, flat=True)[3]
             marker = rec[144 + 4 * V:144 + 5 * V]
-            assert not marker[D > 0].any()
+            assert list(marker[D > 0]) == [0xF0 + int(d) for d in D[D > 0]]
             # the canonical record of the same block decodes to the same bytes
             rec1 = oracle.encode_block(x, oracle.params(ans=ans))
             assert oracle.decode_block(rec1)[1].tobytes() == x.tobytes()
@@ -249,6 +251,7 @@ def test_corrupt_flat_records_are_refused(oracle):
     assert int(nv[0]) * 3 % 8 == 3
     bad = rec.copy(); bad[end - 1] |= 0x80
     assert oracle.decode_block(bad)[0] == 3
-    # a flat node marked as ANS coded
-    bad = rec.copy(); bad[144 + 4] = 5
-    assert oracle.decode_block(bad)[0] == 3
+    # a flat node marked as ANS coded, raw, or flat of another depth
+    for m in (5, 0, 0xF2, 0xF4):
+        bad = rec.copy(); bad[144 + 4] = m
+        assert oracle.decode_block(bad)[0] == 3
