@@ -49,6 +49,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pivco", choices=["pivco", "reference"])
     ap.add_argument("--workload", default="skew80", choices=sorted(WORKLOADS))
+    ap.add_argument("--tree", default="flat", choices=["flat", "canonical"],
+                    help="records of the regrouped tree with flat subtrees (PVC2, Sec. 2.2.3-2.2.4) or of the "
+                         "canonical tree (PVC1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-config", action="store_true", help="measure the headline workload only")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -86,11 +89,13 @@ def whole_job_gbs(raw_per_rank, steps, tot_ms_max, world):
 
 def kernel_record(kernel, workload):
     """DRAM bytes and warp instructions per launch of `kernel` on `workload`
-    from the committed ncu summary (profiles/traffic.json), only while the
-    kernel's source file is byte-identical to the one profiled (else {})."""
+    (records of the tree --tree names: "skew80", "skew80/canonical") from the
+    committed ncu summary (profiles/traffic.json), only while the kernel's
+    source file is byte-identical to the one profiled (else {})."""
     import hashlib
+    key = workload if FLAT else workload + "/canonical"
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload][kernel]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[key][kernel]
         src = open(os.path.join(ROOT, KERNEL_SOURCES[kernel]), "rb").read()
     except (OSError, KeyError, ValueError):
         return {}
@@ -170,6 +175,12 @@ def _oracle_round_trip(oracle, prm, x, sub_off):
     assert not st.any() and np.array_equal(out, x)
 
 
+# tree of the records every leg codes (set from --tree): regrouped with flat subtrees, or canonical
+FLAT = True
+TREE_DESC = {"flat": "regrouped tree with flat subtrees (records PVC2, Sec. 2.2.3-2.2.4)",
+             "canonical": "canonical tree (records PVC1)"}
+
+
 def cpu_baseline(w, budget_s=10.0, ans=False):
     """The oracle as it stands, on the host: single-threaded over a bounded
     prefix of the same blocks (about budget_s), then on every host core
@@ -178,7 +189,7 @@ def cpu_baseline(w, budget_s=10.0, ans=False):
     Returns GB/s of raw bytes per (encode + decode)."""
     import oracle
     oracle.build()
-    prm = oracle.params(ans=ans)
+    prm = oracle.params(ans=ans, flat=FLAT)
     nb, t_all, raw_all, used = 1, 0.0, 0, 0
     while used < w.nblk and t_all < budget_s:
         take = min(nb, w.nblk - used)
@@ -227,7 +238,7 @@ def serving_leg(P, seconds=2.0, budget=8 << 30, pool_n=48, seed=4, repeats=3):
     for r in reqs:
         data = torch.from_numpy(r.data).cuda()
         boff = torch.from_numpy(r.blk_off.astype(np.int64)).cuda()
-        enc = P.encode(data, boff, P.params(ans=r.ans))
+        enc = P.encode(data, boff, P.params(ans=r.ans, flat=FLAT))
         tot = int(enc.off[-1].item())
         comp = torch.empty(max(tot, 1), dtype=torch.uint8, pin_memory=True)
         comp[:tot].copy_(enc.comp[:tot])
@@ -319,13 +330,15 @@ def make_workload(name):
 
 def run_reference(args):
     """Reference arm: the oracle (the paper's method restated plainly in C)."""
+    global FLAT
+    FLAT = args.tree == "flat"
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w = make_workload(args.workload)
     import oracle
     oracle.build()
-    prm = oracle.params(ans=w.ans)
+    prm = oracle.params(ans=w.ans, flat=FLAT)
     # each step: a bounded sample of the workload (16 blocks, <= a few MB)
     take = min(w.nblk, 16)
     lo, hi = 0, int(w.blk_off[take])
@@ -347,7 +360,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "sample_blocks": take,
-                       "sample_bytes": hi - lo},
+                       "sample_bytes": hi - lo, "tree": args.tree},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": "first %d blocks (%d bytes) per step, single-threaded" % (take, hi - lo)},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -371,7 +384,7 @@ def measure(P, torch, w, dev, stream, flush, steps, warmup, autotune):
     blk_off = torch.from_numpy(w.blk_off.astype(np.int64)).to(dev)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        enc = P.Encoder(nblk, P.params(ans=w.ans), dev)
+        enc = P.Encoder(nblk, P.params(ans=w.ans, flat=FLAT), dev)
         enc.ensure(enc.plan(data, blk_off, stream))
         res = enc.run(data, blk_off, stream, replan=False)
         dec = P.Decoder(nblk, dev)
@@ -533,7 +546,9 @@ def summarize(r, world, dev, peak_gbs, issue_peak, workload):
 
 
 def main(argv=None):
+    global FLAT
     args = parse_args(argv)
+    FLAT = args.tree == "flat"
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -597,7 +612,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         h_in = torch.from_numpy(w.data).pin_memory()
         h_out = torch.empty(raw, dtype=torch.uint8).pin_memory()
-        with P.HostCodec(w.blk_off, P.params(ans=w.ans), segments=args.e2e_segments) as hc:
+        with P.HostCodec(w.blk_off, P.params(ans=w.ans, flat=FLAT), segments=args.e2e_segments) as hc:
             h_comp = torch.empty(max(hc.capacity, 1), dtype=torch.uint8).pin_memory()
             e2e_t = []
             e2e_ok = True
@@ -630,6 +645,7 @@ def main(argv=None):
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "blocks": r["nblk"],
+                       "tree": TREE_DESC[args.tree],
                        "raw_bytes_per_gpu": raw, "compressed_bytes": r["rec_bytes"],
                        "ratio": round(raw / r["rec_bytes"], 4),
                        "l2": "L2 flushed (256 MiB write) before each leg; inputs 256 MiB > 129 MB L2",

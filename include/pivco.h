@@ -32,16 +32,27 @@
  *
  * Block record (the wire format, App. D adapted to GPU-sized blocks):
  *    0 u32 rec_bytes (multiple of 16)   4 u32 n (symbols)
- *    8 u16 n_int (internal nodes)  10 u8 kind (0 empty, 1 constant, 2 coded)
- *   11 u8 aux (kind 1: the symbol)  12 "PVC1"
+ *    8 u16 n_int (nodes)  10 u8 kind (0 empty, 1 constant, 2 coded)
+ *   11 u8 aux (kind 1: the symbol)  12 "PVC1" (canonical tree) or "PVC2"
+ *      (regrouped tree with flat subtrees, Sec. 2.2.3-2.2.4)
  *   kind 2: 16 u8 lens[128] (4-bit code lengths, symbol 2k in the low nibble)
  *          144 u32 n_v[n_int] (symbols through each node, breadth-first order)
  *              u8 marker[n_int] (0 raw; 1..50 | 0x80 XOR: ANS table id;
- *                                0xFF: selected for ANS but stored raw)
- *              zero pad to 4, u32 alen[#nonzero markers] (body bytes)
- *              bodies: raw ceil(n_v/8)-byte bitmaps of marker-0 nodes,
+ *                                0xFF: selected for ANS but stored raw;
+ *                                0xF0 + D: flat node of depth D = 2..8)
+ *              zero pad to 4, u32 alen[#markers other than 0 and flat]
+ *              bodies: raw bodies of the marker-0 and flat nodes
+ *                      (ceil(n_v/8) bytes, ceil(n_v*D/8) for a flat node),
  *                      then the bodies of the other nodes; zero pad to 16.
- *   Bitmap bit j is bit (j & 7) of byte j >> 3 (Sec. 2.4.2 bit order).
+ *   Bitmap bit j is bit (j & 7) of byte j >> 3 (Sec. 2.4.2 bit order).  A
+ *   flat node's body holds the D-bit index x of each of its symbols (the
+ *   x-th of its 2^D symbols in ascending order), value j at bits
+ *   [jD, jD + D), least significant bit first.
+ *   The regrouped tree (PVC2): each length class, ascending by symbol, is
+ *   cut into groups of the largest power of two left; a group of 2^D is an
+ *   item of length l - D; items get canonical codes in (length, first
+ *   symbol) order and symbol x of a group the code (item code << D) | x.  A
+ *   group of 2^D >= 4 symbols is one flat node; nodes are breadth-first.
  *   An ANS body is u32 nwords[S] for S = ceil(bytes / 16384) segments, then
  *   per segment W = min(32, ceil(seg_bytes / 512)) u32 final rANS states and
  *   nwords u16 renormalisation words.
@@ -68,7 +79,10 @@ typedef int32_t pivco_status;
  * The ANS fields are the three knobs of the selection rule of Sec. 5.2:
  * a node's bitmap is ANS-coded when it has at least ans_min_bytes bytes (32),
  * its skew max(n0, n1) / n exceeds ans_skew_num / ans_skew_den (5/8 = 0.625),
- * and (depth + fse_H) / (depth + 1) is below ans_ratio_pct / 100 (0.95). */
+ * and (depth + fse_H) / (depth + 1) is below ans_ratio_pct / 100 (0.95).
+ * flat = 1 codes with the regrouped tree of Sec. 2.2.3-2.2.4 (record tag
+ * "PVC2", see the record format above); 0 with the canonical tree ("PVC1").
+ * Both kinds of record decode through every decode call. */
 typedef struct pivco_params {
     int32_t max_len;
     int32_t ans_enable;
@@ -76,6 +90,7 @@ typedef struct pivco_params {
     int32_t ans_skew_num;
     int32_t ans_skew_den;
     int32_t ans_ratio_pct;
+    int32_t flat;
 } pivco_params;
 
 /* Library version string (host, static storage). */

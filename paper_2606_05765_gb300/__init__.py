@@ -81,14 +81,16 @@ _OTHER = {
 
 
 class Params(C.Structure):
-    """Encoder parameters (struct pivco_params): L = 11 (App. D) and the
-    Sec. 5.2 ANS knobs (32 bytes, skew > 5/8, ratio < 95 %)."""
+    """Encoder parameters (struct pivco_params): L = 11 (App. D), the
+    Sec. 5.2 ANS knobs (32 bytes, skew > 5/8, ratio < 95 %) and the
+    regrouped tree with flat subtrees (Sec. 2.2.3-2.2.4, records "PVC2")."""
     _fields_ = [("max_len", C.c_int32), ("ans_enable", C.c_int32), ("ans_min_bytes", C.c_int32),
-                ("ans_skew_num", C.c_int32), ("ans_skew_den", C.c_int32), ("ans_ratio_pct", C.c_int32)]
+                ("ans_skew_num", C.c_int32), ("ans_skew_den", C.c_int32), ("ans_ratio_pct", C.c_int32),
+                ("flat", C.c_int32)]
 
 
-def params(max_len=11, ans=False):
-    return Params(max_len, 1 if ans else 0, 32, 5, 8, 95)
+def params(max_len=11, ans=False, flat=False):
+    return Params(max_len, 1 if ans else 0, 32, 5, 8, 95, 1 if flat else 0)
 
 
 class PivcoError(RuntimeError):

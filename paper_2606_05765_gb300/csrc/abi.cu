@@ -154,7 +154,7 @@ pivco_status pivco_build_layout(const uint32_t *hist, const uint8_t *lens, int32
     if (nblk < 0 || !params || (nblk > 0 && (!hist || !lens || !layout || !rec_bound || !status))) return PIVCO_ERR_INVALID_ARG;
     const pivco_params &p = *params;
     if (p.max_len < 1 || p.max_len > (int32_t)kMaxLen || p.ans_min_bytes < 0 || p.ans_skew_den <= 0 ||
-        p.ans_skew_num < 0 || p.ans_ratio_pct < 0)
+        p.ans_skew_num < 0 || p.ans_ratio_pct < 0 || (p.flat != 0 && p.flat != 1))
         return PIVCO_ERR_INVALID_ARG;
     if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_build_layout(hist, lens, nblk, p, reinterpret_cast<BlockLayout *>(layout), rec_bound, status,
@@ -169,7 +169,7 @@ pivco_status pivco_plan_blocks(const uint8_t *in, const uint64_t *blk_off, int32
         return PIVCO_ERR_INVALID_ARG;
     const pivco_params &p = *params;
     if (p.max_len < 1 || p.max_len > (int32_t)kMaxLen || p.ans_min_bytes < 0 || p.ans_skew_den <= 0 ||
-        p.ans_skew_num < 0 || p.ans_ratio_pct < 0)
+        p.ans_skew_num < 0 || p.ans_ratio_pct < 0 || (p.flat != 0 && p.flat != 1))
         return PIVCO_ERR_INVALID_ARG;
     if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
     return ok_or_cuda(launch_block_plan(in, blk_off, nblk, p, hist, chunk_hist, lens,

@@ -104,7 +104,7 @@ pivco_status pivco_host_codec_create(const uint64_t *blk_off, int32_t nblk, cons
     if (!codec || !params || nblk < 0 || (nblk > 0 && !blk_off) || segments < 1) return PIVCO_ERR_INVALID_ARG;
     const pivco_params &p = *params;
     if (p.max_len < 1 || p.max_len > (int32_t)pv::kMaxLen || p.ans_min_bytes < 0 || p.ans_skew_den <= 0 ||
-        p.ans_skew_num < 0 || p.ans_ratio_pct < 0)
+        p.ans_skew_num < 0 || p.ans_ratio_pct < 0 || (p.flat != 0 && p.flat != 1))
         return PIVCO_ERR_INVALID_ARG;
     if (nblk > 0 && blk_off[0] != 0) return PIVCO_ERR_INVALID_ARG;
     for (int b = 0; b < nblk; b++)

@@ -429,6 +429,7 @@ struct LaySmem {
     uint16_t codes[256];
     int32_t scratch[256];
     TreeShape ts;
+    FlatTree F;
     unsigned long long s_part[kLayThreads / 32];
 };
 
@@ -464,6 +465,7 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
     if (K <= 1) {
         if (t == 0) {
             L.kind = K == 0 ? 0 : 1;
+            L.flat = sp.p.flat ? 1 : 0;
             L.rec_bound = kHdr;
             L.body0 = kHdr;
         }
@@ -471,52 +473,108 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
         __syncthreads();
     } else {
         build_tree_shape(lens, ts, codes, sorted, scratch);
-        if (!ts.ok || ts.K != K || n > 0xFFFFFFFFull) {
+        const bool flat = sp.p.flat != 0;
+        FlatTree &F = Y.F;
+        if (flat && t < 32) flat_tree_build(ts.cnt, ts.len_base, sorted, F);
+        __syncthreads();
+        if (!ts.ok || ts.K != K || n > 0xFFFFFFFFull || (flat && !F.ok)) {
             st = PIVCO_ERR_INVALID_ARG;
         } else {
-            const int V = ts.n_int;
+            const int V = flat ? F.n_nodes : ts.n_int;
+            const int maxd = flat ? F.maxd : ts.max_len;     // node levels
+            const int32_t *fst = flat ? F.first : ts.first;
             if (t == 0) {
                 L.kind = 2;
+                L.flat = flat ? 1 : 0;
                 L.n_int = (uint16_t)V;
-                L.max_depth = (uint8_t)ts.max_len;
-                for (int d = 0; d <= 16; d++) L.depth_first[d] = (uint8_t)min(ts.first[min(d, (int)kMaxLen + 1)], 255);
-                for (int d = ts.max_len; d <= 16; d++) L.depth_first[d] = (uint8_t)V;
-                for (int d = 0; d <= 16; d++) L.tree_a[d] = (uint16_t)ts.a[d];
+                L.max_depth = (uint8_t)maxd;
+                for (int d = 0; d <= 16; d++) L.depth_first[d] = (uint8_t)(d < maxd ? fst[d] : V);
+                for (int d = 0; d <= 16; d++) L.tree_a[d] = (uint16_t)(flat ? F.a[d] : ts.a[d]);
             }
-            L.code[t] = codes[t];
-            L.len[t] = lens[t];
-            if (t < V) {
-                const int d = node_depth(ts, t);
-                L.depth[t] = (uint8_t)d;
-                L.child[t][0] = (int16_t)node_child(ts, sorted, t, d, 0);
-                L.child[t][1] = (int16_t)node_child(ts, sorted, t, d, 1);
-            }
-            if (t < K) L.ci[sorted[t]] = (uint8_t)t;
-            __syncthreads();
-            // n_v bottom-up, one depth at a time: a node's count is its
-            // children's; its leaves (a contiguous run of the canonical order)
-            // start at its left child's and end at its right child's
-            for (int d = ts.max_len - 1; d >= 0; d--) {
-                const int v = ts.first[d] + t;
-                if (v < ts.first[d + 1]) {
-                    uint32_t c = 0;
-                    for (int k = 0; k < 2; k++) {
-                        const int ch = L.child[v][k];
-                        c += ch >= 0 ? L.nv[ch] : h[-ch - 1];
-                    }
-                    L.nv[v] = c;
-                    const int c0 = L.child[v][0], c1 = L.child[v][1];
-                    L.nlo[v] = c0 >= 0 ? L.nlo[c0] : L.ci[-c0 - 1];
-                    L.nhi1[v] = c1 >= 0 ? L.nhi1[c1] : L.ci[-c1 - 1];
+            if (flat) {
+                // regrouped codes: symbol x of item i is (code_i << D) | x
+                if (t < F.nitems) {
+                    const uint32_t c = flat_item_code(F, t), D = F.iD[t];
+                    for (uint32_t x = 0; x < (1u << D); x++) codes[sorted[F.iso[t] + x]] = (uint16_t)((c << D) | x);
                 }
                 __syncthreads();
             }
+            L.code[t] = codes[t];
+            L.len[t] = lens[t];
+            bool okn = true;
             if (t < V) {
-                const int c = L.child[t][1];
-                const uint64_t n1 = c >= 0 ? L.nv[c] : h[-c - 1];
-                L.sel[t] = ans_select(L.nv[t], n1, L.depth[t], sp);
+                int d = 0;
+                uint32_t chv = 0;
+                if (flat) {
+                    okn = flat_node(F, sorted, t, d, chv);
+                } else {
+                    d = node_depth(ts, t);
+                    chv = ((uint32_t)node_child(ts, sorted, t, d, 0) & 0xFFFFu) |
+                          ((uint32_t)node_child(ts, sorted, t, d, 1) << 16);
+                }
+                L.depth[t] = (uint8_t)d;
+                // (a canonical node's word holds its children as 16-bit ints: never flat)
+                const uint32_t D = flat ? ch_flat_d(chv) : 0u;
+                if (D == 1 || D > 8) okn = false;
+                L.fd[t] = (uint8_t)D;
+                L.fbase[t] = D ? (uint8_t)(chv & 0xFFu) : 0;
+                for (int c = 0; c < 2; c++) {
+                    const uint32_t x = D ? 0u : (chv >> (16 * c)) & 0xFFFFu;
+                    L.child[t][c] = flat ? (int16_t)((x & 0x8000u) ? -(int)(x & 0xFFu) - 1 : (int)x)
+                                         : (int16_t)(chv >> (16 * c));
+                }
             }
-            __syncthreads();
+            if (__syncthreads_or(!okn)) {
+                st = PIVCO_ERR_INVALID_ARG;
+            } else {
+                if (flat) {
+                    // code index: the place of a symbol's code among the left-aligned codes
+                    if (lens[t]) {
+                        const uint32_t key = (uint32_t)codes[t] << (15 - lens[t]);
+                        int r = 0;
+                        for (int s2 = 0; s2 < 256; s2++)
+                            r += lens[s2] && ((uint32_t)codes[s2] << (15 - lens[s2])) < key;
+                        L.ci[t] = (uint8_t)r;
+                    }
+                } else if (t < K) {
+                    L.ci[sorted[t]] = (uint8_t)t;
+                }
+                __syncthreads();
+                // n_v bottom-up, one depth at a time: a node's count is its
+                // children's (a flat node's, its symbols'); its leaves (a
+                // contiguous run of the code order) start at its left child's
+                // and end at its right child's
+                for (int d = maxd - 1; d >= 0; d--) {
+                    const int v = fst[d] + t;
+                    if (v < fst[d + 1] && v < V) {
+                        const uint32_t D = L.fd[v];
+                        if (D) {
+                            const uint32_t base = L.fbase[v];
+                            uint32_t c = 0;
+                            for (uint32_t x = 0; x < (1u << D); x++) c += h[sorted[base + x]];
+                            L.nv[v] = c;
+                            L.nlo[v] = L.ci[sorted[base]];
+                            L.nhi1[v] = L.ci[sorted[base + (1u << D) - 1]];
+                        } else {
+                            uint32_t c = 0;
+                            for (int k = 0; k < 2; k++) {
+                                const int ch = L.child[v][k];
+                                c += ch >= 0 ? L.nv[ch] : h[-ch - 1];
+                            }
+                            L.nv[v] = c;
+                            const int c0 = L.child[v][0], c1 = L.child[v][1];
+                            L.nlo[v] = c0 >= 0 ? L.nlo[c0] : L.ci[-c0 - 1];
+                            L.nhi1[v] = c1 >= 0 ? L.nhi1[c1] : L.ci[-c1 - 1];
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (t < V && !L.fd[t]) {
+                    const int c = L.child[t][1];
+                    const uint64_t n1 = c >= 0 ? L.nv[c] : h[-c - 1];
+                    L.sel[t] = ans_select(L.nv[t], n1, L.depth[t], sp);
+                }
+                __syncthreads();
             if (t < 32) {
                 // bodies: the raw (unselected) nodes first, then the selected ones, node order
                 const int lane = t;
@@ -525,14 +583,14 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                     const int v = base + lane;
                     const bool in = v < V;
                     nsel += __popc(__ballot_sync(0xffffffffu, in && L.sel[v]));
-                    raw_tot += __reduce_add_sync(0xffffffffu, (in && !L.sel[v]) ? (L.nv[v] + 7) / 8 : 0u);
+                    raw_tot += __reduce_add_sync(0xffffffffu, (in && !L.sel[v]) ? (uint32_t)(((uint64_t)L.nv[v] * max(1u, (uint32_t)L.fd[v]) + 7) / 8) : 0u);
                 }
                 const uint32_t off0 = ((kNvOff + 5u * V + 3u) & ~3u) + 4u * nsel;
                 uint32_t c_raw = off0, c_sel = off0 + raw_tot;
                 for (int base = 0; base < V; base += 32) {
                     const int v = base + lane;
                     const bool in = v < V, sel = in && L.sel[v];
-                    const uint32_t by = in ? (L.nv[v] + 7) / 8 : 0u;
+                    const uint32_t by = in ? (uint32_t)(((uint64_t)L.nv[v] * max(1u, (uint32_t)L.fd[v]) + 7) / 8) : 0u;
                     uint32_t xr = (in && !sel) ? by : 0u, xs = sel ? by : 0u;
                     uint32_t ir = xr, is = xs;
                     for (int o = 1; o < 32; o <<= 1) {
@@ -549,6 +607,7 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                     L.body_end = c_sel;
                     L.rec_bound = (c_sel + 15u) & ~15u;
                 }
+            }
             }
         }
     }

@@ -39,8 +39,9 @@ constexpr int kTileCtas = 4;                 // tile CTAs per SM the kernels are
 constexpr uint32_t kNtabHdr = 32;            // node table header (see plan_block)
 
 // bytes of a block's node table: header, then per node u32 bitmap source,
-// u32 children and u32 first rank-directory entry
-__host__ __device__ inline uint32_t ntab_bytes(uint32_t V) { return (kNtabHdr + 12u * V + 15u) & ~15u; }
+// u32 children and u32 first rank-directory entry, then the block's 256
+// symbols in (length, symbol) order (the tables of its flat nodes)
+__host__ __device__ inline uint32_t ntab_bytes(uint32_t V) { return (kNtabHdr + 12u * V + 256u + 15u) & ~15u; }
 
 // rank-directory granularity, and whether every coded block gets a directory
 // (random access) rather than only those split into several tiles: header
@@ -151,7 +152,7 @@ struct __align__(16) WarpRec {
     uint32_t soff[256];      // scratch offset of an ANS node within its block
     uint32_t segbase[256];   // first ANS segment of the node within its block
     uint8_t marker[256];
-    uint32_t V, n, kind, rb, scratch_bytes, nsegs;
+    uint32_t V, n, kind, rb, scratch_bytes, nsegs, flat;
 };
 
 __device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &R) {
@@ -181,10 +182,11 @@ __device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &
         n = ld_le32(rec + 4);
         V = (uint32_t)rec[8] | ((uint32_t)rec[9] << 8);
         kind = rec[10];
-        ok = rec[12] == 'P' && rec[13] == 'V' && rec[14] == 'C' && rec[15] == '1' && rb >= kHdr && !(rb & 15u) &&
-             rb <= avail;
+        ok = rec[12] == 'P' && rec[13] == 'V' && rec[14] == 'C' && (rec[15] == '1' || rec[15] == '2') && rb >= kHdr &&
+             !(rb & 15u) && rb <= avail;
     }
-    if (lane == 0) { R.rb = rb; R.n = n; R.kind = kind; R.scratch_bytes = 0; R.nsegs = 0; R.V = 0; }
+    const uint32_t flat = ok && rec[15] == '2';
+    if (lane == 0) { R.rb = rb; R.n = n; R.kind = kind; R.scratch_bytes = 0; R.nsegs = 0; R.V = 0; R.flat = flat; }
     if (!ok) return false;
     if (kind != 2) {
         const uint32_t aux = rec[11];
@@ -198,25 +200,29 @@ __device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &
         R.nv[v] = ld_le32(rec + kNvOff + 4 * v);
         const uint8_t m = rec[kNvOff + 4 * V + v];
         R.marker[v] = m;
-        if (m && m != kMarkRawSel && ((m & 0x7F) < 1 || (m & 0x7F) > 50)) ok = false;
+        // flat markers (0xF0 + D) only in records of the regrouped tree
+        if (mark_flat_d(m) ? !flat : (m && m != kMarkRawSel && ((m & 0x7F) < 1 || (m & 0x7F) > 50))) ok = false;
     }
     __syncwarp();
     const uint32_t alen_off = (kNvOff + 5 * V + 3) & ~3u;
-    const uint32_t nsel = warp_scan_loop_d(Vi, [&](int v) { return (uint32_t)(R.marker[v] != 0); },
+    const uint32_t nsel = warp_scan_loop_d(Vi, [&](int v) { return (uint32_t)mark_listed(R.marker[v]); },
                                            [&](int v, uint32_t p) { R.segbase[v] = p; });
     if (alen_off + 4 * nsel > rb) ok = false;
     __syncwarp();
     if (__any_sync(0xffffffffu, !ok)) return false;
     for (int v = lane; v < Vi; v += 32) {
-        const uint32_t raw = (R.nv[v] + 7) / 8;
-        const uint32_t al = R.marker[v] ? ld_le32(rec + alen_off + 4 * R.segbase[v]) : raw;
+        // raw body bytes: ceil(n_v / 8), ceil(n_v D / 8) for a flat node
+        const uint32_t fd = mark_flat_d(R.marker[v]);
+        const uint32_t raw = (uint32_t)(((uint64_t)R.nv[v] * (fd ? fd : 1u) + 7) / 8);
+        const uint32_t al = mark_listed(R.marker[v]) ? ld_le32(rec + alen_off + 4 * R.segbase[v]) : raw;
         R.alen[v] = al;
         if (R.marker[v] == kMarkRawSel && al != raw) ok = false;
+        if (fd && (uint64_t)R.nv[v] * fd > 0xFFFFFFFFull) ok = false;
     }
     __syncwarp();
     const uint32_t base1 = alen_off + 4 * nsel;
-    const uint32_t raw_tot = warp_scan_loop_d(Vi, [&](int v) { return R.marker[v] ? 0u : R.alen[v]; },
-                                              [&](int v, uint32_t p) { if (!R.marker[v]) R.body_off[v] = base1 + p; });
+    const uint32_t raw_tot = warp_scan_loop_d(Vi, [&](int v) { return mark_listed(R.marker[v]) ? 0u : R.alen[v]; },
+                                              [&](int v, uint32_t p) { if (!mark_listed(R.marker[v])) R.body_off[v] = base1 + p; });
     const uint32_t base2 = base1 + raw_tot;
     uint64_t sel_tot = 0;
     {
@@ -224,26 +230,26 @@ __device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &
         uint64_t carry = 0;
         for (int base = 0; base < Vi; base += 32) {
             const int v = base + lane;
-            const uint64_t x = (v < Vi && R.marker[v]) ? R.alen[v] : 0;
+            const uint64_t x = (v < Vi && mark_listed(R.marker[v])) ? R.alen[v] : 0;
             uint64_t inc = x;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += y;
             }
-            if (v < Vi && R.marker[v]) R.body_off[v] = (uint32_t)(base2 + carry + inc - x);
+            if (v < Vi && mark_listed(R.marker[v])) R.body_off[v] = (uint32_t)(base2 + carry + inc - x);
             carry += __shfl_sync(0xffffffffu, inc, 31);
         }
         sel_tot = carry;
     }
     if ((((uint64_t)base2 + sel_tot + 15) & ~15ull) != rb) ok = false;
     const uint32_t stot = warp_scan_loop_d(Vi, [&](int v) {
-        return (R.marker[v] && R.marker[v] != kMarkRawSel) ? scratch_stride((R.nv[v] + 7) / 8) : 0u;
+        return mark_ans(R.marker[v]) ? scratch_stride((R.nv[v] + 7) / 8) : 0u;
     }, [&](int v, uint32_t p) { R.soff[v] = p; });
     const uint32_t segs = warp_scan_loop_d(Vi, [&](int v) {
-        return (R.marker[v] && R.marker[v] != kMarkRawSel) ? ans_seg_count((R.nv[v] + 7) / 8) : 0u;
+        return mark_ans(R.marker[v]) ? ans_seg_count((R.nv[v] + 7) / 8) : 0u;
     }, [&](int v, uint32_t p) { R.segbase[v] = p; });
-    for (int v = lane; v < Vi; v += 32)
-        if (R.nv[v] < 2 || R.nv[v] > n) ok = false;
+    for (int v = lane; v < Vi; v += 32)   // every symbol under a node occurs at least once
+        if (R.nv[v] < (2u << (mark_flat_d(R.marker[v]) ? mark_flat_d(R.marker[v]) - 1 : 0)) || R.nv[v] > n) ok = false;
     if (lane == 0 && R.nv[0] != n) ok = false;
     if (lane == 0) { R.scratch_bytes = stot; R.nsegs = segs; }
     __syncwarp();
@@ -265,16 +271,20 @@ __device__ inline bool warp_parse(const uint8_t *grec, uint64_t avail, WarpRec &
 //   32 u32 src[V]     bit address of node v's bitmap: 8 x record byte offset,
 //                     or 8 x block scratch offset | 2^31 for ANS-coded nodes
 //      u32 ch[V]      children: child c in bits [16c, 16c + 16), 0x8000 |
-//                     symbol for a leaf, else the child's node index
+//                     symbol for a leaf, else the child's node index; a
+//                     flat node's word is ch_flat(D, base)
 //      u32 u[V]       node v's first rank-directory entry (blocks with one)
+//      u8 sym[256]    the symbols in (length, symbol) order: flat node
+//                     symbol x is sym[base + x]
 // ---------------------------------------------------------------------------
 struct PlanScratch {
     uint32_t cntl[16], lvl[16], run[16];
     int32_t a[17], first[18], start[17];
-    int32_t good, maxd;
+    int32_t good, maxd, K;
     uint32_t ch[256];
     uint32_t u[256];
     uint8_t sorted[256];
+    FlatTree F;
 };
 
 __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const uint64_t *__restrict__ comp_off,
@@ -326,8 +336,10 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
                 }
             }
             Q.first[17] = f;
-            Q.good = good && K >= 2 && f == K - 1 && f == (int32_t)R.V;
+            // (a regrouped tree has its own node count, checked below)
+            Q.good = good && K >= 2 && f == K - 1 && (R.flat || f == (int32_t)R.V);
             Q.maxd = m;
+            Q.K = K;
         }
         __syncwarp();
         const bool good = Q.good != 0;
@@ -342,8 +354,25 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
             if (l && r == 0) Q.run[l] += __popc(peers);
             __syncwarp();
         }
-        // children of every internal node and the symbols of each depth
+        // children of every node and the symbols of each depth
         bool okn = good;
+        if (R.flat && good) {
+            // the regrouped tree with flat subtrees (Sec. 2.2.3-2.2.4); its
+            // flat nodes must be the record's (markers 0xF0 + D)
+            flat_tree_build(reinterpret_cast<const int32_t *>(Q.cntl), Q.start, Q.sorted, Q.F);
+            okn = Q.F.ok && Q.F.n_nodes == (int32_t)R.V;
+            if (okn && lane < 18) Q.first[lane] = lane < Q.F.maxd ? Q.F.first[lane] : Q.F.n_nodes;
+            if (okn && lane == 0) Q.maxd = Q.F.maxd;
+            for (int v = lane; v < (int)R.V && okn; v += 32) {
+                int d = 0;
+                uint32_t chv = 0;
+                if (!flat_node(Q.F, Q.sorted, v, d, chv)) okn = false;
+                const uint32_t D = ch_flat_d(chv);
+                if (D != mark_flat_d(R.marker[v]) || (D && (chv & 0xFFu) + (1u << D) > (uint32_t)Q.K)) okn = false;
+                if (d >= 1) atomicAdd(&Q.lvl[d], R.nv[v]);
+                Q.ch[v] = chv;
+            }
+        } else {
         int d = 0;   // depth of node v (v grows, so the search goes on from the last one)
         for (int v = lane; v < (int)R.V && good; v += 32) {
             while (d < 15 && Q.first[d + 1] <= v) d++;
@@ -365,6 +394,7 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
                 code2 |= code << (16 * c);
             }
             Q.ch[v] = code2;
+        }
         }
         __syncwarp();
         ok = __all_sync(0xffffffffu, okn);
@@ -434,10 +464,12 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         uint32_t *src = reinterpret_cast<uint32_t *>(nt + kNtabHdr);
         for (int v = lane; v < (int)R.V; v += 32) {
             const uint8_t m = R.marker[v];
-            src[v] = (m && m != kMarkRawSel) ? (8u * R.soff[v]) | 0x80000000u : 8u * R.body_off[v];
+            src[v] = mark_ans(m) ? (8u * R.soff[v]) | 0x80000000u : 8u * R.body_off[v];
             src[R.V + v] = Q.ch[v];
             src[2 * R.V + v] = ent ? Q.u[v] : 0u;
         }
+        uint8_t *sym = nt + kNtabHdr + 12 * R.V;
+        for (int i = lane; i < 256; i += 32) sym[i] = Q.sorted[i];
     }
     __syncwarp();
 }
@@ -533,7 +565,7 @@ __device__ inline int ans_item(uint32_t g, const uint8_t *__restrict__ comp, con
         int node = -1;
         for (int v = lane; v < (int)R.V; v += 32) {
             const uint8_t m = R.marker[v];
-            if (m && m != kMarkRawSel) {
+            if (mark_ans(m)) {
                 const uint32_t s0 = R.segbase[v], ns = ans_seg_count((R.nv[v] + 7) / 8);
                 if (j >= s0 && j < s0 + ns) node = v;
             }
@@ -634,6 +666,7 @@ struct __align__(16) CtaTile {
     uint16_t wn_off[16];                       // first window-node entry of each level
     WinSum win[2][kTileWarps];                 // window summaries, two rounds deep
     uint8_t wnode[kWnodeMax];                  // node holding the first group of each window
+    uint8_t ftab[256];                         // the block's symbols in (length, symbol) order (flat nodes)
     uint8_t first[17];
     uint8_t maxd;
     uint8_t pad[2];
@@ -766,6 +799,48 @@ __device__ inline void merge32(const CtaTile &S, const uint8_t *bin, uint32_t ch
     }
 }
 
+// 32 output symbols of a flat node (Sec. 2.2.3, merge_flat_D): the D-bit
+// indices at bit address pos (a raw body in the record), each mapped through
+// the node's symbols tab[0 .. 2^D).
+template <int D>
+__device__ inline void flat32_t(const TileSrc &s, uint32_t pos, const uint8_t *tab, uint32_t (&o)[8]) {
+    const uint64_t e = pos & 0x7FFFFFFFu;
+    const uint64_t wi = e >> 5;
+    const uint32_t sh = (uint32_t)e & 31u;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(s.rec);
+    const uint64_t lim = s.rec_bytes;
+    uint32_t x[D + 1], b[D];
+#pragma unroll
+    for (int k = 0; k <= D; k++) x[k] = 4 * (wi + k) + 4 <= lim ? __ldcg(w + wi + k) : 0u;
+#pragma unroll
+    for (int k = 0; k < D; k++) b[k] = __funnelshift_r(x[k], x[k + 1], sh);
+    constexpr uint32_t m = (1u << D) - 1u;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int bit = (4 * q + i) * D, k = bit >> 5, r = bit & 31;
+            uint32_t v = b[k] >> r;
+            if (r + D > 32) v |= b[k + 1] << (32 - r);
+            word |= (uint32_t)tab[v & m] << (8 * i);
+        }
+        o[q] = word;
+    }
+}
+
+__device__ inline void flat32(const TileSrc &s, uint32_t D, uint32_t pos, const uint8_t *tab, uint32_t (&o)[8]) {
+    switch (D) {
+        case 2: flat32_t<2>(s, pos, tab, o); break;
+        case 3: flat32_t<3>(s, pos, tab, o); break;
+        case 4: flat32_t<4>(s, pos, tab, o); break;
+        case 5: flat32_t<5>(s, pos, tab, o); break;
+        case 6: flat32_t<6>(s, pos, tab, o); break;
+        case 7: flat32_t<7>(s, pos, tab, o); break;
+        default: flat32_t<8>(s, pos, tab, o); break;
+    }
+}
+
 // the children's demands must be the node's zeros and ones
 __device__ inline bool children_ok(const CtaTile &S, uint32_t chv, uint32_t dv, uint32_t ones) {
     const uint32_t c0 = chv & 0xFFFFu, c1 = chv >> 16;
@@ -867,6 +942,7 @@ __device__ inline void ct_demand(CtaTile &S, const TileSrc &src, uint32_t V, uin
     if (lane == 0) S.dem[0] = C;
     __syncwarp();
     for (uint32_t v = 0; v < V; v++) {   // breadth-first: parents before children
+        if (ch_flat_d(S.ch[v])) continue;   // a flat node has no children to split for
         const uint32_t dv = S.dem[v];
         uint32_t ones = 0;
         for (uint32_t e = 32 * lane; e < dv; e += 1024) {
@@ -922,13 +998,13 @@ __device__ inline void ct_fetch(const CtaTile &S, const TileSrc &src, int d, uin
         if (base < G) {
             const uint32_t u = S.wnode[S.wn_off[d] + (base >> 5)];
             L = wt_locate(S, S.first[d + 1], G, base, (uint32_t)S.gs[u] == base ? u - 1 : u);
-            if (L.act) ld = tile_ld(src, S.pos[L.v], L.kk);
+            if (L.act && !ch_flat_d(S.ch[L.v])) ld = tile_ld(src, S.pos[L.v], L.kk);
         }
     } else if (d == 0) {
         L.dv = S.dem[0];
         L.kk = 32u * (base + lane);
         L.act = L.kk < L.dv;
-        if (L.act) ld = tile_ld(src, S.pos[0], L.kk);
+        if (L.act && !ch_flat_d(S.ch[0])) ld = tile_ld(src, S.pos[0], L.kk);
     }
 }
 
@@ -996,10 +1072,14 @@ __device__ inline bool ct_level(CtaTile &S, const TileSrc &src, int d, const uin
         par ^= 1u;
         if (s0 < 0) r1 += cin;   // groups of the node that runs in from the previous window
         if (act) {
-            const uint32_t chv = S.ch[v];
-            if (kk + 32 >= dv && !children_ok(S, chv, dv, r1 + pc)) bad = true;
+            const uint32_t chv = S.ch[v], fD = ch_flat_d(chv);
             uint32_t o[8];
-            merge32(S, bin, chv, kk - r1, r1, w, sel, o);
+            if (fD) {
+                flat32(src, fD, S.pos[v] + kk * fD, S.ftab + (chv & 0xFFu), o);
+            } else {
+                if (kk + 32 >= dv && !children_ok(S, chv, dv, r1 + pc)) bad = true;
+                merge32(S, bin, chv, kk - r1, r1, w, sel, o);
+            }
             uint8_t *p = bout + S.sp[v] + kk;
             // spans are 4-byte aligned: 32-bit stores, the ones inside the node's span
             uint32_t *p4 = reinterpret_cast<uint32_t *>(p);
@@ -1058,7 +1138,8 @@ __device__ inline bool ct_root(CtaTile &S, const TileSrc &src, uint8_t *out, con
         if (act) {
             const uint32_t r1 = cin + inc - pc;
             uint32_t o[8];
-            merge32(S, bin, chv, kk - r1, r1, w, sel, o);
+            if (const uint32_t fD = ch_flat_d(chv)) flat32(src, fD, S.pos[0] + kk * fD, S.ftab + (chv & 0xFFu), o);
+            else merge32(S, bin, chv, kk - r1, r1, w, sel, o);
             st_out32(out + kk, o, min(32u, dv - kk));
         }
     }
@@ -1129,6 +1210,7 @@ __device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, c
     const uint32_t *nv = reinterpret_cast<const uint32_t *>(rec + kNvOff);
     if (t < 17) S.first[t] = nt[t];
     if (t == 17) S.maxd = nt[17];
+    if (t < 64) reinterpret_cast<uint32_t *>(S.ftab)[t] = reinterpret_cast<const uint32_t *>(nt + kNtabHdr + 12 * V)[t];
     const uint64_t sbase = G.scratch + W.blk_scratch[b];
     TileSrc src;
     src.rec = rec;
@@ -1141,11 +1223,14 @@ __device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, c
         const uint32_t nvv = __ldg(nv + v);
         const uint32_t cs = ntile > 1 ? cursors[(size_t)k * V + v] : 0u;
         const uint32_t e = ntile > 1 ? cursors[(size_t)(k + 1) * V + v] : nvv;
-        const uint32_t s0 = nsrc[v];
-        if (e < cs || e > nvv || (uint64_t)(s0 & 0x7FFFFFFFu) + nvv >= 0x80000000ull) bad = 1;
-        S.pos[v] = s0 + cs;
+        const uint32_t s0 = nsrc[v], chv = nsrc[V + v];
+        const uint32_t bpe = max(1u, ch_flat_d(chv));   // bits per symbol of the node's body
+        if (e < cs || e > nvv || bpe > 8 || (uint64_t)(s0 & 0x7FFFFFFFu) + (uint64_t)nvv * bpe >= 0x80000000ull ||
+            (bpe > 1 && ((s0 >> 31) || (chv & 0xFFu) + (1u << bpe) > 256u)))
+            bad = 1;
+        S.pos[v] = s0 + cs * bpe;
         S.dem[v] = e - cs;
-        S.ch[v] = nsrc[V + v];
+        S.ch[v] = chv;
     }
     __syncthreads();
     if (t == 0 && S.dem[0] != P1 - P0) bad = 1;
@@ -1188,19 +1273,19 @@ __device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, c
             if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
             return;
         }
-        if ((uint32_t)t < V) S.pos[t] += S.dem[t];
+        if ((uint32_t)t < V) S.pos[t] += S.dem[t] * max(1u, ch_flat_d(S.ch[t]));
         __syncthreads();
         P += C;
         C = min(C, P1 - P);
     }
     if (chunked && (uint32_t)t < V) {   // the chunks must end exactly at the tile's end cursors
         const uint32_t ce = ntile > 1 ? cursors[(size_t)(k + 1) * V + t] : __ldg(nv + t);
-        if (S.pos[t] != nsrc[t] + ce) bad = 1;
+        if (S.pos[t] != nsrc[t] + ce * max(1u, ch_flat_d(S.ch[t]))) bad = 1;
     }
-    // the last tile checks the pad bits of every bitmap
+    // the last tile checks the pad bits of every body
     if (k + 1 == ntile && (uint32_t)t < V) {
-        const uint32_t nvv = __ldg(nv + t);
-        if ((nvv & 7) && (tile_bits(src, nsrc[t], nvv & ~7u) & 0xFFu) >> (nvv & 7)) bad = 1;
+        const uint32_t nb = __ldg(nv + t) * max(1u, ch_flat_d(S.ch[t]));
+        if ((nb & 7) && (tile_bits(src, nsrc[t], nb & ~7u) & 0xFFu) >> (nb & 7)) bad = 1;
     }
     if (__syncthreads_or(bad) && t == 0) status[b] = PIVCO_ERR_CORRUPT;
 }
@@ -1350,6 +1435,7 @@ __device__ inline void dir_cta(int b, const uint8_t *__restrict__ comp, const ui
             const uint32_t k = 1 + i / nd, v = f0 + i % nd;
             const uint32_t c = cur[(size_t)k * V + v], nvv = D.nv[v];
             if (c > nvv) { bad = 1; continue; }
+            if (ch_flat_d(D.ch[v])) continue;   // no children below a flat node
             const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
             uint32_t sb = c / dir_bits;
             if (sb >= nsb) sb = nsb - 1;
@@ -1494,6 +1580,7 @@ __device__ inline void dir_warp(int b, const uint8_t *__restrict__ comp, const u
             const uint32_t k = 1 + i / nd, v = f0 + i % nd;
             const uint32_t c = cw[(size_t)k * V + v], nvv = nvs[v];
             if (c > nvv) { bad = 1; continue; }
+            if (ch_flat_d(nch[v])) continue;   // no children below a flat node
             const uint32_t nsb = (nvv + dir_bits - 1) / dir_bits;
             uint32_t sb = c / dir_bits;
             if (sb >= nsb) sb = nsb - 1;
@@ -1619,6 +1706,8 @@ struct BatchSmem {
     uint32_t pad[2];
 };
 static_assert(sizeof(PlanAnsSmem) <= sizeof(CtaTile), "plans fit the tiles' shared memory");
+// kTileCtas CTAs per SM: dynamic + static shared memory + 1 KiB reserved each, of 228 KiB
+static_assert(kTileCtas * (sizeof(BatchSmem) + 128 + 1024) <= 228 * 1024, "tile CTAs per SM");
 
 // One request's (batch's) queue: where its records, output and workspace are.
 struct BatchQueue {
@@ -1956,6 +2045,13 @@ __global__ void __launch_bounds__(256) access_kernel(const uint8_t *__restrict__
                     for (int d = 0; d <= (int)kMaxLen && v < V; d++) {
                         const uint32_t nvv = __ldg(nv + v);
                         if (x >= nvv) break;
+                        if (const uint32_t D = ch_flat_d(nch[v])) {
+                            // a flat node: the D-bit index of the position, then its symbol
+                            const uint32_t xi = tile_bits(src, nsrc[v], x * D) & ((1u << D) - 1u);
+                            out = nt[kNtabHdr + 12 * V + (nch[v] & 0xFFu) + xi];
+                            st = PIVCO_OK;
+                            break;
+                        }
                         const uint32_t bit = tile_bits(src, nsrc[v], x) & 1u;
                         const uint32_t sb = x / dir_bits;
                         const uint32_t ones = dirp[nu[v] + sb] + tile_popc(src, nsrc[v], sb * dir_bits, x - sb * dir_bits);
@@ -2023,7 +2119,7 @@ size_t decode_ws_bound(const uint8_t *comp, const uint64_t *comp_off, int nblk, 
             const uint32_t nv = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
             const uint8_t m = rec[kNvOff + 4 * V + v];
             ent += (nv + (uint64_t)tu.dir_bits - 1) / tu.dir_bits;
-            if (m && m != kMarkRawSel) scratch += scratch_stride((nv + 7) / 8);
+            if (mark_ans(m)) scratch += scratch_stride((nv + 7) / 8);
         }
         uint64_t ntile = ((uint64_t)n + t_min - 1) / t_min;
         if (ntile > (1u << 21)) ntile = 1u << 21;

@@ -18,7 +18,8 @@
 // round (one barrier), a carry across rounds.  Below the root a symbol
 // travels as its remaining code bits, most significant first in 16 bits, so
 // a node's bit is bit 15 and the child receives the value shifted left by
-// one.
+// one.  A flat node (Sec. 2.2.3) takes the top D bits of each value, its
+// symbol's index in the flat group, and packs them D bits per symbol.
 
 #include "pivco_dev.cuh"
 
@@ -41,9 +42,9 @@ struct __align__(16) EncSmem {
                                             // (spans start on 16-byte boundaries)
     uint32_t pos[256];                      // bit address of node v's first bit of the current chunk
     uint32_t dem[256];                      // symbols of node v in the current chunk
-    uint32_t ch[256];                       // children: 0x8000 | symbol for a leaf, else the node index
+    uint32_t ch[256];                       // children word (node-table format; ch_flat for a flat node)
     uint32_t bitsrc[256];                   // bit address of node v's bitmap in the record
-    uint32_t nv[256];                       // symbols of node v in the block (the layout's)
+    uint32_t nv[256];                       // bits of node v's body (n_v, n_v D for a flat node)
     uint16_t code16[256];                   // code of symbol s, most significant bit at bit 15 (0: absent)
     uint16_t sp[256];                       // first symbol of node v's span in its level buffer
     uint16_t gs[256];                       // first 32-symbol group of node v within its level
@@ -304,6 +305,50 @@ __device__ inline void enc_split(uint32_t la, uint32_t ra, bool i0, bool i1, con
     }
 }
 
+// Packs the top D bits of the 16-bit values y (value j in half j & 1 of
+// y[j >> 1]; the first vl valid) D bits per value, value j at bits [jD,
+// jD + D) (Sec. 2.2.3 packed indices, App. D), and writes the vl D bits at
+// bit address a of the record: words inside the run are stored, the two it
+// shares with its neighbours are ORed into the zeroed body.
+template <int D>
+__device__ inline void flat_emit(uint32_t *rec32, uint32_t a, const uint32_t (&y)[16], uint32_t vl) {
+    uint32_t w[D];
+#pragma unroll
+    for (int k = 0; k < D; k++) w[k] = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        const uint32_t x = (uint32_t)j < vl ? ((y[j >> 1] >> (16 * (j & 1))) & 0xFFFFu) >> (16 - D) : 0u;
+        const int b = j * D, wi = b >> 5, sh = b & 31;
+        w[wi] |= x << sh;
+        if (sh + D > 32) w[wi + 1] |= x >> (32 - sh);
+    }
+    const uint32_t sh = a & 31u, wi = a >> 5, end = sh + vl * (uint32_t)D;
+    uint32_t prev = 0;
+#pragma unroll
+    for (int k = 0; k <= D; k++) {
+        const uint32_t cur = k < D ? w[k] : 0u;
+        const uint32_t o = sh ? (cur << sh) | (prev >> (32 - sh)) : cur;
+        prev = cur;
+        const uint32_t lo = 32u * (uint32_t)k;
+        if (lo < end) {
+            if (lo >= sh && lo + 32u <= end) rec32[wi + k] = o;
+            else if (o) atomicOr(&rec32[wi + k], o);
+        }
+    }
+}
+
+__device__ inline void flat_emit_d(uint32_t D, uint32_t *rec32, uint32_t a, const uint32_t (&y)[16], uint32_t vl) {
+    switch (D) {
+        case 2: flat_emit<2>(rec32, a, y, vl); break;
+        case 3: flat_emit<3>(rec32, a, y, vl); break;
+        case 4: flat_emit<4>(rec32, a, y, vl); break;
+        case 5: flat_emit<5>(rec32, a, y, vl); break;
+        case 6: flat_emit<6>(rec32, a, y, vl); break;
+        case 7: flat_emit<7>(rec32, a, y, vl); break;
+        default: flat_emit<8>(rec32, a, y, vl); break;
+    }
+}
+
 __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(const uint8_t *__restrict__ in,
                                                                             const uint64_t *__restrict__ blk_off,
                                                                             const BlockLayout *__restrict__ layout,
@@ -361,7 +406,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         else if (t == 9) v = (uint8_t)(V >> 8);
         else if (t == 10) v = (uint8_t)kind;
         else if (t == 11) v = kind == 1 ? L.csym : 0;
-        else v = (uint8_t)"PVC1"[t - 12];
+        else v = t == 15 ? (L.flat ? '2' : '1') : (uint8_t)"PVC"[t - 12];
         rec[t] = v;
     }
     if (kind != 2) {
@@ -376,7 +421,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         reinterpret_cast<uint32_t *>(rec + kLensOff)[t] = x;
     }
     if (t < V) reinterpret_cast<uint32_t *>(rec + kNvOff)[t] = L.nv[t];
-    if (t < V) rec[kNvOff + 4 * V + t] = L.sel[t] ? kMarkRawSel : 0;
+    if (t < V) rec[kNvOff + 4 * V + t] = L.fd[t] ? (uint8_t)(kMarkFlat + L.fd[t]) : (L.sel[t] ? kMarkRawSel : 0);
     {
         const uint32_t pad_lo = kNvOff + 5 * V, alen_off = (pad_lo + 3) & ~3u;
         if (pad_lo + t < alen_off) rec[pad_lo + t] = 0;
@@ -410,10 +455,10 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 const int ch = L.child[t][c];
                 code2 |= (ch >= 0 ? (uint32_t)ch : (0x8000u | (uint32_t)(-ch - 1))) << (16 * c);
             }
-            S.ch[t] = code2;
+            S.ch[t] = L.fd[t] ? ch_flat(L.fd[t], L.fbase[t]) : code2;
             S.bitsrc[t] = 8u * L.body_off[t];
             S.pos[t] = 8u * L.body_off[t];
-            S.nv[t] = L.nv[t];
+            S.nv[t] = L.nv[t] * max(1u, (uint32_t)L.fd[t]);
         }
         if (t < 17) S.first[t] = L.depth_first[t];
         if (t == 0) { S.maxd = L.max_depth; S.hot = 0xFFFFu; S.bad = 0; }
@@ -474,6 +519,13 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         }
         __syncthreads();
         if (S.bad) break;
+        // no node's bits of this chunk may run past its body (counts that do
+        // not describe the input could otherwise carry a cursor beyond it)
+        if (t < V && (uint64_t)S.pos[t] + (uint64_t)S.dem[t] * max(1u, ch_flat_d(S.ch[t])) >
+                         (uint64_t)S.bitsrc[t] + S.nv[t])
+            S.bad = 1;
+        __syncthreads();
+        if (S.bad) break;
         for (int d = warp; d < (int)S.maxd; d += kEncWarps)
             if (!enc_layout_level(S, d) && lane == 0) S.fits = 0;
         __syncthreads();
@@ -492,7 +544,20 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         }
         // ---- the root: input bytes -> codes; bits; children ----
         uint32_t par = 0;
-        {
+        if (const uint32_t rD = ch_flat_d(S.ch[0])) {
+            // a flat root (the whole alphabet one group): the packed indices
+            for (uint32_t kk = 32u * t; kk < C; kk += 32u * kEncThreads) {
+                uint32_t x[8];
+                ldg32(src + P + kk, src_end, x);
+                uint32_t y[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const uint32_t s0 = (x[j >> 1] >> (16 * (j & 1))) & 0xFFu, s1 = (x[j >> 1] >> (16 * (j & 1) + 8)) & 0xFFu;
+                    y[j] = (uint32_t)S.code16[s0] | ((uint32_t)S.code16[s1] << 16);
+                }
+                flat_emit_d(rD, rec32, S.pos[0] + kk * rD, y, min(32u, C - kk));
+            }
+        } else {
             const uint32_t chv = S.ch[0], c0n = chv & 0xFFFFu, c1n = chv >> 16;
             const bool i0c = !(c0n & 0x8000u), i1c = !(c1n & 0x8000u);
             const uint32_t nb = smem_addr(S.buf[1]);
@@ -594,10 +659,12 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
 #pragma unroll
                     for (int j = 0; j < 16; j++) y[j] = 0;
                 }
+                const uint32_t fD = act ? ch_flat_d(S.ch[v]) : 0u;   // a flat node's lanes have no ranks
                 uint32_t bw = top_bits8(y[0], y[1], y[2], y[3]) | (top_bits8(y[4], y[5], y[6], y[7]) << 8) |
                               (top_bits8(y[8], y[9], y[10], y[11]) << 16) |
                               (top_bits8(y[12], y[13], y[14], y[15]) << 24);
                 if (vl < 32) bw &= (1u << vl) - 1u;
+                if (fD) bw = 0;
                 const uint32_t pc = __popc(bw);
                 uint32_t inc = pc;
 #pragma unroll
@@ -614,8 +681,10 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 const uint32_t cin = enc_round_carry(S, par, rc_sum);
                 par ^= 1u;
                 if (s0 < 0) r1 += cin;   // groups of the node that runs in from the window before
-                enc_put_bits(rec32, act, v, S.pos[v] + kk, bw, vl);
-                if (act) {
+                enc_put_bits(rec32, act && !fD, v, S.pos[v] + kk, bw, vl);
+                if (act && fD) {
+                    flat_emit_d(fD, rec32, S.pos[v] + kk * fD, y, vl);
+                } else if (act) {
                     const uint32_t chv = S.ch[v], c0n = chv & 0xFFFFu, c1n = chv >> 16;
                     const bool i0c = !(c0n & 0x8000u), i1c = !(c1n & 0x8000u);
                     const uint32_t ob = smem_addr(bout);
@@ -629,7 +698,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
             }
             __syncthreads();
         }
-        if (t < V) S.pos[t] += S.dem[t];
+        if (t < V) S.pos[t] += S.dem[t] * max(1u, ch_flat_d(S.ch[t]));
         __syncthreads();
         if (S.bad) break;
         P += C;

@@ -15,6 +15,22 @@ constexpr uint32_t kLensOff = 16;    // 128 bytes of 4-bit lengths
 constexpr uint32_t kNvOff = 144;     // u32 n_v[n_int]
 constexpr uint32_t kMaxLen = 15;     // 4-bit length field
 constexpr uint8_t kMarkRawSel = 0xFF;
+constexpr uint8_t kMarkFlat = 0xF0;  // a flat node of depth D (2..8) has marker 0xF0 + D
+
+// depth D of a flat node's marker (0 for any other marker)
+__host__ __device__ inline uint32_t mark_flat_d(uint32_t m) { return (m >= 0xF2u && m <= 0xF8u) ? m - 0xF0u : 0u; }
+// a node with an entry in the record's alen table: ANS coded, or selected and kept raw
+__host__ __device__ inline bool mark_listed(uint32_t m) { return m != 0 && !mark_flat_d(m); }
+// a node whose body is an ANS stream
+__host__ __device__ inline bool mark_ans(uint32_t m) { return mark_listed(m) && m != kMarkRawSel; }
+
+// Children word of a node (node tables of encoder and decoder): child c in
+// bits [16c, 16c + 16), 0x8000 | symbol for a leaf, else the child's node
+// index.  A flat node (Sec. 2.2.3) is 0x80008000 | D << 24 | base: both
+// halves read as leaves, D in bits 24..30, base (the index of its first
+// symbol in the block's (length, symbol) order) in bits 0..7.
+__host__ __device__ inline uint32_t ch_flat(uint32_t D, uint32_t base) { return 0x80008000u | (D << 24) | base; }
+__host__ __device__ inline uint32_t ch_flat_d(uint32_t chv) { return (chv >> 24) & 0x7Fu; }
 constexpr uint32_t kAnsSeg = 16384;  // bitmap bytes per ANS segment
 constexpr uint32_t kAnsScale = 15;
 constexpr uint32_t kAnsM = 1u << kAnsScale;
@@ -56,22 +72,24 @@ struct BlockLayout {
     uint8_t max_depth;     // longest code length
     uint8_t n_sel;         // nodes selected for ANS
     uint8_t status;        // PIVCO_* of layout construction
-    uint8_t pad0;
+    uint8_t flat;          // regrouped tree with flat subtrees (record tag PVC2)
     uint8_t depth_first[17];   // first node id at depth d (breadth-first); [d+1]-[d] = count
     uint8_t pad1[15];
     uint16_t tree_a[17];       // leaf-covered prefix count at depth d (TreeShape::a)
     uint16_t pad2[15];
-    uint16_t code[256];    // canonical code of symbol s (lens[s] bits, MSB = first decision)
+    uint16_t code[256];    // code of symbol s (lens[s] bits, MSB = first decision; canonical or regrouped)
     uint8_t len[256];      // code length of symbol s
     uint32_t nv[256];      // symbols through node v
     uint32_t body_off[256];    // byte offset of node v's body in the record (raw layout)
     int16_t child[256][2];     // >= 0 internal id; < 0 leaf, symbol = -c - 1
     uint8_t sel[256];          // ANS candidate marker (table id | 0x80 XOR), 0 if not selected
     uint8_t depth[256];
+    uint8_t fd[256];           // D of a flat node, 0 for an ordinary node
+    uint8_t fbase[256];        // flat node: index of its first symbol in (length, symbol) order
     uint8_t pad3[8];
     // (from here on not staged by the encoder, which loads it straight into its tables)
-    uint8_t ci[256];           // canonical index of symbol s: its place in (length, symbol) order
-    uint8_t nlo[256];          // the leaves under node v are canonical indices nlo[v] .. nhi1[v]
+    uint8_t ci[256];           // code index of symbol s: its place in the order of codes (left-aligned)
+    uint8_t nlo[256];          // the leaves under node v are code indices nlo[v] .. nhi1[v]
     uint8_t nhi1[256];
 };
 static_assert(offsetof(BlockLayout, ci) % 16 == 0 && offsetof(BlockLayout, nhi1) + 256 == offsetof(BlockLayout, ci) + 768,
@@ -185,6 +203,149 @@ __device__ inline int node_child(const TreeShape &ts, const uint8_t *sorted, int
     const int32_t q = 2 * p + b;
     if (q < ts.a[d + 1]) return -(int)sorted[ts.len_base[d + 1] + (q - 2 * ts.a[d])] - 1;
     return ts.first[d + 1] + (q - ts.a[d + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// Regrouped tree with flat subtrees (Sec. 2.2.3-2.2.4).  Each length class l
+// (symbols ascending) is cut into groups of the largest power of two left,
+// first 2^D symbols first; a group is an item of length l - D.  The items
+// form a canonical tree ordered by (item length, first symbol): a[d] counts
+// the d-bit prefixes covered by items of length <= d, the items of length d
+// hold prefixes 2 a[d-1] .. a[d] - 1 by rank, the prefixes a[d] .. 2^d - 1
+// are ordinary nodes.  An item of two symbols is an ordinary node with two
+// leaves, one of 2^D >= 4 a flat node, one of a single symbol a leaf.  Nodes
+// are numbered breadth-first (depth, prefix): at each depth the item nodes
+// (by rank) come before the item tree's own nodes.  Symbol x of item i has
+// the code (code_i << D) | x.
+// ---------------------------------------------------------------------------
+constexpr int kMaxItems = 144;    // 15 length classes x at most 9 groups each
+struct FlatTree {
+    int32_t a[18];
+    int32_t first[18];            // first node id at depth d
+    int32_t nin[18];              // item nodes (pairs and flat groups) at depth d
+    int32_t icnt[18];             // items of length d
+    int32_t nitems, maxd, n_nodes, ok;
+    uint8_t it_of[16][9];         // item of length d and rank r
+    uint8_t in_of[16][9];         // k-th item node of depth d
+    uint8_t iD[kMaxItems], il[kMaxItems], irank[kMaxItems], ik[kMaxItems];
+    uint16_t iso[kMaxItems];      // index of the item's first symbol in (length, symbol) order
+};
+
+// Builds the item tree of the code lengths (one warp, all lanes).  cnt[l]:
+// symbols of length l (l = 1..15); start[l]: index of the first of them in
+// `sorted` (the symbols in (length, symbol) order).  F.ok = 0 unless the items
+// make a full tree.
+__device__ inline void flat_tree_build(const int32_t *cnt, const int32_t *start, const uint8_t *sorted, FlatTree &F) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        int n = 0;
+        bool ok = true;
+        for (int d = 0; d < 18; d++) F.icnt[d] = 0;
+        for (int l = 1; l <= (int)kMaxLen; l++) {
+            const int c = cnt[l];
+            if (c < 0 || c > 256) ok = false;
+            int acc = 0;
+            for (int D = 8; D >= 0 && ok; D--) {
+                if (!((c >> D) & 1)) continue;
+                if (D > l || n >= kMaxItems) { ok = false; break; }
+                F.iD[n] = (uint8_t)D;
+                F.il[n] = (uint8_t)(l - D);
+                F.iso[n] = (uint16_t)(start[l] + acc);
+                F.icnt[l - D]++;
+                acc += 1 << D;
+                n++;
+            }
+        }
+        F.nitems = n;
+        F.ok = ok;
+    }
+    __syncwarp();
+    // rank of an item among the items of its length, by first symbol
+    for (int i = lane; i < F.nitems; i += 32) {
+        const uint32_t fs = sorted[F.iso[i]];
+        int r = 0;
+        for (int j = 0; j < F.nitems; j++) r += F.il[j] == F.il[i] && sorted[F.iso[j]] < fs;
+        F.irank[i] = (uint8_t)r;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        bool ok = F.ok != 0;
+        int maxil = 0;
+        for (int i = 0; i < F.nitems; i++) {
+            if (F.irank[i] >= 9 || F.il[i] > 15) { ok = false; break; }
+            F.it_of[F.il[i]][F.irank[i]] = (uint8_t)i;
+            maxil = F.il[i] > maxil ? F.il[i] : maxil;
+        }
+        // Kraft equality at the item level: the items fill the tree
+        int64_t a = 0;
+        for (int d = 0; d < 18; d++) {
+            a = d ? 2 * a + F.icnt[d] : F.icnt[0];
+            F.a[d] = (int32_t)(a > 0x7FFFFFFF ? 0x7FFFFFFF : a);
+            if (d <= 15 && a > (int64_t(1) << d)) ok = false;
+            if (d < maxil && a >= (int64_t(1) << d)) ok = false;
+            if (d == maxil && a != (int64_t(1) << d)) ok = false;
+        }
+        int f = 0, maxd = 0;
+        for (int d = 0; d < 17; d++) {
+            F.first[d] = f;
+            int k = 0;
+            if (ok && d <= maxil)
+                for (int r = 0; r < F.icnt[d] && r < 9; r++) {
+                    const int i = F.it_of[d][r];
+                    if (F.iD[i] >= 1) { F.in_of[d][k] = (uint8_t)i; F.ik[i] = (uint8_t)k; k++; }
+                }
+            F.nin[d] = k;
+            const int open = (ok && d < maxil) ? (1 << d) - F.a[d] : 0;
+            if (k + open > 0) maxd = d + 1;
+            f += k + open;
+        }
+        F.first[17] = f;
+        F.nin[17] = 0;
+        F.maxd = maxd;
+        F.n_nodes = f;
+        F.ok = ok && f >= 1 && f <= 255;
+    }
+    __syncwarp();
+}
+
+// code of item i's prefix (its item length F.il[i] bits)
+__device__ inline uint32_t flat_item_code(const FlatTree &F, int i) {
+    const int l = F.il[i];
+    return l ? (uint32_t)(2 * F.a[l - 1] + F.irank[i]) : 0u;
+}
+
+// Node v of the regrouped tree: its depth and children word (ch_flat for a
+// flat node).  Returns false for ids or children out of range.
+__device__ inline bool flat_node(const FlatTree &F, const uint8_t *sorted, int v, int &depth, uint32_t &chv) {
+    int d = 0;
+    while (d < F.maxd - 1 && F.first[d + 1] <= v) d++;
+    depth = d;
+    chv = 0;
+    if (v < 0 || v >= F.n_nodes) return false;
+    const int k = v - F.first[d];
+    if (k < F.nin[d]) {
+        const int i = F.in_of[d][k];
+        if (F.iD[i] == 1) chv = ((0x8000u | sorted[F.iso[i] + 1]) << 16) | (0x8000u | sorted[F.iso[i]]);
+        else chv = ch_flat(F.iD[i], F.iso[i]);
+        return true;
+    }
+    const int32_t p = F.a[d] + (k - F.nin[d]);
+    for (int b = 0; b < 2; b++) {
+        const int32_t q = 2 * p + b;
+        uint32_t code;
+        if (d + 1 > 15) return false;
+        if (q < F.a[d + 1]) {
+            const int32_t r = q - 2 * F.a[d];
+            if (r < 0 || r >= F.icnt[d + 1] || r >= 9) return false;
+            const int i = F.it_of[d + 1][r];
+            code = F.iD[i] == 0 ? (0x8000u | sorted[F.iso[i]]) : (uint32_t)(F.first[d + 1] + F.ik[i]);
+        } else {
+            code = (uint32_t)(F.first[d + 1] + F.nin[d + 1] + (q - F.a[d + 1]));
+        }
+        if (!(code & 0x8000u) && (code <= (uint32_t)v || code >= (uint32_t)F.n_nodes)) return false;
+        chv |= code << (16 * b);
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------

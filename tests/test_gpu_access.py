@@ -43,12 +43,13 @@ def _queries(w, n_rand, seed):
     return b.astype(np.uint32), p.astype(np.uint32)
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
-def test_access_equals_input(P, name):
+def test_access_equals_input(P, name, flat):
     import torch
     w = WORKLOADS[name]()
     boff = off64(w.blk_off)
-    enc = P.encode(dev(w.data), boff, P.params(ans=True))
+    enc = P.encode(dev(w.data), boff, P.params(ans=True, flat=flat))
     assert not enc.status.cpu().numpy().any()
     acc = P.Access(enc.comp, enc.off, w.nblk)
     assert not acc.status.cpu().numpy()[: w.nblk].any()
@@ -60,11 +61,12 @@ def test_access_equals_input(P, name):
     assert np.array_equal(sym.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("dir_bits", [32, 96, 256])
-def test_access_any_granularity(P, dir_bits):
+def test_access_any_granularity(P, dir_bits, flat):
     import torch
     w = WORKLOADS["mixed_24"]()
-    enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=True))
+    enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=True, flat=flat))
     P.set_tuning(16384, dir_bits, 0)
     try:
         acc = P.Access(enc.comp, enc.off, w.nblk)

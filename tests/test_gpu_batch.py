@@ -27,29 +27,34 @@ def P():
 
 @pytest.fixture(scope="module")
 def encoded(P):
+    """Every workload coded with ANS, canonical (PVC1) and regrouped with
+    flat subtrees (PVC2)."""
     out = {}
     for name, make in WORKLOADS.items():
         w = make()
-        enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=True))
-        assert not enc.status.cpu().numpy().any()
-        out[name] = (w, enc)
+        for flat in (False, True):
+            enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=True, flat=flat))
+            assert not enc.status.cpu().numpy().any()
+            out[name, flat] = (w, enc)
     return out
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
-def test_batched_equals_input(P, encoded, name):
-    w, enc = encoded[name]
+def test_batched_equals_input(P, encoded, name, flat):
+    w, enc = encoded[name, flat]
     out, st = P.decode(enc.comp, enc.off, off64(w.blk_off), batched=True)
     assert not st.cpu().numpy().any()
     assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("tuning", [(128, 32, 1), (4096, 256, 0), (16384, 96, 2), (65536, 160, 3), (1 << 20, 64, 0)])
-def test_tunings_do_not_change_output(P, encoded, tuning):
+def test_tunings_do_not_change_output(P, encoded, tuning, flat):
     P.set_tuning(*tuning)
     try:
         for name in ["zipf1_256k", "mixed_24", "skew95_4x128k", "edge", "shifting"]:
-            w, enc = encoded[name]
+            w, enc = encoded[name, flat]
             for batched in (False, True):
                 out, st = P.decode(enc.comp, enc.off, off64(w.blk_off), batched=batched)
                 assert not st.cpu().numpy().any(), (name, batched)
@@ -87,7 +92,7 @@ def test_graph_replay(P):
 
 def test_autotune_keeps_output(P, encoded):
     import torch
-    w, enc = encoded["mixed_24"]
+    w, enc = encoded["mixed_24", True]
     d = P.Decoder(w.nblk, batched=True)
     d.prepare(enc.comp, enc.off)
     out = torch.empty(w.data.size, dtype=torch.uint8, device="cuda")

@@ -1,6 +1,7 @@
 """GPU parity at the full sizes of the measured configurations, in the launch
 configuration the benchmark times: the encode sequence and the persistent
-decode each captured as a CUDA graph and replayed.
+decode each captured as a CUDA graph and replayed; regrouped trees with flat
+subtrees (the benchmark's records) and canonical ones.
 
 The oracle codes one block in milliseconds, so it checks a seeded sample of
 blocks record by record (first, last and random ones); the whole batch is
@@ -34,8 +35,9 @@ def P():
     P.set_tuning()
 
 
+@pytest.mark.parametrize("flat", [True, False])
 @pytest.mark.parametrize("name", list(CONFIGS))
-def test_full_size_graph_path(P, oracle, name):
+def test_full_size_graph_path(P, oracle, name, flat):
     import torch
     w = CONFIGS[name]()
     nblk = w.nblk
@@ -43,7 +45,7 @@ def test_full_size_graph_path(P, oracle, name):
     data = torch.from_numpy(w.data).cuda()
     blk_off = torch.from_numpy(w.blk_off.astype(np.int64)).cuda()
     with torch.cuda.stream(stream):
-        enc = P.Encoder(nblk, P.params(ans=w.ans))
+        enc = P.Encoder(nblk, P.params(ans=w.ans, flat=flat))
         enc.ensure(enc.plan(data, blk_off, stream))
         dec = P.Decoder(nblk)
         res = enc.run(data, blk_off, stream)
@@ -65,7 +67,7 @@ def test_full_size_graph_path(P, oracle, name):
     comp, off, rb = enc.comp.cpu().numpy(), enc.off.cpu().numpy(), enc.rec_bytes.cpu().numpy()
     rng = np.random.default_rng(2026)
     sample = sorted({0, nblk - 1, *rng.choice(nblk, size=min(nblk, 10), replace=False).tolist()})
-    prm = oracle.params(ans=w.ans)
+    prm = oracle.params(ans=w.ans, flat=flat)
     for b in sample:
         blk = w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])]
         ref = oracle.encode_block(blk, prm)

@@ -76,8 +76,8 @@ WORKLOADS = {
 }
 
 
-def oracle_records(oracle, w, ans):
-    prm = oracle.params(ans=ans)
+def oracle_records(oracle, w, ans, flat=False):
+    prm = oracle.params(ans=ans, flat=flat)
     return [oracle.encode_block(w.data[int(w.blk_off[b]):int(w.blk_off[b + 1])], prm) for b in range(w.nblk)]
 
 
@@ -125,27 +125,31 @@ def test_code_lengths(P, oracle):
             assert np.array_equal(got[i], oracle.code_lengths(h, L)), (L, i)
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("ans", [False, True])
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
-def test_encode_records(P, oracle, name, ans):
+def test_encode_records(P, oracle, name, ans, flat):
+    """Whole records, canonical (PVC1) and regrouped with flat subtrees
+    (PVC2, Sec. 2.2.3-2.2.4), byte for byte."""
     w = WORKLOADS[name]()
-    enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=ans))
+    enc = P.encode(dev(w.data), off64(w.blk_off), P.params(ans=ans, flat=flat))
     st = enc.status.cpu().numpy()
     assert not st.any(), st
     comp, off, rb = enc.comp.cpu().numpy(), enc.off.cpu().numpy(), enc.rec_bytes.cpu().numpy()
-    refs = oracle_records(oracle, w, ans)
+    refs = oracle_records(oracle, w, ans, flat)
     for b, ref in enumerate(refs):
         got = comp[int(off[b]):int(off[b]) + int(rb[b])]
         assert got.size == ref.size, (b, got.size, ref.size)
         assert np.array_equal(got, ref), b
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("ans", [False, True])
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
-def test_decode_oracle_records(P, oracle, name, ans):
+def test_decode_oracle_records(P, oracle, name, ans, flat):
     """The GPU decodes the oracle's dense records to the original bytes."""
     w = WORKLOADS[name]()
-    buf, rec_off, sizes = oracle.encode_batch(w.data, w.blk_off, oracle.params(ans=ans))
+    buf, rec_off, sizes = oracle.encode_batch(w.data, w.blk_off, oracle.params(ans=ans, flat=flat))
     out, st = P.decode(dev(buf if buf.size else np.zeros(16, np.uint8)), off64(rec_off), off64(w.blk_off))
     assert not st.cpu().numpy().any()
     assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
@@ -163,7 +167,9 @@ def test_decode_rejects_corrupt_records(P, oracle):
     rng = np.random.default_rng(3)
     x = rng.choice(40, 30000, p=rng.dirichlet(np.ones(40))).astype(np.uint8)
     y = (rng.random(200000) < 0.95).astype(np.uint8)
-    recs = [oracle.encode_block(x), oracle.encode_block(y, oracle.params(ans=True))]
+    z = rng.integers(0, 64, 20000).astype(np.uint8)
+    recs = [oracle.encode_block(x), oracle.encode_block(y, oracle.params(ans=True)),
+            oracle.encode_block(x, oracle.params(flat=True)), oracle.encode_block(z, oracle.params(flat=True))]
     cases = []
     for r in recs:
         V = int(r[8])
@@ -172,6 +178,11 @@ def test_decode_rejects_corrupt_records(P, oracle):
         c = r.copy(); c[144 + 4 * V] = 99; cases.append((c, r))                    # marker
         c = r.copy(); c[16] = 0xEE; cases.append((c, r))                           # code lengths
         c = r.copy(); c[-20] ^= 0x5A; cases.append((c, r))                         # body bytes
+        c = r.copy(); c[15] ^= 3; cases.append((c, r))                             # tree kind: PVC1 <-> PVC2
+        fm = [v for v in range(V) if r[144 + 4 * V + v] >= 0xF2]
+        if fm:                                                                     # a flat node's marker
+            c = r.copy(); c[144 + 4 * V + fm[0]] += 1; cases.append((c, r))
+            c = r.copy(); c[144 + 4 * V + fm[0]] = 0; cases.append((c, r))
     for c, r in cases:
         n = int(np.frombuffer(r[4:8].tobytes(), np.uint32)[0])
         out, st = P.decode(dev(c), off64([0, c.size]), off64([0, n]))
@@ -264,14 +275,15 @@ def test_histogram_chunks(P, oracle, name):
             assert np.array_equal(gch[b, c], want), (b, c)
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("name", ["shifting", "mixed_24", "edge"])
-def test_encode_plain_equals_chunked(P, name):
+def test_encode_plain_equals_chunked(P, name, flat):
     """pivco_encode_blocks (chunks counted in the encoder) and
     pivco_encode_blocks_chunked write the same records."""
     import torch
     w = WORKLOADS[name]()
     data, boff = dev(w.data), off64(w.blk_off)
-    enc = P.Encoder(w.nblk)
+    enc = P.Encoder(w.nblk, P.params(flat=flat))
     total = enc.plan(data, boff)
     enc.ensure(total)
     P.encode_blocks_chunked(data, boff, w.nblk, enc.layout, enc.chunk_hist, enc.comp, enc.off, enc.rec_bytes,
@@ -373,16 +385,17 @@ def test_misaligned_records_rejected(P):
         assert np.array_equal(out.cpu().numpy()[: w.data.size], w.data)
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
 @pytest.mark.parametrize("ans", [False, True])
-def test_plan_blocks_equals_steps(P, name, ans):
+def test_plan_blocks_equals_steps(P, name, ans, flat):
     """The one-launch plan writes what the histogram, code-length and layout
     calls write one after another."""
     import torch
     w = WORKLOADS[name]()
     n = w.nblk
     data, boff = dev(w.data), off64(w.blk_off)
-    prm = P.params(ans=ans)
+    prm = P.params(ans=ans, flat=flat)
 
     def bufs():
         return (torch.zeros(n * 256, dtype=torch.int32, device="cuda"),
