@@ -603,6 +603,23 @@ def main(argv=None):
             del wc, rc
             torch.cuda.empty_cache()
 
+    # the same workload coded with the other tree (canonical against the
+    # regrouped one with flat subtrees, Sec. 2.2.3-2.2.4)
+    other_tree = None
+    if not args.no_per_config:
+        FLAT = not FLAT
+        ro = measure(P, torch, w, dev, stream, flush, max(3, args.steps // 4), 3, not args.no_autotune)
+        so = summarize(ro, world, dev, peak_gbs, issue_peak, args.workload)
+        FLAT = not FLAT
+        other_tree = {"tree": TREE_DESC["canonical" if FLAT else "flat"], "value": so["value"],
+                      "encode_gbs": so["encode_gbs"], "decode_gbs": so["decode_gbs"],
+                      "compressed_bytes": ro["rec_bytes"], "verified": ro["ok"],
+                      "encode_kernel_ms": so["roofline"]["kernels"]["encode_kernel"]["ms"],
+                      "decode_batch_kernel_ms": so["roofline"]["kernels"]["decode_batch_kernel"]["ms"]}
+        ok = ok and ro["ok"]
+        del ro
+        torch.cuda.empty_cache()
+
     # end to end through the public host-buffer API (pivco_host_compress /
     # pivco_host_decompress) with pinned host buffers: every step copies the
     # raw bytes in and the records out, then the records in and the bytes out
@@ -657,6 +674,7 @@ def main(argv=None):
             "roofline": dict(head["roofline"], peak_source="%s (MEASURED_PEAKS.json hbm_gbs, sm_max_mhz; %d SMs)"
                              % (peak_kind, sms)),
             "per_config": per_config,
+            "other_tree": other_tree,
             "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks, "verified": ok,
             "checks": r["checks"],

@@ -492,10 +492,15 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                 for (int d = 0; d <= 16; d++) L.tree_a[d] = (uint16_t)(flat ? F.a[d] : ts.a[d]);
             }
             if (flat) {
-                // regrouped codes: symbol x of item i is (code_i << D) | x
-                if (t < F.nitems) {
-                    const uint32_t c = flat_item_code(F, t), D = F.iD[t];
-                    for (uint32_t x = 0; x < (1u << D); x++) codes[sorted[F.iso[t] + x]] = (uint16_t)((c << D) | x);
+                // regrouped codes (symbol x of item i is (code_i << D) | x) and
+                // code indices (its item's code-order offset + x), per symbol
+                if (t < K) {
+                    const int sy = sorted[t], l = lens[sy];
+                    int i;
+                    uint32_t x;
+                    flat_sym(F, ts.cnt, l, t - ts.len_base[l], i, x);
+                    codes[sy] = (uint16_t)((flat_item_code(F, i) << F.iD[i]) | x);
+                    L.ci[sy] = (uint8_t)(F.ioff[i] + x);
                 }
                 __syncthreads();
             }
@@ -528,13 +533,30 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                 st = PIVCO_ERR_INVALID_ARG;
             } else {
                 if (flat) {
-                    // code index: the place of a symbol's code among the left-aligned codes
-                    if (lens[t]) {
-                        const uint32_t key = (uint32_t)codes[t] << (15 - lens[t]);
-                        int r = 0;
-                        for (int s2 = 0; s2 < 256; s2++)
-                            r += lens[s2] && ((uint32_t)codes[s2] << (15 - lens[s2])) < key;
-                        L.ci[t] = (uint8_t)r;
+                    // a flat node's count from prefix sums of the block's
+                    // counts in code order (its symbols are consecutive there)
+                    uint32_t *hc = reinterpret_cast<uint32_t *>(scratch);   // 256 counts, then warp sums
+                    hc[t] = 0;
+                    __syncthreads();
+                    if (lens[t]) hc[L.ci[t]] = h[t];
+                    __syncthreads();
+                    uint32_t x = hc[t], inc = x;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if ((t & 31) >= o) inc += y;
+                    }
+                    __shared__ uint32_t wsum[kLayThreads / 32];
+                    if ((t & 31) == 31) wsum[t >> 5] = inc;
+                    __syncthreads();
+                    for (int w2 = 0; w2 < (t >> 5); w2++) inc += wsum[w2];
+                    __syncthreads();
+                    hc[t] = inc - x;            // exclusive prefix: counts of code indices < t
+                    __syncthreads();
+                    if (t < V && L.fd[t]) {
+                        const uint32_t D = L.fd[t], lo = L.ci[sorted[L.fbase[t]]], hi = lo + (1u << D) - 1u;
+                        L.nlo[t] = (uint8_t)lo;
+                        L.nhi1[t] = (uint8_t)hi;
+                        L.nv[t] = (hi + 1 < 256 ? hc[hi + 1] : (uint32_t)n) - hc[lo];
                     }
                 } else if (t < K) {
                     L.ci[sorted[t]] = (uint8_t)t;
@@ -547,15 +569,7 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                 for (int d = maxd - 1; d >= 0; d--) {
                     const int v = fst[d] + t;
                     if (v < fst[d + 1] && v < V) {
-                        const uint32_t D = L.fd[v];
-                        if (D) {
-                            const uint32_t base = L.fbase[v];
-                            uint32_t c = 0;
-                            for (uint32_t x = 0; x < (1u << D); x++) c += h[sorted[base + x]];
-                            L.nv[v] = c;
-                            L.nlo[v] = L.ci[sorted[base]];
-                            L.nhi1[v] = L.ci[sorted[base + (1u << D) - 1]];
-                        } else {
+                        if (!L.fd[v]) {   // (a flat node's count and range are set)
                             uint32_t c = 0;
                             for (int k = 0; k < 2; k++) {
                                 const int ch = L.child[v][k];

@@ -227,8 +227,10 @@ struct FlatTree {
     int32_t nitems, maxd, n_nodes, ok;
     uint8_t it_of[16][9];         // item of length d and rank r
     uint8_t in_of[16][9];         // k-th item node of depth d
+    uint8_t item_ld[16][9];       // item of length class l made of 2^D symbols
     uint8_t iD[kMaxItems], il[kMaxItems], irank[kMaxItems], ik[kMaxItems];
     uint16_t iso[kMaxItems];      // index of the item's first symbol in (length, symbol) order
+    uint16_t ioff[kMaxItems];     // symbols of the items before it in code order
 };
 
 // Builds the item tree of the code lengths (one warp, all lanes).  cnt[l]:
@@ -237,75 +239,109 @@ struct FlatTree {
 // make a full tree.
 __device__ inline void flat_tree_build(const int32_t *cnt, const int32_t *start, const uint8_t *sorted, FlatTree &F) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        int n = 0;
-        bool ok = true;
-        for (int d = 0; d < 18; d++) F.icnt[d] = 0;
-        for (int l = 1; l <= (int)kMaxLen; l++) {
-            const int c = cnt[l];
-            if (c < 0 || c > 256) ok = false;
-            int acc = 0;
-            for (int D = 8; D >= 0 && ok; D--) {
-                if (!((c >> D) & 1)) continue;
-                if (D > l || n >= kMaxItems) { ok = false; break; }
-                F.iD[n] = (uint8_t)D;
-                F.il[n] = (uint8_t)(l - D);
-                F.iso[n] = (uint16_t)(start[l] + acc);
-                F.icnt[l - D]++;
-                acc += 1 << D;
-                n++;
-            }
-        }
-        F.nitems = n;
-        F.ok = ok;
+    // lane l makes the items of length class l: one per set bit D of its
+    // count, largest first, each taking the next 2^D symbols of the class
+    const int c = (lane >= 1 && lane <= (int)kMaxLen) ? cnt[lane] : 0;
+    bool ok = c >= 0 && c <= 256 && (c >> (lane < 9 ? lane + 1 : 9)) == 0;   // at most 2^l symbols of length l
+    const int mine = __popc((uint32_t)c & 0x1FFu);
+    int base = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, base, o);
+        if (lane >= o) base += y;
     }
+    const int total = __shfl_sync(0xffffffffu, base, 31);
+    base -= mine;
+    if (lane < 18) F.icnt[lane] = 0;
+    __syncwarp();
+    if (ok && total <= kMaxItems) {
+        int i = base, acc = 0;
+        for (int D = 8; D >= 0; D--) {
+            if (!((c >> D) & 1)) continue;
+            F.iD[i] = (uint8_t)D;
+            F.il[i] = (uint8_t)(lane - D);
+            F.iso[i] = (uint16_t)(start[lane] + acc);
+            F.item_ld[lane][D] = (uint8_t)i;
+            atomicAdd(&F.icnt[lane - D], 1);
+            acc += 1 << D;
+            i++;
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok) && total <= kMaxItems;
+    const int n = ok ? total : 0;
     __syncwarp();
     // rank of an item among the items of its length, by first symbol
-    for (int i = lane; i < F.nitems; i += 32) {
+    for (int i = lane; i < n; i += 32) {
         const uint32_t fs = sorted[F.iso[i]];
         int r = 0;
-        for (int j = 0; j < F.nitems; j++) r += F.il[j] == F.il[i] && sorted[F.iso[j]] < fs;
+        for (int j = 0; j < n; j++) r += F.il[j] == F.il[i] && sorted[F.iso[j]] < fs;
         F.irank[i] = (uint8_t)r;
+        if (r < 9) F.it_of[F.il[i]][r] = (uint8_t)i;
+        else ok = false;
     }
+    int maxil = 0;
+    for (int i = lane; i < n; i += 32) maxil = max(maxil, (int)F.il[i]);
+    maxil = __reduce_max_sync(0xffffffffu, (uint32_t)maxil);
+    ok = __all_sync(0xffffffffu, ok);
     __syncwarp();
-    if (lane == 0) {
-        bool ok = F.ok != 0;
-        int maxil = 0;
-        for (int i = 0; i < F.nitems; i++) {
-            if (F.irank[i] >= 9 || F.il[i] > 15) { ok = false; break; }
-            F.it_of[F.il[i]][F.irank[i]] = (uint8_t)i;
-            maxil = F.il[i] > maxil ? F.il[i] : maxil;
-        }
-        // Kraft equality at the item level: the items fill the tree
+    // depth d = lane: Kraft equality at the item level (a[d] d-bit prefixes
+    // covered by items of length <= d), the item nodes of depth d in rank
+    // order, then the item tree's own nodes
+    int cnt_d = 0;
+    if (lane < 18) {
         int64_t a = 0;
-        for (int d = 0; d < 18; d++) {
-            a = d ? 2 * a + F.icnt[d] : F.icnt[0];
-            F.a[d] = (int32_t)(a > 0x7FFFFFFF ? 0x7FFFFFFF : a);
-            if (d <= 15 && a > (int64_t(1) << d)) ok = false;
-            if (d < maxil && a >= (int64_t(1) << d)) ok = false;
-            if (d == maxil && a != (int64_t(1) << d)) ok = false;
+        for (int j = 0; j <= lane; j++) a = 2 * a + F.icnt[j];
+        F.a[lane] = (int32_t)(a > 0x7FFFFFFF ? 0x7FFFFFFF : a);
+        if (lane <= 15 && a > (int64_t(1) << lane)) ok = false;
+        if (lane < maxil && a >= (int64_t(1) << lane)) ok = false;
+        if (lane == maxil && a != (int64_t(1) << lane)) ok = false;
+        int k = 0;
+        if (lane <= maxil && lane < 16)
+            for (int r = 0; r < F.icnt[lane] && r < 9; r++) {
+                const int i = F.it_of[lane][r];
+                if (F.iD[i] >= 1) { F.in_of[lane][k] = (uint8_t)i; F.ik[i] = (uint8_t)k; k++; }
+            }
+        F.nin[lane] = k;
+        const int64_t open = lane < maxil ? (int64_t(1) << lane) - a : 0;
+        cnt_d = lane < 17 ? k + (int)(open > 0 ? open : 0) : 0;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    int f = cnt_d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, f, o);
+        if (lane >= o) f += y;
+    }
+    if (lane < 18) F.first[lane] = f - cnt_d;
+    const int n_nodes = __shfl_sync(0xffffffffu, f, 31);
+    const uint32_t used = __ballot_sync(0xffffffffu, cnt_d > 0);
+    // code order of the items: by (length, rank); the symbols of the items
+    // before each one
+    if (ok) {
+        for (int i = lane; i < n; i += 32) {
+            uint32_t off = 0;
+            for (int j = 0; j < n; j++)
+                if (F.il[j] < F.il[i] || (F.il[j] == F.il[i] && F.irank[j] < F.irank[i])) off += 1u << F.iD[j];
+            F.ioff[i] = (uint16_t)off;
         }
-        int f = 0, maxd = 0;
-        for (int d = 0; d < 17; d++) {
-            F.first[d] = f;
-            int k = 0;
-            if (ok && d <= maxil)
-                for (int r = 0; r < F.icnt[d] && r < 9; r++) {
-                    const int i = F.it_of[d][r];
-                    if (F.iD[i] >= 1) { F.in_of[d][k] = (uint8_t)i; F.ik[i] = (uint8_t)k; k++; }
-                }
-            F.nin[d] = k;
-            const int open = (ok && d < maxil) ? (1 << d) - F.a[d] : 0;
-            if (k + open > 0) maxd = d + 1;
-            f += k + open;
-        }
-        F.first[17] = f;
-        F.nin[17] = 0;
-        F.maxd = maxd;
-        F.n_nodes = f;
-        F.ok = ok && f >= 1 && f <= 255;
+    }
+    if (lane == 0) {
+        F.nitems = n;
+        F.maxd = used ? 32 - __clz(used) : 0;
+        F.n_nodes = n_nodes;
+        F.ok = ok && n_nodes >= 1 && n_nodes <= 255;
     }
     __syncwarp();
+}
+
+// Symbol number r (0-based) of length class l: its item (l, D) is the group
+// whose range holds r, D the highest bit where the class count has a one
+// and r a zero; x = r's low D bits is its index in the group.
+__device__ inline void flat_sym(const FlatTree &F, const int32_t *cnt, int l, int r, int &item, uint32_t &x) {
+    const uint32_t c = (uint32_t)cnt[l], m = c & ~(uint32_t)r;
+    const int D = m ? 31 - __clz(m) : 0;
+    item = F.item_ld[l][D];
+    x = (uint32_t)r & ((1u << D) - 1u);
 }
 
 // code of item i's prefix (its item length F.il[i] bits)
