@@ -382,8 +382,10 @@ uint64_t pivco_get_wait_limit(void);
 /* ---- Batching (not in the paper: the GPU scheduling of many blocks) ----
  * pivco_decode_batched decodes the same records as pivco_decode_blocks (same
  * arguments, same workspace size, identical output) with one persistent
- * launch whose work queue is keyed by (block, stage): record plans, ANS
- * segments, rank directories, root tiles.  Each item waits (bounded, 1 s)
+ * launch whose work queue is keyed by (block, stage): record plans, first
+ * tiles (the only tile of a block that needs no ANS segment and no
+ * directory, as soon as its own plan is complete), ANS segments, rank
+ * directories, the other tiles.  Each item waits (bounded, by default 1 s)
  * only on items earlier in the queue; an expired wait marks the block
  * PIVCO_ERR_TIMEOUT. */
 pivco_status pivco_decode_batched(const uint8_t *comp, const uint64_t *comp_off, int32_t nblk,

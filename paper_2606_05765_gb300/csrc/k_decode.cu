@@ -451,9 +451,11 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
             if (to) atomicExch(&hdr32[13], 1u);
         }
     }
-    // the node table (only where the workspace holds it: a sizing run may not)
+    // the node table (only where the workspace holds it: a sizing run may
+    // not; and never from a partial prefix, which would place it over
+    // another block's table)
     const uint64_t nbase = decode_ws_fixed_bytes(nblk) + (eb >> 22);
-    if (ok && coded && nbase + ntab_bytes(R.V) <= ws_bytes) {
+    if (ok && coded && !to && nbase + ntab_bytes(R.V) <= ws_bytes) {
         uint8_t *nt = ws + nbase;
         if (lane < 17) nt[lane] = (uint8_t)Q.first[lane];
         if (lane == 17) nt[17] = (uint8_t)Q.maxd;
@@ -470,6 +472,14 @@ __device__ inline void plan_block(int b, const uint8_t *__restrict__ comp, const
         }
         uint8_t *sym = nt + kNtabHdr + 12 * R.V;
         for (int i = lane; i < 256; i += 32) sym[i] = Q.sorted[i];
+    }
+    __syncwarp();
+    // the plan is complete (status, offsets, node table); a block of one tile
+    // with no ANS segment and no directory can be decoded from here on
+    if (lane == 0) {
+        const bool simple = ok && !to && ntile == 1 && sg == 0 && !all_dirs;
+        __threadfence();
+        atomicExch(&W.plan_done[b], simple ? 3u : 1u);
     }
     __syncwarp();
 }
@@ -495,6 +505,7 @@ __global__ void dec_ws_init_kernel(uint8_t *ws, int nblk, uint32_t dir_bits, uin
         W.states_b[i] = 0;
         W.segs_done[i] = 0;
         W.dir_done[i] = 0;
+        W.plan_done[i] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x < 16) {
         uint32_t *h = reinterpret_cast<uint32_t *>(ws);
@@ -811,7 +822,7 @@ __device__ inline void flat32_t(const TileSrc &s, uint32_t pos, const uint8_t *t
     const uint64_t lim = s.rec_bytes;
     uint32_t x[D + 1], b[D];
 #pragma unroll
-    for (int k = 0; k <= D; k++) x[k] = 4 * (wi + k) + 4 <= lim ? __ldcg(w + wi + k) : 0u;
+    for (int k = 0; k <= D; k++) x[k] = 4 * (wi + k) + 4 <= lim ? __ldca(w + wi + k) : 0u;
 #pragma unroll
     for (int k = 0; k < D; k++) b[k] = __funnelshift_r(x[k], x[k + 1], sh);
     constexpr uint32_t m = (1u << D) - 1u;
@@ -839,6 +850,14 @@ __device__ inline void flat32(const TileSrc &s, uint32_t D, uint32_t pos, const 
         case 7: flat32_t<7>(s, pos, tab, o); break;
         default: flat32_t<8>(s, pos, tab, o); break;
     }
+}
+
+// L1 prefetch of the words under 32 indices of a flat node (<= 36 bytes)
+__device__ inline void flat_prefetch(const TileSrc &s, uint32_t D, uint32_t pos) {
+    const uint64_t e = pos & 0x7FFFFFFFu;
+    const uint64_t b0 = (e >> 5) * 4, b1 = ((e + 32ull * D) >> 5) * 4;
+    if (b0 < s.rec_bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"(s.rec + b0));
+    if ((b1 >> 7) != (b0 >> 7) && b1 < s.rec_bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"(s.rec + b1));
 }
 
 // the children's demands must be the node's zeros and ones
@@ -998,13 +1017,21 @@ __device__ inline void ct_fetch(const CtaTile &S, const TileSrc &src, int d, uin
         if (base < G) {
             const uint32_t u = S.wnode[S.wn_off[d] + (base >> 5)];
             L = wt_locate(S, S.first[d + 1], G, base, (uint32_t)S.gs[u] == base ? u - 1 : u);
-            if (L.act && !ch_flat_d(S.ch[L.v])) ld = tile_ld(src, S.pos[L.v], L.kk);
+            if (L.act) {
+                const uint32_t fD = ch_flat_d(S.ch[L.v]);
+                if (fD) flat_prefetch(src, fD, S.pos[L.v] + L.kk * fD);
+                else ld = tile_ld(src, S.pos[L.v], L.kk);
+            }
         }
     } else if (d == 0) {
         L.dv = S.dem[0];
         L.kk = 32u * (base + lane);
         L.act = L.kk < L.dv;
-        if (L.act && !ch_flat_d(S.ch[0])) ld = tile_ld(src, S.pos[0], L.kk);
+        if (L.act) {
+            const uint32_t fD = ch_flat_d(S.ch[0]);
+            if (fD) flat_prefetch(src, fD, S.pos[0] + L.kk * fD);
+            else ld = tile_ld(src, S.pos[0], L.kk);
+        }
     }
 }
 
@@ -1239,6 +1266,9 @@ __device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, c
         const uint32_t dc = ((c0 & 0x8000u) ? 0u : S.dem[c0]) + ((c1 & 0x8000u) ? 0u : S.dem[c1]);
         if (dc > S.dem[t]) bad = 1;
     }
+    // the node table's levels: at most 16, first nodes non-decreasing up to V
+    if (t == 0 && (S.maxd < 1 || S.maxd > 16 || S.first[0] != 0 || S.first[S.maxd] != V)) bad = 1;
+    if (t >= 1 && t <= 16 && t <= S.maxd && S.first[t] < S.first[t - 1]) bad = 1;
     if (__syncthreads_or(bad)) {
         if (t == 0) status[b] = PIVCO_ERR_CORRUPT;
         return;
@@ -1727,10 +1757,12 @@ __device__ inline uint64_t wait_bound(const BatchQueue &q) { return reinterpret_
 __device__ inline uint32_t batch_nplan(int nblk) { return (uint32_t)((nblk + kPlanWarps - 1) / kPlanWarps); }
 __device__ inline uint32_t batch_ndir(int nblk) { return (uint32_t)((nblk + kDecWarps - 1) / kDecWarps); }
 
-// Items of a batch's queue once all plans are done (header written by the last plan).
+// Items of a batch's queue once all plans are done (header written by the last plan):
+// plans, first tiles (one per block), ANS segments, directories, tiles.
 __device__ inline uint32_t batch_items_total(const BatchQueue &q) {
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(q.ws);
-    return batch_nplan(q.nblk) + (hdr[2] + kPlanWarps - 1) / kPlanWarps + batch_ndir(q.nblk) + hdr[6];
+    return batch_nplan(q.nblk) + (uint32_t)q.nblk + (hdr[2] + kPlanWarps - 1) / kPlanWarps + batch_ndir(q.nblk) +
+           hdr[6];
 }
 
 enum : int { kItemDone = 0, kItemNone = 1, kItemStop = 2 };
@@ -1763,7 +1795,26 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
         if (t == 0) { __threadfence(); atomicAdd(&hdr[10], 1u); }
         return kItemDone;
     }
-    // everything after the plans needs all plans
+    if (item < nplan + (uint32_t)nblk) {
+        // ---- first tiles: block b's only tile as soon as its own plan is
+        // complete, when it needs no ANS segment and no directory (its node
+        // table and offsets are then all it reads); other blocks' tiles come
+        // after the directories ----
+        const int b = (int)(item - nplan);
+        if (t == 0) {
+            const int okw = wait_geq(&W.plan_done[b], 1u, wait_bound(q));
+            if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
+            B.ok = okw ? (int)*reinterpret_cast<volatile uint32_t *>(&W.plan_done[b]) : 0;
+        }
+        __syncthreads();
+        const int pd = B.ok;
+        __syncthreads();
+        if (pd & 2) cta_tile(W.blk_tile[b], q.comp, q.comp_off, nblk, q.out, q.out_off, q.ws, q.ws_bytes, q.status,
+                             B.u.tile, B.sel, b);
+        __syncthreads();
+        return kItemDone;
+    }
+    // everything after the plans and first tiles needs all plans
     int ok = 1;
     if (t == 0) {
         ok = wait_geq(&hdr[10], nplan, wait_bound(q));
@@ -1785,7 +1836,7 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
     }
     const uint32_t total_segs = hdr[2];
     const uint32_t nseg_items = (total_segs + kPlanWarps - 1) / kPlanWarps;
-    uint32_t it = item - nplan;
+    uint32_t it = item - nplan - (uint32_t)nblk;
     if (it < nseg_items) {
         // ---- ANS segments ----
         const uint32_t g = it * kPlanWarps + warp;
@@ -1839,14 +1890,20 @@ __device__ inline int batch_item(const BatchQueue &q, uint32_t item, BatchSmem &
     }
     it -= ndir;
     if (it >= hdr[6]) return kItemNone;
-    // ---- tile it: after its block's ANS segments and directory ----
+    // ---- tile it: after its block's ANS segments and directory (a tile
+    // decoded among the first tiles is skipped) ----
     if (warp == 0) {
         const int b = find_block_warp(W.blk_tile, nblk, it, (int)((uint64_t)it * (uint32_t)nblk / max(hdr[6], 1u)));
         if (lane == 0) {
-            const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
-            int okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
-            if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u, wait_bound(q));
-            if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
+            int okw = 1;
+            if (W.plan_done[b] & 2u) {
+                okw = 0;
+            } else {
+                const uint32_t nsegs = (b + 1 < nblk ? W.blk_seg[b + 1] : total_segs) - W.blk_seg[b];
+                okw = wait_geq(&W.segs_done[b], nsegs, wait_bound(q));
+                if (okw && W.blk_ntile[b] > 1) okw = wait_geq(&W.dir_done[b], 1u, wait_bound(q));
+                if (!okw) q.status[b] = PIVCO_ERR_TIMEOUT;
+            }
             B.blk = b;
             B.ok = okw;
         }

@@ -464,9 +464,10 @@ cudaError_t launch_ans_decode(const uint8_t *bodies, const uint64_t *body_off, c
 struct DecWs {
     uint64_t *states_a, *states_b, *blk_scratch, *blk_dir;
     uint32_t *blk_seg, *blk_tile, *blk_T, *blk_ntile, *segs_done, *dir_done;
+    uint32_t *plan_done;   // 1 | 2 (one tile, no ANS, no directory) once the block's plan is complete
 };
 __host__ __device__ inline size_t decode_ws_fixed_bytes(int nblk) {
-    const size_t f = 64 + 32ull * nblk + 24ull * nblk;
+    const size_t f = 64 + 32ull * nblk + 28ull * nblk;
     return (f + 255) & ~(size_t)255;
 }
 
@@ -490,6 +491,7 @@ __host__ __device__ inline DecWs dec_ws(uint8_t *ws, int nblk) {
     w.blk_ntile = w.blk_T + nblk;
     w.segs_done = w.blk_ntile + nblk;
     w.dir_done = w.segs_done + nblk;
+    w.plan_done = w.dir_done + nblk;
     return w;
 }
 struct DecRegions {

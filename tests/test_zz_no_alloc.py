@@ -60,7 +60,7 @@ def test_static_matches_workspace_decode_twice(P):
 
 def test_static_rejects_oversized_batch(P):
     import torch
-    # the plan part alone of 400k blocks (56 bytes each) exceeds 16 MiB: refused on the host
+    # the plan part alone of 400k blocks (60 bytes each) exceeds 16 MiB: refused on the host
     n = 400_000
     comp = torch.zeros(16, dtype=torch.uint8, device="cuda")
     offs = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
