@@ -150,7 +150,7 @@ pivco_status pivco_exclusive_scan(const uint64_t *in, int32_t n, uint64_t *out, 
  * for ANS are written raw with marker 0xFF; pivco_ans_encode_blocks then codes
  * them.  rec_bytes[b] (device) receives the record size.  status[b] (device). */
 pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
-                                 const void *layout, uint8_t *out, const uint64_t *out_off,
+                                 void *layout, uint8_t *out, const uint64_t *out_off,
                                  uint64_t *rec_bytes, int32_t *status, void *stream);
 
 /* The encoder's warp chunks counted in the histogram pass.  Block b of n
@@ -169,11 +169,16 @@ pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int
  * `in` (another input, or stale) never give a wrong record with an OK
  * status: a block is either refused (status[b] = PIVCO_ERR_INVALID_ARG) or,
  * when the sums it used are right after all, encoded exactly; nothing is
- * written outside each block's record. */
+ * written outside each block's record.  A block whose levels do not fit
+ * the encoder's buffers is coded chunk by chunk by several CTAs (a work
+ * list of (block, chunk) items); each chunk starts at the node cursors its
+ * preceding chunks' histograms give.  Both encode calls keep that work list
+ * in scratch words at the end of the layout records, so one layout serves
+ * one encode call at a time. */
 pivco_status pivco_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
                                     uint32_t *hist, uint32_t *chunk_hist, void *stream);
 pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_off, int32_t nblk,
-                                         const void *layout, const uint32_t *chunk_hist, uint8_t *out,
+                                         void *layout, const uint32_t *chunk_hist, uint8_t *out,
                                          const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status,
                                          void *stream);
 

@@ -184,13 +184,13 @@ pivco_status pivco_exclusive_scan(const uint64_t *in, int32_t n, uint64_t *out, 
     return ok_or_cuda(launch_scan(in, n, out, ws, status_out, S(stream)));
 }
 
-pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, const void *layout,
+pivco_status pivco_encode_blocks(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, void *layout,
                                  uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes, int32_t *status,
                                  void *stream) {
     if (nblk < 0 || (nblk > 0 && (!blk_off || !layout || !out || !out_off || !rec_bytes || !status)))
         return PIVCO_ERR_INVALID_ARG;
     if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
-    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), nullptr, out,
+    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<BlockLayout *>(layout), nullptr, out,
                                     out_off, rec_bytes, status, S(stream)));
 }
 
@@ -201,13 +201,13 @@ pivco_status pivco_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, 
     return ok_or_cuda(launch_histogram_chunks(in, blk_off, nblk, hist, chunk_hist, S(stream)));
 }
 
-pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, const void *layout,
+pivco_status pivco_encode_blocks_chunked(const uint8_t *in, const uint64_t *blk_off, int32_t nblk, void *layout,
                                          const uint32_t *chunk_hist, uint8_t *out, const uint64_t *out_off,
                                          uint64_t *rec_bytes, int32_t *status, void *stream) {
     if (nblk < 0 || (nblk > 0 && (!blk_off || !layout || !chunk_hist || !out || !out_off || !rec_bytes || !status)))
         return PIVCO_ERR_INVALID_ARG;
     if (nblk > 0 && !layout_aligned(layout)) return PIVCO_ERR_INVALID_ARG;
-    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<const BlockLayout *>(layout), chunk_hist, out,
+    return ok_or_cuda(launch_encode(in, blk_off, nblk, reinterpret_cast<BlockLayout *>(layout), chunk_hist, out,
                                     out_off, rec_bytes, status, S(stream)));
 }
 

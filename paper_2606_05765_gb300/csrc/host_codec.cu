@@ -246,7 +246,7 @@ pivco_status pivco_host_compress(pivco_host_codec *c, const uint8_t *in, uint8_t
         HC_TRY(pv::launch_block_plan(src, g.boff, g.nb, c->prm, g.hist, g.chunk, g.lens,
                                      reinterpret_cast<pv::BlockLayout *>(g.layout), g.bound, g.status, cmp));
         HC_TRY(pv::launch_scan(g.bound, g.nb, g.off, g.scan_ws, g.status, cmp));
-        HC_TRY(pv::launch_encode(src, g.boff, g.nb, reinterpret_cast<const pv::BlockLayout *>(g.layout), g.chunk,
+        HC_TRY(pv::launch_encode(src, g.boff, g.nb, reinterpret_cast<pv::BlockLayout *>(g.layout), g.chunk,
                                  g.comp, g.off, g.rec_bytes, g.status, cmp));
         if (c->prm.ans_enable)
             HC_TRY(pv::launch_ans_encode_blocks(reinterpret_cast<const pv::BlockLayout *>(g.layout), g.nb, g.comp,

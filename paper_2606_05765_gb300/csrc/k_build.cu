@@ -588,6 +588,14 @@ __device__ inline void build_layout_block(int b, const uint32_t *h, const uint8_
                     const uint64_t n1 = c >= 0 ? L.nv[c] : h[-c - 1];
                     L.sel[t] = ans_select(L.nv[t], n1, L.depth[t], sp);
                 }
+                // a big block: some level (depth >= 1) of the whole block
+                // does not fit an encoder level buffer (spans of whole
+                // 16-byte units), so the chunked encoder splits it
+                if (t >= 1 && t < maxd) {
+                    uint64_t lvl = 0;
+                    for (int v = fst[t]; v < fst[t + 1]; v++) lvl += ((uint64_t)L.nv[v] + 7u) & ~7ull;
+                    if (lvl > (uint64_t)kEBuf && enc_nchunks(n) >= 2) L.big = 1;
+                }
                 __syncthreads();
             if (t < 32) {
                 // bodies: the raw (unselected) nodes first, then the selected ones, node order

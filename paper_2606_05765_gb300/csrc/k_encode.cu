@@ -28,7 +28,6 @@ namespace pv {
 constexpr int kEncThreads = 256;
 constexpr int kEncWarps = kEncThreads / 32;
 constexpr int kEncCtasPerSm = 3;
-constexpr int kEBuf = 13824;                // symbols per level buffer (a skew80 64 KiB block in one chunk)
 constexpr int kESlack = 48;                 // over-read room (symbols)
 constexpr int kEWinPerLvl = 32;             // windows of a level below the root (<= kEBuf/32 + 128 groups)
 
@@ -349,24 +348,28 @@ __device__ inline void flat_emit_d(uint32_t D, uint32_t *rec32, uint32_t a, cons
     }
 }
 
-__global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(const uint8_t *__restrict__ in,
-                                                                            const uint64_t *__restrict__ blk_off,
-                                                                            const BlockLayout *__restrict__ layout,
-                                                                            const uint32_t *__restrict__ chunk_hist,
-                                                                            uint8_t *__restrict__ out,
-                                                                            const uint64_t *__restrict__ out_off,
-                                                                            uint64_t *__restrict__ rec_bytes,
-                                                                            int32_t *__restrict__ status) {
-    extern __shared__ __align__(128) uint8_t smem_raw[];
-    EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
-    const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+// Codes plan chunks cA .. cB - 1 of block b with the whole CTA (every
+// thread calls it with the same arguments).  whole: the block entire, its
+// header written, its body zeroed here and its status written; else one
+// chunk of a big block: the reset pass has checked the block, zeroed its
+// body and set its status, the chunk starts at the node cursors the counts
+// of the chunks before it give, chunk 0 writes the header and tables, and
+// the status only ever turns to an error.
+template <bool whole>
+__device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_t *__restrict__ in,
+                                   const uint64_t *__restrict__ blk_off, const BlockLayout *__restrict__ layout,
+                                   const uint32_t *__restrict__ chunk_hist, uint8_t *__restrict__ out,
+                                   const uint64_t *__restrict__ out_off, uint64_t *__restrict__ rec_bytes,
+                                   int32_t *__restrict__ status, EncSmem &S) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint64_t i0 = blk_off[b], i1 = blk_off[b + 1], o0 = out_off[b], o1 = out_off[b + 1];
-    // the block's input is read by the root pass: ask L2 for it now, so
+    const uint32_t nw = enc_nchunks(i1 - i0), cEnd = cB < nw ? cB : nw;
+    // the item's input is read by the root pass: ask L2 for it now, so
     // those reads find it there
     {
-        const uint8_t *p0 = in + i0;
-        const uint64_t nb = i1 - i0;
-        for (uint64_t i = 128ull * t; i < nb; i += 128ull * kEncThreads)
+        const uint64_t lo = enc_chunk_start(i1 - i0, cA, nw), hi = enc_chunk_start(i1 - i0, cEnd, nw);
+        const uint8_t *p0 = in + i0 + lo;
+        for (uint64_t i = 128ull * t; i < hi - lo; i += 128ull * kEncThreads)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + i));
     }
     // the block's layout, staged into shared memory once (coalesced); it
@@ -390,14 +393,15 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     if (L.status != 0) st = L.status;
     else if (L.n != n || (reinterpret_cast<uintptr_t>(rec) & 15)) st = PIVCO_ERR_INVALID_ARG;
     else if (cap < L.rec_bound) st = PIVCO_ERR_CAPACITY;
-    if (st != PIVCO_OK) {
-        if (t == 0) { status[b] = st; rec_bytes[b] = 0; }
+    if (st != PIVCO_OK || (!whole && kind != 2)) {   // (the reset pass has reported a big block's)
+        if (t == 0 && whole) { status[b] = st; rec_bytes[b] = 0; }
         return;
     }
     const int V = L.n_int;
     const uint32_t rec_bound = L.rec_bound;   // the staged layout is overwritten once the levels start
+    const bool head = whole || cA == 0;   // this item writes the header and tables
     // ---- record header (App. D, adapted) ----
-    if (t < 16) {
+    if (t < 16 && head) {
         uint8_t v = 0;
         const uint32_t rb = L.rec_bound;
         if (t < 4) v = (uint8_t)(rb >> (8 * t));
@@ -414,15 +418,15 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
         return;
     }
     // the record start is 16-byte aligned: the length nibbles and n_v as words
-    if (t < 32) {
+    if (t < 32 && head) {
         uint32_t x = 0;
 #pragma unroll
         for (int j = 0; j < 8; j++) x |= (uint32_t)(L.len[8 * t + j] & 15u) << (4 * j);
         reinterpret_cast<uint32_t *>(rec + kLensOff)[t] = x;
     }
-    if (t < V) reinterpret_cast<uint32_t *>(rec + kNvOff)[t] = L.nv[t];
-    if (t < V) rec[kNvOff + 4 * V + t] = L.fd[t] ? (uint8_t)(kMarkFlat + L.fd[t]) : (L.sel[t] ? kMarkRawSel : 0);
-    {
+    if (t < V && head) reinterpret_cast<uint32_t *>(rec + kNvOff)[t] = L.nv[t];
+    if (t < V && head) rec[kNvOff + 4 * V + t] = L.fd[t] ? (uint8_t)(kMarkFlat + L.fd[t]) : (L.sel[t] ? kMarkRawSel : 0);
+    if (head) {
         const uint32_t pad_lo = kNvOff + 5 * V, alen_off = (pad_lo + 3) & ~3u;
         if (pad_lo + t < alen_off) rec[pad_lo + t] = 0;
         if (warp == 0 && L.n_sel) {
@@ -434,10 +438,11 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 }
             });
         }
-        for (uint32_t i = L.body_end + t; i < L.rec_bound; i += kEncThreads) rec[i] = 0;
+        if (whole)
+            for (uint32_t i = L.body_end + t; i < L.rec_bound; i += kEncThreads) rec[i] = 0;
     }
     // ---- the bitmaps are ORed into a zeroed body ----
-    {
+    if (whole) {
         const uint32_t b0 = L.body0, b1 = L.body_end;
         const uint32_t h0 = min(b1, (b0 + 15u) & ~15u), h1 = max(h0, b1 & ~15u);
         for (uint32_t i = b0 + t; i < h0; i += kEncThreads) rec[i] = 0;
@@ -479,12 +484,24 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     // counting scratch in the second level buffer (free between chunks)
     uint32_t *hist = reinterpret_cast<uint32_t *>(S.buf[1]);
     uint32_t *hc = hist + 256, *ps = hist + 512;
+    // a chunk of a big block starts every node's cursor after the symbols
+    // the chunks before it put there
+    if (cA > 0) {
+        uint32_t h = 0;
+        for (uint32_t c = 0; c < cA; c++) h += __ldg(chunk_hist + ((size_t)b * kEncChunks + c) * 256 + t);
+        hist[t] = h;
+        __syncthreads();
+        if (warp == 0) enc_counts(S, hist, S.dem, hc, ps);
+        __syncthreads();
+        if (t < V) S.pos[t] += S.dem[t] * max(1u, ch_flat_d(S.ch[t]));
+        __syncthreads();
+    }
     // ---- chunks: runs of the planning pass's chunks, or parts of one ----
-    const uint32_t nw = enc_nchunks(n);
-    uint32_t c0 = 0, k = nw;       // the run of plan chunks tried: c0 .. c0 + k - 1
-    uint32_t P = 0, sub = 0;       // sub > 0: cutting plan chunk c0 into parts of `sub` symbols
+    uint32_t c0 = cA, k = cEnd - cA;    // the run of plan chunks tried: c0 .. c0 + k - 1
+    uint32_t P = enc_chunk_start(n, cA, nw), sub = 0;   // sub > 0: cutting plan chunk c0 into parts of `sub` symbols
+    const uint32_t Pend = enc_chunk_start(n, cEnd, nw);
     uint32_t acc = 0;              // count of symbol t in the coded parts of plan chunk c0
-    while (P < (uint32_t)n) {
+    while (P < Pend) {
         const uint32_t Q1 = enc_chunk_start(n, c0 + (sub ? 1u : k), nw);   // end of the run / plan chunk
         const uint32_t C = sub ? min(sub, Q1 - P) : Q1 - P;
         // the chunk's histogram: the planning pass's chunk counts, or counted here
@@ -713,32 +730,151 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
                 acc = 0;
                 sub = 0;   // whole runs again
                 c0 += 1;
-                k = nw - c0;
+                k = cEnd - c0;
             }
         } else {
             c0 += k;
-            k = nw - c0;
+            k = cEnd - c0;
         }
     }
     __syncthreads();
+    // a chunk of a big block ends where the next one starts: the cursors
+    // after the symbols of chunks 0 .. cEnd - 1
+    if (cEnd < nw && !S.bad) {
+        uint32_t h = 0;
+        for (uint32_t c = 0; c < cEnd; c++) h += __ldg(chunk_hist + ((size_t)b * kEncChunks + c) * 256 + t);
+        hist[t] = h;
+        __syncthreads();
+        if (warp == 0) enc_counts(S, hist, S.dem, hc, ps);
+        __syncthreads();
+        if (t < V) S.nv[t] = S.pos[t] == S.bitsrc[t] + S.dem[t] * max(1u, ch_flat_d(S.ch[t])) ? S.pos[t] - S.bitsrc[t]
+                                                                                             : 0xFFFFFFFFu;
+        __syncthreads();
+    }
     if (t == 0) {
-        // every node's cursor ends exactly at the end of its bitmap
+        // every node's cursor ends exactly at the end of its bitmap (of the
+        // item's part of it)
         uint32_t bad = S.bad;
         for (int v = 0; v < V && !bad; v++) bad = S.pos[v] != S.bitsrc[v] + S.nv[v];
-        status[b] = bad ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
-        rec_bytes[b] = bad ? 0 : rec_bound;
+        if (whole) {
+            status[b] = bad ? PIVCO_ERR_INVALID_ARG : PIVCO_OK;
+            rec_bytes[b] = bad ? 0 : rec_bound;
+        } else if (bad) {
+            atomicExch(&status[b], PIVCO_ERR_INVALID_ARG);
+            rec_bytes[b] = 0;
+        }
+    }
+    __syncthreads();
+}
+
+// The big blocks of a chunked encode (their levels do not fit the buffers):
+// checked, their bodies zeroed and their status set OK, and listed; then
+// every chunk of theirs is an item of the encode kernel's work list.  One
+// CTA per block.
+__global__ void __launch_bounds__(kEncThreads) encode_reset_kernel(const uint64_t *__restrict__ blk_off,
+                                                                   BlockLayout *__restrict__ layout,
+                                                                   uint8_t *__restrict__ out,
+                                                                   const uint64_t *__restrict__ out_off,
+                                                                   uint64_t *__restrict__ rec_bytes,
+                                                                   int32_t *__restrict__ status) {
+    const int b = blockIdx.x, t = threadIdx.x;
+    const BlockLayout &L = *layout_of(layout, b);
+    if (!L.big || L.kind != 2) return;
+    const uint64_t n = blk_off[b + 1] - blk_off[b];
+    uint8_t *rec = out + out_off[b];
+    const uint64_t cap = out_off[b + 1] - out_off[b];
+    int st = PIVCO_OK;
+    if (L.status != 0) st = L.status;
+    else if (L.n != n || (reinterpret_cast<uintptr_t>(rec) & 15)) st = PIVCO_ERR_INVALID_ARG;
+    else if (cap < L.rec_bound) st = PIVCO_ERR_CAPACITY;
+    if (st != PIVCO_OK) {
+        if (t == 0) { status[b] = st; rec_bytes[b] = 0; }
+        return;
+    }
+    // the body and the record's tail, zeroed (the chunks OR their bits in)
+    const uint32_t b0 = L.body0, b1 = L.rec_bound;
+    const uint32_t h0 = min(b1, (b0 + 15u) & ~15u);
+    for (uint32_t i = b0 + t; i < h0; i += kEncThreads) rec[i] = 0;
+    for (uint32_t i = h0 + 16 * t; i < b1; i += 16 * kEncThreads)
+        *reinterpret_cast<uint4 *>(rec + i) = make_uint4(0u, 0u, 0u, 0u);
+    if (t == 0) {
+        status[b] = PIVCO_OK;
+        rec_bytes[b] = L.rec_bound;
+        const uint32_t i = atomicAdd(&layout->list_len, 1u);
+        layout_of(layout, (int)i)->list_entry = (uint32_t)b;
     }
 }
 
-cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, const BlockLayout *layout,
+// One CTA per block (a big block of a chunked encode is left to the chunk
+// kernel).
+__global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(const uint8_t *__restrict__ in,
+                                                                            const uint64_t *__restrict__ blk_off,
+                                                                            const BlockLayout *__restrict__ layout,
+                                                                            const uint32_t *__restrict__ chunk_hist,
+                                                                            uint8_t *__restrict__ out,
+                                                                            const uint64_t *__restrict__ out_off,
+                                                                            uint64_t *__restrict__ rec_bytes,
+                                                                            int32_t *__restrict__ status) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
+    if (chunk_hist && layout_of(layout, (int)blockIdx.x)->big) return;
+    encode_item<true>((int)blockIdx.x, 0, kEncChunks, in, blk_off, layout, chunk_hist, out, out_off, rec_bytes,
+                      status, S);
+}
+
+// The work list of big blocks' chunks, (block, chunk) by (block, chunk):
+// persistent CTAs take tickets until the list is done.
+__global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_chunks_kernel(const uint8_t *__restrict__ in,
+                                                                                   const uint64_t *__restrict__ blk_off,
+                                                                                   BlockLayout *__restrict__ layout,
+                                                                                   const uint32_t *__restrict__ chunk_hist,
+                                                                                   uint8_t *__restrict__ out,
+                                                                                   const uint64_t *__restrict__ out_off,
+                                                                                   uint64_t *__restrict__ rec_bytes,
+                                                                                   int32_t *__restrict__ status) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
+    __shared__ uint32_t s_tk;
+    const uint32_t items = *reinterpret_cast<volatile uint32_t *>(&layout->list_len) * kEncChunks;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tk = atomicAdd(&layout->list_ticket, 1u);
+        __syncthreads();
+        const uint32_t tk = s_tk;
+        if (tk >= items) return;
+        const int bb = (int)layout_of(layout, (int)(tk / kEncChunks))->list_entry;
+        const uint32_t c = tk % kEncChunks;
+        if (c < enc_nchunks(blk_off[bb + 1] - blk_off[bb]))
+            encode_item<false>(bb, c, c + 1, in, blk_off, layout, chunk_hist, out, out_off, rec_bytes, status, S);
+    }
+}
+
+cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, BlockLayout *layout,
                           const uint32_t *chunk_hist, uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes,
                           int32_t *status, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     const int smem = (int)sizeof(EncSmem);
     cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    // the work list of big blocks: emptied, then filled by the reset pass
+    e = cudaMemsetAsync(&layout->list_len, 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    if (chunk_hist) {
+        encode_reset_kernel<<<nblk, kEncThreads, 0, st>>>(blk_off, layout, out, out_off, rec_bytes, status);
+        count_launches(1);
+    }
     encode_kernel<<<nblk, kEncThreads, smem, st>>>(in, blk_off, layout, chunk_hist, out, out_off, rec_bytes, status);
     count_launches(1);
+    if (chunk_hist) {
+        e = cudaFuncSetAttribute(encode_chunks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        encode_chunks_kernel<<<sms * kEncCtasPerSm, kEncThreads, smem, st>>>(in, blk_off, layout, chunk_hist, out,
+                                                                             out_off, rec_bytes, status);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -746,6 +882,9 @@ cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, 
 
 namespace pv {
 cudaError_t prepare_encode_kernels() {
-    return cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmem));
+    cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(encode_chunks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmem));
+    return e;
 }
 }  // namespace pv

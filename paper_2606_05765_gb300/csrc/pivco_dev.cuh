@@ -74,7 +74,8 @@ struct BlockLayout {
     uint8_t status;        // PIVCO_* of layout construction
     uint8_t flat;          // regrouped tree with flat subtrees (record tag PVC2)
     uint8_t depth_first[17];   // first node id at depth d (breadth-first); [d+1]-[d] = count
-    uint8_t pad1[15];
+    uint8_t big;               // the levels of the whole block do not fit the encoder's buffers
+    uint8_t pad1[14];
     uint16_t tree_a[17];       // leaf-covered prefix count at depth d (TreeShape::a)
     uint16_t pad2[15];
     uint16_t code[256];    // code of symbol s (lens[s] bits, MSB = first decision; canonical or regrouped)
@@ -91,11 +92,25 @@ struct BlockLayout {
     uint8_t ci[256];           // code index of symbol s: its place in the order of codes (left-aligned)
     uint8_t nlo[256];          // the leaves under node v are code indices nlo[v] .. nhi1[v]
     uint8_t nhi1[256];
+    // scratch of the chunked encoder (the work list of big blocks; written
+    // by the encode call, not by the plan): entry i of the list lives in
+    // block i's layout, its length and the chunk ticket in block 0's
+    uint32_t list_entry;
+    uint32_t list_len;
+    uint32_t list_ticket;
+    uint32_t pad4;
 };
 static_assert(offsetof(BlockLayout, ci) % 16 == 0 && offsetof(BlockLayout, nhi1) + 256 == offsetof(BlockLayout, ci) + 768,
               "the canonical tables are one 16-byte aligned run");
 static_assert(sizeof(BlockLayout) <= 8192, "layout too large");
 constexpr int32_t kLayoutBytes = 8192;
+// block b's layout record: records are kLayoutBytes apart (not sizeof(BlockLayout))
+__host__ __device__ inline BlockLayout *layout_of(BlockLayout *layout, int b) {
+    return reinterpret_cast<BlockLayout *>(reinterpret_cast<uint8_t *>(layout) + (size_t)b * kLayoutBytes);
+}
+__host__ __device__ inline const BlockLayout *layout_of(const BlockLayout *layout, int b) {
+    return reinterpret_cast<const BlockLayout *>(reinterpret_cast<const uint8_t *>(layout) + (size_t)b * kLayoutBytes);
+}
 
 // ---------------------------------------------------------------------------
 // Canonical tree from code lengths (Sec. 1 canonical coding, App. D).
@@ -412,6 +427,7 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 // floor(n w / nw) rounded down to a multiple of 32.  The encoder gives chunk w
 // to its warp w; the chunked histogram counts each chunk on its own.
 constexpr uint32_t kEncChunks = 8;
+constexpr int kEBuf = 13824;         // symbols per encoder level buffer (a skew80 64 KiB block in one chunk)
 constexpr uint32_t kEncMinChunk = 4096;
 __host__ __device__ inline uint32_t enc_nchunks(uint64_t n) {
     const uint64_t c = n / kEncMinChunk;
@@ -435,7 +451,7 @@ cudaError_t launch_build_layout(const uint32_t *hist, const uint8_t *lens, int n
                                 BlockLayout *layout, uint64_t *rec_bound, int32_t *status, cudaStream_t st);
 cudaError_t launch_scan(const uint64_t *in, int n, uint64_t *out, void *ws, int32_t *status, cudaStream_t st);
 size_t scan_ws_bytes(int n);
-cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, const BlockLayout *layout,
+cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, BlockLayout *layout,
                           const uint32_t *chunk_hist, uint8_t *out, const uint64_t *out_off, uint64_t *rec_bytes,
                           int32_t *status, cudaStream_t st);
 cudaError_t launch_ans_encode_blocks(const BlockLayout *layout, int nblk, uint8_t *out, const uint64_t *out_off,

@@ -440,3 +440,32 @@ def test_unaligned_input(P, oracle, shift):
     for b in range(w.nblk):
         lo = int(off[b])
         assert np.array_equal(a[lo:lo + int(rb[b])], r[lo:lo + int(rb[b])]), b
+
+
+@pytest.mark.parametrize("flat", [False, True])
+def test_big_blocks_coded_chunk_by_chunk(P, oracle, flat):
+    """Blocks whose levels do not fit the encoder's buffers are coded one
+    plan chunk per work item, possibly by different CTAs at once; their
+    records are the oracle's byte for byte, beside small blocks coded whole,
+    ragged sizes included, and they decode."""
+    rng = np.random.default_rng(41)
+    blocks = [rng.integers(0, 200, 200001).astype(np.uint8),                         # high entropy, 8 chunks
+              rng.choice(256, 131072, p=rng.dirichlet(np.ones(256) * 0.3)).astype(np.uint8),
+              rng.integers(0, 5, 16383).astype(np.uint8),                            # 3 chunks, ragged end
+              np.full(5000, 4, np.uint8),                                            # constant, whole
+              rng.integers(0, 3, 4000).astype(np.uint8),                             # small, whole
+              rng.integers(0, 97, 65536 + 33).astype(np.uint8)]
+    off = np.zeros(len(blocks) + 1, np.uint64)
+    off[1:] = np.cumsum([b.size for b in blocks])
+    data = np.concatenate(blocks)
+    enc = P.encode(dev(data), off64(off), P.params(flat=flat))
+    st = enc.status.cpu().numpy()
+    assert not st.any(), st
+    comp, coff, rb = enc.comp.cpu().numpy(), enc.off.cpu().numpy(), enc.rec_bytes.cpu().numpy()
+    for b, x in enumerate(blocks):
+        ref = oracle.encode_block(x, oracle.params(flat=flat))
+        got = comp[int(coff[b]):int(coff[b]) + int(rb[b])]
+        assert got.size == ref.size and np.array_equal(got, ref), b
+    out, st = P.decode(enc.comp, enc.off, off64(off))
+    assert not st.cpu().numpy().any()
+    assert np.array_equal(out.cpu().numpy()[: data.size], data)
