@@ -6,7 +6,32 @@ namespace pv {
 // ---------------------------------------------------------------------------
 // Standalone bitmap ANS (one warp per bitmap; segments sequential).
 // ---------------------------------------------------------------------------
-constexpr int kAnsStageWords = kAnsSeg;   // at most one word per byte
+constexpr int kAnsStageWords = 4096;      // words staged in shared memory (the rest of a segment's go to global memory)
+
+// The words of a coded segment in decoder order at dst (one warp): word k is
+// emission nw - 1 - k.  Emissions cap .. nw - 1 were written at dst in
+// emission order (ans_encode_segment's ovf): reversed in place, they become
+// words 0 .. nw - cap - 1; the staged emissions 0 .. cap - 1 are the rest.
+__device__ inline void ans_place_words(const uint16_t *stage, uint32_t cap, uint32_t nw, uint8_t *dst) {
+    const int lane = threadIdx.x & 31;
+    if (nw > cap) {
+        const uint32_t L = nw - cap;
+        for (uint32_t i0 = 0; i0 < L / 2; i0 += 32) {
+            const uint32_t i = i0 + lane, j = L - 1 - i;
+            uint8_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+            if (i < L / 2) { a0 = dst[2 * i]; a1 = dst[2 * i + 1]; b0 = dst[2 * j]; b1 = dst[2 * j + 1]; }
+            __syncwarp();
+            if (i < L / 2) { dst[2 * i] = b0; dst[2 * i + 1] = b1; dst[2 * j] = a0; dst[2 * j + 1] = a1; }
+            __syncwarp();
+        }
+    }
+    const uint32_t ns = nw < cap ? nw : cap;
+    for (uint32_t k = nw - ns + lane; k < nw; k += 32) {
+        const uint16_t w = stage[cap - nw + k];
+        dst[2 * k] = (uint8_t)w;
+        dst[2 * k + 1] = (uint8_t)(w >> 8);
+    }
+}
 
 __global__ void __launch_bounds__(32) ans_encode_kernel(const uint8_t *__restrict__ bm, const uint64_t *__restrict__ bm_off,
                                                         const uint8_t *__restrict__ table, uint8_t *__restrict__ bodies,
@@ -25,7 +50,7 @@ __global__ void __launch_bounds__(32) ans_encode_kernel(const uint8_t *__restric
         if (lane == 0) { status[i] = PIVCO_ERR_INVALID_ARG; body_bytes[i] = 0; }
         return;
     }
-    load_ans_table(T, A, tid, lane, 32);
+    load_ans_table(T, A, tid, lane, 32, true);
     __syncwarp();
     const uint8_t xr = (tb & 0x80) ? 0xFF : 0;
     const uint8_t *src = bm + bm_off[i];
@@ -36,17 +61,18 @@ __global__ void __launch_bounds__(32) ans_encode_kernel(const uint8_t *__restric
     for (uint32_t s = 0; s < S && ok; s++) {
         const uint32_t sb = min(kAnsSeg, nbytes - s * kAnsSeg), W = ans_seg_lanes(sb);
         uint32_t x;
-        const uint32_t nw = ans_encode_segment(src + (size_t)s * kAnsSeg, sb, T, xr, stage, kAnsStageWords, x);
+        const uint8_t *ss = src + (size_t)s * kAnsSeg;
+        // words past the stage go where the segment's words will be (after its states)
+        const uint64_t wo = pos + 4ull * W;
+        const uint32_t room = wo < cap ? (uint32_t)min((cap - wo) / 2, (uint64_t)0xFFFFFFFFu) : 0u;
+        const uint32_t nw = ans_encode_segment(ss, sb, T, xr, stage, kAnsStageWords, dst + wo, room, x);
         __syncwarp();
         if (pos + 4ull * W + 2ull * nw > cap) { ok = false; break; }
         if (lane == 0) st_le32(dst + 4 * s, nw);
         if (lane < (int)W) st_le32(dst + pos + 4 * lane, x);
         pos += 4ull * W;
-        for (uint32_t k = lane; k < nw; k += 32) {
-            const uint16_t w = stage[kAnsStageWords - nw + k];
-            dst[pos + 2 * k] = (uint8_t)w;
-            dst[pos + 2 * k + 1] = (uint8_t)(w >> 8);
-        }
+        __syncwarp();
+        ans_place_words(stage, kAnsStageWords, nw, dst + pos);
         pos += 2ull * nw;
         __syncwarp();
     }
@@ -59,6 +85,7 @@ __global__ void __launch_bounds__(32) ans_decode_kernel(const uint8_t *__restric
                                                         const uint64_t *__restrict__ bm_off, int32_t *__restrict__ status,
                                                         const __grid_constant__ AnsTables A) {
     __shared__ AnsSm T;
+    __shared__ uint8_t wst[2 * kAnsWordWin];
     const int i = blockIdx.x, lane = threadIdx.x;
     const uint32_t nbytes = (uint32_t)(bm_off[i + 1] - bm_off[i]);
     const uint8_t tb = table[i];
@@ -79,7 +106,7 @@ __global__ void __launch_bounds__(32) ans_decode_kernel(const uint8_t *__restric
         if (!ans_segment_at(body, blen, nbytes, s, sp, nw)) { ok = false; break; }
         const uint32_t sb = min(kAnsSeg, nbytes - s * kAnsSeg), W = ans_seg_lanes(sb);
         ok = ans_decode_segment(body + sp, body + sp + 4 * W, nw, sb, T, (tb & 0x80) ? 0xFF : 0,
-                                bm + bm_off[i] + (size_t)s * kAnsSeg);
+                                bm + bm_off[i] + (size_t)s * kAnsSeg, wst);
         total += 4ull * W + 2ull * nw;
     }
     if (ok && total != blen) ok = false;
@@ -138,7 +165,7 @@ __global__ void __launch_bounds__(32) ans_encode_blocks_kernel(const BlockLayout
         const int tid = (tb & 0x7F) - 1;
         const uint32_t raw = (L.nv[v] + 7) / 8;
         __syncwarp();
-        load_ans_table(T, A, tid, lane, 32);
+        load_ans_table(T, A, tid, lane, 32, true);
         __syncwarp();
         const uint8_t xr = (tb & 0x80) ? 0xFF : 0;
         const uint8_t *src = rec + L.body_off[v];
@@ -148,19 +175,20 @@ __global__ void __launch_bounds__(32) ans_encode_blocks_kernel(const BlockLayout
         for (uint32_t s = 0; s < S && ok; s++) {
             const uint32_t sb = min(kAnsSeg, raw - s * kAnsSeg), W = ans_seg_lanes(sb);
             uint32_t x;
-            const uint32_t nw = ans_encode_segment(src + (size_t)s * kAnsSeg, sb, T, xr, stage, kAnsStageWords, x);
+            const uint8_t *ss = src + (size_t)s * kAnsSeg;
+            uint8_t *dst = wslot + wpos;
+            // words past the stage go where the segment's words will be
+            const uint64_t wo = wpos + pos + 4ull * W;
+            const uint32_t room = wo < wcap ? (uint32_t)min((wcap - wo) / 2, (uint64_t)0xFFFFFFFFu) : 0u;
+            const uint32_t nw = ans_encode_segment(ss, sb, T, xr, stage, kAnsStageWords, dst + pos + 4ull * W, room, x);
             __syncwarp();
             const uint64_t np = pos + 4ull * W + 2ull * nw;
             if (np >= raw || wpos + np > wcap) { ok = false; break; }
-            uint8_t *dst = wslot + wpos;
             if (lane == 0) st_le32(dst + 4 * s, nw);
             if (lane < (int)W) st_le32(dst + pos + 4 * lane, x);
             pos += 4ull * W;
-            for (uint32_t k = lane; k < nw; k += 32) {
-                const uint16_t w = stage[kAnsStageWords - nw + k];
-                dst[pos + 2 * k] = (uint8_t)w;
-                dst[pos + 2 * k + 1] = (uint8_t)(w >> 8);
-            }
+            __syncwarp();
+            ans_place_words(stage, kAnsStageWords, nw, dst + pos);
             pos += 2ull * nw;
             __syncwarp();
         }

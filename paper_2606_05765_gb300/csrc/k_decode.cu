@@ -143,9 +143,11 @@ __device__ inline int find_block_warp(const uint32_t *key, int n, uint32_t g, in
 // length nibbles, n_v, the markers and the alen table of any record
 constexpr uint32_t kStage = 2448;
 static_assert(kStage >= kNvOff + 5 * 255 + 3 + 4 * 255 && kStage % 16 == 0, "the stage holds a record's tables");
+static_assert(kStage >= 2 * kAnsWordWin, "the stage holds the ANS decoder's word window");
 
 struct __align__(16) WarpRec {
-    uint8_t stg[kStage];     // the record's first kStage bytes (zeros past its end)
+    uint8_t stg[kStage];     // the record's first kStage bytes (zeros past its end); after the
+                             // parse, the ANS decoder's word window
     uint32_t nv[256];
     uint32_t body_off[256];
     uint32_t alen[256];
@@ -603,7 +605,7 @@ __device__ inline int ans_item(uint32_t g, const uint8_t *__restrict__ comp, con
                 __syncwarp();
                 const uint32_t sbytes = min(kAnsSeg, raw - s * kAnsSeg), Wl = ans_seg_lanes(sbytes);
                 ok = ans_decode_segment(body + sp, body + sp + 4 * Wl, nw, sbytes, T, (mk & 0x80) ? 0xFF : 0,
-                                        scratch + sdst + (size_t)s * kAnsSeg);
+                                        scratch + sdst + (size_t)s * kAnsSeg, R.stg);
                 if (ok && s + 1 == ans_seg_count(raw) && sp + 4ull * Wl + 2ull * nw != blen) ok = false;
                 if (s + 1 == ans_seg_count(raw) && lane < 16) scratch[sdst + raw + lane] = 0;
             }
