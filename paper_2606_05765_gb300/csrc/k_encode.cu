@@ -36,8 +36,11 @@ struct EncWin {                             // one window of a round
     uint32_t flags;                         // 1 its first node starts at its first group, 2 a node starts in it, 4 active
 };
 
-struct __align__(16) EncSmem {
-    uint16_t buf[2][kEBuf + kESlack];       // depth d >= 1 reads buf[d & 1], writes its children to the other
+template <int kBufT, int kWinT>
+struct __align__(16) EncSmemT {
+    static constexpr int kBuf = kBufT;      // symbols per level buffer
+    static constexpr int kWin = kWinT;      // windows of a level below the root (>= (kBuf / 32 + 256) / 32)
+    uint16_t buf[2][kBufT + kESlack];       // depth d >= 1 reads buf[d & 1], writes its children to the other
                                             // (spans start on 16-byte boundaries)
     uint32_t pos[256];                      // bit address of node v's first bit of the current chunk
     uint32_t dem[256];                      // symbols of node v in the current chunk
@@ -48,7 +51,7 @@ struct __align__(16) EncSmem {
     uint16_t sp[256];                       // first symbol of node v's span in its level buffer
     uint16_t gs[256];                       // first 32-symbol group of node v within its level
     uint16_t lg[16];                        // groups of each level
-    uint8_t wnode[16][kEWinPerLvl];         // node holding the first group of each window of a level
+    uint8_t wnode[16][kWinT];               // node holding the first group of each window of a level
     EncWin win[2][kEncWarps];               // window summaries, two rounds deep
     uint8_t ci[256];                        // canonical index of symbol s (its place in (length, symbol) order)
     uint8_t nlo[256];                       // node v's leaves are canonical indices nlo[v] .. nhi1[v]
@@ -60,9 +63,17 @@ struct __align__(16) EncSmem {
     uint8_t maxd;
     uint8_t pad[14];
 };
+// the whole-block encoder's buffers (3 CTAs per SM), and the chunk
+// encoder's (2 CTAs per SM, parts of big blocks almost twice as long)
+using EncSmem = EncSmemT<kEBuf, kEWinPerLvl>;
+constexpr int kEBufBig = 25600;
+constexpr int kEncChunkCtasPerSm = 2;
+using EncSmemBig = EncSmemT<kEBufBig, 36>;
 static_assert(offsetof(BlockLayout, ci) <= sizeof(EncSmem::buf[1]) && offsetof(BlockLayout, ci) % 16 == 0,
               "the staged part of the layout fits a level buffer");
 static_assert(sizeof(EncSmem::buf[0]) >= 4 * 1024 + 4, "a level buffer holds the counting scratch");
+static_assert(kEncChunkCtasPerSm * (sizeof(EncSmemBig) + 1024) <= 228 * 1024, "chunk encoder CTAs per SM");
+static_assert((kEBufBig / 32 + 256) / 32 <= 36, "window table of the chunk encoder");
 
 template <typename F, typename G>
 __device__ inline uint32_t warp_scan_loop(int n, F f, G out) {
@@ -129,7 +140,8 @@ __device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32
 // leaves under a node are the contiguous canonical range nlo .. nhi1, so its
 // count is a difference of two prefix sums.  One warp; hc (256) and ps (257)
 // are scratch.
-__device__ inline void enc_counts(const EncSmem &S, const uint32_t *h, uint32_t *cnt, uint32_t *hc, uint32_t *ps) {
+template <typename SM>
+__device__ inline void enc_counts(const SM &S, const uint32_t *h, uint32_t *cnt, uint32_t *hc, uint32_t *ps) {
     const int lane = threadIdx.x & 31;
     const int V = S.first[S.maxd];
 #pragma unroll
@@ -159,7 +171,9 @@ __device__ inline void enc_counts(const EncSmem &S, const uint32_t *h, uint32_t 
 // Spans, groups and window nodes of level d for the current demands (one
 // warp; the levels are independent).  False when the level (depth >= 1)
 // does not fit a buffer or has more windows than its window-node table.
-__device__ inline bool enc_layout_level(EncSmem &S, int d) {
+template <typename SM>
+__device__ inline bool enc_layout_level(SM &S, int d) {
+    constexpr int kBuf = SM::kBuf;
     const int lane = threadIdx.x & 31;
     bool fits = true;
     const int f0 = S.first[d], f1 = S.first[d + 1];
@@ -169,8 +183,8 @@ __device__ inline bool enc_layout_level(EncSmem &S, int d) {
         uint64_t x = 0;
         if (v < f1) {
             const uint32_t dv = S.dem[v];
-            if (d && dv > (uint32_t)kEBuf) fits = false;
-            const uint32_t el = d ? ((min(dv, (uint32_t)kEBuf) + 7u) & ~7u) : 0u;   // spans of whole 16-byte units
+            if (d && dv > (uint32_t)kBuf) fits = false;
+            const uint32_t el = d ? ((min(dv, (uint32_t)kBuf) + 7u) & ~7u) : 0u;   // spans of whole 16-byte units
             x = ((uint64_t)el << 32) | max(1u, (dv + 31u) >> 5);
         }
         uint64_t inc = x;
@@ -181,20 +195,20 @@ __device__ inline bool enc_layout_level(EncSmem &S, int d) {
         }
         const uint64_t ex = carry + inc - x;
         if (v < f1) {
-            S.sp[v] = (uint16_t)min((uint64_t)kEBuf, ex >> 32);
+            S.sp[v] = (uint16_t)min((uint64_t)kBuf, ex >> 32);
             S.gs[v] = (uint16_t)ex;
         }
         carry += __shfl_sync(0xffffffffu, inc, 31);
     }
-    if (d && (carry >> 32) > (uint64_t)kEBuf) fits = false;
+    if (d && (carry >> 32) > (uint64_t)kBuf) fits = false;
     if ((uint32_t)carry > 0xFFFFu) fits = false;
     const uint32_t G = (uint32_t)carry & 0xFFFFu;
     if (lane == 0) S.lg[d] = (uint16_t)G;
     __syncwarp();
     if (d) {
         const uint32_t nwin = (G + 31) >> 5;
-        if (nwin > (uint32_t)kEWinPerLvl) fits = false;
-        for (uint32_t i = lane; i < nwin && i < (uint32_t)kEWinPerLvl; i += 32) {
+        if (nwin > (uint32_t)SM::kWin) fits = false;
+        for (uint32_t i = lane; i < nwin && i < (uint32_t)SM::kWin; i += 32) {
             int lo = f0, hi = f1;
             while (hi - lo > 1) {
                 const int m = (lo + hi) >> 1;
@@ -210,7 +224,8 @@ __device__ inline bool enc_layout_level(EncSmem &S, int d) {
 // The carry into this warp's window of the round (the ones, before the
 // window, of the node that runs into it) and the carry into the next round;
 // every warp calls it after the round's summaries are written.
-__device__ inline uint32_t enc_round_carry(const EncSmem &S, uint32_t par, uint32_t &rc_sum) {
+template <typename SM>
+__device__ inline uint32_t enc_round_carry(const SM &S, uint32_t par, uint32_t &rc_sum) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const EncWin x = lane < kEncWarps ? S.win[par][lane] : EncWin{0u, 0u};
     uint32_t val = x.sum, seg = (x.flags >> 1) & 1u;
@@ -355,12 +370,12 @@ __device__ inline void flat_emit_d(uint32_t D, uint32_t *rec32, uint32_t a, cons
 // body and set its status, the chunk starts at the node cursors the counts
 // of the chunks before it give, chunk 0 writes the header and tables, and
 // the status only ever turns to an error.
-template <bool whole>
+template <bool whole, typename SM>
 __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_t *__restrict__ in,
                                    const uint64_t *__restrict__ blk_off, const BlockLayout *__restrict__ layout,
                                    const uint32_t *__restrict__ chunk_hist, uint8_t *__restrict__ out,
                                    const uint64_t *__restrict__ out_off, uint64_t *__restrict__ rec_bytes,
-                                   int32_t *__restrict__ status, EncSmem &S) {
+                                   int32_t *__restrict__ status, SM &S) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint64_t i0 = blk_off[b], i1 = blk_off[b + 1], o0 = out_off[b], o1 = out_off[b + 1];
     const uint32_t nw = enc_nchunks(i1 - i0), cEnd = cB < nw ? cB : nw;
@@ -818,13 +833,13 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_kernel(cons
     extern __shared__ __align__(128) uint8_t smem_raw[];
     EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
     if (chunk_hist && layout_of(layout, (int)blockIdx.x)->big) return;
-    encode_item<true>((int)blockIdx.x, 0, kEncChunks, in, blk_off, layout, chunk_hist, out, out_off, rec_bytes,
-                      status, S);
+    encode_item<true, EncSmem>((int)blockIdx.x, 0, kEncChunks, in, blk_off, layout, chunk_hist, out, out_off,
+                               rec_bytes, status, S);
 }
 
 // The work list of big blocks' chunks, (block, chunk) by (block, chunk):
 // persistent CTAs take tickets until the list is done.
-__global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_chunks_kernel(const uint8_t *__restrict__ in,
+__global__ void __launch_bounds__(kEncThreads, kEncChunkCtasPerSm) encode_chunks_kernel(const uint8_t *__restrict__ in,
                                                                                    const uint64_t *__restrict__ blk_off,
                                                                                    BlockLayout *__restrict__ layout,
                                                                                    const uint32_t *__restrict__ chunk_hist,
@@ -833,7 +848,7 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_chunks_kern
                                                                                    uint64_t *__restrict__ rec_bytes,
                                                                                    int32_t *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    EncSmem &S = *reinterpret_cast<EncSmem *>(smem_raw);
+    EncSmemBig &S = *reinterpret_cast<EncSmemBig *>(smem_raw);
     __shared__ uint32_t s_tk;
     const uint32_t items = *reinterpret_cast<volatile uint32_t *>(&layout->list_len) * kEncChunks;
     for (;;) {
@@ -845,7 +860,8 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm) encode_chunks_kern
         const int bb = (int)layout_of(layout, (int)(tk / kEncChunks))->list_entry;
         const uint32_t c = tk % kEncChunks;
         if (c < enc_nchunks(blk_off[bb + 1] - blk_off[bb]))
-            encode_item<false>(bb, c, c + 1, in, blk_off, layout, chunk_hist, out, out_off, rec_bytes, status, S);
+            encode_item<false, EncSmemBig>(bb, c, c + 1, in, blk_off, layout, chunk_hist, out, out_off, rec_bytes,
+                                           status, S);
     }
 }
 
@@ -866,13 +882,14 @@ cudaError_t launch_encode(const uint8_t *in, const uint64_t *blk_off, int nblk, 
     encode_kernel<<<nblk, kEncThreads, smem, st>>>(in, blk_off, layout, chunk_hist, out, out_off, rec_bytes, status);
     count_launches(1);
     if (chunk_hist) {
-        e = cudaFuncSetAttribute(encode_chunks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const int smem_big = (int)sizeof(EncSmemBig);
+        e = cudaFuncSetAttribute(encode_chunks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_big);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        encode_chunks_kernel<<<sms * kEncCtasPerSm, kEncThreads, smem, st>>>(in, blk_off, layout, chunk_hist, out,
-                                                                             out_off, rec_bytes, status);
+        encode_chunks_kernel<<<sms * kEncChunkCtasPerSm, kEncThreads, smem_big, st>>>(in, blk_off, layout, chunk_hist,
+                                                                                      out, out_off, rec_bytes, status);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -884,7 +901,7 @@ namespace pv {
 cudaError_t prepare_encode_kernels() {
     cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(encode_chunks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmem));
+        e = cudaFuncSetAttribute(encode_chunks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EncSmemBig));
     return e;
 }
 }  // namespace pv

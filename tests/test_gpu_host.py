@@ -45,12 +45,13 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("flat", [False, True])
 @pytest.mark.parametrize("segments", [1, 3, 8])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_host_codec_matches_device(P, name, segments):
+def test_host_codec_matches_device(P, name, segments, flat):
     import torch
     w = CASES[name]()
-    prm = P.params(ans=w.ans)
+    prm = P.params(ans=w.ans, flat=flat)
     boff = torch.from_numpy(w.blk_off.astype(np.int64)).cuda()
     ref = P.encode(torch.from_numpy(w.data).cuda(), boff, prm)
     assert not ref.status.cpu().numpy().any()

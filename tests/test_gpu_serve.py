@@ -27,13 +27,15 @@ def P():
 
 
 def _encode_requests(P, reqs):
-    """Records of every request (host), plus its decode alone (host)."""
+    """Records of every request (host), plus its decode alone (host); every
+    other request coded with the regrouped tree (PVC2), so the server decodes
+    both kinds of record in one mix."""
     import torch
     out = []
-    for r in reqs:
+    for i, r in enumerate(reqs):
         data = torch.from_numpy(r.data).cuda()
         boff = torch.from_numpy(r.blk_off.astype(np.int64)).cuda()
-        enc = P.encode(data, boff, P.params(ans=r.ans))
+        enc = P.encode(data, boff, P.params(ans=r.ans, flat=bool(i % 2)))
         assert not enc.status.cpu().numpy().any()
         alone, st = P.decode(enc.comp, enc.off, boff)
         comp = enc.comp[: int(enc.off[-1].item())].cpu().numpy()

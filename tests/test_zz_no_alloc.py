@@ -36,14 +36,15 @@ def _batches():
     return [a, b]
 
 
-def test_static_matches_workspace_decode_twice(P):
+@pytest.mark.parametrize("flat", [False, True])
+def test_static_matches_workspace_decode_twice(P, flat):
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for w in _batches():
             data = _dev(w.data)
             boff = _dev(w.blk_off.astype(np.int64))
-            enc = P.encode(data, boff, P.params(ans=True), stream)
+            enc = P.encode(data, boff, P.params(ans=True, flat=flat), stream)
             assert not enc.status.cpu().numpy().any()
             # the existing entry point, with a workspace the caller sized
             ref_out, ref_st = P.decode(enc.comp, enc.off, boff, stream)
