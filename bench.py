@@ -55,7 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-config", action="store_true", help="measure the headline workload only")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--e2e-segments", type=int, default=4)
+    ap.add_argument("--e2e-segments", type=int, default=8)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default decode tuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load time per arrival rate")
