@@ -9,93 +9,99 @@ namespace pv {
 
 // ---------------------------------------------------------------------------
 // Histogram.  Grid (nblk, slices); each CTA counts one slice of one block.
-// Per-warp shared histograms; the slice's most frequent byte (sampled) is
-// counted in registers with a byte-wise compare so skewed data (P(top) up to
-// 0.95) does not serialise on one shared-memory bin.
+// Per-warp shared histograms.  Skewed data (P(top) up to 0.95) would
+// serialise on the most frequent byte's counter, so each warp samples its
+// most frequent byte and counts it in 32 per-lane counters (bins 256 + lane,
+// one bank each), summed into its bin at the end; every byte is one
+// shared-memory add, with no branch.
 // ---------------------------------------------------------------------------
 constexpr int kHistThreads = 256;
 constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kHistBins = 256 + 32;
 
 __global__ void zero_u32_kernel(uint32_t *p, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = 0;
 }
 
-__device__ inline void hist_add_word(uint32_t w, uint32_t hot4, uint32_t hot, uint32_t *wh, uint32_t &hot_cnt) {
-    const uint32_t eq = __vcmpeq4(w, hot4);
-    hot_cnt += __popc(eq) >> 3;
+// counts byte v: the hot byte in the lane's own counter
+__device__ inline void hist_add_byte(uint32_t v, uint32_t hot, uint32_t hot_bin, uint32_t *wh) {
+    atomicAdd(&wh[v == hot ? hot_bin : v], 1u);
+}
+__device__ inline void hist_add_word(uint32_t w, uint32_t hot, uint32_t hot_bin, uint32_t *wh) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const uint32_t b = (w >> (8 * k)) & 0xFF;
-        if (b != hot) atomicAdd(&wh[b], 1u);
+    for (int k = 0; k < 4; k++) hist_add_byte(__byte_perm(w, 0u, 0x4440u + k), hot, hot_bin, wh);
+}
+__device__ inline void hist_add_vec(const uint4 &q, uint32_t hot, uint32_t hot_bin, uint32_t *wh) {
+    hist_add_word(q.x, hot, hot_bin, wh);
+    hist_add_word(q.y, hot, hot_bin, wh);
+    hist_add_word(q.z, hot, hot_bin, wh);
+    hist_add_word(q.w, hot, hot_bin, wh);
+}
+
+// The most frequent of 32 samples of in[lo, hi) (warp-uniform; 0 when empty)
+__device__ inline uint32_t hist_hot_byte(const uint8_t *__restrict__ in, uint64_t lo, uint64_t hi) {
+    const int lane = threadIdx.x & 31;
+    if (hi <= lo) return 0;
+    const uint64_t pos = lo + ((uint64_t)lane * 2654435761u) % (hi - lo);
+    const uint32_t v = in[pos];
+    const uint32_t peers = __match_any_sync(0xffffffffu, v);
+    int best = __popc(peers), bl = lane;
+    for (int o = 16; o; o >>= 1) {
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
     }
+    return __shfl_sync(0xffffffffu, v, bl);
+}
+
+// Counts in[lo, hi) into the warp's histogram my (kHistBins, zeroed) with
+// stride-`step` work sharing starting at `first` (lane or thread index):
+// head bytes up to 16-byte alignment, 16-byte loads four in flight, the tail.
+__device__ inline void hist_range(const uint8_t *__restrict__ in, uint64_t lo, uint64_t hi, uint32_t first,
+                                  uint32_t step, uint32_t hot, uint32_t *my) {
+    const uint32_t hot_bin = 256u + (threadIdx.x & 31);
+    // (the 16-byte boundary of the address: `in` itself may be unaligned)
+    uint64_t a = lo + ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(in + lo) & 15u)) & 15u);
+    if (a > hi) a = hi;
+    for (uint64_t i = lo + first; i < a; i += step) hist_add_byte(in[i], hot, hot_bin, my);
+    const uint64_t nvec = (hi - a) / 16;
+    const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
+    uint64_t i = first;
+    for (; i + 3 * step < nvec; i += 4 * step) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = __ldg(vp + i + u * step);
+#pragma unroll
+        for (int u = 0; u < 4; u++) hist_add_vec(q[u], hot, hot_bin, my);
+    }
+    for (; i < nvec; i += step) hist_add_vec(__ldg(vp + i), hot, hot_bin, my);
+    for (uint64_t j = a + nvec * 16 + first; j < hi; j += step) hist_add_byte(in[j], hot, hot_bin, my);
+}
+
+// Adds the warp's 32 hot-byte counters into the hot byte's bin (whole warp,
+// after its counting)
+__device__ inline void hist_fold_hot(uint32_t *my, uint32_t hot) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const uint32_t c = __reduce_add_sync(0xffffffffu, my[256 + lane]);
+    if (lane == 0) my[hot] += c;
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(kHistThreads) histogram_kernel(const uint8_t *__restrict__ in,
                                                                  const uint64_t *__restrict__ blk_off,
                                                                  uint32_t *__restrict__ hist, int slices) {
-    __shared__ uint32_t wh[kHistWarps][256];
+    __shared__ uint32_t wh[kHistWarps][kHistBins];
     const int b = blockIdx.x, sl = blockIdx.y;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5;
     const uint64_t lo0 = blk_off[b], hi0 = blk_off[b + 1];
     const uint64_t n = hi0 - lo0;
     const uint64_t span = ((n + slices - 1) / slices + 15) & ~uint64_t(15);
     const uint64_t lo = lo0 + min(n, span * sl), hi = lo0 + min(n, span * (sl + 1));
-    for (int i = t; i < kHistWarps * 256; i += kHistThreads) (&wh[0][0])[i] = 0;
-    // hot byte: most frequent of 32 samples of this slice (warp-uniform)
-    uint32_t hot = 0;
-    if (hi > lo) {
-        const uint64_t pos = lo + ((uint64_t)lane * 2654435761u) % (hi - lo);
-        const uint32_t v = in[pos];
-        const uint32_t peers = __match_any_sync(0xffffffffu, v);
-        const int cnt = __popc(peers);
-        int best = cnt, bl = lane;
-        for (int o = 16; o; o >>= 1) {
-            const int ob = __shfl_xor_sync(0xffffffffu, best, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
-        }
-        hot = __shfl_sync(0xffffffffu, v, bl);
-    }
-    const uint32_t hot4 = hot * 0x01010101u;
-    uint32_t hot_cnt = 0;
+    for (int i = t; i < kHistWarps * kHistBins; i += kHistThreads) (&wh[0][0])[i] = 0;
+    const uint32_t hot = hist_hot_byte(in, lo, hi);
     __syncthreads();
-    uint32_t *my = wh[warp];
-    // head bytes up to 16-byte alignment, then 16-byte vector loads, then tail
-    // (the 16-byte boundary of the address: `in` itself may be unaligned)
-    uint64_t a = lo + ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(in + lo) & 15u)) & 15u);
-    if (a > hi) a = hi;
-    for (uint64_t i = lo + t; i < a; i += kHistThreads) {
-        const uint32_t v = in[i];
-        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
-    }
-    const uint64_t nvec = (hi - a) / 16;
-    const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
-    // four loads in flight per thread, then their bytes
-    uint64_t i = t;
-    for (; i + 3 * kHistThreads < nvec; i += 4 * kHistThreads) {
-        uint4 q[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) q[u] = __ldg(vp + i + u * kHistThreads);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            hist_add_word(q[u].x, hot4, hot, my, hot_cnt);
-            hist_add_word(q[u].y, hot4, hot, my, hot_cnt);
-            hist_add_word(q[u].z, hot4, hot, my, hot_cnt);
-            hist_add_word(q[u].w, hot4, hot, my, hot_cnt);
-        }
-    }
-    for (; i < nvec; i += kHistThreads) {
-        const uint4 q = __ldg(vp + i);
-        hist_add_word(q.x, hot4, hot, my, hot_cnt);
-        hist_add_word(q.y, hot4, hot, my, hot_cnt);
-        hist_add_word(q.z, hot4, hot, my, hot_cnt);
-        hist_add_word(q.w, hot4, hot, my, hot_cnt);
-    }
-    for (uint64_t i = a + nvec * 16 + t; i < hi; i += kHistThreads) {
-        const uint32_t v = in[i];
-        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
-    }
-    for (int o = 16; o; o >>= 1) hot_cnt += __shfl_xor_sync(0xffffffffu, hot_cnt, o);
-    if (lane == 0 && hot_cnt) atomicAdd(&my[hot], hot_cnt);
+    hist_range(in, lo, hi, (uint32_t)t, kHistThreads, hot, wh[warp]);
+    hist_fold_hot(wh[warp], hot);
     __syncthreads();
     for (int s = t; s < 256; s += kHistThreads) {
         uint32_t sum = 0;
@@ -127,7 +133,7 @@ cudaError_t launch_histogram(const uint8_t *in, const uint64_t *blk_off, int nbl
 // histogram also goes to h_sm (shared) when given.
 __device__ inline void histogram_chunks_block(int b, const uint8_t *__restrict__ in,
                                               const uint64_t *__restrict__ blk_off, uint32_t *__restrict__ hist,
-                                              uint32_t *__restrict__ chunk_hist, uint32_t (*wh)[256],
+                                              uint32_t *__restrict__ chunk_hist, uint32_t (*wh)[kHistBins],
                                               uint32_t *h_sm) {
     static_assert(kHistWarps == kEncChunks, "one warp per encoder chunk");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -135,59 +141,11 @@ __device__ inline void histogram_chunks_block(int b, const uint8_t *__restrict__
     const uint32_t nw = enc_nchunks(n);
     const uint64_t lo = blk_off[b] + enc_chunk_start(n, warp, nw), hi = blk_off[b] + enc_chunk_start(n, warp + 1, nw);
     uint32_t *my = wh[warp];
-    for (int i = lane; i < 256; i += 32) my[i] = 0;
-    // hot byte: the most frequent of 32 samples of the chunk (warp-uniform)
-    uint32_t hot = 0;
-    if (hi > lo) {
-        const uint64_t pos = lo + ((uint64_t)lane * 2654435761u) % (hi - lo);
-        const uint32_t v = in[pos];
-        const uint32_t peers = __match_any_sync(0xffffffffu, v);
-        int best = __popc(peers), bl = lane;
-        for (int o = 16; o; o >>= 1) {
-            const int ob = __shfl_xor_sync(0xffffffffu, best, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
-        }
-        hot = __shfl_sync(0xffffffffu, v, bl);
-    }
-    const uint32_t hot4 = hot * 0x01010101u;
-    uint32_t hot_cnt = 0;
+    for (int i = lane; i < kHistBins; i += 32) my[i] = 0;
+    const uint32_t hot = hist_hot_byte(in, lo, hi);
     __syncwarp();
-    // head bytes up to 16-byte alignment, then 16-byte loads (four in flight per lane), then the tail
-    // (the 16-byte boundary of the address: `in` itself may be unaligned)
-    uint64_t a = lo + ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(in + lo) & 15u)) & 15u);
-    if (a > hi) a = hi;
-    for (uint64_t i = lo + lane; i < a; i += 32) {
-        const uint32_t v = in[i];
-        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
-    }
-    const uint64_t nvec = (hi - a) / 16;
-    const uint4 *vp = reinterpret_cast<const uint4 *>(in + a);
-    uint64_t i = lane;
-    for (; i + 96 < nvec; i += 128) {
-        uint4 q[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) q[u] = __ldg(vp + i + 32 * u);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            hist_add_word(q[u].x, hot4, hot, my, hot_cnt);
-            hist_add_word(q[u].y, hot4, hot, my, hot_cnt);
-            hist_add_word(q[u].z, hot4, hot, my, hot_cnt);
-            hist_add_word(q[u].w, hot4, hot, my, hot_cnt);
-        }
-    }
-    for (; i < nvec; i += 32) {
-        const uint4 q = __ldg(vp + i);
-        hist_add_word(q.x, hot4, hot, my, hot_cnt);
-        hist_add_word(q.y, hot4, hot, my, hot_cnt);
-        hist_add_word(q.z, hot4, hot, my, hot_cnt);
-        hist_add_word(q.w, hot4, hot, my, hot_cnt);
-    }
-    for (uint64_t i = a + nvec * 16 + lane; i < hi; i += 32) {
-        const uint32_t v = in[i];
-        if (v == hot) hot_cnt++; else atomicAdd(&my[v], 1u);
-    }
-    for (int o = 16; o; o >>= 1) hot_cnt += __shfl_xor_sync(0xffffffffu, hot_cnt, o);
-    if (lane == 0 && hot_cnt) atomicAdd(&my[hot], hot_cnt);
+    hist_range(in, lo, hi, (uint32_t)lane, 32u, hot, my);
+    hist_fold_hot(my, hot);
     __syncthreads();
     for (int s = t; s < 256; s += kHistThreads) {
         uint32_t sum = 0;
@@ -205,7 +163,7 @@ __global__ void __launch_bounds__(kHistThreads) histogram_chunks_kernel(const ui
                                                                         const uint64_t *__restrict__ blk_off,
                                                                         uint32_t *__restrict__ hist,
                                                                         uint32_t *__restrict__ chunk_hist) {
-    __shared__ uint32_t wh[kHistWarps][256];
+    __shared__ uint32_t wh[kHistWarps][kHistBins];
     histogram_chunks_block(blockIdx.x, in, blk_off, hist, chunk_hist, wh, nullptr);
 }
 
@@ -667,7 +625,7 @@ struct PlanSmem {
     uint32_t h[256];
     uint8_t lens[256];
     union {
-        uint32_t wh[kHistWarps][256];
+        uint32_t wh[kHistWarps][kHistBins];
         ClSmem cl;
         LaySmem lay;
     } u;
