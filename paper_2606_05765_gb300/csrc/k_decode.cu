@@ -897,13 +897,17 @@ __device__ inline void st_out32(uint8_t *p, const uint32_t (&o)[8], uint32_t val
     }
 }
 
-// Spans, groups and window nodes of every level for the current demands
-// (one warp).  False when a level (depth >= 1) does not fit a buffer.
+// Spans, groups and window nodes of every level for the current demands,
+// by the whole CTA: warp w lays out levels w, w + 8, ... (a level's spans
+// and groups are a scan over its own nodes); the levels' window-node tables
+// then follow one another in depth order.  False (in every thread) when a
+// level (depth >= 1) does not fit a buffer or the window nodes do not fit
+// their table.
 __device__ inline bool ct_layout(CtaTile &S) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int maxd = S.maxd;
     bool fits = true;
-    uint32_t wn = 0;   // window-node entries so far
-    for (int d = 0; d < (int)S.maxd; d++) {
+    for (int d = warp; d < maxd; d += kTileWarps) {
         const int f0 = S.first[d], f1 = S.first[d + 1];
         uint64_t carry = 0;
         for (int base = f0; base < f1; base += 32) {
@@ -930,27 +934,35 @@ __device__ inline bool ct_layout(CtaTile &S) {
         }
         if (d && (carry >> 32) > (uint64_t)kLvlBuf) fits = false;
         if ((uint32_t)carry > 0xFFFFu) fits = false;
-        const uint32_t G = (uint32_t)carry & 0xFFFFu;
-        if (lane == 0) { S.lg[d] = (uint16_t)G; S.wn_off[d] = (uint16_t)wn; }
-        __syncwarp();
-        if (d) {
-            // the node holding the first group of each window of the level:
-            // the last node whose first group is at or before it
-            const uint32_t nwin = (G + 31) >> 5;
-            if (wn + nwin > (uint32_t)kWnodeMax) fits = false;
-            for (uint32_t i = lane; i < nwin && wn + i < (uint32_t)kWnodeMax; i += 32) {
-                int lo = f0, hi = f1;
-                while (hi - lo > 1) {
-                    const int m = (lo + hi) >> 1;
-                    if ((uint32_t)S.gs[m] <= 32u * i) lo = m; else hi = m;
-                }
-                S.wnode[wn + i] = (uint8_t)lo;
+        if (lane == 0) S.lg[d] = (uint16_t)carry;
+    }
+    __syncthreads();
+    // window-node table offsets: lane d holds level d's windows (none at the root)
+    const uint32_t nwin_l = lane >= 1 && lane < maxd ? ((uint32_t)S.lg[lane] + 31) >> 5 : 0u;
+    uint32_t wi = nwin_l;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+    }
+    if (__shfl_sync(0xffffffffu, wi, 31) > (uint32_t)kWnodeMax) fits = false;
+    const uint32_t wn_l = wi - nwin_l;
+    for (int d = warp; d < maxd; d += kTileWarps) {
+        const uint32_t wn = __shfl_sync(0xffffffffu, wn_l, d), nwin = __shfl_sync(0xffffffffu, nwin_l, d);
+        if (lane == 0) S.wn_off[d] = (uint16_t)wn;
+        // the node holding the first group of each window of the level: the
+        // last node whose first group is at or before it
+        const int f0 = S.first[d], f1 = S.first[d + 1];
+        for (uint32_t i = lane; i < nwin && wn + i < (uint32_t)kWnodeMax; i += 32) {
+            int lo = f0, hi = f1;
+            while (hi - lo > 1) {
+                const int m = (lo + hi) >> 1;
+                if ((uint32_t)S.gs[m] <= 32u * i) lo = m; else hi = m;
             }
-            wn += nwin;
+            S.wnode[wn + i] = (uint8_t)lo;
         }
     }
-    __syncwarp();
-    return __all_sync(0xffffffffu, fits);
+    return !__syncthreads_or(!fits);
 }
 
 // Demands of a chunk of C root symbols from the current cursors, top-down:
@@ -1283,13 +1295,7 @@ __device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, c
             if (warp == 0) ct_demand(S, src, V, C);
             __syncthreads();
         }
-        if (warp == 0) {
-            const bool f = ct_layout(S);
-            if (lane == 0) S.flag = f;
-        }
-        __syncthreads();
-        const bool fits = S.flag != 0;
-        __syncthreads();
+        const bool fits = ct_layout(S);
         if (!fits) {
             chunked = true;
             C = max(32u, (C / 2) & ~31u);
