@@ -1052,6 +1052,11 @@ __device__ inline void ct_fetch(const CtaTile &S, const TileSrc &src, int d, uin
 // One level (depth d >= 1) of the current chunk into its buffer.  nx / nld
 // hold the warp's window of this level's first round on entry and of the
 // next level's first round on return; par alternates the summary slots.
+// The level ends without a barrier: a round reads the level buffer below it
+// only after its summary barrier, so the next level's first barrier (or the
+// root's) is the one that orders this level's writes before those reads and
+// its reads before the next level's writes to the other buffer.  Returns
+// false when this thread found the level corrupt (the caller combines).
 __device__ inline bool ct_level(CtaTile &S, const TileSrc &src, int d, const uint32_t *sel, WtLoc &nx, BitLd &nld,
                                 uint32_t &par) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1129,7 +1134,7 @@ __device__ inline bool ct_level(CtaTile &S, const TileSrc &src, int d, const uin
                 if (4u * j < dv - kk) p4[j] = o[j];
         }
     }
-    return !__syncthreads_or(bad);   // (also: the level's output is complete)
+    return !bad;
 }
 
 // The root level of the current chunk into the output.
