@@ -1072,6 +1072,14 @@ __device__ inline bool ct_level(CtaTile &S, const TileSrc &src, int d, const uin
         const BitLd ld = nld;
         if (r0 + 32 * kTileWarps < G) ct_fetch(S, src, d, base + 32 * kTileWarps, nx, nld);
         else ct_fetch(S, src, d - 1, 32 * warp, nx, nld);
+        if (base >= G) {
+            // past the level's end (its last round only): an empty summary
+            // and nothing to merge; the carry into later rounds is not needed
+            if (lane == 0) S.win[par][warp] = WinSum{0u, 0u};
+            __syncthreads();
+            par ^= 1u;
+            continue;
+        }
         const uint32_t starts = L.starts, v = L.v, kk = L.kk, dv = L.dv;
         const bool act = L.act;
         uint32_t w = 0;

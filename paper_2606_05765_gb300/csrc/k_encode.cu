@@ -657,6 +657,14 @@ __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_
             uint32_t rc_sum = 0;
             for (uint32_t r0 = 0; r0 < G; r0 += 32 * kEncWarps) {
                 const uint32_t base = r0 + 32u * warp;
+                if (base >= G) {
+                    // past the level's end (its last round only): an empty
+                    // summary and nothing to code
+                    if (lane == 0) S.win[par][warp] = EncWin{0u, 0u};
+                    __syncthreads();
+                    par ^= 1u;
+                    continue;
+                }
                 // this warp's window: the node of each group
                 uint32_t v = 0, kk = 0, dv = 0, starts = 0;
                 bool act = false;
