@@ -1099,14 +1099,16 @@ __device__ inline bool ct_level(CtaTile &S, const TileSrc &src, int d, const uin
         const int s0 = sl ? 31 - __clz(sl) : -1;
         const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
         uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u);
-        if (lane == 31) S.win[par][warp] = WinSum{r1 + pc, (starts & 1u) | (starts ? 2u : 0u) | (base < G ? 4u : 0u)};
+        // a level of one window (warp 0's, in the first round) takes no carry
+        const bool one = G <= 32;
+        if (lane == 31 && !one) S.win[par][warp] = WinSum{r1 + pc, (starts & 1u) | (starts ? 2u : 0u) | (base < G ? 4u : 0u)};
         __syncthreads();
         // the carry into each window of the round: lane p takes window p's
         // summary; the carry out of a window is a segmented inclusive sum of
         // the windows' sums (a segment starts at a window where a node
         // starts), the first segment continuing the previous round's carry
-        uint32_t cin;
-        {
+        uint32_t cin = 0;
+        if (!one) {
             const WinSum x = lane < kTileWarps ? S.win[par][lane] : WinSum{0u, 0u};
             uint32_t val = x.sum, seg = (x.flags >> 1) & 1u;
 #pragma unroll
@@ -1232,8 +1234,7 @@ __device__ inline void cta_tile(uint32_t gt, const uint8_t *__restrict__ comp, c
     }
     __syncthreads();
     b = S.blk;
-    const int32_t st0 = S.flag;
-    __syncthreads();
+    const int32_t st0 = S.flag;   // (nothing in the tile writes blk or flag again)
     if (st0 != PIVCO_OK) return;
     const uint32_t k = gt - W.blk_tile[b], ntile = W.blk_ntile[b], T = W.blk_T[b];
     const uint8_t *rec = comp + comp_off[b];

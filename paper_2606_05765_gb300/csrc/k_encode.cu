@@ -716,9 +716,12 @@ __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_
                 const int s0 = sl ? 31 - __clz(sl) : -1;
                 const uint32_t before = __shfl_sync(0xffffffffu, inc, s0 > 0 ? s0 - 1 : 0);
                 uint32_t r1 = inc - pc - (s0 > 0 ? before : 0u);
-                if (lane == 31) S.win[par][warp] = EncWin{r1 + pc, (starts & 1u) | (starts ? 2u : 0u) | (base < G ? 4u : 0u)};
+                // a level of one window (warp 0's, in the first round) takes no carry
+                const bool one = G <= 32;
+                if (lane == 31 && !one)
+                    S.win[par][warp] = EncWin{r1 + pc, (starts & 1u) | (starts ? 2u : 0u) | (base < G ? 4u : 0u)};
                 __syncthreads();
-                const uint32_t cin = enc_round_carry(S, par, rc_sum);
+                const uint32_t cin = one ? 0u : enc_round_carry(S, par, rc_sum);
                 par ^= 1u;
                 if (s0 < 0) r1 += cin;   // groups of the node that runs in from the window before
                 enc_put_bits(rec32, act && !fD, v, S.pos[v] + kk, bw, vl);
