@@ -189,36 +189,31 @@ cudaError_t launch_histogram_chunks(const uint8_t *in, const uint64_t *blk_off, 
 // ---------------------------------------------------------------------------
 constexpr int kPmThreads = 256;
 
-// # of a[0..n) below x (a sorted, n <= 256): a fixed 9-step search with no
-// data-dependent branch
+// # of a[0..256) below x, a sorted with its unused tail holding the type's
+// maximum (above every x searched for): binary lifting over 255 places, then
+// one compare for the last, with no bounds checks
 template <typename W>
-__device__ inline int count_less_w(const W *a, int n, W x) {
+__device__ inline int count_less_w(const W *a, W x) {
     int pos = 0;
 #pragma unroll
-    for (int step = 256; step >= 1; step >>= 1) {
-        const int q = pos + step;
-        const bool ok = q <= n && a[max(0, min(q, n) - 1)] < x;   // the index stays in [0, 256)
-        pos = ok ? q : pos;
-    }
-    return pos;
+    for (int step = 128; step >= 1; step >>= 1) pos = a[pos + step - 1] < x ? pos + step : pos;
+    return pos + (a[pos] < x ? 1 : 0);
 }
-// # of a[0..n) not above x
+// # of a[0..256) not above x (the same tail)
 template <typename W>
-__device__ inline int count_le_w(const W *a, int n, W x) {
+__device__ inline int count_le_w(const W *a, W x) {
     int pos = 0;
 #pragma unroll
-    for (int step = 256; step >= 1; step >>= 1) {
-        const int q = pos + step;
-        const bool ok = q <= n && a[max(0, min(q, n) - 1)] <= x;
-        pos = ok ? q : pos;
-    }
-    return pos;
+    for (int step = 128; step >= 1; step >>= 1) pos = a[pos + step - 1] <= x ? pos + step : pos;
+    return pos + (a[pos] <= x ? 1 : 0);
 }
 
 // Levels max_len - 1 .. 1 of package-merge: each level merges the sorted
 // leaves with the packages of the level below; leafpos[l][i] is leaf i's
 // place at level l.  W: the weight type (32 bits when no package can reach
-// 2^32, which halves the shared-memory traffic of the searches).
+// 2^32 - 1, which halves the shared-memory traffic of the searches).  leafw
+// (256 places) holds the type's maximum past the K leaves; pw is given the
+// same tail at every level, so the searches need no bounds.
 template <typename W>
 __device__ inline void pm_levels(const W *leafw, W *pw, W (*lw)[512], uint16_t (*leafpos)[256], int K, int max_len) {
     const int t = threadIdx.x;
@@ -229,14 +224,14 @@ __device__ inline void pm_levels(const W *leafw, W *pw, W (*lw)[512], uint16_t (
         const W *prev = lw[(lvl + 1) & 1];
         W *cur = lw[lvl & 1];
         const int P = len_prev / 2;
-        for (int j = t; j < P; j += kPmThreads) pw[j] = prev[2 * j] + prev[2 * j + 1];
+        for (int j = t; j < 256; j += kPmThreads) pw[j] = j < P ? prev[2 * j] + prev[2 * j + 1] : ~W(0);
         __syncthreads();
         for (int i = t; i < K; i += kPmThreads) {
-            const int pos = i + count_less_w(pw, P, leafw[i]);
+            const int pos = i + count_less_w(pw, leafw[i]);
             cur[pos] = leafw[i];
             leafpos[lvl][i] = (uint16_t)pos;
         }
-        for (int j = t; j < P; j += kPmThreads) cur[j + count_le_w(leafw, K, pw[j])] = pw[j];
+        for (int j = t; j < P; j += kPmThreads) cur[j + count_le_w(leafw, pw[j])] = pw[j];
         len_prev = K + P;
         __syncthreads();
     }
@@ -283,20 +278,19 @@ __device__ inline int code_lengths_block(const uint32_t *h, int max_len, ClSmem 
                     key = (lower == up) ? (key < other ? key : other) : (key < other ? other : key);
                 }
             }
-            if (t < K) {
-                leafw[t] = key >> 8;
-                leafsym[t] = (uint8_t)(key & 0xFF);
-            }
+            leafw[t] = t < K ? key >> 8 : ~0ull;   // (the searches' tail past the leaves)
+            if (t < K) leafsym[t] = (uint8_t)(key & 0xFF);
         }
         __syncthreads();
         // an item of a level holds at most one copy of a leaf per level
-        // below, so no weight exceeds max_len * K * (largest count)
-        if ((uint64_t)max_len * (uint64_t)K * leafw[K - 1] < (1ull << 32)) {
+        // below, so no weight exceeds max_len * K * (largest count); 32-bit
+        // weights stay below 2^32 - 1, the searches' tail value
+        if ((uint64_t)max_len * (uint64_t)K * leafw[K - 1] < (1ull << 32) - 1) {
             uint32_t *leafw32 = reinterpret_cast<uint32_t *>(pw), *pw32 = leafw32 + 256;
             uint32_t (*lw32)[512] = reinterpret_cast<uint32_t (*)[512]>(&lw[0][0]);
-            const uint32_t w = t < K ? (uint32_t)leafw[t] : 0u;
+            const uint32_t w = t < K ? (uint32_t)leafw[t] : 0xFFFFFFFFu;
             __syncthreads();
-            if (t < K) leafw32[t] = w;
+            leafw32[t] = w;
             __syncthreads();
             pm_levels<uint32_t>(leafw32, pw32, lw32, leafpos, K, max_len);
         } else {

@@ -110,6 +110,12 @@ def test_code_lengths(P, oracle):
         else:
             h[syms[:min(K, 25)]] = [int(1.618 ** j) + 1 for j in range(min(K, 25))]   # limit binds
         hs.append(h)
+    for i in range(24):
+        # counts large enough for package weights past 32 bits (the 64-bit path)
+        h = np.zeros(256, np.uint32)
+        K = int(rng.integers(2, 257))
+        h[rng.choice(256, K, replace=False)] = rng.integers(1 << 20, 1 << 31, K)
+        hs.append(h)
     H = np.stack(hs)
     for L in (11, 8, 15):
         st = torch.empty(len(hs), dtype=torch.int32, device="cuda")
