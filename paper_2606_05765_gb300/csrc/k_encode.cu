@@ -58,7 +58,8 @@ struct __align__(16) EncSmemT {
     uint8_t nhi1[256];
     uint32_t pmask[8];                      // symbols that have a code
     uint32_t hot;                           // the symbol with the shortest code (the most frequent one)
-    uint32_t bad, fits, tot;
+    uint32_t bad, fits;
+    uint32_t lvl_max;                       // symbols of the largest level below the root (a try's layout)
     uint8_t first[17];
     uint8_t maxd;
     uint8_t pad[14];
@@ -71,7 +72,7 @@ constexpr int kEncChunkCtasPerSm = 2;
 using EncSmemBig = EncSmemT<kEBufBig, 36>;
 static_assert(offsetof(BlockLayout, ci) <= sizeof(EncSmem::buf[1]) && offsetof(BlockLayout, ci) % 16 == 0,
               "the staged part of the layout fits a level buffer");
-static_assert(sizeof(EncSmem::buf[0]) >= 4 * 1024 + 4, "a level buffer holds the counting scratch");
+static_assert(sizeof(EncSmem::buf[0]) >= 4 * (288 + 256 + 257), "a level buffer holds the counting scratch");
 static_assert(kEncChunkCtasPerSm * (sizeof(EncSmemBig) + 1024) <= 228 * 1024, "chunk encoder CTAs per SM");
 static_assert((kEBufBig / 32 + 256) / 32 <= 36, "window table of the chunk encoder");
 
@@ -114,26 +115,36 @@ __device__ inline void ldg32(const uint8_t *p, const uint8_t *end, uint32_t (&x)
     }
 }
 
-// adds the 32 bytes x (first vl valid) to a shared histogram.  The block's
-// most frequent symbol h is counted with a 4-byte compare and added once per
-// warp; only the other bytes use atomics (skewed data would otherwise
-// serialize on one counter).
+// adds the 32 bytes x (first vl valid) to a shared histogram of 256 bins
+// and 32 per-lane bins (256 + lane, one bank each) that take the block's most
+// frequent symbol h (skewed data would otherwise serialize on one counter):
+// one shared add per byte, no branch for a full lane; hist_fold_hot adds the
+// lane bins into bin h
 __device__ inline void hist_add32(uint32_t *hist, const uint32_t (&x)[8], uint32_t vl, uint32_t h) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t h4 = h * 0x01010101u;
-    uint32_t hot = 0;
+    const uint32_t hb = 256u + (threadIdx.x & 31);
+    if (vl >= 32) {
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        const uint32_t nb = vl > 4u * q ? min(4u, vl - 4u * q) : 0u;   // valid bytes of word q
-        const uint32_t bm = nb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
-        const uint32_t m = __vcmpeq4(x[q], h4) & bm;
-        hot += __popc(m) >> 3;
+        for (int q = 0; q < 8; q++)
 #pragma unroll
-        for (int i = 0; i < 4; i++)
-            if ((uint32_t)i < nb && !((m >> (8 * i)) & 1u)) atomicAdd(&hist[(x[q] >> (8 * i)) & 0xFFu], 1u);
+            for (int i = 0; i < 4; i++) {
+                const uint32_t v = __byte_perm(x[q], 0u, 0x4440u + i);
+                atomicAdd(&hist[v == h ? hb : v], 1u);
+            }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t v = __byte_perm(x[q], 0u, 0x4440u + i);
+                if ((uint32_t)(4 * q + i) < vl) atomicAdd(&hist[v == h ? hb : v], 1u);
+            }
     }
-    hot = __reduce_add_sync(0xffffffffu, hot);
-    if (lane == 0 && hot) atomicAdd(&hist[h], hot);
+}
+// the lane bins of hist_add32 into bin h (one warp, after the CTA's counting)
+__device__ inline void hist_fold_hot(uint32_t *hist, uint32_t h) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t c = __reduce_add_sync(0xffffffffu, hist[256 + lane]);
+    if (lane == 0) hist[h] += c;
 }
 
 // Node symbol counts of a histogram h by prefix sums in canonical order: the
@@ -178,11 +189,13 @@ __device__ inline bool enc_layout_level(SM &S, int d) {
     bool fits = true;
     const int f0 = S.first[d], f1 = S.first[d + 1];
     uint64_t carry = 0;
+    uint32_t raw = 0;   // this lane's nodes' symbols, rounded as spans are (capped: only sizes near a buffer matter)
     for (int base = f0; base < f1; base += 32) {
         const int v = base + lane;
         uint64_t x = 0;
         if (v < f1) {
             const uint32_t dv = S.dem[v];
+            raw = min(raw + ((min(dv, 1u << 24) + 7u) & ~7u), 1u << 25);
             if (d && dv > (uint32_t)kBuf) fits = false;
             const uint32_t el = d ? ((min(dv, (uint32_t)kBuf) + 7u) & ~7u) : 0u;   // spans of whole 16-byte units
             x = ((uint64_t)el << 32) | max(1u, (dv + 31u) >> 5);
@@ -203,7 +216,11 @@ __device__ inline bool enc_layout_level(SM &S, int d) {
     if (d && (carry >> 32) > (uint64_t)kBuf) fits = false;
     if ((uint32_t)carry > 0xFFFFu) fits = false;
     const uint32_t G = (uint32_t)carry & 0xFFFFu;
-    if (lane == 0) S.lg[d] = (uint16_t)G;
+    const uint32_t lraw = __reduce_add_sync(0xffffffffu, raw);
+    if (lane == 0) {
+        S.lg[d] = (uint16_t)G;
+        if (d) atomicMax(&S.lvl_max, lraw);
+    }
     __syncwarp();
     if (d) {
         const uint32_t nwin = (G + 31) >> 5;
@@ -498,7 +515,7 @@ __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_
     uint32_t *rec32 = reinterpret_cast<uint32_t *>(rec);
     // counting scratch in the second level buffer (free between chunks)
     uint32_t *hist = reinterpret_cast<uint32_t *>(S.buf[1]);
-    uint32_t *hc = hist + 256, *ps = hist + 512;
+    uint32_t *hc = hist + 288, *ps = hist + 544;   // (after the 32 lane bins of the counting)
     // a chunk of a big block starts every node's cursor after the symbols
     // the chunks before it put there
     if (cA > 0) {
@@ -520,20 +537,20 @@ __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_
         const uint32_t Q1 = enc_chunk_start(n, c0 + (sub ? 1u : k), nw);   // end of the run / plan chunk
         const uint32_t C = sub ? min(sub, Q1 - P) : Q1 - P;
         // the chunk's histogram: the planning pass's chunk counts, or counted here
-        for (int s2 = t; s2 < 256; s2 += kEncThreads) hist[s2] = 0;
+        for (int s2 = t; s2 < 256 + 32; s2 += kEncThreads) hist[s2] = 0;
         __syncthreads();
         if (chunk_hist && !sub) {
             uint32_t h = 0;
             for (uint32_t c = c0; c < c0 + k; c++) h += __ldg(chunk_hist + ((size_t)b * kEncChunks + c) * 256 + t);
             hist[t] = h;
         } else {
-            // warp-uniform trip counts: hist_add32 reduces over the whole warp
-            for (uint32_t kw = P + 1024u * warp; kw < P + C; kw += 1024u * kEncWarps) {
-                const uint32_t kb = kw + 32u * lane;
-                uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                if (kb < P + C) ldg32(src + kb, src_end, x);
-                hist_add32(hist, x, kb < P + C ? min(32u, P + C - kb) : 0u, hot);
+            for (uint32_t kb = P + 32u * t; kb < P + C; kb += 32u * kEncThreads) {
+                uint32_t x[8];
+                ldg32(src + kb, src_end, x);
+                hist_add32(hist, x, min(32u, P + C - kb), hot);
             }
+            __syncthreads();
+            if (warp == 0) hist_fold_hot(hist, hot);
         }
         __syncthreads();
         const uint32_t hcount = hist[t];
@@ -547,7 +564,7 @@ __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_
             tot = __reduce_add_sync(0xffffffffu, tot);
             if (__any_sync(0xffffffffu, nocode) || tot != C) { if (lane == 0) S.bad = 1; }
             else enc_counts(S, hist, S.dem, hc, ps);
-            if (lane == 0) S.fits = 1;
+            if (lane == 0) { S.fits = 1; S.lvl_max = 0; }
         }
         __syncthreads();
         if (S.bad) break;
@@ -570,8 +587,15 @@ __device__ inline void encode_item(int b, uint32_t cA, uint32_t cB, const uint8_
                 if (t == 0) S.bad = 1;
                 break;
             }
-            if (!sub && k > 1) k = (k + 1) / 2;
-            else sub = max(32u, ((sub ? sub : C) / 2) & ~31u);
+            if (!sub && k > 1) {
+                k = (k + 1) / 2;
+            } else {
+                // parts whose largest level fills at most 7/8 of a buffer,
+                // scaled from this try's largest level, and at least halved
+                const uint32_t cur = sub ? sub : C, lm = S.lvl_max;
+                const uint32_t est = lm ? (uint32_t)((uint64_t)cur * (SM::kBuf - SM::kBuf / 8) / lm) : cur / 2;
+                sub = max(32u, min(cur / 2, est) & ~31u);
+            }
             continue;
         }
         // ---- the root: input bytes -> codes; bits; children ----
