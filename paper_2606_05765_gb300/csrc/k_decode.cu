@@ -4,28 +4,30 @@
 //   plan       one warp per record: validates the header and body layout,
 //              sizes the ANS scratch, builds the block's node table (bitmap
 //              source and children of every internal node, from the
-//              canonical tree of the code lengths) and splits the block into
-//              root tiles whose levels fit one warp's buffers; per-block
-//              offsets come from two single-pass scans with decoupled look-back.
+//              canonical or the regrouped tree of the code lengths) and
+//              splits the block into root tiles whose levels fit a CTA's
+//              level buffers; per-block offsets come from two single-pass
+//              scans with decoupled look-back.
 //   ans        one warp per 16 KiB ANS segment: decodes the bitmap bytes into
 //              the workspace scratch.
 //   directory  for blocks with several tiles: per-node rank directories
 //              (exclusive popcount per superblock) and, from them, every
 //              node's bitmap cursor at every tile boundary (the root cursor is
 //              the position; a child's cursor is the parent's rank0 / rank1).
-//   tiles      one warp per tile, independent of the other warps.  With both
+//   tiles      one CTA per tile, independent of the other tiles.  With both
 //              boundary cursors known, every node's bit range in the tile is
 //              known.  Bottom-up, level by level, every node rebuilds its
 //              symbol sequence
 //                  out_v[k] = bit ? R[rank1(k)] : L[k - rank1(k)]
 //              from its children's sequences or leaf constants (the MVV /
-//              MCV / MVC / MCC cases of Sec. 3.2).  A lane takes one 32-bit
-//              bitmap word (32 symbols) of one node; ranks come from a
-//              segmented warp scan of the words' popcounts; 4 output symbols
-//              are one byte permute of a left and a right 4-byte window.  The
-//              root writes the output.  A tile whose levels do not fit is
-//              decoded in shorter chunks whose bit ranges are found top-down
-//              from popcounts.
+//              MCV / MVC / MCC cases of Sec. 3.2), a flat node from its
+//              packed indices.  A lane takes one 32-bit bitmap word (32
+//              symbols) of one node; ranks come from a segmented warp scan of
+//              the words' popcounts and the windows' summaries; 4 output
+//              symbols are one byte permute of a left and a right 4-byte
+//              window.  The root writes the output.  A tile whose levels do
+//              not fit is decoded in shorter chunks whose bit ranges are
+//              found top-down from popcounts.
 #include "ans_dev.cuh"
 #include "lookback.cuh"
 
