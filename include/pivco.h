@@ -246,7 +246,7 @@ pivco_status pivco_decode_blocks_static(const uint8_t *comp, const uint64_t *com
                                         uint8_t *out, const uint64_t *out_off, int32_t *status,
                                         void *stream);
 
-/* ---- Serving (spec serving pattern; the paper has no serving system) ----
+/* ---- Serving (a device-resident request loop; the paper has no serving system) ----
  * A decompression server: a device-resident request loop (one persistent
  * kernel that takes the work items of the batched decode, request after
  * request) fed by a host scheduler thread that admits requests by a device
